@@ -1,0 +1,331 @@
+"""Plain FP64 CPU oracle for the CNOP Rayleigh-Taylor hot path.
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package. The product path (the
+CUDA library and its Python binding) never imports, loads or calls it, and the
+two share no code: the only common module is ``rt_inputs`` (seeded draws and
+plain parameter values).
+
+The time stepper, its tangent and its reverse sweep live in ``rt_oracle.cpp``
+(plain C++, FP64, built with ``-O2 -ffp-contract=off``); the CNOP pieces that
+act on whole fields (constraint, projection, random start, spectral projected
+gradient with a non-monotone line search, 1D Fourier spectrum, five-mode
+reconstruction) are plain NumPy here. Each function names the paper passage it
+follows.
+
+Parity status: every function below is pinned by a ``-m "not gpu"`` test
+(``tests/test_oracle_*.py``) against closed forms, textbook solutions,
+invariants or brute force, except ``spg`` at finite amplitude, whose result has
+no closed form; it is pinned only in the small-amplitude limit, where it must
+reproduce the leading eigenvector of the tangent-linear problem.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rt_oracle.cpp")
+_LIB_PATH = os.path.join(_HERE, "_build", "librt_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C++ oracle into ``oracle/_build/librt_oracle.so``."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    stale = (not os.path.exists(_LIB_PATH)
+             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
+    if force or stale:
+        cmd = ["g++", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c++17",
+               "-shared", "-fPIC", "-o", _LIB_PATH, _SRC]
+        subprocess.check_call(cmd)
+    return _LIB_PATH
+
+
+class OParams(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("g_y", ctypes.c_double),
+                ("rho_h", ctypes.c_double), ("rho_l", ctypes.c_double),
+                ("y_int", ctypes.c_double), ("h_s", ctypes.c_double),
+                ("p_ref", ctypes.c_double), ("y_ref", ctypes.c_double),
+                ("bc_y", ctypes.c_int), ("limiter", ctypes.c_int),
+                ("cfl", ctypes.c_double), ("T", ctypes.c_double),
+                ("nsteps", ctypes.c_int), ("ncomp", ctypes.c_int),
+                ("objective", ctypes.c_int)]
+
+
+def _params(w) -> OParams:
+    return OParams(w.nx, w.ny, w.x0, w.x1, w.y0, w.y1, w.gamma, w.g_y,
+                   w.rho_heavy, w.rho_light, w.y_int, w.h_s, w.p_ref, w.y_ref,
+                   w.bc_y, w.limiter, w.cfl, w.T, w.nsteps, w.ncomp, w.objective)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB_PATH)
+        dp = ctypes.POINTER(ctypes.c_double)
+        pp = ctypes.POINTER(OParams)
+        L.o_base_state.argtypes = [pp, dp, dp]
+        L.o_cfl_wmin.argtypes = [pp, dp]
+        L.o_cfl_wmin.restype = ctypes.c_double
+        L.o_stage.argtypes = [pp, dp, ctypes.c_double, dp, dp]
+        L.o_run_state.argtypes = [pp, dp, dp, ctypes.c_int]
+        L.o_run_state.restype = ctypes.c_int
+        L.o_inject.argtypes = [pp, dp, dp]
+        L.o_forward.argtypes = [pp, dp, dp, ctypes.c_int, dp, ctypes.c_int, dp, dp, dp, dp]
+        L.o_forward.restype = ctypes.c_int
+        L.o_tangent.argtypes = [pp, dp, dp, dp, ctypes.c_int, dp, dp, dp]
+        L.o_tangent_state.argtypes = [pp, dp, dp, dp, ctypes.c_int, dp, dp]
+        L.o_gradient.argtypes = [pp, dp, dp, ctypes.c_int, dp, dp, dp]
+        L.o_step_vjp.argtypes = [pp, dp, ctypes.c_double, dp, dp]
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def grid_spacing(w):
+    return (w.x1 - w.x0) / w.nx, (w.y1 - w.y0) / w.ny
+
+
+def cell_centres(w):
+    dx, dy = grid_spacing(w)
+    x = w.x0 + (np.arange(w.nx) + 0.5) * dx
+    y = w.y0 + (np.arange(w.ny) + 0.5) * dy
+    return x, y
+
+
+# ----------------------------------------------------------------- the stepper
+def base_state(w):
+    """Sec. 2.2, Eq. rho0: tanh density and hydrostatic pressure at cell centres."""
+    rho0 = np.zeros(w.ny)
+    p0 = np.zeros(w.ny)
+    lib().o_base_state(ctypes.byref(_params(w)), _ptr(rho0), _ptr(p0))
+    return rho0, p0
+
+
+def inject(w, v):
+    """Sec. 3.1: conserved initial state from the velocity perturbation v."""
+    v = _f64(v)
+    U = np.zeros((4, w.ny, w.nx))
+    lib().o_inject(ctypes.byref(_params(w)), _ptr(v), _ptr(U))
+    return U
+
+
+def cfl_wmin(w, U):
+    return lib().o_cfl_wmin(ctypes.byref(_params(w)), _ptr(_f64(U)))
+
+
+def stage(w, U, dt, base=None):
+    """One RK stage of the finite-volume scheme (stage 2 when base is given)."""
+    out = np.zeros((4, w.ny, w.nx))
+    b = None if base is None else _f64(base)
+    lib().o_stage(ctypes.byref(_params(w)), _ptr(_f64(U)), float(dt), _ptr(b), _ptr(out))
+    return out
+
+
+def run_state(w, U, max_steps=10**7):
+    """Advance an arbitrary conserved state with the step control of w."""
+    U = _f64(U).copy()
+    dts = np.zeros(max_steps if max_steps < 10**6 else 10**6)
+    n = lib().o_run_state(ctypes.byref(_params(w)), _ptr(U), _ptr(dts), len(dts))
+    return U, dts[:n].copy()
+
+
+def forward(w, v, dt_replay=None, ek0=None, max_steps=400000):
+    """Forward map F_t (Sec. 3.1) from perturbation v: returns a dict with the
+    final state U, e_k, J_ke (total kinetic energy), J_pap (Eq. objective
+    against ek0) and the time-step sequence dt."""
+    v = _f64(v)
+    U = np.zeros((4, w.ny, w.nx))
+    ek = np.zeros((w.ny, w.nx))
+    J = np.zeros(2)
+    dts = np.zeros(max_steps)
+    rep = None if dt_replay is None else _f64(dt_replay)
+    n = lib().o_forward(ctypes.byref(_params(w)), _ptr(v), _ptr(rep),
+                        0 if rep is None else len(rep), _ptr(dts), max_steps,
+                        _ptr(None if ek0 is None else _f64(ek0)), _ptr(U), _ptr(ek), _ptr(J))
+    dt = rep.copy() if rep is not None else dts[:n].copy()
+    return {"U": U, "ek": ek, "J_ke": J[0], "J_pap": J[1], "dt": dt, "nsteps": n}
+
+
+def objective_value(w, out):
+    return out["J_pap"] if w.objective == 1 else out["J_ke"]
+
+
+def tangent(w, v, dv, dt, ek0=None):
+    """J and its directional derivative along dv with the dt sequence frozen."""
+    J = np.zeros(2)
+    dJ = np.zeros(2)
+    lib().o_tangent(ctypes.byref(_params(w)), _ptr(_f64(v)), _ptr(_f64(dv)), _ptr(_f64(dt)),
+                    len(dt), _ptr(None if ek0 is None else _f64(ek0)), _ptr(J), _ptr(dJ))
+    k = 1 if w.objective == 1 else 0
+    return J[k], dJ[k]
+
+
+def tangent_state(w, v, dv, dt):
+    U = np.zeros((4, w.ny, w.nx))
+    dU = np.zeros((4, w.ny, w.nx))
+    lib().o_tangent_state(ctypes.byref(_params(w)), _ptr(_f64(v)), _ptr(_f64(dv)),
+                          _ptr(_f64(dt)), len(dt), _ptr(U), _ptr(dU))
+    return U, dU
+
+
+def gradient(w, v, dt, ek0=None):
+    """Sec. 3.4: exact discrete gradient of J (w.objective) with respect to v,
+    dt sequence frozen. Returns (J, grad) with grad shaped like v."""
+    v = _f64(v)
+    J = np.zeros(2)
+    g = np.zeros_like(v)
+    lib().o_gradient(ctypes.byref(_params(w)), _ptr(v), _ptr(_f64(dt)), len(dt),
+                     _ptr(None if ek0 is None else _f64(ek0)), _ptr(J), _ptr(g))
+    return (J[1] if w.objective == 1 else J[0]), g
+
+
+def value_and_gradient(w, v, ek0=None):
+    """CFL-controlled forward, then the reverse sweep with that dt sequence."""
+    out = forward(w, v, ek0=ek0)
+    J, g = gradient(w, v, out["dt"], ek0=ek0)
+    return J, g, out
+
+
+def step_vjp(w, U, dt, lam):
+    out = np.zeros((4, w.ny, w.nx))
+    lib().o_step_vjp(ctypes.byref(_params(w)), _ptr(_f64(U)), float(dt), _ptr(_f64(lam)), _ptr(out))
+    return out
+
+
+def baseline_ek(w):
+    """Sec. 2.3 / Eq. objective: e_k at the horizon of the unperturbed run."""
+    out = forward(w, np.zeros((w.ncomp, w.ny, w.nx)))
+    return out["ek"]
+
+
+# ------------------------------------------------------------- CNOP, Sec. 3.4
+def constraint(w, v):
+    """Eq. constraint: C(v) = sum over cells and perturbed components of rho0 v^2 / 2 dx dy."""
+    rho0, _ = base_state(w)
+    dx, dy = grid_spacing(w)
+    v = np.asarray(v, dtype=np.float64).reshape(w.ncomp, w.ny, w.nx)
+    return float(np.sum(0.5 * rho0[None, :, None] * v * v) * dx * dy)
+
+
+def project(w, v, eps):
+    """Eq. projection: radial rescale onto C <= eps (identity inside the ball)."""
+    C = constraint(w, v)
+    if C <= eps:
+        return np.array(v, dtype=np.float64, copy=True)
+    return np.asarray(v, dtype=np.float64) * np.sqrt(eps / C)
+
+
+def scale_to_budget(w, v, eps):
+    """Rescale v so that C(v) = eps exactly (up to rounding)."""
+    return np.asarray(v, dtype=np.float64) * np.sqrt(eps / constraint(w, v))
+
+
+def random_start(w, xi, h_loc, eps):
+    """Sec. 3.4: zero-mean Gaussian field localised at the interface with width
+    h_loc, scaled to C = eps. Reading: envelope exp(-(y - y_int)^2 / (2 h_loc^2))."""
+    _, y = cell_centres(w)
+    env = np.exp(-((y - w.y_int) ** 2) / (2.0 * h_loc * h_loc))
+    v = np.asarray(xi, dtype=np.float64).reshape(w.ncomp, w.ny, w.nx) * env[None, :, None]
+    return scale_to_budget(w, v, eps)
+
+
+def spg(w, v_start, eps, iters, memory=10, armijo=1e-4, alpha_min=1e-30, alpha_max=1e30,
+        max_backtracks=30, ek0=None, log=None):
+    """Spectral projected gradient ascent on J over {C <= eps} with the radial
+    projection of Eq. projection and a non-monotone (max over the last
+    ``memory`` values) Armijo backtracking line search (Sec. 3.4).
+
+    Iteration k: d = P(v + alpha g) - v; accept v + lam d once
+    J(v + lam d) >= max_recent J + armijo * lam * <g, d>, halving lam otherwise;
+    then alpha = <s, s> / <s, y'> with s the step and y' = -(g_new - g_old)
+    (the gradient change of the minimised objective -J), clipped to
+    [alpha_min, alpha_max], and alpha_max when <s, y'> <= 0. The first alpha
+    is ||v0|| / ||g0||. Returns a dict with v, J, the history and counts."""
+    v = project(w, v_start, eps)
+    J, g, _ = value_and_gradient(w, v, ek0)
+    evals, grads = 1, 1
+    hist = [J]
+    alpha = float(np.linalg.norm(v) / max(np.linalg.norm(g), 1e-300))
+    alpha = min(max(alpha, alpha_min), alpha_max)
+    records = []
+    for k in range(iters):
+        d = project(w, v + alpha * g, eps) - v
+        gd = float(np.sum(g * d))
+        Jref = max(hist[-memory:])
+        lam = 1.0
+        accepted = False
+        for _ in range(max_backtracks):
+            vt = v + lam * d
+            Jt = objective_value(w, forward(w, vt, ek0=ek0))
+            evals += 1
+            if Jt >= Jref + armijo * lam * gd:
+                accepted = True
+                break
+            lam *= 0.5
+        if not accepted:
+            break
+        Jn, gn, _ = value_and_gradient(w, vt, ek0)
+        grads += 1
+        s = vt - v
+        yv = -(gn - g)
+        sy = float(np.sum(s * yv))
+        alpha = alpha_max if sy <= 0.0 else min(max(float(np.sum(s * s)) / sy, alpha_min), alpha_max)
+        v, J, g = vt, Jn, gn
+        hist.append(J)
+        chi = float(np.max(np.abs(project(w, v + g, eps) - v)))
+        records.append({"iter": k, "J": J, "lam": lam, "alpha": alpha, "chi": chi})
+        if log is not None:
+            log(records[-1])
+    return {"v": v, "J": J, "history": hist, "records": records, "evals": evals, "grads": grads}
+
+
+# ------------------------------------------------- spectra, Sec. 4.2 Eq. fourier_coeff
+def spectrum(vy):
+    """Row y_peak of largest rms along x (ties: lowest row), its DFT u_n and the
+    normalised energies E_n over the positive modes n = 1 .. nx/2."""
+    vy = np.asarray(vy, dtype=np.float64)
+    rms = np.sqrt(np.mean(vy * vy, axis=1))
+    y_peak = int(np.argmax(rms))
+    nx = vy.shape[1]
+    j = np.arange(nx)
+    n = np.arange(1, nx // 2 + 1)
+    # plain DFT of the definition, u_n = sum_j u_j exp(-2 pi i n j / N)
+    u_hat = np.array([np.sum(vy[y_peak] * np.exp(-2j * np.pi * m * j / nx)) for m in n])
+    pw = np.abs(u_hat) ** 2
+    return y_peak, n, pw / np.sum(pw)
+
+
+def five_modes(w, v, eps, count=5):
+    """Sec. 3.5 / 4.2: keep the ``count`` positive horizontal modes with the
+    largest E_n at y_peak (ties: lower n), apply that index set to every row
+    and component, and rescale to C = eps."""
+    v = np.asarray(v, dtype=np.float64).reshape(w.ncomp, w.ny, w.nx)
+    _, n, E = spectrum(v[-1])
+    order = np.argsort(-E, kind="stable")[:count]
+    keep = set(int(n[o]) for o in order)
+    nx = w.nx
+    mask = np.zeros(nx, dtype=bool)
+    for m in keep:
+        mask[m % nx] = True
+        mask[(-m) % nx] = True
+    out = np.real(np.fft.ifft(np.fft.fft(v, axis=2) * mask[None, None, :], axis=2))
+    return scale_to_budget(w, out, eps), sorted(keep)

@@ -1,0 +1,236 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: printed
+closed forms, a textbook exact Riemann solution, conservation laws, exact
+symmetries, the linear Rayleigh-Taylor growth rate, numerical quadrature,
+finite differences and a second differentiation mode.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import rt_inputs as I
+from tests import riemann_exact
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _golden(name):
+    with open(os.path.join(HERE, "golden", name)) as f:
+        return json.load(f)
+
+
+def _cons(rho, u, v, p, gamma):
+    return np.stack([rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)])
+
+
+def _prim(U, gamma):
+    r = U[0]
+    u, v = U[1] / r, U[2] / r
+    return r, u, v, (gamma - 1.0) * (U[3] - 0.5 * r * (u * u + v * v))
+
+
+# ------------------------------------------------------------ printed closed forms
+def test_paper_closed_forms():
+    """Sec. 2.2: A = 1/3 and tau_RT = (A g k)^(-1/2) ~ 0.49 for n_k = 2, g = L = 1;
+    Sec. 5: k h_s ~ 1.3 for n ~ 10 with h_s = 0.02 L."""
+    gd = _golden("paper_closed_forms.json")
+    a = gd["atwood"]
+    A = (a["rho_h"] - a["rho_l"]) / (a["rho_h"] + a["rho_l"])
+    assert A == pytest.approx(a["value"], rel=1e-15)
+    t = gd["tau_rt"]
+    k = 2 * math.pi * t["n_k"] / t["L"]
+    assert abs((A * t["g"] * k) ** -0.5 - t["value"]) <= t["tol"]
+    kh = gd["k_h_s"]
+    assert abs(2 * math.pi * kh["n"] / kh["L"] * kh["h_s"] - kh["value"]) <= kh["tol"]
+
+
+def test_exact_riemann_matches_toro_table():
+    gd = _golden("toro_sod.json")
+    L, R = gd["left"], gd["right"]
+    ps, us, rl, rr = riemann_exact.star_state((L["rho"], L["u"], L["p"]), (R["rho"], R["u"], R["p"]), gd["gamma"])
+    tol = 0.6 * 10.0 ** (-gd["digits"])
+    assert abs(ps - gd["p_star"]) <= tol
+    assert abs(us - gd["u_star"]) <= tol
+    assert abs(rl - gd["rho_star_left"]) <= tol
+    assert abs(rr - gd["rho_star_right"]) <= tol
+
+
+# ------------------------------------------------------------------- base state
+@pytest.mark.parametrize("w", [I.rt_box(8, 96), I.paper_unit_square(64)])
+def test_base_state_against_quadrature(oracle_lib, w):
+    """Sec. 2.2, Eq. rho0 and dp/dy = -rho g: compare with the tanh formula and
+    with adaptive quadrature of rho0 from the pressure anchor."""
+    rho0, p0 = oracle_lib.base_state(w)
+    _, y = oracle_lib.cell_centres(w)
+
+    def rho(s):
+        return 0.5 * (w.rho_heavy + w.rho_light) + 0.5 * (w.rho_heavy - w.rho_light) * math.tanh((s - w.y_int) / w.h_s)
+
+    for j in range(0, w.ny, 7):
+        assert rho0[j] == pytest.approx(rho(y[j]), rel=1e-14, abs=1e-14)
+        integral, _ = integrate.quad(rho, w.y_ref, y[j], points=[w.y_int], limit=200, epsabs=1e-13, epsrel=1e-13)
+        assert p0[j] == pytest.approx(w.p_ref + w.g_y * integral, rel=1e-11)
+    # heavy fluid on top, pressure falls upward
+    assert rho0[-1] > rho0[0] and np.all(np.diff(p0) < 0)
+
+
+# ------------------------------------------------------------------------- Sod
+def _sod_y(oracle_lib, ny):
+    g = 1.4
+    w = I.Workload(nx=2, ny=ny, x0=0.0, x1=2.0 / ny, y0=0.0, y1=1.0, g_y=0.0, T=0.2, nsteps=0, cfl=0.4)
+    _, y = oracle_lib.cell_centres(w)
+    left = y < 0.5
+    rho = np.where(left, 1.0, 0.125)[:, None] * np.ones((1, 2))
+    p = np.where(left, 1.0, 0.1)[:, None] * np.ones((1, 2))
+    z = np.zeros_like(rho)
+    U, _ = oracle_lib.run_state(w, _cons(rho, z, z, p, g))
+    return w, y, U
+
+
+def test_sod_along_y_converges_to_exact(oracle_lib):
+    """PLM + HLLC + RK2 with g = 0, reflecting walls: L1 density error against
+    the exact Riemann solution falls under refinement; the star pressure and
+    velocity in the plateau match the exact values."""
+    errs = []
+    for ny in (100, 200, 400):
+        w, y, U = _sod_y(oracle_lib, ny)
+        r, u, v, p = _prim(U, 1.4)
+        assert np.all(u == 0.0)
+        assert np.array_equal(U[:, :, 0], U[:, :, 1])
+        ex = riemann_exact.sample((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4, (y - 0.5) / 0.2)
+        errs.append(np.mean(np.abs(r[:, 0] - ex[0])))
+        if ny == 400:
+            ps, us, _, _ = riemann_exact.star_state((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4)
+            plateau = (y > 0.5 + 0.2 * (us + 0.1)) & (y < 0.5 + 0.2 * 1.6)
+            assert abs(np.mean(p[plateau, 0]) - ps) < 2e-3
+            assert abs(np.mean(v[plateau, 0]) - us) < 5e-3
+    assert errs[1] < 0.75 * errs[0] and errs[2] < 0.75 * errs[1]
+    assert errs[2] < 6e-3
+
+
+def test_sod_along_x_periodic_pair(oracle_lib):
+    """The same problem along x on a periodic [0, 2] with a mirrored pair."""
+    nx = 400
+    g = 1.4
+    w = I.Workload(nx=nx, ny=2, x0=0.0, x1=2.0, y0=0.0, y1=2.0 * 2 / nx, g_y=0.0, T=0.2, nsteps=0)
+    x, _ = oracle_lib.cell_centres(w)
+    inner = (x > 0.5) & (x < 1.5)
+    rho = np.ones((2, 1)) * np.where(inner, 1.0, 0.125)[None, :]
+    p = np.ones((2, 1)) * np.where(inner, 1.0, 0.1)[None, :]
+    z = np.zeros_like(rho)
+    U, _ = oracle_lib.run_state(w, _cons(rho, z, z, p, g))
+    r, u, v, pp = _prim(U, g)
+    assert np.all(v == 0.0)
+    win = (x > 1.0) & (x < 1.95)
+    ex = riemann_exact.sample((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), g, (x[win] - 1.5) / 0.2)
+    assert np.mean(np.abs(r[0, win] - ex[0])) < 6e-3
+    assert np.mean(np.abs(u[0, win] - ex[1])) < 1.5e-2
+    # the two halves are mirror images: rho(x) = rho(2 - x) up to rounding
+    assert np.max(np.abs(r[0] - r[0, ::-1])) < 1e-12
+
+
+# --------------------------------------------------------------- conservation
+def test_conservation_without_gravity(oracle_lib):
+    """g = 0, periodic x, reflecting y: mass, x-momentum and energy are
+    conserved to rounding; y-momentum changes only through the wall pressure."""
+    w = I.rt_box(16, 48, g_y=0.0, nsteps=300)
+    v = 0.05 * I.gaussian_field(3, 2, w.ny, w.nx)
+    U0 = oracle_lib.inject(w, v)
+    out = oracle_lib.forward(w, v)
+    U = out["U"]
+    for k in (0, 1, 3):
+        s0, s1 = U0[k].sum(), U[k].sum()
+        scale = np.abs(U0[k]).sum()
+        assert abs(s1 - s0) <= 1e-13 * scale * 1.0
+    assert abs(U[2].sum() - U0[2].sum()) > 0.0  # walls exchange y momentum
+
+
+def test_mass_and_x_momentum_with_gravity(oracle_lib):
+    w = I.rt_box(16, 48, nsteps=300)
+    v = oracle_lib.scale_to_budget(w, I.gaussian_field(4, 2, w.ny, w.nx), 1e-3)
+    U0 = oracle_lib.inject(w, v)
+    U = oracle_lib.forward(w, v)["U"]
+    assert abs(U[0].sum() - U0[0].sum()) <= 1e-13 * U0[0].sum()
+    assert abs(U[1].sum() - U0[1].sum()) <= 1e-13 * np.abs(U0[1]).sum()
+
+
+# -------------------------------------------------------------- exact symmetries
+def test_unperturbed_state_is_x_invariant(oracle_lib):
+    """v0 = 0: u_x stays exactly zero and every column is bitwise identical."""
+    w = I.rt_box(16, 48, nsteps=100)
+    U = oracle_lib.forward(w, np.zeros((2, w.ny, w.nx)))["U"]
+    assert np.all(U[1] == 0.0)
+    assert np.all(U == U[:, :, :1])
+
+
+def test_uniform_state_without_gravity_is_steady(oracle_lib):
+    w = I.Workload(nx=8, ny=12, x0=0.0, x1=1.0, y0=0.0, y1=1.5, g_y=0.0, nsteps=20)
+    rho = np.full((12, 8), 1.3)
+    z = np.zeros_like(rho)
+    U0 = _cons(rho, z, z, np.full_like(rho, 0.7), 1.4)
+    U, _ = oracle_lib.run_state(w, U0)
+    assert np.array_equal(U, U0)
+
+
+def test_uniform_translation_along_x_is_preserved(oracle_lib):
+    """A uniform flow along x (periodic) is an exact solution; the finite-volume
+    update keeps it to rounding."""
+    w = I.Workload(nx=8, ny=12, x0=0.0, x1=1.0, y0=0.0, y1=1.5, g_y=0.0, nsteps=20)
+    one = np.ones((12, 8))
+    U0 = _cons(1.3 * one, 0.4 * one, 0.0 * one, 0.7 * one, 1.4)
+    U, _ = oracle_lib.run_state(w, U0)
+    assert np.max(np.abs(U - U0)) < 1e-14
+
+
+def test_x_translation_commutes_bitwise(oracle_lib):
+    """Shifting v0 by k cells along x shifts the final state bitwise; J agrees
+    up to summation order."""
+    w = I.rt_box(16, 48, nsteps=60)
+    v = oracle_lib.scale_to_budget(w, I.gaussian_field(7, 2, w.ny, w.nx), 1e-4)
+    a = oracle_lib.forward(w, v)
+    b = oracle_lib.forward(w, np.roll(v, 5, axis=2))
+    assert np.array_equal(np.roll(a["U"], 5, axis=2), b["U"])
+    assert np.array_equal(a["dt"], b["dt"])
+    assert b["J_ke"] == pytest.approx(a["J_ke"], rel=1e-14)
+
+
+def test_horizon_clipping(oracle_lib):
+    w = I.rt_box(8, 24, T=0.05, nsteps=0)
+    out = oracle_lib.forward(w, np.zeros((2, w.ny, w.nx)))
+    assert out["dt"].sum() == pytest.approx(0.05, rel=1e-14)
+    assert np.all(out["dt"][:-1] >= out["dt"][-1])
+
+
+# -------------------------------------------------------- linear RT growth rate
+def test_linear_rayleigh_taylor_growth_rate(oracle_lib):
+    """Sec. 2.2, Eq. sigma: a small single-mode seed grows at sigma = sqrt(A g k)
+    in the thin-interface limit. The finite interface lowers the rate, so the
+    fitted rate of the perturbation kinetic energy must lie in
+    [0.8, 1.02] sqrt(A g k)."""
+    w = I.rt_box(32, 96, g_y=-1.0, nsteps=0, T=2.4, limiter=I.LIM_NONE)
+    x, y = oracle_lib.cell_centres(w)
+    k = 2 * math.pi / (w.x1 - w.x0)
+    vy = 1e-6 * np.cos(k * x)[None, :] * np.exp(-k * np.abs(y))[:, None]
+    v = np.stack([np.zeros_like(vy), vy])
+    base = oracle_lib.forward(w, np.zeros_like(v))
+    dts = base["dt"]
+    t = np.cumsum(dts)
+    rho0, _ = oracle_lib.base_state(w)
+
+    def pert_ke(m):
+        a = oracle_lib.forward(w, v, dt_replay=dts[:m])["U"]
+        b = oracle_lib.forward(w, 0 * v, dt_replay=dts[:m])["U"]
+        du = (a[1:3] - b[1:3]) / rho0[None, :, None]
+        return np.sum(0.5 * rho0[None, :, None] * du * du)
+
+    m1 = int(np.searchsorted(t, 1.2))
+    m2 = len(dts)
+    sigma = math.log(pert_ke(m2) / pert_ke(m1)) / (2 * (t[m2 - 1] - t[m1 - 1]))
+    A = (w.rho_heavy - w.rho_light) / (w.rho_heavy + w.rho_light)
+    ideal = math.sqrt(A * abs(w.g_y) * k)
+    assert 0.8 * ideal <= sigma <= 1.02 * ideal, (sigma, ideal)
