@@ -1,0 +1,298 @@
+"""Benchmark: batched forward + adjoint gradient of the RT CNOP hot path.
+
+Workload (one step): rt_gradient on a batch of 32 instances of the 256x768
+Rayleigh-Taylor box (gamma 1.4, g_y -0.1, rho 2 over 1, h_s 0.01, p 2.5 at
+y = 0, periodic x / reflecting y, PLM minmod + HLLC + SSP-RK2, CFL 0.4),
+horizon T = 2.0, FP32 state with FP64 reductions, seeded i.i.d. (vx, vy)
+perturbations scaled to C = 1e-4, sqrt(N) checkpointing. One step is one
+gradient evaluation of every instance: forward to T, recomputation, adjoint.
+
+Metric: cell-updates/s of forward+adjoint (cells x RK2 steps of all
+instances / device time of the gradient call). Also reported: gradient
+evaluations/s, the same metric end to end through the C ABI with host
+buffers, an FP64 single-instance comparison, the roofline of the dominant
+kernel, and the FP64 CPU oracle's rate on a bounded sample.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank runs its own batch (weak scaling, no data-path
+collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import rt_inputs as I  # noqa: E402
+
+BATCH = 32
+NX, NY = 256, 768
+T_HORIZON = 2.0
+DELTA = 1e-4
+METRIC = "cell-updates/s fwd+adjoint; CNOP gradient evals/s at 256x768, batch 32, vs FP64"
+UNIT = "cell-updates/s"
+WORKLOAD = "rt-box 256x768 x32 instances, T=2.0, FP32 state + FP64 reductions, rt_gradient (fwd+ckpt recompute+adjoint)"
+# algorithmic bytes per cell per adjoint launch (FP32): stage-2 adjoint reads
+# U1, lam^{n+1}, writes lam1 (12 s); stage-1 adjoint reads U^n, lam1,
+# lam^{n+1}, writes lam^n (16 s); s = 4 bytes; launches alternate.
+ADJ_BYTES_PER_CELL = {"stage2_adjoint": 12 * 4, "stage1_adjoint": 16 * 4, "mean": 14 * 4}
+STEP_BYTES_PER_CELL_UPDATE = 76 * 4  # forward 20s + recompute 20s + adjoint 36s (sqrt checkpointing)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6400.0)), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = list(self.rows)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def bench_inputs(rank):
+    """Seeded (vx, vy) fields of the rank's batch (seeds rank*32 .. rank*32+31)."""
+    seeds = range(rank * BATCH, rank * BATCH + BATCH)
+    return I.gaussian_batch(seeds, 2, NY, NX).reshape(-1)
+
+
+def workload_problems():
+    return [I.single_256().replace(T=T_HORIZON) for _ in range(BATCH)]
+
+
+def cpu_oracle_sample(n_steps=3):
+    """FP64 CPU oracle on a bounded sample of the workload: one 256x768
+    instance, n_steps CFL steps forward plus the reverse sweep. Returns
+    (cell-updates/s, seconds, sample description)."""
+    import oracle
+    w = I.single_256().replace(nsteps=n_steps)
+    v = oracle.scale_to_budget(w, I.gaussian_field(0, 2, NY, NX), DELTA)
+    t0 = time.perf_counter()
+    out = oracle.forward(w, v)
+    oracle.gradient(w, v, out["dt"])
+    dt = time.perf_counter() - t0
+    cells = NX * NY * out["nsteps"]
+    return cells / dt, dt, f"1 instance 256x768 FP64, {out['nsteps']} CFL steps forward + reverse sweep"
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        cpu_oracle_sample(2)
+    vals, secs = [], 0.0
+    desc = ""
+    for _ in range(args.steps):
+        v, s, desc = cpu_oracle_sample(2)
+        vals.append(v)
+        secs += s
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD + " (oracle: bounded sample per step)", "grid": [NX, NY], "T": T_HORIZON},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import paper_2608_04085_b300 as rt
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    probs = workload_problems()
+    xi = bench_inputs(rank)
+    ctx = rt.Context(probs, precision=rt.RT_FP32_STATE, ckpt=rt.RT_CKPT_SQRT)
+    # scale each instance onto C = 1e-4 (Eq. constraint) with the library's projection kernel
+    v_host = ctx.project(xi, DELTA, to_budget=True)
+    v_dev = torch.from_numpy(v_host).to(dev)
+    g_dev = torch.empty_like(v_dev)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        ctx.gradient(v_dev, out=g_dev)
+    ctx.set_kernel_timing(8)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    ms_total, cells_total, launches, ktimes = 0.0, 0.0, 0, []
+    for _ in range(args.steps):
+        J, _, st = ctx.gradient(v_dev, out=g_dev)
+        ms_total += st["ms"]
+        cells_total += st["cell_updates"]
+        launches += st["launches"]
+        ktimes.append(ctx.kernel_times())
+    barrier()
+    clk = clocks.stop()
+    ctx.set_kernel_timing(0)
+    steps_run = st["steps"]
+
+    # end to end through the C ABI with host buffers (copies inside the call)
+    g_host = np.zeros(ctx.total)
+    e2e_ms = 0.0
+    for _ in range(max(1, min(args.steps, 2))):
+        t0 = time.perf_counter()
+        J_h, _, st_h = ctx.gradient(v_host, out=g_host)
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+        e2e_cells = st_h["cell_updates"]
+    e2e_rate = e2e_cells / (e2e_ms / max(1, min(args.steps, 2)) * 1e-3)
+
+    t_max = ms_total
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms_total, cells_total], dtype=torch.float64, device=dev)
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        t_max = float(mx[0])
+        cells_total = float(tt[1])
+
+    # FP64 single-instance comparison (same grid and seed-0 input, bounded horizon)
+    fp64 = None
+    if rank == 0:
+        p64 = [I.single_256().replace(T=0.2)]
+        with rt.Context(p64, precision=rt.RT_FP64, ckpt=rt.RT_CKPT_SQRT) as c64:
+            v64 = v_host[: c64.total].copy()
+            c64.gradient(v64)
+            _, _, s64 = c64.gradient(v64)
+        rate64 = s64["cell_updates"] / (s64["ms"] * 1e-3)
+        fp64 = {"cell_updates_per_s": rate64, "steps_sampled": s64["steps"], "T_sampled": 0.2,
+                "grad_evals_per_s_at_T2": rate64 / (NX * NY * steps_run)}
+
+    if rank == 0:
+        value = cells_total / (t_max * 1e-3)
+        grad_evals = BATCH * world * args.steps / (t_max * 1e-3)
+        peak, peak_kind = measured_peaks()
+        # dominant kernel: the adjoint stage (mean over both adjoint launches of a step)
+        adj_ms = statistics.mean(k["adjoint"][0] for k in ktimes)
+        st1_ms = statistics.mean(k["stage1"][0] for k in ktimes)
+        st2_ms = statistics.mean(k["stage2"][0] for k in ktimes)
+        cells_per_launch = BATCH * NX * NY
+        achieved = ADJ_BYTES_PER_CELL["mean"] * cells_per_launch / (adj_ms * 1e-3) / 1e9
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "instances_per_gpu": BATCH, "grid": [NX, NY], "T": T_HORIZON,
+                       "rk2_steps": steps_run, "checkpointing": "sqrt(N)", "l2": "working set > L2 (no flush)"},
+            "grad_evals_per_s": grad_evals,
+            "e2e": {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": int(ctx.total * 8),
+                    "d2h_bytes_per_step": int(ctx.total * 8 + BATCH * 8)},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "roofline": {"bound": "hbm", "kernel": "k_adjoint<float>", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": peak_kind + " hbm_gbs",
+                         "algorithmic_bytes_per_cell": ADJ_BYTES_PER_CELL["mean"],
+                         "mean_launch_ms": {"adjoint": adj_ms, "stage1": st1_ms, "stage2": st2_ms}},
+            "step_roofline": {"bytes_per_cell_update": STEP_BYTES_PER_CELL_UPDATE,
+                              "achieved_gbs": value * STEP_BYTES_PER_CELL_UPDATE / 1e9,
+                              "frac": value * STEP_BYTES_PER_CELL_UPDATE / 1e9 / peak},
+            "fp64_single_instance": fp64,
+            "speedup_vs_fp64_single": grad_evals / world / fp64["grad_evals_per_s_at_T2"] if fp64 else None,
+        }
+        if not args.no_cpu:
+            rate, secs, desc = cpu_oracle_sample(3)
+            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+                                    "seconds": secs}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,205 @@
+/* rt_cnop.h -- C ABI of the B300 library for conditional nonlinear optimal
+ * perturbations (CNOP) of the 2D compressible Rayleigh-Taylor instability.
+ *
+ * The paper (arXiv 2608.04085) defines the problem this library solves:
+ *   * Sec. 2.1, Eqs. mass/momentum/energy and total_energy: 2D compressible
+ *     Euler equations with a uniform gravity source, ideal-gas EOS;
+ *   * Sec. 2.1-2.2, Eq. rho0: periodic x; tanh density interface in
+ *     hydrostatic balance; y boundary reflecting or hydrostatic;
+ *   * Sec. 2.3: finite-volume Godunov scheme with HLLC fluxes and a gravity
+ *     source (this library: PLM on primitive variables, HLLC with Davis wave
+ *     speeds, SSP-RK2, CFL time step);
+ *   * Sec. 3.1, Eqs. ke, objective, constraint: the forward map F_t from a
+ *     velocity perturbation v0, the objective J (final kinetic energy, or the
+ *     squared kinetic-energy-density anomaly) and the budget C(v0) <= eps;
+ *   * Sec. 3.4, Eq. projection: exact discrete gradient dJ/dv0 by reverse
+ *     mode with checkpointing, projection P onto the budget, and a projected
+ *     gradient maximisation with a non-monotone Armijo line search.
+ *
+ * Conventions shared by every call:
+ *   * Every call returns rt_status; no C++ exception crosses the ABI. On
+ *     failure rt_last_error(ctx) returns a message owned by the context.
+ *   * A context owns all device memory (states, checkpoints, dt records) and
+ *     runs on the CUDA stream given to rt_init (NULL = legacy default
+ *     stream). Calls are synchronous with respect to the host: they return
+ *     after their device work has finished.
+ *   * Perturbations and gradients are FP64, layout [instance][component][ny][nx]
+ *     (C-contiguous, x fastest); instances are concatenated in order, each
+ *     with perturb_ncomp components (1: u_y only; 2: u_x then u_y).
+ *     rt_field_offset / rt_field_size give each instance's place.
+ *   * Pointer arguments are host pointers unless RT_DEVICE_PTRS is set in
+ *     `flags`, in which case the perturbation / gradient arrays are device
+ *     pointers on the context's device (e.g. torch.Tensor.data_ptr()).
+ *     Scalar outputs (J, C, statistics) are always host arrays.
+ *   * The caller owns every array it passes; the library keeps no pointer to
+ *     caller memory after a call returns.
+ */
+#ifndef RT_CNOP_H
+#define RT_CNOP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rt_ctx rt_ctx;
+
+typedef enum {
+  RT_OK = 0,
+  RT_EINVAL = 1,        /* bad argument, shape or parameter */
+  RT_ENOMEM = 2,        /* device or host allocation failed */
+  RT_ECUDA = 3,         /* a CUDA runtime call failed */
+  RT_ENONFINITE = 4,    /* non-positive density/pressure or NaN in a state */
+  RT_ETIMEOUT = 5,      /* a bounded device wait gave up */
+  RT_ENOTCONVERGED = 6, /* optimiser stopped without an accepted step */
+  RT_ESTATE = 7         /* call out of order (e.g. replay before any run) */
+} rt_status;
+
+enum { RT_BC_REFLECT = 0, RT_BC_HYDROSTATIC = 1 };
+enum { RT_LIM_MINMOD = 0, RT_LIM_MC = 1, RT_LIM_NONE = 2 };
+enum { RT_OBJ_KE = 0, RT_OBJ_EK_ANOMALY_L2 = 1 };
+enum { RT_FP64 = 0, RT_FP32_STATE = 1 };
+enum { RT_CKPT_AUTO = 0, RT_CKPT_STORE_ALL = 1, RT_CKPT_SQRT = 2 };
+
+/* flags for rt_forward / rt_gradient / rt_constraint / rt_project */
+enum { RT_DEVICE_PTRS = 1, RT_REPLAY_DT = 2 };
+
+/* One RT problem (Sec. 2.1-2.3). Geometry: cells are (x1-x0)/nx by
+ * (y1-y0)/ny. Base state: rho0(y) = (rho_heavy+rho_light)/2 +
+ * (rho_heavy-rho_light)/2 tanh((y-y_int)/h_s) and p0 from dp/dy = rho0 g_y
+ * with p0(y_ref) = p_ref. g_y is the signed acceleration (paper -1, negative
+ * = downward). nsteps > 0 runs that many CFL steps; otherwise the run ends
+ * at time T, the last step clipped to T - t. */
+typedef struct {
+  int nx, ny;
+  double x0, x1, y0, y1;
+  double gamma, g_y;
+  double rho_heavy, rho_light, y_int, h_s;
+  double p_ref, y_ref;
+  int bc_y;          /* RT_BC_REFLECT | RT_BC_HYDROSTATIC */
+  int limiter;       /* RT_LIM_MINMOD | RT_LIM_MC | RT_LIM_NONE */
+  double cfl;
+  double T;
+  int nsteps;
+  int perturb_ncomp; /* 1: u_y only (Sec. 3.1); 2: (u_x, u_y) */
+  int objective;     /* RT_OBJ_KE | RT_OBJ_EK_ANOMALY_L2 */
+} rt_problem;
+
+typedef struct {
+  int precision;            /* RT_FP64, or RT_FP32_STATE: FP32 state with FP64 reductions */
+  int ckpt;                 /* RT_CKPT_AUTO | RT_CKPT_STORE_ALL | RT_CKPT_SQRT */
+  double ckpt_hbm_cap_bytes;/* cap on checkpoint + segment memory; 0 = 60% of free memory */
+  int max_steps;            /* upper bound on steps per run (sizes the dt record); 0 = 200000 */
+} rt_options;
+
+typedef struct {
+  int steps;                /* largest step count over instances in the last run */
+  int segments;             /* checkpoint segments used by the last gradient */
+  int bad_instance;         /* first instance with a non-finite state, or -1 */
+  long long bad_cell;       /* its cell index (j*nx + i), or -1 */
+  double cell_updates;      /* sum over instances of cells x steps advanced */
+  double ms;                /* device time of the call, CUDA events on the stream */
+  long long launches;       /* kernels launched by the call */
+} rt_run_stats;
+
+/* Create a context for n_instances problems (instances may differ in grid
+ * and physics but share precision and checkpoint policy). Builds the base
+ * state of every instance (Sec. 2.2) on the host in FP64, uploads it, and,
+ * for instances using RT_OBJ_EK_ANOMALY_L2, runs the unperturbed baseline
+ * (Eq. objective) once. cuda_stream is a cudaStream_t or NULL.
+ * Errors: RT_EINVAL (nx < 4, ny < 2, non-positive densities/pressures,
+ * unknown enums), RT_ENOMEM, RT_ECUDA. *out is NULL on failure. */
+rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options* opt,
+                  void* cuda_stream, rt_ctx** out);
+
+/* Release every device buffer of the context. NULL is ignored. */
+void rt_destroy(rt_ctx* ctx);
+
+/* Message of the last failed call on this context ("" if none). */
+const char* rt_last_error(const rt_ctx* ctx);
+
+/* Number of instances, and the offset / length (in doubles) of instance i's
+ * perturbation field inside the concatenated layout. */
+int rt_num_instances(const rt_ctx* ctx);
+size_t rt_field_offset(const rt_ctx* ctx, int inst);
+size_t rt_field_size(const rt_ctx* ctx, int inst);
+size_t rt_field_total(const rt_ctx* ctx);
+
+/* Forward map F_t (Sec. 3.1): inject v0 into the base state, march every
+ * instance to its horizon, and write J_out[i] = J of instance i (its
+ * `objective`); J_ke_out[i] (nullable) = final total kinetic energy.
+ * RT_REPLAY_DT re-uses the dt sequence recorded by the previous run instead
+ * of the CFL control (frozen-dt finite differences). st is nullable.
+ * Errors: RT_EINVAL, RT_ESTATE (replay without a previous run),
+ * RT_ENONFINITE (st->bad_* says where), RT_ECUDA. */
+rt_status rt_forward(rt_ctx* ctx, const double* v0, int flags, double* J_out,
+                     double* J_ke_out, rt_run_stats* st);
+
+/* Exact discrete gradient dJ/dv0 (Sec. 3.4) of the same map, dt sequence
+ * frozen at the one the forward pass chose, by a hand-written adjoint of the
+ * time stepper with sqrt(N) (or store-all) checkpointing. grad_out has the
+ * layout of v0. Errors as rt_forward. */
+rt_status rt_gradient(rt_ctx* ctx, const double* v0, int flags, double* J_out,
+                      double* grad_out, rt_run_stats* st);
+
+/* Eq. constraint: C_out[i] = sum over cells and components of
+ * rho0 v^2 / 2 dx dy for instance i. */
+rt_status rt_constraint(rt_ctx* ctx, const double* v, int flags, double* C_out);
+
+/* Eq. projection, in place: v_i <- v_i * min(1, sqrt(eps_i / C(v_i)));
+ * with to_budget != 0, v_i <- v_i * sqrt(eps_i / C(v_i)) (scale onto the
+ * sphere C = eps). eps has one entry per instance. */
+rt_status rt_project(rt_ctx* ctx, double* v, int flags, const double* eps, int to_budget);
+
+/* Final conserved state (rho, m_x, m_y, E) of instance i after the last
+ * forward run, as FP64 [4][ny][nx] into a host array. */
+rt_status rt_get_state(rt_ctx* ctx, int inst, double* out);
+
+/* dt sequence of instance i recorded by the last run; *n_out = its length.
+ * At most max_n values are written. */
+rt_status rt_get_dt(rt_ctx* ctx, int inst, double* out, int max_n, int* n_out);
+
+/* Kernel timing (no counterpart in the paper; measurement support). With
+ * every > 0, each later call records CUDA events around every `every`-th
+ * launch of the three time-step kernels on the context's stream; 0 turns
+ * it off. rt_kernel_times returns, for the kernels of the last call indexed
+ * 0 = stage 1, 1 = stage 2, 2 = adjoint stage: mean device time per sampled
+ * launch (ms), number of samples, and number of launches (any array may be
+ * NULL). */
+rt_status rt_set_kernel_timing(rt_ctx* ctx, int every);
+rt_status rt_kernel_times(rt_ctx* ctx, double* mean_ms, long long* samples, long long* launches);
+
+typedef struct {
+  int max_iter;          /* outer iterations */
+  int gll_memory;        /* non-monotone memory M (max of the last M values) */
+  int max_backtracks;    /* per iteration; 0 = 30 */
+  double armijo_c;       /* sufficient-increase constant, e.g. 1e-4 */
+  double alpha_min, alpha_max; /* spectral step safeguards */
+  double h_loc;          /* > 0: multiply v_inout by exp(-(y-y_int)^2/(2 h_loc^2)) first */
+  const double* eps;     /* budget per instance */
+} cnop_params;
+
+typedef struct {
+  int iterations;        /* accepted iterations (minimum over instances) */
+  int forward_evals;     /* batched forward runs (line-search trials) */
+  int gradient_evals;    /* batched gradient runs */
+  double ms;             /* device time of the whole solve */
+} cnop_result;
+
+/* CNOP by spectral projected gradient ascent (Sec. 3.4): every instance
+ * starts from v_inout (a seeded random field; optionally localised by h_loc),
+ * scaled onto C = eps, then iterates d = P(v + alpha g) - v, a non-monotone
+ * Armijo backtracking line search along d, and the Barzilai-Borwein step
+ * alpha = <s,s>/<s,y'> with y' = -(g_new - g_old). All instances advance in
+ * lockstep through batched forward and gradient runs. On return v_inout
+ * holds the CNOP of every instance and J_out[i] (nullable) its objective.
+ * Errors: as rt_gradient; RT_ENOTCONVERGED when an instance found no
+ * acceptable step (its last accepted iterate is returned). */
+rt_status cnop_solve(rt_ctx* ctx, const cnop_params* prm, double* v_inout, int flags,
+                     double* J_out, cnop_result* res);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RT_CNOP_H */

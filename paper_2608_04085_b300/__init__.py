@@ -1,0 +1,326 @@
+"""B300 (sm_103a) library for conditional nonlinear optimal perturbations of
+the 2D compressible Rayleigh-Taylor instability (arXiv 2608.04085).
+
+This module is the thin Python binding of the C ABI declared in
+``include/rt_cnop.h``: it only marshals arguments (ctypes structures, host
+NumPy arrays or device tensor pointers) and raises on error statuses. Every
+step of the computation runs in the CUDA library ``librt_cnop.so``; there is
+no CPU fallback, and importing the binding fails loudly when that library has
+not been built (``python -m paper_2608_04085_b300.build``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librt_cnop.so")
+
+RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENONFINITE, RT_ETIMEOUT, RT_ENOTCONVERGED, RT_ESTATE = range(8)
+RT_BC_REFLECT, RT_BC_HYDROSTATIC = 0, 1
+RT_LIM_MINMOD, RT_LIM_MC, RT_LIM_NONE = 0, 1, 2
+RT_OBJ_KE, RT_OBJ_EK_ANOMALY_L2 = 0, 1
+RT_FP64, RT_FP32_STATE = 0, 1
+RT_CKPT_AUTO, RT_CKPT_STORE_ALL, RT_CKPT_SQRT = 0, 1, 2
+RT_DEVICE_PTRS, RT_REPLAY_DT = 1, 2
+
+_STATUS = {1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENONFINITE", 5: "RT_ETIMEOUT",
+           6: "RT_ENOTCONVERGED", 7: "RT_ESTATE"}
+
+#: every entry point declared in include/rt_cnop.h
+EXPORTS = ("rt_init", "rt_destroy", "rt_last_error", "rt_num_instances", "rt_field_offset",
+           "rt_field_size", "rt_field_total", "rt_forward", "rt_gradient", "rt_constraint",
+           "rt_project", "rt_get_state", "rt_get_dt", "rt_set_kernel_timing", "rt_kernel_times",
+           "cnop_solve")
+
+
+class RtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class RtProblem(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("g_y", ctypes.c_double),
+                ("rho_heavy", ctypes.c_double), ("rho_light", ctypes.c_double),
+                ("y_int", ctypes.c_double), ("h_s", ctypes.c_double),
+                ("p_ref", ctypes.c_double), ("y_ref", ctypes.c_double),
+                ("bc_y", ctypes.c_int), ("limiter", ctypes.c_int),
+                ("cfl", ctypes.c_double), ("T", ctypes.c_double),
+                ("nsteps", ctypes.c_int), ("perturb_ncomp", ctypes.c_int),
+                ("objective", ctypes.c_int)]
+
+
+class RtOptions(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("ckpt", ctypes.c_int),
+                ("ckpt_hbm_cap_bytes", ctypes.c_double), ("max_steps", ctypes.c_int)]
+
+
+class RtRunStats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("segments", ctypes.c_int), ("bad_instance", ctypes.c_int),
+                ("bad_cell", ctypes.c_longlong), ("cell_updates", ctypes.c_double), ("ms", ctypes.c_double),
+                ("launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class CnopParams(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int), ("gll_memory", ctypes.c_int), ("max_backtracks", ctypes.c_int),
+                ("armijo_c", ctypes.c_double), ("alpha_min", ctypes.c_double), ("alpha_max", ctypes.c_double),
+                ("h_loc", ctypes.c_double), ("eps", ctypes.POINTER(ctypes.c_double))]
+
+
+class CnopResult(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("forward_evals", ctypes.c_int),
+                ("gradient_evals", ctypes.c_int), ("ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def library():
+    """Load librt_cnop.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library {LIB_PATH} is missing; build it with "
+                               "`python -m paper_2608_04085_b300.build` (there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+        L.rt_init.argtypes = [ctypes.POINTER(RtProblem), ip, ctypes.POINTER(RtOptions), vp, ctypes.POINTER(vp)]
+        L.rt_init.restype = ip
+        L.rt_destroy.argtypes = [vp]
+        L.rt_destroy.restype = None
+        L.rt_last_error.argtypes = [vp]
+        L.rt_last_error.restype = ctypes.c_char_p
+        L.rt_num_instances.argtypes = [vp]
+        L.rt_num_instances.restype = ip
+        for f in ("rt_field_offset", "rt_field_size"):
+            getattr(L, f).argtypes = [vp, ip]
+            getattr(L, f).restype = ctypes.c_size_t
+        L.rt_field_total.argtypes = [vp]
+        L.rt_field_total.restype = ctypes.c_size_t
+        L.rt_forward.argtypes = [vp, vp, ip, dp, dp, ctypes.POINTER(RtRunStats)]
+        L.rt_forward.restype = ip
+        L.rt_gradient.argtypes = [vp, vp, ip, dp, vp, ctypes.POINTER(RtRunStats)]
+        L.rt_gradient.restype = ip
+        L.rt_constraint.argtypes = [vp, vp, ip, dp]
+        L.rt_constraint.restype = ip
+        L.rt_project.argtypes = [vp, vp, ip, dp, ip]
+        L.rt_project.restype = ip
+        L.rt_get_state.argtypes = [vp, ip, dp]
+        L.rt_get_state.restype = ip
+        L.rt_get_dt.argtypes = [vp, ip, dp, ip, ctypes.POINTER(ip)]
+        L.rt_get_dt.restype = ip
+        L.rt_set_kernel_timing.argtypes = [vp, ip]
+        L.rt_set_kernel_timing.restype = ip
+        llp = ctypes.POINTER(ctypes.c_longlong)
+        L.rt_kernel_times.argtypes = [vp, dp, llp, llp]
+        L.rt_kernel_times.restype = ip
+        L.cnop_solve.argtypes = [vp, ctypes.POINTER(CnopParams), vp, ip, dp, ctypes.POINTER(CnopResult)]
+        L.cnop_solve.restype = ip
+        _lib = L
+    return _lib
+
+
+def _field(w, name, alt=None, default=None):
+    if isinstance(w, dict):
+        if name in w:
+            return w[name]
+        if alt and alt in w:
+            return w[alt]
+        return default
+    if hasattr(w, name):
+        return getattr(w, name)
+    if alt and hasattr(w, alt):
+        return getattr(w, alt)
+    return default
+
+
+def make_problem(w) -> RtProblem:
+    """rt_problem from any object or dict with the field names of rt_problem
+    (``ncomp`` is accepted for ``perturb_ncomp``)."""
+    p = RtProblem()
+    for name, _ in RtProblem._fields_:
+        alt = "ncomp" if name == "perturb_ncomp" else None
+        val = _field(w, name, alt)
+        if val is None:
+            raise ValueError(f"problem is missing field {name!r}")
+        setattr(p, name, val)
+    return p
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Context:
+    """A batch of RT instances on the current CUDA device (see rt_init)."""
+
+    def __init__(self, problems, precision=RT_FP64, ckpt=RT_CKPT_AUTO, ckpt_cap_bytes=0.0, max_steps=0,
+                 stream=None):
+        L = library()
+        if not isinstance(problems, (list, tuple)):
+            problems = [problems]
+        self.problems = list(problems)
+        arr = (RtProblem * len(problems))(*[make_problem(w) for w in problems])
+        opt = RtOptions(precision, ckpt, float(ckpt_cap_bytes), int(max_steps))
+        if stream is None:
+            stream = self._torch_stream()
+        self._stream = stream
+        h = ctypes.c_void_p()
+        st = L.rt_init(arr, len(problems), ctypes.byref(opt), ctypes.c_void_p(stream or 0), ctypes.byref(h))
+        if st != RT_OK:
+            raise RtError(st, "rt_init failed (see stderr)")
+        self._h = h
+        self.n = L.rt_num_instances(h)
+        self.total = L.rt_field_total(h)
+        self.offsets = [L.rt_field_offset(h, i) for i in range(self.n)]
+        self.sizes = [L.rt_field_size(h, i) for i in range(self.n)]
+
+    @staticmethod
+    def _torch_stream():
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return 0
+
+    def _check(self, st):
+        if st != RT_OK:
+            raise RtError(st, library().rt_last_error(self._h).decode())
+
+    def _arg(self, a):
+        """(pointer, flags, keepalive) for a host ndarray or a CUDA tensor."""
+        if hasattr(a, "data_ptr") and getattr(a, "is_cuda", False):
+            import torch
+            assert a.dtype == torch.float64 and a.is_contiguous() and a.numel() == self.total
+            return ctypes.c_void_p(a.data_ptr()), RT_DEVICE_PTRS, a
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        assert a.size == self.total, (a.size, self.total)
+        return a.ctypes.data_as(ctypes.c_void_p), 0, a
+
+    def close(self):
+        if getattr(self, "_h", None):
+            library().rt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------ entry points
+    def forward(self, v0, replay=False):
+        """(J[n], J_ke[n], stats) of the forward map (rt_forward)."""
+        p, flags, keep = self._arg(v0)
+        J = np.zeros(self.n)
+        Jke = np.zeros(self.n)
+        st = RtRunStats()
+        self._check(library().rt_forward(self._h, p, flags | (RT_REPLAY_DT if replay else 0), _dptr(J),
+                                          _dptr(Jke), ctypes.byref(st)))
+        del keep
+        return J, Jke, st.as_dict()
+
+    def gradient(self, v0, out=None):
+        """(J[n], dJ/dv0, stats) (rt_gradient). For a CUDA tensor input the
+        gradient is a CUDA tensor, else a NumPy array."""
+        p, flags, keep = self._arg(v0)
+        if out is None:
+            if flags & RT_DEVICE_PTRS:
+                import torch
+                out = torch.empty_like(v0)
+            else:
+                out = np.zeros(self.total)
+        gp, gflags, gkeep = self._arg(out)
+        assert gflags == flags, "v0 and the gradient must both be host or both be device arrays"
+        J = np.zeros(self.n)
+        st = RtRunStats()
+        self._check(library().rt_gradient(self._h, p, flags, _dptr(J), gp, ctypes.byref(st)))
+        del keep, gkeep
+        return J, out, st.as_dict()
+
+    def constraint(self, v):
+        p, flags, keep = self._arg(v)
+        C = np.zeros(self.n)
+        self._check(library().rt_constraint(self._h, p, flags, _dptr(C)))
+        return C
+
+    def project(self, v, eps, to_budget=False):
+        """P(v) (Eq. projection), or the rescale onto C = eps; returns a new array."""
+        if hasattr(v, "clone"):
+            out = v.clone()
+        else:
+            out = np.array(v, dtype=np.float64, copy=True).ravel()
+        p, flags, keep = self._arg(out)
+        e = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, dtype=np.float64), (self.n,)))
+        self._check(library().rt_project(self._h, p, flags, _dptr(e), int(bool(to_budget))))
+        return out
+
+    def state(self, inst=0):
+        w = self.problems[inst]
+        out = np.zeros((4, _field(w, "ny"), _field(w, "nx")))
+        self._check(library().rt_get_state(self._h, inst, _dptr(out)))
+        return out
+
+    def dt(self, inst=0):
+        n = ctypes.c_int(0)
+        self._check(library().rt_get_dt(self._h, inst, None, 0, ctypes.byref(n)))
+        out = np.zeros(max(n.value, 1))
+        self._check(library().rt_get_dt(self._h, inst, _dptr(out), n.value, ctypes.byref(n)))
+        return out[:n.value]
+
+    def set_kernel_timing(self, every):
+        """Sample CUDA-event timings of every `every`-th time-step kernel launch."""
+        self._check(library().rt_set_kernel_timing(self._h, int(every)))
+
+    def kernel_times(self):
+        """{'stage1'|'stage2'|'adjoint': (mean ms per sampled launch, samples, launches)}."""
+        ms = np.zeros(3)
+        sa = (ctypes.c_longlong * 3)()
+        la = (ctypes.c_longlong * 3)()
+        self._check(library().rt_kernel_times(self._h, _dptr(ms), sa, la))
+        return {k: (ms[i], sa[i], la[i]) for i, k in enumerate(("stage1", "stage2", "adjoint"))}
+
+    def cnop(self, v_start, eps, iters, gll_memory=10, armijo_c=1e-4, alpha_min=1e-30, alpha_max=1e30,
+             max_backtracks=30, h_loc=0.0, raise_on_stall=False):
+        """CNOP by projected spectral gradient (cnop_solve). Returns (v, J, result)."""
+        if hasattr(v_start, "clone"):
+            v = v_start.clone()
+        else:
+            v = np.array(v_start, dtype=np.float64, copy=True).ravel()
+        p, flags, keep = self._arg(v)
+        e = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, dtype=np.float64), (self.n,)))
+        prm = CnopParams(int(iters), int(gll_memory), int(max_backtracks), float(armijo_c), float(alpha_min),
+                         float(alpha_max), float(h_loc), _dptr(e))
+        J = np.zeros(self.n)
+        res = CnopResult()
+        st = library().cnop_solve(self._h, ctypes.byref(prm), p, flags, _dptr(J), ctypes.byref(res))
+        if st != RT_OK and (raise_on_stall or st != RT_ENOTCONVERGED):
+            self._check(st)
+        return v, J, {k: getattr(res, k) for k, _ in CnopResult._fields_} | {"status": st}
+
+
+def field_layout(problems):
+    """Offsets and sizes of each instance in the concatenated perturbation layout."""
+    off, out = 0, []
+    for w in problems:
+        n = _field(w, "perturb_ncomp", "ncomp") * _field(w, "nx") * _field(w, "ny")
+        out.append((off, n))
+        off += n
+    return out

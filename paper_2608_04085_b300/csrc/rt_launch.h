@@ -1,0 +1,43 @@
+// rt_launch.h -- host-side launchers of the kernels (defined in the FP32 and
+// FP64 translation units) used by the runtime.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "rt_internal.h"
+
+namespace rt {
+
+template <class T>
+cudaError_t launch_inject(const InstDev* insts, const int4* tiles, int ntiles, const double* v, T* U,
+                          const RunDev& run, cudaStream_t s);
+// mode: 0 CFL control, 1 replay counting steps, 2 replay (recompute)
+template <class T>
+cudaError_t launch_stage(int stage, int mode, const InstDev* insts, const int4* tiles, int ntiles, const T* src,
+                         const T* base, T* dst, const RunDev& run, int n, cudaStream_t s);
+template <class T>
+cudaError_t launch_adjoint(const InstDev* insts, const int4* tiles, int ntiles, const T* U, const T* K,
+                           double kscale, const T* E, double escale, T* out, const RunDev& run, int n,
+                           cudaStream_t s);
+template <class T>
+cudaError_t launch_objective(const InstDev* insts, const int4* tiles, int ntiles, T* const* slot_tab, int tab_mod,
+                             const int* nstep, double* ek_out, T* lamA, T* lamB, double* partials,
+                             cudaStream_t s);
+template <class T>
+cudaError_t launch_grad(const InstDev* insts, const int4* tiles, int ntiles, const T* lam, const double* v,
+                        double* g, cudaStream_t s);
+template <class T>
+cudaError_t configure_kernels();
+
+cudaError_t launch_finalize(const InstDev* insts, int n_inst, const double* partials, int width, int scale_by_dA,
+                            double* out, cudaStream_t s);
+// mode 0: C(a)/dA partials; mode 1: <a, b> partials
+cudaError_t launch_field_reduce(int mode, const InstDev* insts, const int4* tiles, int ntiles, const double* a,
+                                const double* b, double* partials, cudaStream_t s);
+cudaError_t launch_field_axpby(const InstDev* insts, const int4* tiles, int ntiles, double* out,
+                               const double* alpha, const double* a, const double* beta, const double* b,
+                               cudaStream_t s);
+cudaError_t launch_localise(const InstDev* insts, const int4* tiles, int ntiles, double h_loc, double* v,
+                            cudaStream_t s);
+
+}  // namespace rt

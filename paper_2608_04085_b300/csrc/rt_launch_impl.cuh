@@ -1,0 +1,74 @@
+// rt_launch_impl.cuh -- launcher templates; included by one translation unit
+// per state type, which instantiates them.
+#pragma once
+
+#include "rt_kernels.cuh"
+#include "rt_launch.h"
+
+namespace rt {
+
+template <class T>
+cudaError_t launch_inject(const InstDev* insts, const int4* tiles, int ntiles, const double* v, T* U,
+                          const RunDev& run, cudaStream_t s) {
+  k_inject<T><<<ntiles, NTH, 0, s>>>(insts, tiles, v, U, run);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_stage(int stage, int mode, const InstDev* insts, const int4* tiles, int ntiles, const T* src,
+                         const T* base, T* dst, const RunDev& run, int n, cudaStream_t s) {
+  if (stage == 1) {
+    if (mode == 0) k_stage<T, 1, 0><<<ntiles, NTH, 0, s>>>(insts, tiles, src, base, dst, run, n);
+    else k_stage<T, 1, 2><<<ntiles, NTH, 0, s>>>(insts, tiles, src, base, dst, run, n);
+  } else {
+    if (mode == 0) k_stage<T, 2, 0><<<ntiles, NTH, 0, s>>>(insts, tiles, src, base, dst, run, n);
+    else if (mode == 1) k_stage<T, 2, 1><<<ntiles, NTH, 0, s>>>(insts, tiles, src, base, dst, run, n);
+    else k_stage<T, 2, 2><<<ntiles, NTH, 0, s>>>(insts, tiles, src, base, dst, run, n);
+  }
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_adjoint(const InstDev* insts, const int4* tiles, int ntiles, const T* U, const T* K,
+                           double kscale, const T* E, double escale, T* out, const RunDev& run, int n,
+                           cudaStream_t s) {
+  k_adjoint<T><<<ntiles, NTH, ADJ_SMEM_ELEMS * sizeof(T), s>>>(insts, tiles, U, K, (T)kscale, E, (T)escale, out,
+                                                                 run, n);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_objective(const InstDev* insts, const int4* tiles, int ntiles, T* const* slot_tab, int tab_mod,
+                             const int* nstep, double* ek_out, T* lamA, T* lamB, double* partials,
+                             cudaStream_t s) {
+  k_objective<T><<<ntiles, NTH, 0, s>>>(insts, tiles, slot_tab, tab_mod, nstep, ek_out, lamA, lamB, partials);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_grad(const InstDev* insts, const int4* tiles, int ntiles, const T* lam, const double* v,
+                        double* g, cudaStream_t s) {
+  k_grad<T><<<ntiles, NTH, 0, s>>>(insts, tiles, lam, v, g);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t configure_kernels() {
+  return cudaFuncSetAttribute(k_adjoint<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(ADJ_SMEM_ELEMS * sizeof(T)));
+}
+
+#define RT_INSTANTIATE_LAUNCHERS(T)                                                                              \
+  template cudaError_t launch_inject<T>(const InstDev*, const int4*, int, const double*, T*, const RunDev&,       \
+                                        cudaStream_t);                                                           \
+  template cudaError_t launch_stage<T>(int, int, const InstDev*, const int4*, int, const T*, const T*, T*,        \
+                                       const RunDev&, int, cudaStream_t);                                        \
+  template cudaError_t launch_adjoint<T>(const InstDev*, const int4*, int, const T*, const T*, double, const T*,  \
+                                         double, T*, const RunDev&, int, cudaStream_t);                          \
+  template cudaError_t launch_objective<T>(const InstDev*, const int4*, int, T* const*, int, const int*, double*, \
+                                           T*, T*, double*, cudaStream_t);                                       \
+  template cudaError_t launch_grad<T>(const InstDev*, const int4*, int, const T*, const double*, double*,         \
+                                      cudaStream_t);                                                             \
+  template cudaError_t configure_kernels<T>();
+
+}  // namespace rt

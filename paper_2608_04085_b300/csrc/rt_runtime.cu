@@ -1,0 +1,981 @@
+// rt_runtime.cu -- host runtime behind the C ABI of include/rt_cnop.h.
+//
+// Owns the device memory of a batch of RT instances (state slots, adjoint
+// slots, checkpoints, dt records), drives the time loop (two stage kernels
+// per step, no host synchronisation inside the loop), the checkpointed
+// reverse sweep of the gradient (Sec. 3.4: exact discrete gradient with
+// checkpointing), and the projected spectral-gradient CNOP loop.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/rt_cnop.h"
+#include "rt_internal.h"
+#include "rt_launch.h"
+
+using rt::InstDev;
+using rt::RunDev;
+
+struct rt_ctx {
+  int n_inst = 0;
+  rt_options opt{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::vector<rt_problem> prob;
+  std::vector<InstDev> h_inst;
+  InstDev* d_inst = nullptr;
+  std::vector<int4> h_tiles;
+  int4* d_tiles = nullptr;
+  int ntiles = 0;
+  long long total_cells = 0;
+  size_t total_v = 0;
+  std::vector<long long> cell_off, v_off;
+  size_t esz = 8;          // bytes per state element
+  size_t slot_bytes = 0;   // one state of every instance
+  double* d_base = nullptr;  // rho0 / p0 of all instances
+  double* d_ek0 = nullptr;   // baseline e_k (anomaly objective) or null
+  double* d_ek = nullptr;    // e_k scratch
+  void* sA = nullptr;        // forward ping-pong
+  void* sB = nullptr;
+  void* sU1 = nullptr;       // stage-1 state
+  void* lA = nullptr;        // adjoint ping-pong
+  void* lB = nullptr;
+  void* l1 = nullptr;        // stage-1 cotangent
+  std::vector<void*> pool;   // checkpoint / stored-state slots
+  void** d_tab = nullptr;    // device table of slot pointers
+  int tab_cap = 0;
+  RunDev run{};
+  double* d_partials = nullptr;  // [ntiles * 2]
+  double* d_sums = nullptr;      // [n_inst * 2]
+  double* d_scal = nullptr;      // [n_inst * 4] per-instance scalars for field kernels
+  double* d_v = nullptr;         // perturbation (device copy)
+  double* d_g = nullptr;         // gradient
+  double* d_w1 = nullptr;        // CNOP work fields
+  double* d_w2 = nullptr;
+  double* d_w3 = nullptr;
+  double* d_w4 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::string err;
+  // last run
+  bool have_run = false;
+  int last_steps = 0;
+  int last_kind = 0;         // 0: ping-pong final state; 2: stored slots
+  std::vector<int> h_nstep;
+  double mem_cap = 0.0;
+  // launch accounting and sampled kernel timing (0: stage 1, 1: stage 2, 2: adjoint)
+  long long launches = 0;
+  long long kind_launches[3] = {0, 0, 0};
+  int time_every = 0;
+  std::vector<cudaEvent_t> evpool;
+  std::vector<std::pair<int, int>> evused;  // (kind, index of the start event; end = index + 1)
+  double kind_ms[3] = {0, 0, 0};
+  long long kind_samples[3] = {0, 0, 0};
+};
+
+namespace {
+
+const double kMaxFinite = 1e300;
+
+rt_status fail(rt_ctx* c, rt_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+#define CU(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(c, RT_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                  __FILE__, __LINE__);                                                    \
+  } while (0)
+
+#define CHK(expr)                   \
+  do {                              \
+    rt_status s_ = (expr);          \
+    if (s_ != RT_OK) return s_;     \
+  } while (0)
+
+// Sec. 2.2, Eq. rho0: tanh density at cell centres and the hydrostatic
+// pressure integrated in closed form from the anchor p(y_ref) = p_ref:
+// p0(y) = p_ref + g_y [ (rho_h+rho_l)/2 (y - y_ref)
+//                      + (rho_h-rho_l)/2 h_s (ln cosh z - ln cosh z_ref) ],
+// z = (y - y_int)/h_s, with ln cosh z = |z| + log1p(exp(-2|z|)) - ln 2.
+double lncosh_no_ln2(double z) {
+  const double a = std::fabs(z);
+  return a + std::log1p(std::exp(-2.0 * a));
+}
+
+void base_state(const rt_problem& P, std::vector<double>& rho0, std::vector<double>& p0) {
+  const double dy = (P.y1 - P.y0) / P.ny;
+  const double zr = (P.y_ref - P.y_int) / P.h_s;
+  rho0.resize(P.ny);
+  p0.resize(P.ny);
+  for (int j = 0; j < P.ny; ++j) {
+    const double y = P.y0 + (j + 0.5) * dy;
+    const double z = (y - P.y_int) / P.h_s;
+    rho0[j] = 0.5 * (P.rho_heavy + P.rho_light) + 0.5 * (P.rho_heavy - P.rho_light) * std::tanh(z);
+    const double I = 0.5 * (P.rho_heavy + P.rho_light) * (y - P.y_ref) +
+                     0.5 * (P.rho_heavy - P.rho_light) * P.h_s * (lncosh_no_ln2(z) - lncosh_no_ln2(zr));
+    p0[j] = P.p_ref + P.g_y * I;
+  }
+}
+
+rt_status validate(rt_ctx* c, const rt_problem& P, int i) {
+  if (P.nx < 4 || P.ny < 2) return fail(c, RT_EINVAL, "instance %d: need nx >= 4 and ny >= 2", i);
+  if (!(P.x1 > P.x0) || !(P.y1 > P.y0)) return fail(c, RT_EINVAL, "instance %d: empty domain", i);
+  if (!(P.gamma > 1.0)) return fail(c, RT_EINVAL, "instance %d: gamma must exceed 1", i);
+  if (!(P.rho_heavy > 0.0) || !(P.rho_light > 0.0) || !(P.h_s > 0.0))
+    return fail(c, RT_EINVAL, "instance %d: densities and h_s must be positive", i);
+  if (!(P.cfl > 0.0) || P.cfl > 1.0) return fail(c, RT_EINVAL, "instance %d: cfl must be in (0, 1]", i);
+  if (P.nsteps <= 0 && !(P.T > 0.0)) return fail(c, RT_EINVAL, "instance %d: need nsteps > 0 or T > 0", i);
+  if (P.bc_y != RT_BC_REFLECT && P.bc_y != RT_BC_HYDROSTATIC) return fail(c, RT_EINVAL, "instance %d: bc_y", i);
+  if (P.limiter < 0 || P.limiter > 2) return fail(c, RT_EINVAL, "instance %d: limiter", i);
+  if (P.perturb_ncomp != 1 && P.perturb_ncomp != 2) return fail(c, RT_EINVAL, "instance %d: perturb_ncomp", i);
+  if (P.objective != RT_OBJ_KE && P.objective != RT_OBJ_EK_ANOMALY_L2)
+    return fail(c, RT_EINVAL, "instance %d: objective", i);
+  std::vector<double> r, p;
+  base_state(P, r, p);
+  for (int j = 0; j < P.ny; ++j)
+    if (!(p[j] > 0.0)) return fail(c, RT_EINVAL, "instance %d: base pressure not positive at row %d", i, j);
+  return RT_OK;
+}
+
+template <class T> T* slotp(void* p) { return static_cast<T*>(p); }
+
+// Start/stop a sampled timing window around one time-step kernel launch.
+int timing_begin(rt_ctx* c, int kind) {
+  ++c->launches;
+  const long long k = c->kind_launches[kind]++;
+  if (c->time_every <= 0 || k % c->time_every != 0) return -1;
+  const int idx = (int)(2 * c->evused.size());
+  if (idx + 1 >= (int)c->evpool.size()) return -1;
+  cudaEventRecord(c->evpool[idx], c->stream);
+  c->evused.push_back({kind, idx});
+  return idx;
+}
+void timing_end(rt_ctx* c, int idx) {
+  if (idx >= 0) cudaEventRecord(c->evpool[idx + 1], c->stream);
+}
+
+template <class T>
+cudaError_t stage(rt_ctx* c, int st, int mode, const T* src, const T* base, T* dst, int n) {
+  const int ev = timing_begin(c, st - 1);
+  cudaError_t e = rt::launch_stage<T>(st, mode, c->d_inst, c->d_tiles, c->ntiles, src, base, dst, c->run, n, c->stream);
+  timing_end(c, ev);
+  return e;
+}
+
+template <class T>
+cudaError_t adjoint(rt_ctx* c, const T* U, const T* K, double ks, const T* E, double es, T* out, int n) {
+  const int ev = timing_begin(c, 2);
+  cudaError_t e = rt::launch_adjoint<T>(c->d_inst, c->d_tiles, c->ntiles, U, K, ks, E, es, out, c->run, n, c->stream);
+  timing_end(c, ev);
+  return e;
+}
+
+void reset_accounting(rt_ctx* c) {
+  c->launches = 0;
+  for (int k = 0; k < 3; ++k) { c->kind_launches[k] = 0; c->kind_ms[k] = 0.0; c->kind_samples[k] = 0; }
+  c->evused.clear();
+}
+
+// Called after the stream has drained: fold the sampled event pairs.
+void collect_timing(rt_ctx* c) {
+  for (auto& u : c->evused) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->evpool[u.second], c->evpool[u.second + 1]) == cudaSuccess) {
+      c->kind_ms[u.first] += ms;
+      c->kind_samples[u.first] += 1;
+    }
+  }
+  c->evused.clear();
+}
+
+rt_status upload_inst(rt_ctx* c) {
+  CU(cudaMemcpyAsync(c->d_inst, c->h_inst.data(), c->h_inst.size() * sizeof(InstDev), cudaMemcpyHostToDevice,
+                     c->stream));
+  return RT_OK;
+}
+
+rt_status ensure_pool(rt_ctx* c, size_t n) {
+  while (c->pool.size() < n) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, c->slot_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, RT_ENOMEM, "cannot allocate checkpoint slot %zu (%zu bytes)", c->pool.size(), c->slot_bytes);
+    }
+    c->pool.push_back(p);
+  }
+  if ((int)n + 2 > c->tab_cap) {
+    if (c->d_tab) cudaFree(c->d_tab);
+    c->tab_cap = (int)n + 64;
+    CU(cudaMalloc(&c->d_tab, c->tab_cap * sizeof(void*)));
+  }
+  return RT_OK;
+}
+
+rt_status upload_tab(rt_ctx* c, const std::vector<void*>& tab) {
+  if ((int)tab.size() > c->tab_cap) {
+    if (c->d_tab) cudaFree(c->d_tab);
+    c->tab_cap = (int)tab.size() + 64;
+    CU(cudaMalloc(&c->d_tab, c->tab_cap * sizeof(void*)));
+  }
+  CU(cudaMemcpyAsync(c->d_tab, tab.data(), tab.size() * sizeof(void*), cudaMemcpyHostToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));  // tab is a stack vector of the caller
+  return RT_OK;
+}
+
+rt_status read_run(rt_ctx* c, std::vector<int>& nstep, std::vector<double>& t, std::vector<int>& status) {
+  nstep.resize(c->n_inst);
+  t.resize(c->n_inst);
+  status.resize(c->n_inst);
+  CU(cudaMemcpyAsync(nstep.data(), c->run.nstep, c->n_inst * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(t.data(), c->run.t, c->n_inst * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(status.data(), c->run.status, c->n_inst * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return RT_OK;
+}
+
+rt_status nonfinite(rt_ctx* c, const std::vector<int>& status, rt_run_stats* st) {
+  for (int i = 0; i < c->n_inst; ++i)
+    if (status[i] != 0) {
+      long long cell = -1;
+      cudaMemcpy(&cell, c->run.bad_cell + i, sizeof(long long), cudaMemcpyDeviceToHost);
+      if (st) { st->bad_instance = i; st->bad_cell = cell; }
+      return fail(c, RT_ENONFINITE, "instance %d: non-positive density/pressure or NaN at cell %lld", i, cell);
+    }
+  return RT_OK;
+}
+
+// Forward plan: kind 0 = ping-pong sA/sB; kind 1 = ping-pong plus a copy of
+// every S-th state into pool[k]; kind 2 = every state n stored in pool[n].
+struct Plan {
+  int kind = 0;
+  int S = 0;
+  int slots = 0;  // pool slots available to kind 2
+};
+
+template <class T>
+rt_status inject(rt_ctx* c, const double* d_v, void* U0) {
+  CU(cudaMemsetAsync(c->run.wmin, 0xff, 2 * c->n_inst * sizeof(unsigned long long), c->stream));
+  CU(cudaMemsetAsync(c->run.status, 0, c->n_inst * sizeof(int), c->stream));
+  CU(rt::launch_inject<T>(c->d_inst, c->d_tiles, c->ntiles, d_v, slotp<T>(U0), c->run, c->stream));
+  ++c->launches;
+  return RT_OK;
+}
+
+// Estimated step count: fixed-step instances give theirs; horizon instances
+// T / (cfl * min crossing time of the initial state).
+rt_status estimate_steps(rt_ctx* c, int* n_est) {
+  std::vector<unsigned long long> w(c->n_inst);
+  CU(cudaMemcpyAsync(w.data(), c->run.wmin, c->n_inst * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                     c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  long long best = 1;
+  for (int i = 0; i < c->n_inst; ++i) {
+    if (!c->h_inst[i].enabled) continue;
+    const rt_problem& P = c->prob[i];
+    if (P.nsteps > 0) { best = std::max<long long>(best, P.nsteps); continue; }
+    double wm;
+    std::memcpy(&wm, &w[i], sizeof(double));
+    if (!(wm > 0.0) || !(wm < kMaxFinite)) continue;
+    best = std::max<long long>(best, (long long)std::ceil(P.T / (P.cfl * wm)));
+  }
+  *n_est = (int)std::min<long long>(best, c->opt.max_steps);
+  return RT_OK;
+}
+
+bool all_done(rt_ctx* c, const std::vector<int>& nstep, const std::vector<double>& t, const std::vector<int>& status) {
+  for (int i = 0; i < c->n_inst; ++i) {
+    if (!c->h_inst[i].enabled || status[i] != 0) continue;
+    const rt_problem& P = c->prob[i];
+    if (P.nsteps > 0 ? nstep[i] < P.nsteps : t[i] < P.T) return false;
+  }
+  return true;
+}
+
+// March every instance from the injected state to its horizon. mode 0: CFL
+// control; mode 1: replay the recorded dt sequence for `replay_steps` steps.
+template <class T>
+rt_status march(rt_ctx* c, const Plan& plan, int mode, int n_est, int replay_steps, int* n_done) {
+  int n = 0;
+  int target = mode == 1 ? replay_steps : n_est;
+  const int smode = mode == 1 ? 1 : 0;
+  std::vector<int> nstep, status;
+  std::vector<double> t;
+  for (;;) {
+    for (; n < target; ++n) {
+      if (n >= c->opt.max_steps) return fail(c, RT_EINVAL, "step limit %d reached", c->opt.max_steps);
+      void *src, *dst;
+      if (plan.kind == 2) {
+        if (n + 1 >= plan.slots) return fail(c, RT_ENOMEM, "stored-state plan ran out of slots at step %d", n);
+        src = c->pool[n];
+        dst = c->pool[n + 1];
+      } else {
+        src = (n & 1) ? c->sB : c->sA;
+        dst = (n & 1) ? c->sA : c->sB;
+        if (plan.kind == 1 && n % plan.S == 0) {
+          const size_t k = n / plan.S;
+          CHK(ensure_pool(c, plan.S + k + 1));
+          CU(cudaMemcpyAsync(c->pool[plan.S + k], src, c->slot_bytes, cudaMemcpyDeviceToDevice, c->stream));
+        }
+      }
+      CU(stage<T>(c, 1, smode == 1 ? 2 : 0, slotp<T>(src), nullptr, slotp<T>(c->sU1), n));
+      CU(stage<T>(c, 2, smode, slotp<T>(c->sU1), slotp<T>(src), slotp<T>(dst), n));
+    }
+    CHK(read_run(c, nstep, t, status));
+    CHK(nonfinite(c, status, nullptr));
+    if (mode == 1 || all_done(c, nstep, t, status)) break;
+    target = n + std::max(16, n / 16);
+  }
+  *n_done = n;
+  c->h_nstep = nstep;
+  int mx = 0;
+  for (int i = 0; i < c->n_inst; ++i) mx = std::max(mx, nstep[i]);
+  c->last_steps = mx;
+  c->last_kind = plan.kind == 2 ? 2 : 0;
+  c->have_run = true;
+  return RT_OK;
+}
+
+template <class T>
+rt_status objective(rt_ctx* c, const Plan& plan, bool cotangent, double* ek_out) {
+  std::vector<void*> tab;
+  int mod;
+  if (plan.kind == 2) {
+    tab.assign(c->pool.begin(), c->pool.begin() + plan.slots);
+    mod = 0;
+  } else {
+    tab = {c->sA, c->sB};
+    mod = 2;
+  }
+  CHK(upload_tab(c, tab));
+  CU(rt::launch_objective<T>(c->d_inst, c->d_tiles, c->ntiles, reinterpret_cast<T* const*>(c->d_tab), mod,
+                             c->run.nstep, ek_out, cotangent ? slotp<T>(c->lA) : nullptr,
+                             cotangent ? slotp<T>(c->lB) : nullptr, c->d_partials, c->stream));
+  CU(rt::launch_finalize(c->d_inst, c->n_inst, c->d_partials, 2, 1, c->d_sums, c->stream));
+  c->launches += 2;
+  return RT_OK;
+}
+
+rt_status copy_in(rt_ctx* c, const double* v, int flags, double* dst) {
+  const size_t bytes = c->total_v * sizeof(double);
+  CU(cudaMemcpyAsync(dst, v, bytes, (flags & RT_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     c->stream));
+  return RT_OK;
+}
+
+rt_status copy_out(rt_ctx* c, const double* src, int flags, double* out) {
+  const size_t bytes = c->total_v * sizeof(double);
+  CU(cudaMemcpyAsync(out, src, bytes, (flags & RT_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     c->stream));
+  return RT_OK;
+}
+
+rt_status read_J(rt_ctx* c, double* J_out, double* J_ke_out) {
+  std::vector<double> s(2 * c->n_inst);
+  CU(cudaMemcpyAsync(s.data(), c->d_sums, s.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < c->n_inst; ++i) {
+    if (J_out) J_out[i] = c->prob[i].objective == RT_OBJ_EK_ANOMALY_L2 ? s[2 * i + 1] : s[2 * i];
+    if (J_ke_out) J_ke_out[i] = s[2 * i];
+  }
+  return RT_OK;
+}
+
+void fill_stats(rt_ctx* c, rt_run_stats* st, float ms, int segments) {
+  if (!st) return;
+  st->steps = c->last_steps;
+  st->segments = segments;
+  st->bad_instance = -1;
+  st->bad_cell = -1;
+  double cu = 0.0;
+  for (int i = 0; i < c->n_inst; ++i) cu += (double)c->prob[i].nx * c->prob[i].ny * c->h_nstep[i];
+  st->cell_updates = cu;
+  st->ms = ms;
+  st->launches = c->launches;
+}
+
+template <class T>
+rt_status forward_impl(rt_ctx* c, const double* d_v, int flags, double* J_out, double* J_ke_out, int* steps) {
+  const bool replay = (flags & RT_REPLAY_DT) != 0;
+  if (replay && !c->have_run) return fail(c, RT_ESTATE, "RT_REPLAY_DT needs a previous run");
+  const int replay_steps = c->last_steps;
+  Plan plan;
+  CHK(inject<T>(c, d_v, c->sA));
+  int n_est = replay_steps;
+  if (!replay) CHK(estimate_steps(c, &n_est));
+  int n_done = 0;
+  CHK(march<T>(c, plan, replay ? 1 : 0, n_est, replay_steps, &n_done));
+  CHK(objective<T>(c, plan, false, nullptr));
+  CHK(read_J(c, J_out, J_ke_out));
+  if (steps) *steps = n_done;
+  return RT_OK;
+}
+
+// Gradient: forward with checkpoints, terminal cotangent, then for each step
+// in reverse: recompute U1 = stage1(U^n), lam1 = (dStage2/dU1)^T lam^{n+1},
+// lam^n = lam^{n+1}/2 + lam1 + (dL/dU^n)^T lam1 dt (SSP-RK2 transposed).
+template <class T>
+rt_status gradient_impl(rt_ctx* c, const double* d_v, double* J_out, double* d_g, int* segments_out) {
+  CHK(inject<T>(c, d_v, c->sA));
+  int n_est = 1;
+  CHK(estimate_steps(c, &n_est));
+  Plan plan;
+  const double need_all = ((double)n_est * 1.1 + 16.0) * (double)c->slot_bytes;
+  int mode = c->opt.ckpt;
+  if (mode == RT_CKPT_AUTO) mode = need_all <= c->mem_cap ? RT_CKPT_STORE_ALL : RT_CKPT_SQRT;
+  if (mode == RT_CKPT_STORE_ALL) {
+    plan.kind = 2;
+    plan.slots = (int)(n_est * 1.1 + 16);
+    CHK(ensure_pool(c, plan.slots));
+    CHK(inject<T>(c, d_v, c->pool[0]));
+  } else {
+    plan.kind = 1;
+    plan.S = std::max(1, (int)std::ceil(std::sqrt((double)n_est)));
+    CHK(ensure_pool(c, plan.S + n_est / plan.S + 2));
+  }
+  int n_done = 0;
+  rt_status s = march<T>(c, plan, 0, n_est, 0, &n_done);
+  if (s == RT_ENOMEM && plan.kind == 2) {  // the run outgrew the stored-state plan: redo it checkpointed
+    plan = Plan();
+    plan.kind = 1;
+    plan.S = std::max(1, (int)std::ceil(std::sqrt((double)n_est * 1.5)));
+    CHK(ensure_pool(c, plan.S + 2 * n_est / plan.S + 2));
+    CHK(inject<T>(c, d_v, c->sA));
+    s = march<T>(c, plan, 0, n_est, 0, &n_done);
+  }
+  if (s != RT_OK) return s;
+  CHK(objective<T>(c, plan, true, nullptr));
+  CHK(read_J(c, J_out, nullptr));
+  const int N = c->last_steps;
+  T* U1 = slotp<T>(c->sU1);
+  T* lam[2] = {slotp<T>(c->lA), slotp<T>(c->lB)};
+  T* l1 = slotp<T>(c->l1);
+  auto reverse_step = [&](int n, T* Un) -> rt_status {
+    CU(stage<T>(c, 1, 2, Un, nullptr, U1, n));
+    CU(adjoint<T>(c, U1, lam[(n + 1) & 1], 0.5, nullptr, 0.0, l1, n));
+    CU(adjoint<T>(c, Un, l1, 1.0, lam[(n + 1) & 1], 0.5, lam[n & 1], n));
+    return RT_OK;
+  };
+  int segments = 1;
+  if (plan.kind == 2) {
+    for (int n = N - 1; n >= 0; --n) CHK(reverse_step(n, slotp<T>(c->pool[n])));
+  } else {
+    const int S = plan.S;
+    segments = (N + S - 1) / S;
+    for (int k = segments - 1; k >= 0; --k) {
+      const int n0 = k * S, n1 = std::min(N, n0 + S);
+      auto seg = [&](int n) -> T* { return n == n0 ? slotp<T>(c->pool[S + k]) : slotp<T>(c->pool[n - n0]); };
+      for (int n = n0; n < n1 - 1; ++n) {
+        CU(stage<T>(c, 1, 2, seg(n), nullptr, U1, n));
+        CU(stage<T>(c, 2, 2, U1, seg(n), seg(n + 1), n));
+      }
+      for (int n = n1 - 1; n >= n0; --n) CHK(reverse_step(n, seg(n)));
+    }
+  }
+  CU(rt::launch_grad<T>(c->d_inst, c->d_tiles, c->ntiles, lam[0], d_v, d_g, c->stream));
+  ++c->launches;
+  if (segments_out) *segments_out = segments;
+  return RT_OK;
+}
+
+rt_status field_sums(rt_ctx* c, int mode, const double* a, const double* b, std::vector<double>& out) {
+  CU(rt::launch_field_reduce(mode, c->d_inst, c->d_tiles, c->ntiles, a, b, c->d_partials, c->stream));
+  CU(rt::launch_finalize(c->d_inst, c->n_inst, c->d_partials, 1, mode == 0 ? 1 : 0, c->d_sums, c->stream));
+  out.resize(c->n_inst);
+  CU(cudaMemcpyAsync(out.data(), c->d_sums, c->n_inst * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return RT_OK;
+}
+
+// out = alpha_i a + beta_i b (b may be null)
+rt_status axpby(rt_ctx* c, double* out, const std::vector<double>& alpha, const double* a,
+                const std::vector<double>* beta, const double* b) {
+  std::vector<double> sc(2 * c->n_inst, 0.0);
+  for (int i = 0; i < c->n_inst; ++i) {
+    sc[i] = alpha[i];
+    if (beta) sc[c->n_inst + i] = (*beta)[i];
+  }
+  CU(cudaMemcpyAsync(c->d_scal, sc.data(), sc.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CU(rt::launch_field_axpby(c->d_inst, c->d_tiles, c->ntiles, out, c->d_scal, a, beta ? c->d_scal + c->n_inst : nullptr,
+                            b, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return RT_OK;
+}
+
+rt_status ensure_fields(rt_ctx* c, bool cnop) {
+  const size_t bytes = c->total_v * sizeof(double);
+  if (!c->d_v) CU(cudaMalloc(&c->d_v, bytes));
+  if (!c->d_g) CU(cudaMalloc(&c->d_g, bytes));
+  if (cnop) {
+    if (!c->d_w1) CU(cudaMalloc(&c->d_w1, bytes));
+    if (!c->d_w2) CU(cudaMalloc(&c->d_w2, bytes));
+    if (!c->d_w3) CU(cudaMalloc(&c->d_w3, bytes));
+    if (!c->d_w4) CU(cudaMalloc(&c->d_w4, bytes));
+  }
+  return RT_OK;
+}
+
+rt_status set_enabled(rt_ctx* c, const std::vector<char>& en) {
+  for (int i = 0; i < c->n_inst; ++i) c->h_inst[i].enabled = en[i] ? 1 : 0;
+  return upload_inst(c);
+}
+
+// Runs the baseline (v0 = 0) forward of every instance and keeps its final
+// e_k as the reference field of the anomaly objective (Eq. objective).
+template <class T>
+rt_status baseline(rt_ctx* c) {
+  CU(cudaMemsetAsync(c->d_v, 0, c->total_v * sizeof(double), c->stream));
+  CU(cudaMalloc(&c->d_ek0, c->total_cells * sizeof(double)));
+  Plan plan;
+  CHK(inject<T>(c, c->d_v, c->sA));
+  int n_est = 1;
+  CHK(estimate_steps(c, &n_est));
+  int n_done = 0;
+  CHK(march<T>(c, plan, 0, n_est, 0, &n_done));
+  CHK(objective<T>(c, plan, false, c->d_ek0));
+  CU(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < c->n_inst; ++i)
+    c->h_inst[i].ek0 = c->prob[i].objective == RT_OBJ_EK_ANOMALY_L2 ? c->d_ek0 + c->cell_off[i] : nullptr;
+  CHK(upload_inst(c));
+  c->have_run = false;
+  return RT_OK;
+}
+
+struct Timer {
+  rt_ctx* c;
+  explicit Timer(rt_ctx* cc) : c(cc) { cudaEventRecord(c->ev0, c->stream); }
+  float stop() {
+    cudaEventRecord(c->ev1, c->stream);
+    cudaEventSynchronize(c->ev1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    return ms;
+  }
+};
+
+template <class T>
+rt_status cnop_impl(rt_ctx* c, const cnop_params* prm, double* v_inout, int flags, double* J_out, cnop_result* res) {
+  const int N = c->n_inst;
+  CHK(ensure_fields(c, true));
+  double* v = c->d_v;
+  double* g = c->d_g;
+  double* vt = c->d_w1;
+  double* gt = c->d_w2;
+  double* d = c->d_w3;
+  double* tmp = c->d_w4;
+  CHK(copy_in(c, v_inout, flags, v));
+  std::vector<double> eps(prm->eps, prm->eps + N), C, dots, ones(N, 1.0), mones(N, -1.0);
+  if (prm->h_loc > 0.0) CU(rt::launch_localise(c->d_inst, c->d_tiles, c->ntiles, prm->h_loc, v, c->stream));
+  CHK(field_sums(c, 0, v, nullptr, C));
+  std::vector<double> sc(N);
+  for (int i = 0; i < N; ++i) sc[i] = std::sqrt(eps[i] / C[i]);
+  CHK(axpby(c, v, sc, v, nullptr, nullptr));
+  std::vector<char> en(N, 1), stuck(N, 0);
+  CHK(set_enabled(c, en));
+  std::vector<double> J(N), Jt(N), Jn(N);
+  int fevals = 0, gevals = 0, iters = 0;
+  CHK(gradient_impl<T>(c, v, J.data(), g, nullptr));
+  ++gevals;
+  std::vector<double> vv, gg;
+  CHK(field_sums(c, 1, v, v, vv));
+  CHK(field_sums(c, 1, g, g, gg));
+  const double amin = prm->alpha_min > 0 ? prm->alpha_min : 1e-30;
+  const double amax = prm->alpha_max > 0 ? prm->alpha_max : 1e30;
+  std::vector<double> alpha(N);
+  for (int i = 0; i < N; ++i)
+    alpha[i] = std::min(std::max(std::sqrt(vv[i]) / std::max(std::sqrt(gg[i]), 1e-300), amin), amax);
+  std::vector<std::vector<double>> hist(N);
+  for (int i = 0; i < N; ++i) hist[i].push_back(J[i]);
+  const int M = prm->gll_memory > 0 ? prm->gll_memory : 10;
+  const int maxbt = prm->max_backtracks > 0 ? prm->max_backtracks : 30;
+  bool any_stuck = false;
+  for (int k = 0; k < prm->max_iter; ++k) {
+    // d = P(v + alpha g) - v
+    CHK(axpby(c, vt, ones, v, &alpha, g));
+    CHK(field_sums(c, 0, vt, nullptr, C));
+    for (int i = 0; i < N; ++i) sc[i] = C[i] <= eps[i] ? 1.0 : std::sqrt(eps[i] / C[i]);
+    CHK(axpby(c, vt, sc, vt, nullptr, nullptr));
+    CHK(axpby(c, d, ones, vt, &mones, v));
+    std::vector<double> gd;
+    CHK(field_sums(c, 1, g, d, gd));
+    std::vector<double> Jref(N), lam(N, 1.0);
+    for (int i = 0; i < N; ++i) {
+      const size_t h0 = hist[i].size() > (size_t)M ? hist[i].size() - M : 0;
+      Jref[i] = *std::max_element(hist[i].begin() + h0, hist[i].end());
+    }
+    std::vector<char> acc(N, 0);
+    for (int i = 0; i < N; ++i) acc[i] = stuck[i];
+    for (int bt = 0; bt < maxbt; ++bt) {
+      CHK(axpby(c, vt, ones, v, &lam, d));
+      std::vector<char> e(N);
+      for (int i = 0; i < N; ++i) e[i] = !acc[i];
+      CHK(set_enabled(c, e));
+      int steps = 0;
+      CHK(forward_impl<T>(c, vt, RT_DEVICE_PTRS, Jt.data(), nullptr, &steps));
+      ++fevals;
+      bool all = true;
+      for (int i = 0; i < N; ++i) {
+        if (acc[i]) continue;
+        if (Jt[i] >= Jref[i] + prm->armijo_c * lam[i] * gd[i]) acc[i] = 1;
+        else { lam[i] *= 0.5; all = false; }
+      }
+      if (all) break;
+    }
+    for (int i = 0; i < N; ++i)
+      if (!acc[i]) { stuck[i] = 1; any_stuck = true; }
+    for (int i = 0; i < N; ++i)
+      if (stuck[i]) lam[i] = 0.0;
+    CHK(axpby(c, vt, ones, v, &lam, d));
+    std::vector<char> e(N);
+    bool any_live = false;
+    for (int i = 0; i < N; ++i) { e[i] = !stuck[i]; any_live = any_live || e[i]; }
+    if (!any_live) break;
+    CHK(set_enabled(c, e));
+    CHK(gradient_impl<T>(c, vt, Jn.data(), gt, nullptr));
+    ++gevals;
+    // s = vt - v; y' = -(gt - g); alpha = <s,s>/<s,y'>
+    CHK(axpby(c, tmp, ones, vt, &mones, v));
+    std::vector<double> ss, sg, sgt;
+    CHK(field_sums(c, 1, tmp, tmp, ss));
+    CHK(field_sums(c, 1, tmp, g, sg));
+    CHK(field_sums(c, 1, tmp, gt, sgt));
+    for (int i = 0; i < N; ++i) {
+      if (stuck[i]) continue;
+      const double sy = sg[i] - sgt[i];
+      alpha[i] = sy <= 0.0 ? amax : std::min(std::max(ss[i] / sy, amin), amax);
+      J[i] = Jn[i];
+      hist[i].push_back(J[i]);
+    }
+    std::swap(c->d_v, c->d_w1);  // v <- vt
+    std::swap(c->d_g, c->d_w2);  // g <- gt
+    v = c->d_v;
+    g = c->d_g;
+    vt = c->d_w1;
+    gt = c->d_w2;
+    ++iters;
+  }
+  std::fill(en.begin(), en.end(), 1);
+  CHK(set_enabled(c, en));
+  CHK(copy_out(c, v, flags, v_inout));
+  CU(cudaStreamSynchronize(c->stream));
+  if (J_out)
+    for (int i = 0; i < N; ++i) J_out[i] = J[i];
+  if (res) {
+    res->iterations = iters;
+    res->forward_evals = fevals;
+    res->gradient_evals = gevals;
+  }
+  if (any_stuck) return fail(c, RT_ENOTCONVERGED, "an instance found no acceptable step");
+  return RT_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options* opt, void* cuda_stream,
+                  rt_ctx** out) {
+  if (!out) return RT_EINVAL;
+  *out = nullptr;
+  if (!problems || n_instances <= 0) return RT_EINVAL;
+  rt_ctx* c = new (std::nothrow) rt_ctx();
+  if (!c) return RT_ENOMEM;
+  auto bail = [&](rt_status s) {
+    // keep the message readable for a caller that only sees the status
+    fprintf(stderr, "rt_init: %s\n", c->err.c_str());
+    rt_destroy(c);
+    return s;
+  };
+  c->n_inst = n_instances;
+  if (opt) c->opt = *opt;
+  if (c->opt.max_steps <= 0) c->opt.max_steps = 200000;
+  if (c->opt.precision != RT_FP64 && c->opt.precision != RT_FP32_STATE) {
+    fail(c, RT_EINVAL, "precision");
+    return bail(RT_EINVAL);
+  }
+  c->esz = c->opt.precision == RT_FP64 ? sizeof(double) : sizeof(float);
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->prob.assign(problems, problems + n_instances);
+  for (int i = 0; i < n_instances; ++i) {
+    rt_status s = validate(c, c->prob[i], i);
+    if (s != RT_OK) return bail(s);
+  }
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    fail(c, RT_ECUDA, "no CUDA device");
+    return bail(RT_ECUDA);
+  }
+  // instance layout, tiles, base state
+  c->h_inst.resize(n_instances);
+  c->cell_off.resize(n_instances);
+  c->v_off.resize(n_instances);
+  long long cells = 0, voff = 0, rows = 0;
+  for (int i = 0; i < n_instances; ++i) {
+    const rt_problem& P = c->prob[i];
+    c->cell_off[i] = cells;
+    c->v_off[i] = voff;
+    cells += (long long)P.nx * P.ny;
+    voff += (long long)P.perturb_ncomp * P.nx * P.ny;
+    rows += P.ny;
+  }
+  c->total_cells = cells;
+  c->total_v = (size_t)voff;
+  c->slot_bytes = (size_t)(4 * cells) * c->esz;
+  std::vector<double> base(2 * rows);
+  long long roff = 0;
+  for (int i = 0; i < n_instances; ++i) {
+    const rt_problem& P = c->prob[i];
+    std::vector<double> r, p;
+    base_state(P, r, p);
+    std::copy(r.begin(), r.end(), base.begin() + roff);
+    std::copy(p.begin(), p.end(), base.begin() + rows + roff);
+    InstDev& I = c->h_inst[i];
+    I.nx = P.nx;
+    I.ny = P.ny;
+    I.bc_y = P.bc_y;
+    I.limiter = P.limiter;
+    I.nsteps = P.nsteps;
+    I.ncomp = P.perturb_ncomp;
+    I.objective = P.objective;
+    I.enabled = 1;
+    I.cell_off = c->cell_off[i];
+    I.v_off = c->v_off[i];
+    I.dx = (P.x1 - P.x0) / P.nx;
+    I.dy = (P.y1 - P.y0) / P.ny;
+    I.dA = I.dx * I.dy;
+    I.y0 = P.y0;
+    I.y_int = P.y_int;
+    I.gamma = P.gamma;
+    I.gm1 = P.gamma - 1.0;
+    I.g_y = P.g_y;
+    I.cfl = P.cfl;
+    I.T = P.T;
+    I.tile_begin = (int)c->h_tiles.size();
+    for (int y0 = 0; y0 < P.ny; y0 += rt::TILE_Y)
+      for (int x0 = 0; x0 < P.nx; x0 += rt::TILE_X) c->h_tiles.push_back(make_int4(i, x0, y0, 0));
+    I.tile_end = (int)c->h_tiles.size();
+    I.ek0 = nullptr;
+    roff += P.ny;
+  }
+  c->ntiles = (int)c->h_tiles.size();
+  const int N = n_instances;
+#define INIT_CU(call)                                                                            \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) {                                                                     \
+      fail(c, e_ == cudaErrorMemoryAllocation ? RT_ENOMEM : RT_ECUDA, "%s: %s", #call,           \
+           cudaGetErrorString(e_));                                                              \
+      return bail(e_ == cudaErrorMemoryAllocation ? RT_ENOMEM : RT_ECUDA);                       \
+    }                                                                                            \
+  } while (0)
+  INIT_CU(cudaMalloc(&c->d_base, base.size() * sizeof(double)));
+  INIT_CU(cudaMemcpy(c->d_base, base.data(), base.size() * sizeof(double), cudaMemcpyHostToDevice));
+  roff = 0;
+  for (int i = 0; i < N; ++i) {
+    c->h_inst[i].rho0 = c->d_base + roff;
+    c->h_inst[i].p0 = c->d_base + rows + roff;
+    roff += c->prob[i].ny;
+  }
+  INIT_CU(cudaMalloc(&c->d_inst, N * sizeof(InstDev)));
+  INIT_CU(cudaMemcpy(c->d_inst, c->h_inst.data(), N * sizeof(InstDev), cudaMemcpyHostToDevice));
+  INIT_CU(cudaMalloc(&c->d_tiles, c->ntiles * sizeof(int4)));
+  INIT_CU(cudaMemcpy(c->d_tiles, c->h_tiles.data(), c->ntiles * sizeof(int4), cudaMemcpyHostToDevice));
+  void** bufs[6] = {&c->sA, &c->sB, &c->sU1, &c->lA, &c->lB, &c->l1};
+  for (void** b : bufs) INIT_CU(cudaMalloc(b, c->slot_bytes));
+  c->run.n_inst = N;
+  c->run.max_steps = c->opt.max_steps;
+  INIT_CU(cudaMalloc(&c->run.dtrec, (size_t)N * c->opt.max_steps * sizeof(double)));
+  INIT_CU(cudaMalloc(&c->run.t, N * sizeof(double)));
+  INIT_CU(cudaMalloc(&c->run.nstep, N * sizeof(int)));
+  INIT_CU(cudaMalloc(&c->run.wmin, 2 * N * sizeof(unsigned long long)));
+  INIT_CU(cudaMalloc(&c->run.status, N * sizeof(int)));
+  INIT_CU(cudaMalloc(&c->run.bad_cell, N * sizeof(long long)));
+  INIT_CU(cudaMalloc(&c->d_partials, (size_t)c->ntiles * 2 * sizeof(double)));
+  INIT_CU(cudaMalloc(&c->d_sums, (size_t)N * 2 * sizeof(double)));
+  INIT_CU(cudaMalloc(&c->d_scal, (size_t)N * 4 * sizeof(double)));
+  INIT_CU(cudaMalloc(&c->d_ek, c->total_cells * sizeof(double)));
+  INIT_CU(cudaEventCreate(&c->ev0));
+  INIT_CU(cudaEventCreate(&c->ev1));
+  INIT_CU(c->esz == 8 ? rt::configure_kernels<double>() : rt::configure_kernels<float>());
+  size_t freeb = 0, totb = 0;
+  INIT_CU(cudaMemGetInfo(&freeb, &totb));
+  c->mem_cap = c->opt.ckpt_hbm_cap_bytes > 0 ? c->opt.ckpt_hbm_cap_bytes : 0.6 * (double)freeb;
+  bool need_base = false;
+  for (int i = 0; i < N; ++i) need_base = need_base || c->prob[i].objective == RT_OBJ_EK_ANOMALY_L2;
+  if (need_base) {
+    rt_status s = ensure_fields(c, false);
+    if (s == RT_OK) s = c->esz == 8 ? baseline<double>(c) : baseline<float>(c);
+    if (s != RT_OK) return bail(s);
+  }
+#undef INIT_CU
+  *out = c;
+  return RT_OK;
+}
+
+void rt_destroy(rt_ctx* c) {
+  if (!c) return;
+  void* ptrs[] = {c->d_inst, c->d_tiles, c->d_base, c->d_ek0, c->d_ek, c->sA, c->sB, c->sU1, c->lA, c->lB,
+                  c->l1, c->d_tab, c->run.dtrec, c->run.t, c->run.nstep, c->run.wmin, c->run.status,
+                  c->run.bad_cell, c->d_partials, c->d_sums, c->d_scal, c->d_v, c->d_g, c->d_w1, c->d_w2,
+                  c->d_w3, c->d_w4};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (void* p : c->pool) cudaFree(p);
+  for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  delete c;
+}
+
+const char* rt_last_error(const rt_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int rt_num_instances(const rt_ctx* c) { return c ? c->n_inst : 0; }
+size_t rt_field_offset(const rt_ctx* c, int i) { return (c && i >= 0 && i < c->n_inst) ? c->v_off[i] : 0; }
+size_t rt_field_size(const rt_ctx* c, int i) {
+  if (!c || i < 0 || i >= c->n_inst) return 0;
+  return (size_t)c->prob[i].perturb_ncomp * c->prob[i].nx * c->prob[i].ny;
+}
+size_t rt_field_total(const rt_ctx* c) { return c ? c->total_v : 0; }
+
+rt_status rt_forward(rt_ctx* c, const double* v0, int flags, double* J_out, double* J_ke_out, rt_run_stats* st) {
+  if (!c || !v0 || !J_out) return fail(c, RT_EINVAL, "null argument");
+  c->err.clear();
+  CHK(ensure_fields(c, false));
+  reset_accounting(c);
+  Timer tm(c);
+  CHK(copy_in(c, v0, flags, c->d_v));
+  int steps = 0;
+  CHK(c->esz == 8 ? forward_impl<double>(c, c->d_v, flags, J_out, J_ke_out, &steps)
+                  : forward_impl<float>(c, c->d_v, flags, J_out, J_ke_out, &steps));
+  const float ms = tm.stop();
+  collect_timing(c);
+  fill_stats(c, st, ms, 0);
+  return RT_OK;
+}
+
+rt_status rt_gradient(rt_ctx* c, const double* v0, int flags, double* J_out, double* grad_out, rt_run_stats* st) {
+  if (!c || !v0 || !J_out || !grad_out) return fail(c, RT_EINVAL, "null argument");
+  if (flags & RT_REPLAY_DT) return fail(c, RT_EINVAL, "rt_gradient always freezes its own dt sequence");
+  c->err.clear();
+  CHK(ensure_fields(c, false));
+  reset_accounting(c);
+  Timer tm(c);
+  CHK(copy_in(c, v0, flags, c->d_v));
+  int segments = 0;
+  CHK(c->esz == 8 ? gradient_impl<double>(c, c->d_v, J_out, c->d_g, &segments)
+                  : gradient_impl<float>(c, c->d_v, J_out, c->d_g, &segments));
+  CHK(copy_out(c, c->d_g, flags, grad_out));
+  const float ms = tm.stop();
+  collect_timing(c);
+  fill_stats(c, st, ms, segments);
+  return RT_OK;
+}
+
+rt_status rt_constraint(rt_ctx* c, const double* v, int flags, double* C_out) {
+  if (!c || !v || !C_out) return fail(c, RT_EINVAL, "null argument");
+  CHK(ensure_fields(c, false));
+  CHK(copy_in(c, v, flags, c->d_v));
+  std::vector<double> C;
+  CHK(field_sums(c, 0, c->d_v, nullptr, C));
+  std::copy(C.begin(), C.end(), C_out);
+  return RT_OK;
+}
+
+rt_status rt_project(rt_ctx* c, double* v, int flags, const double* eps, int to_budget) {
+  if (!c || !v || !eps) return fail(c, RT_EINVAL, "null argument");
+  CHK(ensure_fields(c, false));
+  CHK(copy_in(c, v, flags, c->d_v));
+  std::vector<double> C;
+  CHK(field_sums(c, 0, c->d_v, nullptr, C));
+  std::vector<double> sc(c->n_inst);
+  for (int i = 0; i < c->n_inst; ++i) {
+    if (!(C[i] > 0.0)) return fail(c, RT_EINVAL, "instance %d: C(v) = 0, cannot scale", i);
+    sc[i] = (!to_budget && C[i] <= eps[i]) ? 1.0 : std::sqrt(eps[i] / C[i]);
+  }
+  CHK(axpby(c, c->d_v, sc, c->d_v, nullptr, nullptr));
+  CHK(copy_out(c, c->d_v, flags, v));
+  CU(cudaStreamSynchronize(c->stream));
+  return RT_OK;
+}
+
+rt_status rt_get_state(rt_ctx* c, int inst, double* out) {
+  if (!c || !out || inst < 0 || inst >= c->n_inst) return fail(c, RT_EINVAL, "bad argument");
+  if (!c->have_run) return fail(c, RT_ESTATE, "no run yet");
+  const rt_problem& P = c->prob[inst];
+  const size_t n = (size_t)4 * P.nx * P.ny;
+  const int s = c->h_nstep[inst];
+  const void* slot = c->last_kind == 2 ? c->pool[s] : ((s & 1) ? c->sB : c->sA);
+  const char* src = static_cast<const char*>(slot) + (size_t)4 * c->cell_off[inst] * c->esz;
+  if (c->esz == 8) {
+    CU(cudaMemcpyAsync(out, src, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+  } else {
+    std::vector<float> f(n);
+    CU(cudaMemcpyAsync(f.data(), src, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    for (size_t k = 0; k < n; ++k) out[k] = f[k];
+  }
+  return RT_OK;
+}
+
+rt_status rt_get_dt(rt_ctx* c, int inst, double* out, int max_n, int* n_out) {
+  if (!c || inst < 0 || inst >= c->n_inst) return fail(c, RT_EINVAL, "bad argument");
+  if (!c->have_run) return fail(c, RT_ESTATE, "no run yet");
+  const int n = c->h_nstep[inst];
+  if (n_out) *n_out = n;
+  const int k = std::min(n, max_n);
+  if (out && k > 0) {
+    CU(cudaMemcpyAsync(out, c->run.dtrec + (size_t)inst * c->opt.max_steps, k * sizeof(double),
+                       cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+  }
+  return RT_OK;
+}
+
+rt_status rt_set_kernel_timing(rt_ctx* c, int every) {
+  if (!c || every < 0) return fail(c, RT_EINVAL, "bad argument");
+  c->time_every = every;
+  if (every > 0 && c->evpool.empty()) {
+    c->evpool.resize(2 * 8192);
+    for (auto& e : c->evpool) CU(cudaEventCreate(&e));
+  }
+  return RT_OK;
+}
+
+rt_status rt_kernel_times(rt_ctx* c, double* mean_ms, long long* samples, long long* launches) {
+  if (!c) return RT_EINVAL;
+  for (int k = 0; k < 3; ++k) {
+    if (mean_ms) mean_ms[k] = c->kind_samples[k] ? c->kind_ms[k] / c->kind_samples[k] : 0.0;
+    if (samples) samples[k] = c->kind_samples[k];
+    if (launches) launches[k] = c->kind_launches[k];
+  }
+  return RT_OK;
+}
+
+rt_status cnop_solve(rt_ctx* c, const cnop_params* prm, double* v_inout, int flags, double* J_out,
+                     cnop_result* res) {
+  if (!c || !prm || !v_inout || !prm->eps) return fail(c, RT_EINVAL, "null argument");
+  if (prm->max_iter < 0) return fail(c, RT_EINVAL, "max_iter < 0");
+  c->err.clear();
+  Timer tm(c);
+  rt_status s = c->esz == 8 ? cnop_impl<double>(c, prm, v_inout, flags, J_out, res)
+                            : cnop_impl<float>(c, prm, v_inout, flags, J_out, res);
+  const float ms = tm.stop();
+  if (res) res->ms = ms;
+  return s;
+}
+
+}  // extern "C"

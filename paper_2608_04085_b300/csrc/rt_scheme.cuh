@@ -1,0 +1,265 @@
+// rt_scheme.cuh -- per-face arithmetic of the finite-volume scheme and of its
+// adjoint, templated on the state type T (float or double).
+//
+// Scheme (Sec. 2.1 Eqs. mass/momentum/energy, Eq. total_energy; Sec. 2.3
+// Godunov-type scheme with HLLC fluxes): PLM reconstruction of the primitive
+// variables (rho, u_x, u_y, p) with a minmod / MC / unlimited slope, HLLC
+// Riemann flux with Davis wave-speed estimates.
+//
+// Evaluation order. Every expression is written in the order in which it is
+// meant to round: the FP64 translation unit is compiled with -fmad=false, so
+// each product and sum rounds separately and the FP64 path reproduces an
+// independent FP64 CPU implementation of the same expressions bit for bit.
+// Branch conventions (all comparisons on values): minmod picks the backward
+// difference on a tie and returns 0 unless both differences have the same
+// strict sign; S_L = min(u_L - c_L, u_R - c_R) and S_R = max(u_L + c_L,
+// u_R + c_R) pick the left argument on a tie; the HLLC branch is F_L if
+// 0 <= S_L, F*_L if S_L < 0 <= S*, F*_R if S* < 0 <= S_R, F_R otherwise.
+// The adjoint differentiates the branch the forward took.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace rt {
+
+enum { LIM_MINMOD = 0, LIM_MC = 1, LIM_NONE = 2 };
+
+// Conserved (rho, m_x, m_y, E) -> primitive (rho, u_x, u_y, p).
+template <class T>
+__device__ __forceinline__ void cons_to_prim(T r, T mx, T my, T E, T gm1, T W[4]) {
+  W[0] = r;
+  W[1] = mx / r;
+  W[2] = my / r;
+  W[3] = gm1 * (E - T(0.5) * (mx * W[1] + my * W[2]));
+}
+
+// Limited PLM slope of q0 from (qm, q0, qp).
+template <class T>
+__device__ __forceinline__ T limited_slope(T qm, T q0, T qp, int lim) {
+  const T dm = q0 - qm, dp = qp - q0;
+  if (lim == LIM_NONE) return T(0.5) * (dm + dp);
+  if (lim == LIM_MINMOD) {
+    if (dm > T(0) && dp > T(0)) return dm <= dp ? dm : dp;
+    if (dm < T(0) && dp < T(0)) return dm >= dp ? dm : dp;
+    return T(0);
+  }
+  const T a = T(2) * dm, c = T(0.5) * (dm + dp), b = T(2) * dp;
+  if (dm > T(0) && dp > T(0)) { const T s = a <= c ? a : c; return s <= b ? s : b; }
+  if (dm < T(0) && dp < T(0)) { const T s = a >= c ? a : c; return s >= b ? s : b; }
+  return T(0);
+}
+
+// The same slope, also returning d slope / d (qm, q0, qp) for the branch taken.
+template <class T>
+__device__ __forceinline__ T limited_slope_d(T qm, T q0, T qp, int lim, T& cm, T& c0, T& cp) {
+  const T dm = q0 - qm, dp = qp - q0;
+  if (lim == LIM_NONE) { cm = T(-0.5); c0 = T(0); cp = T(0.5); return T(0.5) * (dm + dp); }
+  if (lim == LIM_MINMOD) {
+    if ((dm > T(0) && dp > T(0) && dm <= dp) || (dm < T(0) && dp < T(0) && dm >= dp)) {
+      cm = T(-1); c0 = T(1); cp = T(0); return dm;
+    }
+    if ((dm > T(0) && dp > T(0)) || (dm < T(0) && dp < T(0))) { cm = T(0); c0 = T(-1); cp = T(1); return dp; }
+    cm = c0 = cp = T(0);
+    return T(0);
+  }
+  const T a = T(2) * dm, c = T(0.5) * (dm + dp), b = T(2) * dp;
+  int pick = -1;  // 0: a, 1: c, 2: b
+  if (dm > T(0) && dp > T(0)) { const bool ac = a <= c; const T s = ac ? a : c; pick = (s <= b) ? (ac ? 0 : 1) : 2; }
+  else if (dm < T(0) && dp < T(0)) { const bool ac = a >= c; const T s = ac ? a : c; pick = (s >= b) ? (ac ? 0 : 1) : 2; }
+  if (pick == 0) { cm = T(-2); c0 = T(2); cp = T(0); return a; }
+  if (pick == 1) { cm = T(-0.5); c0 = T(0); cp = T(0.5); return c; }
+  if (pick == 2) { cm = T(0); c0 = T(-2); cp = T(2); return b; }
+  cm = c0 = cp = T(0);
+  return T(0);
+}
+
+// HLLC flux in the frame (normal, tangential): F = (mass, normal momentum,
+// tangential momentum, energy).
+template <class T>
+__device__ __forceinline__ void hllc(T rL, T uL, T vL, T pL, T rR, T uR, T vR, T pR,
+                                     T gamma, T gm1, T F[4]) {
+  const T cL = sqrt(gamma * pL / rL);
+  const T cR = sqrt(gamma * pR / rR);
+  const T aL = uL - cL, aR = uR - cR;
+  const T SL = aL <= aR ? aL : aR;
+  const T bL = uL + cL, bR = uR + cR;
+  const T SR = bL >= bR ? bL : bR;
+  const T EL = pL / gm1 + T(0.5) * rL * (uL * uL + vL * vL);
+  const T ER = pR / gm1 + T(0.5) * rR * (uR * uR + vR * vR);
+  const T dL = SL - uL, dR = SR - uR;
+  const T mL = rL * dL, mR = rR * dR;
+  const T Ss = ((pR - pL) + uL * mL - uR * mR) / (mL - mR);
+  const bool left = (SL >= T(0)) || (Ss >= T(0));
+  const bool star = left ? !(SL >= T(0)) : (SR >= T(0));
+  const T r = left ? rL : rR, u = left ? uL : uR, v = left ? vL : vR, p = left ? pL : pR;
+  const T E = left ? EL : ER, S = left ? SL : SR, m = left ? mL : mR;
+  const T f0 = r * u;
+  F[0] = f0;
+  F[1] = f0 * u + p;
+  F[2] = f0 * v;
+  F[3] = u * (E + p);
+  if (star) {
+    const T fac = m / (S - Ss);
+    const T us3 = fac * (E / r + (Ss - u) * (Ss + p / m));
+    F[0] = F[0] + S * (fac - r);
+    F[1] = F[1] + S * (fac * Ss - f0);
+    F[2] = F[2] + S * (fac * v - r * v);
+    F[3] = F[3] + S * (us3 - E);
+  }
+}
+
+// Reverse of hllc(): given the flux cotangent bF, return the cotangents of
+// the left and right rotated primitive states (for the branch taken).
+template <class T>
+__device__ __forceinline__ void hllc_vjp(T rL, T uL, T vL, T pL, T rR, T uR, T vR, T pR,
+                                         T gamma, T gm1, const T bF[4], T bLs[4], T bRs[4]) {
+  const T cL = sqrt(gamma * pL / rL);
+  const T cR = sqrt(gamma * pR / rR);
+  const T aL = uL - cL, aR = uR - cR;
+  const bool slL = aL <= aR;
+  const T SL = slL ? aL : aR;
+  const T bL = uL + cL, bR = uR + cR;
+  const bool srL = bL >= bR;
+  const T SR = srL ? bL : bR;
+  const T EL = pL / gm1 + T(0.5) * rL * (uL * uL + vL * vL);
+  const T ER = pR / gm1 + T(0.5) * rR * (uR * uR + vR * vR);
+  const T dL = SL - uL, dR = SR - uR;
+  const T mL = rL * dL, mR = rR * dR;
+  const T den = mL - mR;
+  const T Ss = ((pR - pL) + uL * mL - uR * mR) / den;
+  const bool left = (SL >= T(0)) || (Ss >= T(0));
+  const bool star = left ? !(SL >= T(0)) : (SR >= T(0));
+  const T r = left ? rL : rR, u = left ? uL : uR, v = left ? vL : vR, p = left ? pL : pR;
+  const T E = left ? EL : ER, S = left ? SL : SR, m = left ? mL : mR;
+  const T f0 = r * u;
+
+  // physical-flux part of the chosen side
+  T b_f0 = bF[0] + bF[1] * u + bF[2] * v;
+  T b_u = bF[1] * f0 + bF[3] * (E + p);
+  T b_p = bF[1] + bF[3] * u;
+  T b_v = bF[2] * f0;
+  T b_E = bF[3] * u;
+  T b_r = T(0), b_S = T(0), b_Ss = T(0), b_m = T(0);
+  if (star) {  // + S (U* - U)
+    const T D = S - Ss;
+    const T fac = m / D;
+    const T A = Ss - u, B = Ss + p / m;
+    const T Q = E / r + A * B;
+    const T us3 = fac * Q;
+    b_S = bF[0] * (fac - r) + bF[1] * (fac * Ss - f0) + bF[2] * (fac * v - r * v) + bF[3] * (us3 - E);
+    T b_fac = S * (bF[0] + bF[1] * Ss + bF[2] * v);
+    b_r -= S * (bF[0] + bF[2] * v);
+    b_Ss += S * bF[1] * fac;
+    b_f0 -= S * bF[1];
+    b_v += S * bF[2] * (fac - r);
+    const T b_us3 = S * bF[3];
+    b_E -= b_us3;
+    b_fac += b_us3 * Q;
+    const T b_Q = b_us3 * fac;
+    b_E += b_Q / r;
+    b_r -= b_Q * E / (r * r);
+    const T b_A = b_Q * B, b_B = b_Q * A;
+    b_Ss += b_A + b_B;
+    b_u -= b_A;
+    b_p += b_B / m;
+    b_m -= b_B * p / (m * m);
+    b_m += b_fac / D;
+    const T b_D = -b_fac * fac / D;
+    b_S += b_D;
+    b_Ss -= b_D;
+  }
+  b_r += b_f0 * u;
+  b_u += b_f0 * r;
+  // E = p/(gamma-1) + rho (u^2 + v^2)/2 of the chosen side
+  b_p += b_E / gm1;
+  b_r += b_E * T(0.5) * (u * u + v * v);
+  b_u += b_E * r * u;
+  b_v += b_E * r * v;
+
+  T brL = T(0), buL = T(0), bvL = T(0), bpL = T(0), bSL = T(0), bmL = T(0);
+  T brR = T(0), buR = T(0), bvR = T(0), bpR = T(0), bSR = T(0), bmR = T(0);
+  if (left) { brL = b_r; buL = b_u; bvL = b_v; bpL = b_p; bSL = b_S; bmL = b_m; }
+  else      { brR = b_r; buR = b_u; bvR = b_v; bpR = b_p; bSR = b_S; bmR = b_m; }
+  // S* = num / den
+  const T b_num = b_Ss / den;
+  const T b_den = -b_Ss * Ss / den;
+  bpR += b_num;
+  bpL -= b_num;
+  buL += b_num * mL;
+  bmL += b_num * uL + b_den;
+  buR -= b_num * mR;
+  bmR -= b_num * uR + b_den;
+  // m = rho (S - u)
+  brL += bmL * dL;
+  brR += bmR * dR;
+  const T bdL = bmL * rL, bdR = bmR * rR;
+  bSL += bdL;
+  buL -= bdL;
+  bSR += bdR;
+  buR -= bdR;
+  // Davis speeds
+  T bcL = T(0), bcR = T(0);
+  if (slL) { buL += bSL; bcL -= bSL; } else { buR += bSL; bcR -= bSL; }
+  if (srL) { buL += bSR; bcL += bSR; } else { buR += bSR; bcR += bSR; }
+  // c = sqrt(gamma p / rho)
+  bpL += bcL * T(0.5) * cL / pL;
+  brL -= bcL * T(0.5) * cL / rL;
+  bpR += bcR * T(0.5) * cR / pR;
+  brR -= bcR * T(0.5) * cR / rR;
+  bLs[0] = brL; bLs[1] = buL; bLs[2] = bvL; bLs[3] = bpL;
+  bRs[0] = brR; bRs[1] = buR; bRs[2] = bvR; bRs[3] = bpR;
+}
+
+// Flux through the face between cells a and b along DIR (0: x, 1: y), from
+// the primitive states w[0..3] of cells a-1, a, b, b+1 (index [cell][var]).
+template <class T, int DIR>
+__device__ __forceinline__ void face_flux(const T w[4][4], int lim, T gamma, T gm1, T F[4]) {
+  T WL[4], WR[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const T sa = limited_slope(w[0][q], w[1][q], w[2][q], lim);
+    const T sb = limited_slope(w[1][q], w[2][q], w[3][q], lim);
+    WL[q] = w[1][q] + T(0.5) * sa;
+    WR[q] = w[2][q] - T(0.5) * sb;
+  }
+  constexpr int n = 1 + DIR, t = 2 - DIR;
+  T f[4];
+  hllc(WL[0], WL[n], WL[t], WL[3], WR[0], WR[n], WR[t], WR[3], gamma, gm1, f);
+  F[0] = f[0];
+  F[n] = f[1];
+  F[t] = f[2];
+  F[3] = f[3];
+}
+
+// Transposed face flux: out[cell][var] = (dF/dW_cell,var)^T mu for the four
+// cells a-1, a, b, b+1.
+template <class T, int DIR>
+__device__ __forceinline__ void face_vjp(const T w[4][4], const T mu[4], int lim, T gamma, T gm1,
+                                         T out[4][4]) {
+  T WL[4], WR[4], am[4], a0[4], ap[4], bm[4], b0[4], bp[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const T sa = limited_slope_d(w[0][q], w[1][q], w[2][q], lim, am[q], a0[q], ap[q]);
+    const T sb = limited_slope_d(w[1][q], w[2][q], w[3][q], lim, bm[q], b0[q], bp[q]);
+    WL[q] = w[1][q] + T(0.5) * sa;
+    WR[q] = w[2][q] - T(0.5) * sb;
+  }
+  constexpr int n = 1 + DIR, t = 2 - DIR;
+  const T bf[4] = {mu[0], mu[n], mu[t], mu[3]};
+  T bl[4], br[4];
+  hllc_vjp(WL[0], WL[n], WL[t], WL[3], WR[0], WR[n], WR[t], WR[3], gamma, gm1, bf, bl, br);
+  T bWL[4], bWR[4];
+  bWL[0] = bl[0]; bWL[n] = bl[1]; bWL[t] = bl[2]; bWL[3] = bl[3];
+  bWR[0] = br[0]; bWR[n] = br[1]; bWR[t] = br[2]; bWR[3] = br[3];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const T bsa = T(0.5) * bWL[q];   // W_L = W_a + s_a / 2
+    const T bsb = T(-0.5) * bWR[q];  // W_R = W_b - s_b / 2
+    out[0][q] = am[q] * bsa;
+    out[1][q] = bWL[q] + a0[q] * bsa + bm[q] * bsb;
+    out[2][q] = bWR[q] + ap[q] * bsa + b0[q] * bsb;
+    out[3][q] = bp[q] * bsb;
+  }
+}
+
+}  // namespace rt

@@ -1,0 +1,44 @@
+"""CPU-side checks of the C ABI: the library builds, loads, and exports every
+entry point that include/rt_cnop.h declares (no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "rt_cnop.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:rt_status|void|const char\*|int|size_t)\s+\**\s*(\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_and_binding_agree():
+    import paper_2608_04085_b300 as rt
+    assert _declared() == sorted(rt.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2608_04085_b300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_struct_sizes_match_header_layout():
+    import paper_2608_04085_b300 as rt
+    # rt_problem: 2 ints, 12 doubles, 2 ints, 2 doubles, 3 ints (+ padding)
+    assert ctypes.sizeof(rt.RtProblem) == 8 + 12 * 8 + 8 + 16 + 16
+    assert ctypes.sizeof(rt.RtOptions) == 24
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    import paper_2608_04085_b300 as rt
+    monkeypatch.setattr(rt, "LIB_PATH", str(tmp_path / "nope.so"))
+    monkeypatch.setattr(rt, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        rt.library()
