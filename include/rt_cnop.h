@@ -199,6 +199,29 @@ typedef struct {
 rt_status cnop_solve(rt_ctx* ctx, const cnop_params* prm, double* v_inout, int flags,
                      double* J_out, cnop_result* res);
 
+/* Allocation-free objective of one final state. The paper has no
+ * counterpart: this exists for callers that must not let a library allocate
+ * device memory (a host framework that owns all device memory through its
+ * own pool with a fixed budget, or a loop that cannot afford the device-wide
+ * synchronisation of cudaMalloc / cudaFree). It needs no context and calls
+ * no allocating routine.
+ *   p      grid and domain of the state (nx, ny, x0, x1, y0, y1 are used);
+ *   state  device FP64 conserved state [4][ny][nx] (rho, m_x, m_y, E), the
+ *          layout rt_get_state returns;
+ *   ek0    device FP64 reference e_k [ny][nx], or NULL for zero;
+ *   J      device FP64 [2]: J[0] = sum e_k dx dy (total kinetic energy),
+ *          J[1] = sum (e_k - ek0)^2 dx dy (Eq. objective form).
+ * The work is queued on cuda_stream (NULL = legacy default stream) and the
+ * call returns without waiting for it. Per-block partial sums live in a
+ * fixed 256 KiB device array inside the library, so grids above 4,194,304
+ * cells return RT_EINVAL (with a message on stderr). The first call on each
+ * device looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current; make that first call before any stream capture. All
+ * calls share the array: calls whose kernels overlap on the GPU race on it.
+ * Errors: RT_EINVAL (null pointer, empty domain, size), RT_ECUDA. */
+rt_status rt_objective_noalloc(const rt_problem* p, const double* state, const double* ek0, double* J,
+                               void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,6 +20,7 @@ UNITS = [
     ("rt_kernels_f64.cu", ["-fmad=false"]),
     ("rt_kernels_f32.cu", []),
     ("rt_runtime.cu", []),
+    ("rt_noalloc.cu", []),
 ]
 
 
