@@ -281,6 +281,22 @@ def run_ours(args):
     return 0
 
 
+def run_profile_case(args):
+    """Small case for ncu captures: 16 instances of the benchmark grid with a
+    short horizon (T = 0.01, about 25 RK2 steps) and store-all checkpointing;
+    about 1.5 GB on the device, each kernel's working set (4 x 50 MB) still
+    larger than L2."""
+    import paper_2608_04085_b300 as rt
+    nb = 16
+    probs = [I.single_256().replace(T=0.01) for _ in range(nb)]
+    with rt.Context(probs, precision=rt.RT_FP32_STATE, ckpt=rt.RT_CKPT_STORE_ALL) as ctx:
+        v = ctx.project(I.gaussian_batch(range(nb), 2, NY, NX).reshape(-1), DELTA, to_budget=True)
+        for k in range(2):
+            _, _, st = ctx.gradient(v)
+            print(json.dumps({"profile_case": k, **st}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -288,7 +304,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--profile-case", action="store_true", help="short-horizon case sized for ncu captures")
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -7,10 +7,11 @@
 
 namespace rt {
 
-// Tile of cells advanced by one CTA: TILE_X x TILE_Y cells, 256 threads.
+// Tile of cells advanced by one CTA: TILE_X x TILE_Y cells, 256 threads,
+// two cells per thread.
 constexpr int TILE_X = 32;
-constexpr int TILE_Y = 8;
-constexpr int TILE_THREADS = TILE_X * TILE_Y;
+constexpr int TILE_Y = 16;
+constexpr int TILE_THREADS = 256;
 
 // Per-instance constants, resident on the device (one entry per instance).
 // State slots hold every instance back to back: instance i's conserved plane
@@ -29,21 +30,32 @@ struct InstDev {
   double y0, y_int;          // domain bottom and interface height
   double gamma, gm1, g_y;
   double cfl, T;
+  float gamma_f, gm1_f, g_f, dx_f, dy_f;  // the same constants rounded once for FP32 kernels
   const double* rho0;        // [ny] base density at cell centres
   const double* p0;          // [ny] base pressure at cell centres
   const double* ek0;         // [nx*ny] baseline e_k for the anomaly objective (or null)
 };
 
-// Per-run device scalars, [n_inst] each unless noted.
+// Per-run device scalars, [n_inst] each unless noted. The time-step control
+// of step n+1 is computed once per instance by the last CTA of step n's
+// stage-2 launch (or of the inject launch for step 0), which writes dt in
+// FP64 (dtrec) and the per-step constants in the state precision (dtc).
 struct RunDev {
   double* dtrec;             // [n_inst][max_steps] dt of every step (0 = inactive)
+  void* dtc;                 // [n_inst][max_steps] StepC<T>: dt, dt/dx, dt/dy, dt*g_y in T
   double* t;                 // simulated time
   int* nstep;                // steps taken
-  unsigned long long* wmin;  // [2][n_inst] running min of the cell crossing time (bits of a positive double)
+  unsigned long long* wmin;  // running min of the cell crossing time (bits of a positive double)
+  unsigned int* counter;     // CTAs of the instance finished in the current launch
   int* status;               // 0 ok; 1 non-finite / non-positive state seen
   long long* bad_cell;       // first bad cell (j*nx+i)
   int max_steps;
   int n_inst;
+};
+
+template <class T>
+struct StepC {
+  T dt, dtdx, dtdy, dtg;
 };
 
 }  // namespace rt

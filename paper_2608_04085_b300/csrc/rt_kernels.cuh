@@ -1,16 +1,17 @@
 // rt_kernels.cuh -- CUDA kernels of the hot path, templated on the state type.
 //
-// One CTA advances one tile of TILE_X x TILE_Y cells of one instance; the
-// tile list covers every instance of the batch, so a single launch advances
-// all instances (uniform or uneven grids alike). Per-instance time-step
-// control lives on the device (RunDev): the host never reads dt inside the
-// time loop.
+// One CTA advances one tile of TILE_X x TILE_Y cells of one instance (two
+// cells per thread); the tile list covers every instance of the batch, so a
+// single launch advances all instances, uniform or uneven grids alike. The
+// per-instance time-step control lives on the device: the last CTA of an
+// instance in each stage-2 launch turns the CFL minimum into the next dt and
+// the next step's constants, so the kernels do no FP64 arithmetic per cell
+// and the host never reads dt inside the time loop.
 //
-//   k_inject     Sec. 3.1: U0 = (rho0, rho0 v, p0/(gamma-1) + rho0|v|^2/2);
-//                also the first CFL reduction.
-//   k_stage<1>   U1 = U + dt L(U)                      (SSP-RK2 stage 1)
-//   k_stage<2>   U' = U/2 + (U1 + dt L(U1))/2           (stage 2) + CFL min of U'
-//                L(U) = finite-volume divergence of PLM+HLLC fluxes + gravity
+//   k_inject     Sec. 3.1: U0 = (rho0, rho0 v, p0/(gamma-1) + rho0|v|^2/2), first CFL minimum
+//   k_stage<1>   U1 = U + dt L(U)                       (SSP-RK2 stage 1)
+//   k_stage<2>   U' = U/2 + (U1 + dt L(U1))/2           (stage 2) + CFL minimum of U'
+//                L(U): finite-volume divergence of PLM+HLLC fluxes + gravity
 //                source (Sec. 2.1 Eqs. mass/momentum/energy, Sec. 2.3).
 //   k_adjoint    out = kap + (d(dt L)/dU)^T kap + escale*E, kap = kscale*K: the
 //                transposed stage map (Sec. 3.4, exact discrete gradient)
@@ -29,24 +30,23 @@
 namespace rt {
 
 constexpr int TX = TILE_X, TY = TILE_Y, NTH = TILE_THREADS;
+constexpr int ROWS_PER_PASS = NTH / TX;  // rows covered by one pass of the block over a tile
+static_assert(TX == 32, "one warp per tile row");
+static_assert(TY % ROWS_PER_PASS == 0, "tile rows must be a multiple of the rows per pass");
 
 __device__ __forceinline__ int wrap_x(int gx, int nx) {
   gx %= nx;
   return gx < 0 ? gx + nx : gx;
 }
 
-__device__ __forceinline__ double warp_min(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// Block-wide sum in a fixed order (deterministic). All threads must call.
+// Block-wide sum in a fixed order (deterministic); the result is valid in
+// thread 0. All threads must call.
 __device__ __forceinline__ double block_sum(double v, double* red) {
   v = warp_sum(v);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -56,19 +56,38 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   double s = 0.0;
   if (threadIdx.x == 0)
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-  return s;  // valid in thread 0
+  return s;
 }
 
-// Cell crossing time min(dx/(|u_x|+c), dy/(|u_y|+c)) of a conserved state,
-// in the state's precision; `bad` flags a non-positive density or pressure
-// or a NaN.
+// Physics constants of an instance in the state precision (no conversion
+// instructions in the kernels).
 template <class T>
-__device__ __forceinline__ T crossing_time(T r, T mx, T my, T E, T gamma, T gm1, T dx, T dy, bool& bad) {
+struct Phys {
+  T gamma, gm1, g, dx, dy;
+};
+template <class T> __device__ __forceinline__ Phys<T> phys(const InstDev& I);
+template <> __device__ __forceinline__ Phys<float> phys<float>(const InstDev& I) {
+  return {I.gamma_f, I.gm1_f, I.g_f, I.dx_f, I.dy_f};
+}
+template <> __device__ __forceinline__ Phys<double> phys<double>(const InstDev& I) {
+  return {I.gamma, I.gm1, I.g_y, I.dx, I.dy};
+}
+
+template <class T>
+__device__ __forceinline__ StepC<T> step_const(const RunDev& run, int inst, int n) {
+  return reinterpret_cast<const StepC<T>*>(run.dtc)[(long long)inst * run.max_steps + n];
+}
+
+// Cell crossing time min(dx/(|u_x|+c), dy/(|u_y|+c)) of a conserved state in
+// the state's precision; `bad` flags a non-positive density or pressure, or
+// a NaN.
+template <class T>
+__device__ __forceinline__ T crossing_time(T r, T mx, T my, T E, const Phys<T>& P, bool& bad) {
   T W[4];
-  cons_to_prim(r, mx, my, E, gm1, W);
-  const T c = sqrt(gamma * W[3] / W[0]);
-  const T wx = dx / (fabs(W[1]) + c);
-  const T wy = dy / (fabs(W[2]) + c);
+  cons_to_prim(r, mx, my, E, P.gm1, W);
+  const T c = sqrt(P.gamma * W[3] / W[0]);
+  const T wx = P.dx / (fabs(W[1]) + c);
+  const T wy = P.dy / (fabs(W[2]) + c);
   const T w = wx <= wy ? wx : wy;
   bad = !(W[0] > T(0)) || !(W[3] > T(0)) || !(w > T(0)) || !(w < T(1e30));
   return w;
@@ -84,12 +103,39 @@ __device__ __forceinline__ T warp_min_t(T v) {
   return v;
 }
 
-// Block min of the crossing time (in T; `w` is +inf-like for idle threads),
-// folded into the instance's running minimum as a positive double; records
-// the first bad cell. All threads must call.
+// Time-step control of step n_next (thread 0 of the instance's last CTA):
+// dt = cfl * min crossing time, clipped to T - t in horizon mode, 0 once the
+// run is over or the state went bad. Resets the running minimum.
 template <class T>
-__device__ __forceinline__ void commit_crossing(T w, long long cell, bool bad, RunDev run, int inst, int parity,
-                                                T* red) {
+__device__ void finish_step(const InstDev& I, const RunDev& run, int inst, int n_next, double t) {
+  const unsigned long long bits = atomicExch(&run.wmin[inst], ~0ull);
+  const double wmin = __longlong_as_double((long long)bits);
+  const bool ok = atomicAdd(&run.status[inst], 0) == 0 && bits != ~0ull;
+  const bool active = ok && I.enabled && (I.nsteps > 0 ? n_next < I.nsteps : t < I.T);
+  double dt = I.cfl * wmin;
+  if (I.nsteps <= 0) {
+    const double rem = I.T - t;
+    if (dt >= rem) dt = rem;
+  }
+  if (!active) dt = 0.0;
+  if (n_next < run.max_steps) {
+    const long long k = (long long)inst * run.max_steps + n_next;
+    run.dtrec[k] = dt;
+    StepC<T> c;
+    c.dt = (T)dt;
+    c.dtdx = (T)(dt / I.dx);
+    c.dtdy = (T)(dt / I.dy);
+    c.dtg = (T)(dt * I.g_y);
+    reinterpret_cast<StepC<T>*>(run.dtc)[k] = c;
+  }
+}
+
+// Fold the block's crossing-time minimum into the instance's running minimum
+// and report whether this CTA is the instance's last one of the launch.
+// All threads must call; the result is valid in thread 0.
+template <class T>
+__device__ __forceinline__ bool commit_crossing(T w, long long cell, bool bad, const InstDev& I, const RunDev& run,
+                                                int inst, T* red) {
   if (bad) {
     if (atomicCAS(&run.status[inst], 0, 1) == 0) run.bad_cell[inst] = cell;
   }
@@ -98,49 +144,40 @@ __device__ __forceinline__ void commit_crossing(T w, long long cell, bool bad, R
   __syncthreads();
   if (lane == 0) red[wid] = m;
   __syncthreads();
+  bool last = false;
   if (threadIdx.x == 0) {
     for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = red[k] < m ? red[k] : m;
-    if (m > T(0) && m < T(3e38))
-      atomicMin(&run.wmin[parity * run.n_inst + inst], (unsigned long long)__double_as_longlong((double)m));
+    if (m > T(0) && m < T(1e30))
+      atomicMin(&run.wmin[inst], (unsigned long long)__double_as_longlong((double)m));
+    __threadfence();
+    const unsigned int ntile = (unsigned int)(I.tile_end - I.tile_begin);
+    if (atomicAdd(&run.counter[inst], 1u) + 1u == ntile) {
+      run.counter[inst] = 0u;
+      __threadfence();
+      last = true;
+    }
   }
-}
-
-// Per-CTA constants of one stage in the state's precision, computed once by
-// thread 0 (the state-precision kernels then do no FP64 arithmetic per cell).
-template <class T>
-struct StepConst {
-  T dt, dtdx, dtdy, dtg;
-  T gamma, gm1, g, dx, dy;
-};
-
-template <class T>
-__device__ __forceinline__ void make_const(StepConst<T>& k, const InstDev& I, double dt) {
-  k.dt = (T)dt;
-  k.dtdx = (T)(dt / I.dx);
-  k.dtdy = (T)(dt / I.dy);
-  k.dtg = (T)(dt * I.g_y);
-  k.gamma = (T)I.gamma;
-  k.gm1 = (T)I.gm1;
-  k.g = (T)I.g_y;
-  k.dx = (T)I.dx;
-  k.dy = (T)I.dy;
+  return last;
 }
 
 // ------------------------------------------------------------------ inject
 template <class T>
 __global__ void __launch_bounds__(NTH) k_inject(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,
-                                                const double* __restrict__ v, T* __restrict__ U, RunDev run) {
+                                                const double* __restrict__ v, T* __restrict__ U, RunDev run,
+                                                int record) {
   __shared__ T red[NTH / 32];
   const int4 tl = tiles[blockIdx.x];
-  const InstDev& I = insts[tl.x];
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int gx = tl.y + tx, gy = tl.z + ty;
+  const int inst = tl.x;
+  const InstDev& I = insts[inst];
+  const Phys<T> P = phys<T>(I);
   const long long cells = (long long)I.nx * I.ny;
-  T w = T(3e38);
+  T w = T(1e30);
   bool bad = false;
-  long long c = 0;
-  if (gx < I.nx && gy < I.ny) {
-    c = (long long)gy * I.nx + gx;
+  long long badc = 0;
+  for (int e = threadIdx.x; e < TX * TY; e += NTH) {
+    const int gx = tl.y + e % TX, gy = tl.z + e / TX;
+    if (gx >= I.nx || gy >= I.ny) continue;
+    const long long c = (long long)gy * I.nx + gx;
     const double* vi = v + I.v_off;
     const double vx = I.ncomp == 2 ? vi[c] : 0.0;
     const double vy = I.ncomp == 2 ? vi[cells + c] : vi[c];
@@ -152,13 +189,14 @@ __global__ void __launch_bounds__(NTH) k_inject(const InstDev* __restrict__ inst
     Ui[cells + c] = u1;
     Ui[2 * cells + c] = u2;
     Ui[3 * cells + c] = u3;
-    const T cw = crossing_time<T>(u0, u1, u2, u3, (T)I.gamma, (T)I.gm1, (T)I.dx, (T)I.dy, bad);
-    if (!bad) w = cw;
+    bool b = false;
+    const T cw = crossing_time<T>(u0, u1, u2, u3, P, b);
+    if (b) { bad = true; badc = c; } else if (cw < w) w = cw;
   }
-  commit_crossing<T>(w, c, bad, run, tl.x, 0, red);
-  if (tl.y == 0 && tl.z == 0 && threadIdx.x == 0) {
-    run.t[tl.x] = 0.0;
-    run.nstep[tl.x] = 0;
+  if (commit_crossing<T>(w, badc, bad, I, run, inst, red)) {
+    run.t[inst] = 0.0;
+    run.nstep[inst] = 0;
+    if (record) finish_step<T>(I, run, inst, 0, 0.0);  // a replay keeps the recorded step 0
   }
 }
 
@@ -167,161 +205,146 @@ __global__ void __launch_bounds__(NTH) k_inject(const InstDev* __restrict__ inst
 // hydrostatic boundary, extrapolate p_g = p_c + g_y rho_c (y_g - y_c).
 template <class T>
 __device__ __forceinline__ void load_prim(const T* __restrict__ Ui, const InstDev& I, long long cells, int gx,
-                                          int gy, T gm1, T g, T W[4]) {
+                                          int gy, const Phys<T>& P, T W[4]) {
   gx = wrap_x(gx, I.nx);
   int sy = gy, side = 0, k = 0;
   if (gy < 0) { sy = -1 - gy; side = -1; k = -1 - gy; }
   else if (gy >= I.ny) { sy = 2 * I.ny - 1 - gy; side = 1; k = gy - I.ny; }
-  if (sy < 0 || sy >= I.ny) {  // beyond the two ghost layers: never used
+  if (sy < 0 || sy >= I.ny) {  // beyond the ghost layers any face uses: never read
     W[0] = T(1); W[1] = T(0); W[2] = T(0); W[3] = T(1);
     return;
   }
   const long long c = (long long)sy * I.nx + gx;
-  cons_to_prim(Ui[c], Ui[cells + c], Ui[2 * cells + c], Ui[3 * cells + c], gm1, W);
+  cons_to_prim(Ui[c], Ui[cells + c], Ui[2 * cells + c], Ui[3 * cells + c], P.gm1, W);
   if (side != 0) {
     W[2] = -W[2];
     if (I.bc_y == 1) {
       const T dyk = (T)((double)(2 * k + 1) * I.dy);
-      if (side < 0) W[3] = W[3] - g * W[0] * dyk;
-      else W[3] = W[3] + g * W[0] * dyk;
+      if (side < 0) W[3] = W[3] - P.g * W[0] * dyk;
+      else W[3] = W[3] + P.g * W[0] * dyk;
     }
   }
 }
 
 // ------------------------------------------------------------------- stage
-// MODE 0: CFL control (records dt, advances t and the step count, CFL min of
-// the new state); MODE 1: replay the recorded dt, count steps; MODE 2: replay
-// the recorded dt without touching any run scalar (checkpoint recomputation).
+// Shared memory (elements of T): primitive tile with 2 ghost layers, x-face
+// and y-face fluxes.
+constexpr int ST_EX = TX + 4, ST_EY = TY + 4;
+constexpr int ST_NFX = (TX + 1) * TY, ST_NFY = TX * (TY + 1);
+constexpr int ST_SMEM_ELEMS = 4 * ST_EX * ST_EY + 4 * ST_NFX + 4 * ST_NFY;
+
+// MODE 0: CFL control (the instance's last CTA records the next dt, advances
+// t and the step count); MODE 1: replay recorded steps, counting them;
+// MODE 2: replay without touching any run scalar (checkpoint recomputation).
 template <class T, int STAGE, int MODE>
 __global__ void __launch_bounds__(NTH) k_stage(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,
                                                const T* __restrict__ src, const T* __restrict__ base,
                                                T* __restrict__ dst, RunDev run, int n) {
-  constexpr int EX = TX + 4, EY = TY + 4;
-  __shared__ T sW[4][EY][EX];
-  __shared__ T sF[4][TY][TX + 1];
-  __shared__ T sG[4][TY + 1][TX];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sW = reinterpret_cast<T*>(smem_raw);  // [4][EY][EX]
+  T* sF = sW + 4 * ST_EX * ST_EY;          // [4][TY][TX+1]
+  T* sG = sF + 4 * ST_NFX;                 // [4][TY+1][TX]
   __shared__ T red[NTH / 32];
-  __shared__ StepConst<T> K;
-  __shared__ double s_dt;
   const int4 tl = tiles[blockIdx.x];
   const int inst = tl.x;
   const InstDev& I = insts[inst];
-  const bool tile0 = (tl.y == 0 && tl.z == 0);
-  if (threadIdx.x == 0) {
-    double dt;
-    if (STAGE == 1 && MODE == 0) {
-      const double t = run.t[inst];
-      const double wmin = __longlong_as_double((long long)run.wmin[(n & 1) * run.n_inst + inst]);
-      const bool active = I.enabled && (I.nsteps > 0 ? n < I.nsteps : t < I.T) && run.status[inst] == 0;
-      dt = I.cfl * wmin;
-      if (I.nsteps <= 0) {
-        const double rem = I.T - t;
-        if (dt >= rem) dt = rem;
-      }
-      if (!active) dt = 0.0;
-      if (tile0) {
-        run.dtrec[(long long)inst * run.max_steps + n] = dt;
-        run.wmin[((n + 1) & 1) * run.n_inst + inst] = ~0ull;
-      }
-    } else {
-      dt = run.dtrec[(long long)inst * run.max_steps + n];
-    }
-    s_dt = dt;
-    make_const(K, I, dt);
-  }
-  __syncthreads();
-  const double dt = s_dt;
-  if (dt == 0.0) return;
+  const StepC<T> sc = step_const<T>(run, inst, n);
+  if (!(sc.dt > T(0))) return;  // instance inactive at this step (uniform over the block)
 
+  const Phys<T> P = phys<T>(I);
   const long long cells = (long long)I.nx * I.ny;
   const T* Si = src + 4 * I.cell_off;
   const int x0 = tl.y, y0 = tl.z;
-  const T gamma = K.gamma, gm1 = K.gm1;
   const int lim = I.limiter;
-  for (int e = threadIdx.x; e < EX * EY; e += NTH) {
-    const int ey = e / EX, ex = e - ey * EX;
+  for (int e = threadIdx.x; e < ST_EX * ST_EY; e += NTH) {
+    const int ey = e / ST_EX, ex = e - ey * ST_EX;
     T W[4];
-    load_prim(Si, I, cells, x0 + ex - 2, y0 + ey - 2, gm1, K.g, W);
+    load_prim(Si, I, cells, x0 + ex - 2, y0 + ey - 2, P, W);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) sW[q][ey][ex] = W[q];
+    for (int q = 0; q < 4; ++q) sW[(q * ST_EY + ey) * ST_EX + ex] = W[q];
   }
   __syncthreads();
-  constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
-  for (int f = threadIdx.x; f < NFX + NFY; f += NTH) {
+  for (int f = threadIdx.x; f < ST_NFX + ST_NFY; f += NTH) {
     T w[4][4], F[4];
-    if (f < NFX) {
+    if (f < ST_NFX) {  // x face fx of row fy: between tile cells fx-1 and fx
       const int fy = f / (TX + 1), fx = f - fy * (TX + 1);
 #pragma unroll
       for (int p = 0; p < 4; ++p)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) w[p][q] = sW[q][fy + 2][fx + p];
-      face_flux<T, 0>(w, lim, gamma, gm1, F);
+        for (int q = 0; q < 4; ++q) w[p][q] = sW[(q * ST_EY + fy + 2) * ST_EX + fx + p];
+      face_flux<T, 0>(w, lim, P.gamma, P.gm1, F);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) sF[q][fy][fx] = F[q];
-    } else {
-      const int g = f - NFX;
+      for (int q = 0; q < 4; ++q) sF[q * ST_NFX + f] = F[q];
+    } else {  // y face fy of column fx: between tile rows fy-1 and fy
+      const int g = f - ST_NFX;
       const int fy = g / TX, fx = g - fy * TX;
 #pragma unroll
       for (int p = 0; p < 4; ++p)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) w[p][q] = sW[q][fy + p][fx + 2];
-      face_flux<T, 1>(w, lim, gamma, gm1, F);
+        for (int q = 0; q < 4; ++q) w[p][q] = sW[(q * ST_EY + fy + p) * ST_EX + fx + 2];
+      face_flux<T, 1>(w, lim, P.gamma, P.gm1, F);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) sG[q][fy][fx] = F[q];
+      for (int q = 0; q < 4; ++q) sG[q * ST_NFY + g] = F[q];
     }
   }
   __syncthreads();
 
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int gx = x0 + tx, gy = y0 + ty;
-  T w = T(3e38);
+  const int tx = threadIdx.x % TX;
+  T w = T(1e30);
   bool bad = false;
-  long long c = 0;
-  if (gx < I.nx && gy < I.ny) {
-    c = (long long)gy * I.nx + gx;
-    const T dtT = K.dt, dtdx = K.dtdx, dtdy = K.dtdy, g = K.g;
-    const T u[4] = {Si[c], Si[cells + c], Si[2 * cells + c], Si[3 * cells + c]};
-    T o[4];
+  long long badc = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      T b = u[k] + dtdx * (sF[k][ty][tx] - sF[k][ty][tx + 1]);
-      b = b + dtdy * (sG[k][ty][tx] - sG[k][ty + 1][tx]);
-      if (k == 2) b = b + dtT * (u[0] * g);
-      if (k == 3) b = b + dtT * (u[2] * g);
-      o[k] = b;
-    }
-    if (STAGE == 2) {
-      const T* Bi = base + 4 * I.cell_off;
+  for (int pass = 0; pass < TY / ROWS_PER_PASS; ++pass) {
+    const int ty = threadIdx.x / TX + pass * ROWS_PER_PASS;
+    const int gx = x0 + tx, gy = y0 + ty;
+    if (gx < I.nx && gy < I.ny) {
+      const long long c = (long long)gy * I.nx + gx;
+      const T u[4] = {Si[c], Si[cells + c], Si[2 * cells + c], Si[3 * cells + c]};
+      T o[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) o[k] = T(0.5) * Bi[k * cells + c] + T(0.5) * o[k];
-    }
-    T* Di = dst + 4 * I.cell_off;
+      for (int k = 0; k < 4; ++k) {
+        const T* Fk = sF + k * ST_NFX + ty * (TX + 1);
+        const T* Gk = sG + k * ST_NFY;
+        T b = u[k] + sc.dtdx * (Fk[tx] - Fk[tx + 1]);
+        b = b + sc.dtdy * (Gk[ty * TX + tx] - Gk[(ty + 1) * TX + tx]);
+        if (k == 2) b = b + sc.dt * (u[0] * P.g);
+        if (k == 3) b = b + sc.dt * (u[2] * P.g);
+        o[k] = b;
+      }
+      if (STAGE == 2) {
+        const T* Bi = base + 4 * I.cell_off;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) Di[k * cells + c] = o[k];
-    if (STAGE == 2 && MODE == 0) {
-      const T cw = crossing_time<T>(o[0], o[1], o[2], o[3], gamma, gm1, K.dx, K.dy, bad);
-      if (!bad) w = cw;
+        for (int k = 0; k < 4; ++k) o[k] = T(0.5) * Bi[k * cells + c] + T(0.5) * o[k];
+      }
+      T* Di = dst + 4 * I.cell_off;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) Di[k * cells + c] = o[k];
+      if (STAGE == 2 && MODE == 0) {
+        bool b = false;
+        const T cw = crossing_time<T>(o[0], o[1], o[2], o[3], P, b);
+        if (b) { bad = true; badc = c; } else if (cw < w) w = cw;
+      }
     }
   }
   if (STAGE == 2 && MODE == 0) {
-    commit_crossing<T>(w, c, bad, run, inst, (n + 1) & 1, red);
-    if (tile0 && threadIdx.x == 0) {
+    if (commit_crossing<T>(w, badc, bad, I, run, inst, red)) {
+      const double dt = run.dtrec[(long long)inst * run.max_steps + n];
       const double t = run.t[inst];
-      run.t[inst] = I.nsteps > 0 ? t + dt : (dt >= I.T - t ? I.T : t + dt);
+      const double tn = I.nsteps > 0 ? t + dt : (dt >= I.T - t ? I.T : t + dt);
+      run.t[inst] = tn;
       run.nstep[inst] = n + 1;
+      finish_step<T>(I, run, inst, n + 1, tn);
     }
   }
-  if (STAGE == 2 && MODE == 1 && tile0 && threadIdx.x == 0) run.nstep[inst] = n + 1;
+  if (STAGE == 2 && MODE == 1 && x0 == 0 && y0 == 0 && threadIdx.x == 0) run.nstep[inst] = n + 1;
 }
 
 // ----------------------------------------------------------------- adjoint
-// Shared-memory layout of k_adjoint (elements of T): primitive tile with 3
-// ghost layers, cotangent tile with 2, and a face buffer reused by the x
-// and y sweeps (16 contributions per face).
+// Shared memory (elements of T): primitive tile with 3 ghost layers,
+// cotangent tile with 2, and 16 contributions per x face and per y face.
 constexpr int ADJ_AX = TX + 6, ADJ_AY = TY + 6, ADJ_KX = TX + 4, ADJ_KY = TY + 4;
 constexpr int ADJ_NFX = (TX + 3) * TY, ADJ_NFY = TX * (TY + 3);
-constexpr int ADJ_FACES = ADJ_NFX > ADJ_NFY ? ADJ_NFX : ADJ_NFY;
-constexpr int ADJ_SMEM_ELEMS = 4 * ADJ_AX * ADJ_AY + 4 * ADJ_KX * ADJ_KY + 16 * ADJ_FACES;
+constexpr int ADJ_SMEM_ELEMS = 4 * ADJ_AX * ADJ_AY + 4 * ADJ_KX * ADJ_KY + 16 * ADJ_NFX + 16 * ADJ_NFY;
 
 template <class T>
 __global__ void __launch_bounds__(NTH) k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,
@@ -329,32 +352,26 @@ __global__ void __launch_bounds__(NTH) k_adjoint(const InstDev* __restrict__ ins
                                                  const T* __restrict__ E, T escale, T* __restrict__ out,
                                                  RunDev run, int n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sW = reinterpret_cast<T*>(smem_raw);      // [4][AY][AX]
-  T* sK = sW + 4 * ADJ_AX * ADJ_AY;              // [4][KY][KX]
-  T* sB = sK + 4 * ADJ_KX * ADJ_KY;              // [16][ADJ_FACES]
-  __shared__ StepConst<T> C;
-  __shared__ double s_dt;
+  T* sW = reinterpret_cast<T*>(smem_raw);  // [4][AY][AX]
+  T* sK = sW + 4 * ADJ_AX * ADJ_AY;        // [4][KY][KX]
+  T* sBx = sK + 4 * ADJ_KX * ADJ_KY;       // [16][NFX]
+  T* sBy = sBx + 16 * ADJ_NFX;             // [16][NFY]
   const int4 tl = tiles[blockIdx.x];
   const int inst = tl.x;
   const InstDev& I = insts[inst];
-  if (threadIdx.x == 0) {
-    const double d = run.dtrec[(long long)inst * run.max_steps + n];
-    s_dt = d;
-    make_const(C, I, d);
-  }
-  __syncthreads();
-  if (s_dt == 0.0) return;
+  const StepC<T> sc = step_const<T>(run, inst, n);
+  if (!(sc.dt > T(0))) return;
+  const Phys<T> P = phys<T>(I);
   const long long cells = (long long)I.nx * I.ny;
   const T* Ui = U + 4 * I.cell_off;
   const T* Ki = K + 4 * I.cell_off;
   const int x0 = tl.y, y0 = tl.z, nx = I.nx, ny = I.ny;
-  const T gamma = C.gamma, gm1 = C.gm1;
   const int lim = I.limiter;
 
   for (int e = threadIdx.x; e < ADJ_AX * ADJ_AY; e += NTH) {
     const int ey = e / ADJ_AX, ex = e - ey * ADJ_AX;
     T W[4];
-    load_prim(Ui, I, cells, x0 + ex - 3, y0 + ey - 3, gm1, C.g, W);
+    load_prim(Ui, I, cells, x0 + ex - 3, y0 + ey - 3, P, W);
 #pragma unroll
     for (int q = 0; q < 4; ++q) sW[(q * ADJ_AY + ey) * ADJ_AX + ex] = W[q];
   }
@@ -369,128 +386,122 @@ __global__ void __launch_bounds__(NTH) k_adjoint(const InstDev* __restrict__ ins
   }
   __syncthreads();
 
-  const T dtdx = C.dtdx, dtdy = C.dtdy;
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  T bW[4] = {T(0), T(0), T(0), T(0)};
-
-  // x faces: fx in [0, TX+3) is the left face of tile cell fx-1
-  for (int f = threadIdx.x; f < ADJ_NFX; f += NTH) {
-    const int fy = f / (TX + 3), fx = f - fy * (TX + 3);
-    T w[4][4], mu[4], o[4][4];
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) w[p][q] = sW[(q * ADJ_AY + fy + 3) * ADJ_AX + fx + p];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      mu[q] = dtdx * (sK[(q * ADJ_KY + fy + 2) * ADJ_KX + fx + 1] - sK[(q * ADJ_KY + fy + 2) * ADJ_KX + fx]);
-    face_vjp<T, 0>(w, mu, lim, gamma, gm1, o);
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) sB[(p * 4 + q) * ADJ_FACES + fy * (TX + 3) + fx] = o[p][q];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int p = 0; p < 4; ++p)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) bW[q] += sB[(p * 4 + q) * ADJ_FACES + ty * (TX + 3) + tx + 3 - p];
-  __syncthreads();
-
-  // y faces: fy in [0, TY+3) is the bottom face of tile row fy-1 (global face y0+fy-1)
-  for (int f = threadIdx.x; f < ADJ_NFY; f += NTH) {
-    const int fy = f / TX, fx = f - fy * TX;
-    const int gf = y0 + fy - 1;
+  // every face once: x face fx of row fy is the left face of tile cell fx-1;
+  // y face fy of column fx is the bottom face of tile row fy-1 (global y0+fy-1)
+  for (int f = threadIdx.x; f < ADJ_NFX + ADJ_NFY; f += NTH) {
     T o[4][4];
-    if (gf >= 0 && gf <= ny) {
+    if (f < ADJ_NFX) {
+      const int fy = f / (TX + 3), fx = f - fy * (TX + 3);
       T w[4][4], mu[4];
 #pragma unroll
       for (int p = 0; p < 4; ++p)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) w[p][q] = sW[(q * ADJ_AY + fy + p) * ADJ_AX + fx + 3];
+        for (int q = 0; q < 4; ++q) w[p][q] = sW[(q * ADJ_AY + fy + 3) * ADJ_AX + fx + p];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        mu[q] = dtdy * (sK[(q * ADJ_KY + fy + 1) * ADJ_KX + fx + 2] - sK[(q * ADJ_KY + fy) * ADJ_KX + fx + 2]);
-      face_vjp<T, 1>(w, mu, lim, gamma, gm1, o);
-    } else {
+        mu[q] = sc.dtdx * (sK[(q * ADJ_KY + fy + 2) * ADJ_KX + fx + 1] - sK[(q * ADJ_KY + fy + 2) * ADJ_KX + fx]);
+      face_vjp<T, 0>(w, mu, lim, P.gamma, P.gm1, o);
 #pragma unroll
       for (int p = 0; p < 4; ++p)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) o[p][q] = T(0);
+        for (int q = 0; q < 4; ++q) sBx[(p * 4 + q) * ADJ_NFX + f] = o[p][q];
+    } else {
+      const int g = f - ADJ_NFX;
+      const int fy = g / TX, fx = g - fy * TX;
+      const int gf = y0 + fy - 1;
+      if (gf >= 0 && gf <= ny) {
+        T w[4][4], mu[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) w[p][q] = sW[(q * ADJ_AY + fy + p) * ADJ_AX + fx + 3];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          mu[q] = sc.dtdy * (sK[(q * ADJ_KY + fy + 1) * ADJ_KX + fx + 2] - sK[(q * ADJ_KY + fy) * ADJ_KX + fx + 2]);
+        face_vjp<T, 1>(w, mu, lim, P.gamma, P.gm1, o);
+      } else {
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) o[p][q] = T(0);
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sBy[(p * 4 + q) * ADJ_NFY + g] = o[p][q];
     }
+  }
+  __syncthreads();
+
+  const int tx = threadIdx.x % TX;
+#pragma unroll
+  for (int pass = 0; pass < TY / ROWS_PER_PASS; ++pass) {
+    const int ty = threadIdx.x / TX + pass * ROWS_PER_PASS;
+    const int gx = x0 + tx, gy = y0 + ty;
+    T bW[4] = {T(0), T(0), T(0), T(0)};
+    // face f touches tile cells f-3 .. f (position p = cell - f + 3)
 #pragma unroll
     for (int p = 0; p < 4; ++p)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) sB[(p * 4 + q) * ADJ_FACES + fy * TX + fx] = o[p][q];
-  }
-  __syncthreads();
+      for (int q = 0; q < 4; ++q) {
+        bW[q] += sBx[(p * 4 + q) * ADJ_NFX + ty * (TX + 3) + tx + 3 - p];
+        bW[q] += sBy[(p * 4 + q) * ADJ_NFY + (ty + 3 - p) * TX + tx];
+      }
+    // ghost rows of the y boundary fold back onto the cells they mirror
+    for (int side = 0; side < 2; ++side) {
+      int k, gly;
+      if (side == 0) { if (gy > 1) continue; k = gy; gly = -1 - k - y0; }
+      else { if (gy < ny - 2 || gy >= ny) continue; k = ny - 1 - gy; gly = ny + k - y0; }
+      T gq[4] = {T(0), T(0), T(0), T(0)};
+      const int f_lo = gly > 0 ? gly : 0, f_hi = (gly + 3) < (TY + 2) ? (gly + 3) : (TY + 2);
+      for (int fy = f_lo; fy <= f_hi; ++fy) {
+        const int p = gly - fy + 3;
 #pragma unroll
-  for (int p = 0; p < 4; ++p)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) bW[q] += sB[(p * 4 + q) * ADJ_FACES + (ty + 3 - p) * TX + tx];
-
-  const int gx = x0 + tx, gy = y0 + ty;
-  // ghost rows of the y boundary fold back onto the cells they mirror
-  for (int side = 0; side < 2; ++side) {
-    int k, gly;
-    if (side == 0) { if (gy > 1) continue; k = gy; gly = -1 - k - y0; }
-    else { if (gy < ny - 2 || gy >= ny) continue; k = ny - 1 - gy; gly = ny + k - y0; }
-    T gq[4] = {T(0), T(0), T(0), T(0)};
-    const int f_lo = gly > 0 ? gly : 0, f_hi = (gly + 3) < (TY + 2) ? (gly + 3) : (TY + 2);
-    for (int fy = f_lo; fy <= f_hi; ++fy) {
-      const int p = gly - fy + 3;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) gq[q] += sB[(p * 4 + q) * ADJ_FACES + fy * TX + tx];
+        for (int q = 0; q < 4; ++q) gq[q] += sBy[(p * 4 + q) * ADJ_NFY + fy * TX + tx];
+      }
+      bW[0] += gq[0];
+      bW[1] += gq[1];
+      bW[2] -= gq[2];
+      bW[3] += gq[3];
+      if (I.bc_y == 1) {
+        const T dyk = (T)((double)(2 * k + 1) * I.dy);
+        if (side == 0) bW[0] -= P.g * dyk * gq[3];
+        else bW[0] += P.g * dyk * gq[3];
+      }
     }
-    bW[0] += gq[0];
-    bW[1] += gq[1];
-    bW[2] -= gq[2];
-    bW[3] += gq[3];
-    if (I.bc_y == 1) {
-      const T dyk = (T)((double)(2 * k + 1) * I.dy);
-      if (side == 0) bW[0] -= C.g * dyk * gq[3];
-      else bW[0] += C.g * dyk * gq[3];
+    if (gx < nx && gy < ny) {
+      const long long c = (long long)gy * nx + gx;
+      const T r = Ui[c], mx = Ui[cells + c], my = Ui[2 * cells + c];
+      const T u = mx / r, v = my / r;
+      T bU[4];
+      bU[0] = bW[0] - (u * bW[1] + v * bW[2]) / r + P.gm1 * T(0.5) * (u * u + v * v) * bW[3];
+      bU[1] = bW[1] / r - P.gm1 * u * bW[3];
+      bU[2] = bW[2] / r - P.gm1 * v * bW[3];
+      bU[3] = P.gm1 * bW[3];
+      T kc[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) kc[q] = sK[(q * ADJ_KY + ty + 2) * ADJ_KX + tx + 2];
+      T o[4];
+      o[0] = kc[0] + bU[0] + sc.dtg * kc[2];
+      o[1] = kc[1] + bU[1];
+      o[2] = kc[2] + bU[2] + sc.dtg * kc[3];
+      o[3] = kc[3] + bU[3];
+      if (E) {
+        const T* Ei = E + 4 * I.cell_off;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) o[q] = o[q] + escale * Ei[q * cells + c];
+      }
+      T* Oi = out + 4 * I.cell_off;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) Oi[q * cells + c] = o[q];
     }
-  }
-
-  if (gx < nx && gy < ny) {
-    const long long c = (long long)gy * nx + gx;
-    const T r = Ui[c], mx = Ui[cells + c], my = Ui[2 * cells + c];
-    const T u = mx / r, v = my / r;
-    T bU[4];
-    bU[0] = bW[0] - (u * bW[1] + v * bW[2]) / r + gm1 * T(0.5) * (u * u + v * v) * bW[3];
-    bU[1] = bW[1] / r - gm1 * u * bW[3];
-    bU[2] = bW[2] / r - gm1 * v * bW[3];
-    bU[3] = gm1 * bW[3];
-    T kc[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) kc[q] = sK[(q * ADJ_KY + ty + 2) * ADJ_KX + tx + 2];
-    const T dtg = C.dtg;
-    T o[4];
-    o[0] = kc[0] + bU[0] + dtg * kc[2];
-    o[1] = kc[1] + bU[1];
-    o[2] = kc[2] + bU[2] + dtg * kc[3];
-    o[3] = kc[3] + bU[3];
-    T* Oi = out + 4 * I.cell_off;
-    if (E) {
-      const T* Ei = E + 4 * I.cell_off;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) o[q] = o[q] + escale * Ei[q * cells + c];
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) Oi[q * cells + c] = o[q];
   }
 }
 
 // --------------------------------------------------------------- objective
 // Final state of instance i: slot_tab[nstep[i] % tab_mod] (tab_mod 2: the
 // forward ping-pong pair) or slot_tab[nstep[i]] (tab_mod 0: stored states).
-template <class T>
-__device__ __forceinline__ int final_slot(const int* nstep, int inst, int tab_mod) {
-  const int s = nstep[inst];
-  return tab_mod ? (s % tab_mod) : s;
-}
-
+// The terminal cotangent dJ/dU goes to lamA / lamB by the same parity.
 template <class T>
 __global__ void __launch_bounds__(NTH) k_objective(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,
                                                    T* const* __restrict__ slot_tab, int tab_mod,
@@ -499,27 +510,28 @@ __global__ void __launch_bounds__(NTH) k_objective(const InstDev* __restrict__ i
   __shared__ double red[NTH / 32];
   const int4 tl = tiles[blockIdx.x];
   const InstDev& I = insts[tl.x];
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int gx = tl.y + tx, gy = tl.z + ty;
   const long long cells = (long long)I.nx * I.ny;
-  const int s = final_slot<T>(nstep, tl.x, tab_mod);
+  const int ns = nstep[tl.x];
+  const int s = tab_mod ? (ns % tab_mod) : ns;
+  const T* Si = slot_tab[s] + 4 * I.cell_off;
   double ke = 0.0, pap = 0.0;
-  if (gx < I.nx && gy < I.ny) {
+  for (int e = threadIdx.x; e < TX * TY; e += NTH) {
+    const int gx = tl.y + e % TX, gy = tl.z + e / TX;
+    if (gx >= I.nx || gy >= I.ny) continue;
     const long long c = (long long)gy * I.nx + gx;
-    const T* Si = slot_tab[s] + 4 * I.cell_off;
     const double r = (double)Si[c], mx = (double)Si[cells + c], my = (double)Si[2 * cells + c];
     const double ek = 0.5 * (mx * mx + my * my) / r;
     const double a = ek - (I.ek0 ? I.ek0[c] : 0.0);
-    ke = ek;
-    pap = a * a;
+    ke += ek;
+    pap += a * a;
     if (ek_out) ek_out[I.cell_off + c] = ek;
     if (lamA) {
       const double wgt = I.objective == 1 ? 2.0 * a * I.dA : I.dA;
-      const double u = mx / r, v = my / r;
-      T* Li = ((nstep[tl.x] & 1) ? lamB : lamA) + 4 * I.cell_off;
-      Li[c] = (T)(-wgt * 0.5 * (u * u + v * v));
+      const double u = mx / r, vv = my / r;
+      T* Li = ((ns & 1) ? lamB : lamA) + 4 * I.cell_off;
+      Li[c] = (T)(-wgt * 0.5 * (u * u + vv * vv));
       Li[cells + c] = (T)(wgt * u);
-      Li[2 * cells + c] = (T)(wgt * v);
+      Li[2 * cells + c] = (T)(wgt * vv);
       Li[3 * cells + c] = T(0);
     }
   }
@@ -531,9 +543,36 @@ __global__ void __launch_bounds__(NTH) k_objective(const InstDev* __restrict__ i
   }
 }
 
+// dJ/dv from dJ/dU0 (transpose of k_inject).
+template <class T>
+__global__ void __launch_bounds__(NTH) k_grad(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,
+                                              const T* __restrict__ lam, const double* __restrict__ v,
+                                              double* __restrict__ g) {
+  const int4 tl = tiles[blockIdx.x];
+  const InstDev& I = insts[tl.x];
+  const long long cells = (long long)I.nx * I.ny;
+  const T* Li = lam + 4 * I.cell_off;
+  const double* vi = v + I.v_off;
+  double* gi = g + I.v_off;
+  for (int e = threadIdx.x; e < TX * TY; e += NTH) {
+    const int gx = tl.y + e % TX, gy = tl.z + e / TX;
+    if (gx >= I.nx || gy >= I.ny) continue;
+    const long long c = (long long)gy * I.nx + gx;
+    const double r0 = I.rho0[gy];
+    const double lE = (double)Li[3 * cells + c];
+    if (I.ncomp == 2) {
+      gi[c] = r0 * ((double)Li[cells + c] + vi[c] * lE);
+      gi[cells + c] = r0 * ((double)Li[2 * cells + c] + vi[cells + c] * lE);
+    } else {
+      gi[c] = r0 * ((double)Li[2 * cells + c] + vi[c] * lE);
+    }
+  }
+}
+
 #ifdef RT_FIELD_KERNELS
-// out[inst*width + w] = scale_inst * sum of partials[t*width + w] over the
-// instance's tiles, summed in a fixed order. One block per instance.
+// out[inst*width + w] = sum of partials[t*width + w] over the instance's
+// tiles (times dA if scale_by_dA), summed in a fixed order. One block per
+// instance.
 __global__ void __launch_bounds__(NTH) k_finalize(const InstDev* __restrict__ insts, const double* __restrict__ partials,
                                                   int width, int scale_by_dA, double* __restrict__ out) {
   __shared__ double red[NTH / 32];
@@ -546,37 +585,8 @@ __global__ void __launch_bounds__(NTH) k_finalize(const InstDev* __restrict__ in
   }
 }
 
-#endif  // RT_FIELD_KERNELS
-
-// dJ/dv from dJ/dU0 (transpose of k_inject).
-template <class T>
-__global__ void __launch_bounds__(NTH) k_grad(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,
-                                              const T* __restrict__ lam, const double* __restrict__ v,
-                                              double* __restrict__ g) {
-  const int4 tl = tiles[blockIdx.x];
-  const InstDev& I = insts[tl.x];
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int gx = tl.y + tx, gy = tl.z + ty;
-  if (gx >= I.nx || gy >= I.ny) return;
-  const long long cells = (long long)I.nx * I.ny;
-  const long long c = (long long)gy * I.nx + gx;
-  const T* Li = lam + 4 * I.cell_off;
-  const double r0 = I.rho0[gy];
-  const double lE = (double)Li[3 * cells + c];
-  const double* vi = v + I.v_off;
-  double* gi = g + I.v_off;
-  if (I.ncomp == 2) {
-    gi[c] = r0 * ((double)Li[cells + c] + vi[c] * lE);
-    gi[cells + c] = r0 * ((double)Li[2 * cells + c] + vi[cells + c] * lE);
-  } else {
-    gi[c] = r0 * ((double)Li[2 * cells + c] + vi[c] * lE);
-  }
-}
-
-#ifdef RT_FIELD_KERNELS
 // Per-tile partial sums over perturbation fields: MODE 0: C(a) / dA =
 // sum rho0 a^2 / 2 (Eq. constraint without the cell area); MODE 1: <a, b>.
-// partials[t] holds tile t's sum.
 template <int MODE>
 __global__ void __launch_bounds__(NTH) k_field_reduce(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,
                                                       const double* __restrict__ a, const double* __restrict__ b,
@@ -584,11 +594,11 @@ __global__ void __launch_bounds__(NTH) k_field_reduce(const InstDev* __restrict_
   __shared__ double red[NTH / 32];
   const int4 tl = tiles[blockIdx.x];
   const InstDev& I = insts[tl.x];
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int gx = tl.y + tx, gy = tl.z + ty;
+  const long long cells = (long long)I.nx * I.ny;
   double s = 0.0;
-  if (gx < I.nx && gy < I.ny) {
-    const long long cells = (long long)I.nx * I.ny;
+  for (int e = threadIdx.x; e < TX * TY; e += NTH) {
+    const int gx = tl.y + e % TX, gy = tl.z + e / TX;
+    if (gx >= I.nx || gy >= I.ny) continue;
     const long long c = (long long)gy * I.nx + gx;
     for (int k = 0; k < I.ncomp; ++k) {
       const double x = a[I.v_off + k * cells + c];
@@ -607,17 +617,18 @@ __global__ void __launch_bounds__(NTH) k_field_axpby(const InstDev* __restrict__
                                                      const double* __restrict__ b) {
   const int4 tl = tiles[blockIdx.x];
   const InstDev& I = insts[tl.x];
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int gx = tl.y + tx, gy = tl.z + ty;
-  if (gx >= I.nx || gy >= I.ny) return;
   const long long cells = (long long)I.nx * I.ny;
-  const long long c = (long long)gy * I.nx + gx;
   const double al = alpha[tl.x], be = beta ? beta[tl.x] : 0.0;
-  for (int k = 0; k < I.ncomp; ++k) {
-    const long long idx = I.v_off + k * cells + c;
-    double x = al * a[idx];
-    if (b) x = x + be * b[idx];
-    out[idx] = x;
+  for (int e = threadIdx.x; e < TX * TY; e += NTH) {
+    const int gx = tl.y + e % TX, gy = tl.z + e / TX;
+    if (gx >= I.nx || gy >= I.ny) continue;
+    const long long c = (long long)gy * I.nx + gx;
+    for (int k = 0; k < I.ncomp; ++k) {
+      const long long idx = I.v_off + k * cells + c;
+      double x = al * a[idx];
+      if (b) x = x + be * b[idx];
+      out[idx] = x;
+    }
   }
 }
 
@@ -627,15 +638,16 @@ __global__ void __launch_bounds__(NTH) k_localise(const InstDev* __restrict__ in
                                                   double h_loc, double* __restrict__ v) {
   const int4 tl = tiles[blockIdx.x];
   const InstDev& I = insts[tl.x];
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int gx = tl.y + tx, gy = tl.z + ty;
-  if (gx >= I.nx || gy >= I.ny) return;
   const long long cells = (long long)I.nx * I.ny;
-  const long long c = (long long)gy * I.nx + gx;
-  const double y = I.y0 + (gy + 0.5) * I.dy;
-  const double d = y - I.y_int;
-  const double env = exp(-(d * d) / (2.0 * h_loc * h_loc));
-  for (int k = 0; k < I.ncomp; ++k) v[I.v_off + k * cells + c] *= env;
+  for (int e = threadIdx.x; e < TX * TY; e += NTH) {
+    const int gx = tl.y + e % TX, gy = tl.z + e / TX;
+    if (gx >= I.nx || gy >= I.ny) continue;
+    const long long c = (long long)gy * I.nx + gx;
+    const double y = I.y0 + (gy + 0.5) * I.dy;
+    const double d = y - I.y_int;
+    const double env = exp(-(d * d) / (2.0 * h_loc * h_loc));
+    for (int k = 0; k < I.ncomp; ++k) v[I.v_off + k * cells + c] *= env;
+  }
 }
 #endif  // RT_FIELD_KERNELS
 

@@ -1,5 +1,6 @@
 // rt_kernels_f32.cu -- FP32-state instantiation of the kernels (compiled with
-// FMA contraction enabled; reductions stay FP64).
+// FMA contraction and fast approximate division / square root; reductions
+// stay FP64).
 #include "rt_launch_impl.cuh"
 
 namespace rt {

@@ -10,7 +10,7 @@ namespace rt {
 
 template <class T>
 cudaError_t launch_inject(const InstDev* insts, const int4* tiles, int ntiles, const double* v, T* U,
-                          const RunDev& run, cudaStream_t s);
+                          const RunDev& run, int record, cudaStream_t s);
 // mode: 0 CFL control, 1 replay counting steps, 2 replay (recompute)
 template <class T>
 cudaError_t launch_stage(int stage, int mode, const InstDev* insts, const int4* tiles, int ntiles, const T* src,

@@ -9,21 +9,21 @@ namespace rt {
 
 template <class T>
 cudaError_t launch_inject(const InstDev* insts, const int4* tiles, int ntiles, const double* v, T* U,
-                          const RunDev& run, cudaStream_t s) {
-  k_inject<T><<<ntiles, NTH, 0, s>>>(insts, tiles, v, U, run);
+                          const RunDev& run, int record, cudaStream_t s) {
+  k_inject<T><<<ntiles, NTH, 0, s>>>(insts, tiles, v, U, run, record);
   return cudaGetLastError();
 }
 
 template <class T>
 cudaError_t launch_stage(int stage, int mode, const InstDev* insts, const int4* tiles, int ntiles, const T* src,
                          const T* base, T* dst, const RunDev& run, int n, cudaStream_t s) {
-  if (stage == 1) {
-    if (mode == 0) k_stage<T, 1, 0><<<ntiles, NTH, 0, s>>>(insts, tiles, src, base, dst, run, n);
-    else k_stage<T, 1, 2><<<ntiles, NTH, 0, s>>>(insts, tiles, src, base, dst, run, n);
+  const size_t sm = ST_SMEM_ELEMS * sizeof(T);
+  if (stage == 1) {  // stage 1 reads the recorded step constants in every mode
+    k_stage<T, 1, 2><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
   } else {
-    if (mode == 0) k_stage<T, 2, 0><<<ntiles, NTH, 0, s>>>(insts, tiles, src, base, dst, run, n);
-    else if (mode == 1) k_stage<T, 2, 1><<<ntiles, NTH, 0, s>>>(insts, tiles, src, base, dst, run, n);
-    else k_stage<T, 2, 2><<<ntiles, NTH, 0, s>>>(insts, tiles, src, base, dst, run, n);
+    if (mode == 0) k_stage<T, 2, 0><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
+    else if (mode == 1) k_stage<T, 2, 1><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
+    else k_stage<T, 2, 2><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
   }
   return cudaGetLastError();
 }
@@ -54,12 +54,19 @@ cudaError_t launch_grad(const InstDev* insts, const int4* tiles, int ntiles, con
 
 template <class T>
 cudaError_t configure_kernels() {
-  return cudaFuncSetAttribute(k_adjoint<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(ADJ_SMEM_ELEMS * sizeof(T)));
+  const int st = (int)(ST_SMEM_ELEMS * sizeof(T));
+  cudaError_t e = cudaFuncSetAttribute(k_stage<T, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, st);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage<T, 2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, st);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage<T, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, st);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage<T, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, st);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adjoint<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(ADJ_SMEM_ELEMS * sizeof(T)));
+  return e;
 }
 
 #define RT_INSTANTIATE_LAUNCHERS(T)                                                                              \
-  template cudaError_t launch_inject<T>(const InstDev*, const int4*, int, const double*, T*, const RunDev&,       \
+  template cudaError_t launch_inject<T>(const InstDev*, const int4*, int, const double*, T*, const RunDev&, int,  \
                                         cudaStream_t);                                                           \
   template cudaError_t launch_stage<T>(int, int, const InstDev*, const int4*, int, const T*, const T*, T*,        \
                                        const RunDev&, int, cudaStream_t);                                        \

@@ -266,31 +266,37 @@ struct Plan {
   int slots = 0;  // pool slots available to kind 2
 };
 
+// Inject v into the base state of every instance (k_inject), which also
+// records dt of step 0. A fresh run (not a replay) first clears the dt
+// records, so that steps no CTA reaches stay inactive.
 template <class T>
-rt_status inject(rt_ctx* c, const double* d_v, void* U0) {
-  CU(cudaMemsetAsync(c->run.wmin, 0xff, 2 * c->n_inst * sizeof(unsigned long long), c->stream));
+rt_status inject(rt_ctx* c, const double* d_v, void* U0, bool replay = false) {
+  if (!replay) {
+    CU(cudaMemsetAsync(c->run.dtrec, 0, (size_t)c->n_inst * c->opt.max_steps * sizeof(double), c->stream));
+    CU(cudaMemsetAsync(c->run.dtc, 0, (size_t)c->n_inst * c->opt.max_steps * sizeof(rt::StepC<T>), c->stream));
+  }
+  CU(cudaMemsetAsync(c->run.wmin, 0xff, c->n_inst * sizeof(unsigned long long), c->stream));
+  CU(cudaMemsetAsync(c->run.counter, 0, c->n_inst * sizeof(unsigned int), c->stream));
   CU(cudaMemsetAsync(c->run.status, 0, c->n_inst * sizeof(int), c->stream));
-  CU(rt::launch_inject<T>(c->d_inst, c->d_tiles, c->ntiles, d_v, slotp<T>(U0), c->run, c->stream));
+  CU(rt::launch_inject<T>(c->d_inst, c->d_tiles, c->ntiles, d_v, slotp<T>(U0), c->run, replay ? 0 : 1, c->stream));
   ++c->launches;
   return RT_OK;
 }
 
 // Estimated step count: fixed-step instances give theirs; horizon instances
-// T / (cfl * min crossing time of the initial state).
+// T / dt0, with dt0 the first step the inject kernel recorded.
 rt_status estimate_steps(rt_ctx* c, int* n_est) {
-  std::vector<unsigned long long> w(c->n_inst);
-  CU(cudaMemcpyAsync(w.data(), c->run.wmin, c->n_inst * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                     c->stream));
+  std::vector<double> dt0(c->n_inst);
+  CU(cudaMemcpy2DAsync(dt0.data(), sizeof(double), c->run.dtrec, (size_t)c->opt.max_steps * sizeof(double),
+                       sizeof(double), c->n_inst, cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
   long long best = 1;
   for (int i = 0; i < c->n_inst; ++i) {
     if (!c->h_inst[i].enabled) continue;
     const rt_problem& P = c->prob[i];
     if (P.nsteps > 0) { best = std::max<long long>(best, P.nsteps); continue; }
-    double wm;
-    std::memcpy(&wm, &w[i], sizeof(double));
-    if (!(wm > 0.0) || !(wm < kMaxFinite)) continue;
-    best = std::max<long long>(best, (long long)std::ceil(P.T / (P.cfl * wm)));
+    if (!(dt0[i] > 0.0) || !(dt0[i] < kMaxFinite)) continue;
+    best = std::max<long long>(best, (long long)std::ceil(P.T / dt0[i]));
   }
   *n_est = (int)std::min<long long>(best, c->opt.max_steps);
   return RT_OK;
@@ -413,7 +419,7 @@ rt_status forward_impl(rt_ctx* c, const double* d_v, int flags, double* J_out, d
   if (replay && !c->have_run) return fail(c, RT_ESTATE, "RT_REPLAY_DT needs a previous run");
   const int replay_steps = c->last_steps;
   Plan plan;
-  CHK(inject<T>(c, d_v, c->sA));
+  CHK(inject<T>(c, d_v, c->sA, replay));
   int n_est = replay_steps;
   if (!replay) CHK(estimate_steps(c, &n_est));
   int n_done = 0;
@@ -763,6 +769,11 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
     I.g_y = P.g_y;
     I.cfl = P.cfl;
     I.T = P.T;
+    I.gamma_f = (float)I.gamma;
+    I.gm1_f = (float)I.gm1;
+    I.g_f = (float)I.g_y;
+    I.dx_f = (float)I.dx;
+    I.dy_f = (float)I.dy;
     I.tile_begin = (int)c->h_tiles.size();
     for (int y0 = 0; y0 < P.ny; y0 += rt::TILE_Y)
       for (int x0 = 0; x0 < P.nx; x0 += rt::TILE_X) c->h_tiles.push_back(make_int4(i, x0, y0, 0));
@@ -800,7 +811,11 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
   INIT_CU(cudaMalloc(&c->run.dtrec, (size_t)N * c->opt.max_steps * sizeof(double)));
   INIT_CU(cudaMalloc(&c->run.t, N * sizeof(double)));
   INIT_CU(cudaMalloc(&c->run.nstep, N * sizeof(int)));
-  INIT_CU(cudaMalloc(&c->run.wmin, 2 * N * sizeof(unsigned long long)));
+  INIT_CU(cudaMalloc(&c->run.wmin, N * sizeof(unsigned long long)));
+  INIT_CU(cudaMalloc(&c->run.counter, N * sizeof(unsigned int)));
+  INIT_CU(cudaMalloc(&c->run.dtc, (size_t)N * c->opt.max_steps * 4 * c->esz));
+  INIT_CU(cudaMemset(c->run.dtc, 0, (size_t)N * c->opt.max_steps * 4 * c->esz));
+  INIT_CU(cudaMemset(c->run.dtrec, 0, (size_t)N * c->opt.max_steps * sizeof(double)));
   INIT_CU(cudaMalloc(&c->run.status, N * sizeof(int)));
   INIT_CU(cudaMalloc(&c->run.bad_cell, N * sizeof(long long)));
   INIT_CU(cudaMalloc(&c->d_partials, (size_t)c->ntiles * 2 * sizeof(double)));
@@ -828,7 +843,7 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
 void rt_destroy(rt_ctx* c) {
   if (!c) return;
   void* ptrs[] = {c->d_inst, c->d_tiles, c->d_base, c->d_ek0, c->d_ek, c->sA, c->sB, c->sU1, c->lA, c->lB,
-                  c->l1, c->d_tab, c->run.dtrec, c->run.t, c->run.nstep, c->run.wmin, c->run.status,
+                  c->l1, c->d_tab, c->run.dtrec, c->run.dtc, c->run.counter, c->run.t, c->run.nstep, c->run.wmin, c->run.status,
                   c->run.bad_cell, c->d_partials, c->d_sums, c->d_scal, c->d_v, c->d_g, c->d_w1, c->d_w2,
                   c->d_w3, c->d_w4};
   for (void* p : ptrs)
