@@ -291,9 +291,13 @@ def run_profile_case(args):
     probs = [I.single_256().replace(T=0.01) for _ in range(nb)]
     with rt.Context(probs, precision=rt.RT_FP32_STATE, ckpt=rt.RT_CKPT_STORE_ALL) as ctx:
         v = ctx.project(I.gaussian_batch(range(nb), 2, NY, NX).reshape(-1), DELTA, to_budget=True)
-        for k in range(2):
+        for k in range(3):
+            ctx.set_kernel_timing(1 if k == 2 else 0)
             _, _, st = ctx.gradient(v)
-            print(json.dumps({"profile_case": k, **st}), flush=True)
+            rec = {"profile_case": k, **st}
+            if k == 2:
+                rec["kernel_ms"] = {name: t[0] for name, t in ctx.kernel_times().items()}
+            print(json.dumps(rec), flush=True)
     return 0
 
 

@@ -61,6 +61,7 @@ enum { RT_LIM_MINMOD = 0, RT_LIM_MC = 1, RT_LIM_NONE = 2 };
 enum { RT_OBJ_KE = 0, RT_OBJ_EK_ANOMALY_L2 = 1 };
 enum { RT_FP64 = 0, RT_FP32_STATE = 1 };
 enum { RT_CKPT_AUTO = 0, RT_CKPT_STORE_ALL = 1, RT_CKPT_SQRT = 2 };
+enum { RT_STAGE_AUTO = 0, RT_STAGE_SWEEP = 1, RT_STAGE_TILE = 2 };
 
 /* flags for rt_forward / rt_gradient / rt_constraint / rt_project */
 enum { RT_DEVICE_PTRS = 1, RT_REPLAY_DT = 2 };
@@ -91,6 +92,8 @@ typedef struct {
   int ckpt;                 /* RT_CKPT_AUTO | RT_CKPT_STORE_ALL | RT_CKPT_SQRT */
   double ckpt_hbm_cap_bytes;/* cap on checkpoint + segment memory; 0 = 60% of free memory */
   int max_steps;            /* upper bound on steps per run (sizes the dt record); 0 = 200000 */
+  int stage_kernel;         /* RT_STAGE_AUTO (time both at rt_init, keep the faster),
+                               RT_STAGE_SWEEP or RT_STAGE_TILE; both give identical values */
 } rt_options;
 
 typedef struct {
@@ -168,6 +171,13 @@ rt_status rt_get_dt(rt_ctx* ctx, int inst, double* out, int max_n, int* n_out);
  * launch (ms), number of samples, and number of launches (any array may be
  * NULL). */
 rt_status rt_set_kernel_timing(rt_ctx* ctx, int every);
+
+/* Stage-kernel variant in use (RT_STAGE_SWEEP or RT_STAGE_TILE; no
+ * counterpart in the paper). With RT_STAGE_AUTO, rt_init timed four CFL
+ * steps of the unperturbed batch with each variant and kept the faster;
+ * tuned_ms (nullable, [2]) receives those mean times per step (sweep, tile),
+ * or zeros when the variant was fixed by the options. */
+int rt_stage_kernel(const rt_ctx* ctx, double* tuned_ms);
 rt_status rt_kernel_times(rt_ctx* ctx, double* mean_ms, long long* samples, long long* launches);
 
 typedef struct {

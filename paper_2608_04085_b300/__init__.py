@@ -24,6 +24,7 @@ RT_LIM_MINMOD, RT_LIM_MC, RT_LIM_NONE = 0, 1, 2
 RT_OBJ_KE, RT_OBJ_EK_ANOMALY_L2 = 0, 1
 RT_FP64, RT_FP32_STATE = 0, 1
 RT_CKPT_AUTO, RT_CKPT_STORE_ALL, RT_CKPT_SQRT = 0, 1, 2
+RT_STAGE_AUTO, RT_STAGE_SWEEP, RT_STAGE_TILE = 0, 1, 2
 RT_DEVICE_PTRS, RT_REPLAY_DT = 1, 2
 
 _STATUS = {1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENONFINITE", 5: "RT_ETIMEOUT",
@@ -32,7 +33,7 @@ _STATUS = {1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENONFINITE", 5:
 #: every entry point declared in include/rt_cnop.h
 EXPORTS = ("rt_init", "rt_destroy", "rt_last_error", "rt_num_instances", "rt_field_offset",
            "rt_field_size", "rt_field_total", "rt_forward", "rt_gradient", "rt_constraint",
-           "rt_project", "rt_get_state", "rt_get_dt", "rt_set_kernel_timing", "rt_kernel_times",
+           "rt_project", "rt_get_state", "rt_get_dt", "rt_set_kernel_timing", "rt_kernel_times", "rt_stage_kernel",
            "cnop_solve", "rt_objective_noalloc")
 
 
@@ -58,7 +59,8 @@ class RtProblem(ctypes.Structure):
 
 class RtOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("ckpt", ctypes.c_int),
-                ("ckpt_hbm_cap_bytes", ctypes.c_double), ("max_steps", ctypes.c_int)]
+                ("ckpt_hbm_cap_bytes", ctypes.c_double), ("max_steps", ctypes.c_int),
+                ("stage_kernel", ctypes.c_int)]
 
 
 class RtRunStats(ctypes.Structure):
@@ -118,6 +120,8 @@ def library():
         L.rt_get_state.restype = ip
         L.rt_get_dt.argtypes = [vp, ip, dp, ip, ctypes.POINTER(ip)]
         L.rt_get_dt.restype = ip
+        L.rt_stage_kernel.argtypes = [vp, dp]
+        L.rt_stage_kernel.restype = ip
         L.rt_set_kernel_timing.argtypes = [vp, ip]
         L.rt_set_kernel_timing.restype = ip
         llp = ctypes.POINTER(ctypes.c_longlong)
@@ -164,13 +168,13 @@ class Context:
     """A batch of RT instances on the current CUDA device (see rt_init)."""
 
     def __init__(self, problems, precision=RT_FP64, ckpt=RT_CKPT_AUTO, ckpt_cap_bytes=0.0, max_steps=0,
-                 stream=None):
+                 stream=None, stage_kernel=RT_STAGE_AUTO):
         L = library()
         if not isinstance(problems, (list, tuple)):
             problems = [problems]
         self.problems = list(problems)
         arr = (RtProblem * len(problems))(*[make_problem(w) for w in problems])
-        opt = RtOptions(precision, ckpt, float(ckpt_cap_bytes), int(max_steps))
+        opt = RtOptions(precision, ckpt, float(ckpt_cap_bytes), int(max_steps), int(stage_kernel))
         if stream is None:
             stream = self._torch_stream()
         self._stream = stream
@@ -284,6 +288,12 @@ class Context:
         out = np.zeros(max(n.value, 1))
         self._check(library().rt_get_dt(self._h, inst, _dptr(out), n.value, ctypes.byref(n)))
         return out[:n.value]
+
+    def stage_kernel(self):
+        """(variant in use, {"sweep": ms/step, "tile": ms/step} from the autotuner)."""
+        t = np.zeros(2)
+        v = library().rt_stage_kernel(self._h, _dptr(t))
+        return v, {"sweep": t[0], "tile": t[1]}
 
     def set_kernel_timing(self, every):
         """Sample CUDA-event timings of every `every`-th time-step kernel launch."""

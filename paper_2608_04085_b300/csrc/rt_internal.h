@@ -13,6 +13,16 @@ constexpr int TILE_X = 32;
 constexpr int TILE_Y = 16;
 constexpr int TILE_THREADS = 256;
 
+// Strip of cells advanced by one warp of the sweep kernels: STRIP_W useful
+// columns (the warp's 32 lanes also cover 2 halo columns on each side) by
+// STRIP_H rows, marched row by row. STRIP_WARPS strips per CTA.
+constexpr int STRIP_W = 28;
+constexpr int STRIP_H = 16;
+constexpr int STRIP_WARPS = 4;
+
+// Stage-kernel variants (same values bit for bit, different schedules).
+enum { STAGE_SWEEP = 1, STAGE_TILE = 2 };
+
 // Per-instance constants, resident on the device (one entry per instance).
 // State slots hold every instance back to back: instance i's conserved plane
 // k (rho, m_x, m_y, E) starts at slot + 4*cell_off + k*nx*ny, row-major with
@@ -26,6 +36,7 @@ struct InstDev {
   long long cell_off;
   long long v_off;
   int tile_begin, tile_end;  // this instance's tiles in the tile list
+  int strip_begin, strip_end;  // this instance's strips in the sweep list
   double dx, dy, dA;
   double y0, y_int;          // domain bottom and interface height
   double gamma, gm1, g_y;

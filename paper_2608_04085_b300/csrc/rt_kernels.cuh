@@ -9,10 +9,11 @@
 // and the host never reads dt inside the time loop.
 //
 //   k_inject     Sec. 3.1: U0 = (rho0, rho0 v, p0/(gamma-1) + rho0|v|^2/2), first CFL minimum
-//   k_stage<1>   U1 = U + dt L(U)                       (SSP-RK2 stage 1)
-//   k_stage<2>   U' = U/2 + (U1 + dt L(U1))/2           (stage 2) + CFL minimum of U'
+//   k_stage_*<1> U1 = U + dt L(U)                       (SSP-RK2 stage 1)
+//   k_stage_*<2> U' = U/2 + (U1 + dt L(U1))/2           (stage 2) + CFL minimum of U'
 //                L(U): finite-volume divergence of PLM+HLLC fluxes + gravity
-//                source (Sec. 2.1 Eqs. mass/momentum/energy, Sec. 2.3).
+//                source (Sec. 2.1 Eqs. mass/momentum/energy, Sec. 2.3);
+//                a warp-sweep variant and a shared-memory tile variant.
 //   k_adjoint    out = kap + (d(dt L)/dU)^T kap + escale*E, kap = kscale*K: the
 //                transposed stage map (Sec. 3.4, exact discrete gradient)
 //   k_objective  J = sum e_k dA and sum (e_k - e_k0)^2 dA (Eqs. ke, objective),
@@ -34,9 +35,16 @@ constexpr int ROWS_PER_PASS = NTH / TX;  // rows covered by one pass of the bloc
 static_assert(TX == 32, "one warp per tile row");
 static_assert(TY % ROWS_PER_PASS == 0, "tile rows must be a multiple of the rows per pass");
 
+// Periodic x index; one correction covers every tile offset when nx is at
+// least the halo width, the modulo handles the rest.
 __device__ __forceinline__ int wrap_x(int gx, int nx) {
-  gx %= nx;
-  return gx < 0 ? gx + nx : gx;
+  if (gx < 0) gx += nx;
+  else if (gx >= nx) gx -= nx;
+  if (gx < 0 || gx >= nx) {
+    gx %= nx;
+    if (gx < 0) gx += nx;
+  }
+  return gx;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -227,17 +235,227 @@ __device__ __forceinline__ void load_prim(const T* __restrict__ Ui, const InstDe
 }
 
 // ------------------------------------------------------------------- stage
+// Two variants of one stage kernel compute the same values bit for bit; the
+// runtime's autotuner picks the faster for the batch at hand.
+//
+// Sweep variant: each warp advances one strip of STRIP_W x STRIP_H cells,
+// marching up the rows. Lane L holds column x0 - 2 + L; the y direction keeps
+// a two-row window of primitive states, the y slope of the current row and
+// the flux through the current row's bottom face in registers; the x
+// neighbours come from warp shuffles. Every slope and every face flux is
+// evaluated once; no shared memory, no block barrier.
+//
+// MODE 0: CFL control (the instance's last warp records the next dt, advances
+// t and the step count); MODE 1: replay recorded steps, counting them;
+// MODE 2: replay without touching any run scalar (checkpoint recomputation).
+template <class T>
+__device__ __forceinline__ T shfl_up1(T v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+template <class T>
+__device__ __forceinline__ T shfl_down1(T v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+
+// Conserved values of row r of column gcol as the sweep needs them: the
+// row itself, or for a ghost row the interior row it mirrors (the primitive
+// transform is applied by raw_to_prim). Rows beyond the ghost layers get a
+// harmless placeholder.
+template <class T>
+__device__ __forceinline__ void load_raw(const T* __restrict__ Ui, int nx, int ny, long long cells, int gcol, int r,
+                                         T u[4]) {
+  int sy = r;
+  if (r < 0) sy = -1 - r;
+  else if (r >= ny) sy = 2 * ny - 1 - r;
+  if (sy < 0 || sy >= ny) {
+    u[0] = T(1); u[1] = T(0); u[2] = T(0); u[3] = T(1);
+    return;
+  }
+  const long long c = (long long)sy * nx + gcol;
+  u[0] = Ui[c];
+  u[1] = Ui[cells + c];
+  u[2] = Ui[2 * cells + c];
+  u[3] = Ui[3 * cells + c];
+}
+
+// Primitive state of row r from load_raw's values, with the y boundary
+// applied exactly as load_prim does.
+template <class T>
+__device__ __forceinline__ void raw_to_prim(const T u[4], const InstDev& I, int r, const Phys<T>& P, T W[4]) {
+  cons_to_prim(u[0], u[1], u[2], u[3], P.gm1, W);
+  int side = 0, k = 0;
+  if (r < 0) { side = -1; k = -1 - r; }
+  else if (r >= I.ny) { side = 1; k = r - I.ny; }
+  if (side != 0) {
+    W[2] = -W[2];
+    if (I.bc_y == 1) {
+      const T dyk = (T)((double)(2 * k + 1) * I.dy);
+      if (side < 0) W[3] = W[3] - P.g * W[0] * dyk;
+      else W[3] = W[3] + P.g * W[0] * dyk;
+    }
+  }
+}
+
+template <class T, int STAGE, int MODE>
+__global__ void __launch_bounds__(32 * STRIP_WARPS, 6) k_stage_sweep(const InstDev* __restrict__ insts,
+                                                            const int4* __restrict__ strips, int nstrips,
+                                                            const T* __restrict__ src, const T* __restrict__ base,
+                                                            T* __restrict__ dst, RunDev run, int n) {
+  const int lane = threadIdx.x & 31;
+  const int si = blockIdx.x * STRIP_WARPS + (threadIdx.x >> 5);
+  if (si >= nstrips) return;  // the whole warp leaves; no block-level synchronisation below
+  const int4 st = strips[si];
+  const int inst = st.x;
+  const InstDev& I = insts[inst];
+  const StepC<T> sc = step_const<T>(run, inst, n);
+  if (!(sc.dt > T(0))) return;  // instance inactive at this step (uniform over the warp)
+
+  const Phys<T> P = phys<T>(I);
+  const int nx = I.nx, ny = I.ny, lim = I.limiter;
+  const long long cells = (long long)nx * ny;
+  const T* Si = src + 4 * I.cell_off;
+  const T* Bi = base + 4 * I.cell_off;
+  T* Di = dst + 4 * I.cell_off;
+  const int x0 = st.y, y0 = st.z;
+  const int col = x0 - 2 + lane;
+  const int gcol = wrap_x(col, nx);
+  const bool writer = lane >= 2 && lane < 2 + STRIP_W && col < nx;
+  const int y1 = (y0 + STRIP_H < ny) ? y0 + STRIP_H : ny;
+
+  // prologue: rows y0-2 .. y0+2, y slopes of rows y0-1 and y0, flux through
+  // the bottom face of row y0
+  T Ua[4], Ub[4], U0[4], U1[4], U2[4];
+  load_raw(Si, nx, ny, cells, gcol, y0 - 2, Ua);
+  load_raw(Si, nx, ny, cells, gcol, y0 - 1, Ub);
+  load_raw(Si, nx, ny, cells, gcol, y0, U0);
+  load_raw(Si, nx, ny, cells, gcol, y0 + 1, U1);
+  load_raw(Si, nx, ny, cells, gcol, y0 + 2, U2);
+  T W0[4], W1[4], s_cur[4], Gb[4];
+  {
+    T Wa[4], Wb[4], WL[4], WR[4];
+    raw_to_prim(Ua, I, y0 - 2, P, Wa);
+    raw_to_prim(Ub, I, y0 - 1, P, Wb);
+    raw_to_prim(U0, I, y0, P, W0);
+    raw_to_prim(U1, I, y0 + 1, P, W1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const T s_lo = limited_slope(Wa[q], Wb[q], W0[q], lim);
+      s_cur[q] = limited_slope(Wb[q], W0[q], W1[q], lim);
+      WL[q] = Wb[q] + T(0.5) * s_lo;
+      WR[q] = W0[q] - T(0.5) * s_cur[q];
+    }
+    face_flux_states<T, 1>(WL, WR, P.gamma, P.gm1, Gb);
+  }
+
+  T wmin = T(1e30);
+  bool bad = false;
+  long long badc = 0;
+  for (int j = y0; j < y1; ++j) {
+    // prefetch row j+3 and, for stage 2, the base state of row j
+    T U3[4], B0[4];
+    load_raw(Si, nx, ny, cells, gcol, j + 3, U3);
+    const long long c = (long long)j * nx + col;
+    if (STAGE == 2) {
+      if (writer) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) B0[k] = Bi[k * cells + c];
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) B0[k] = T(0);
+      }
+    }
+    // x face on the left of this lane's cell in row j
+    T Fl[4];
+    {
+      T WL[4], WR[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const T wm = shfl_up1(W0[q]), wp = shfl_down1(W0[q]);
+        const T sx = limited_slope(wm, W0[q], wp, lim);
+        WL[q] = shfl_up1(W0[q] + T(0.5) * sx);
+        WR[q] = W0[q] - T(0.5) * sx;
+      }
+      face_flux_states<T, 0>(WL, WR, P.gamma, P.gm1, Fl);
+    }
+    T Fr[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Fr[q] = shfl_down1(Fl[q]);
+    // y face between rows j and j+1
+    T W2[4], s_next[4], Gt[4];
+    raw_to_prim(U2, I, j + 2, P, W2);
+    {
+      T WL[4], WR[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        s_next[q] = limited_slope(W0[q], W1[q], W2[q], lim);
+        WL[q] = W0[q] + T(0.5) * s_cur[q];
+        WR[q] = W1[q] - T(0.5) * s_next[q];
+      }
+      face_flux_states<T, 1>(WL, WR, P.gamma, P.gm1, Gt);
+    }
+    if (writer) {
+      T o[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        T b = U0[k] + sc.dtdx * (Fl[k] - Fr[k]);
+        b = b + sc.dtdy * (Gb[k] - Gt[k]);
+        if (k == 2) b = b + sc.dt * (U0[0] * P.g);
+        if (k == 3) b = b + sc.dt * (U0[2] * P.g);
+        o[k] = STAGE == 2 ? T(0.5) * B0[k] + T(0.5) * b : b;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) Di[k * cells + c] = o[k];
+      if (STAGE == 2 && MODE == 0) {
+        bool b = false;
+        const T cw = crossing_time<T>(o[0], o[1], o[2], o[3], P, b);
+        if (b) { bad = true; badc = c; } else if (cw < wmin) wmin = cw;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      W0[q] = W1[q];
+      W1[q] = W2[q];
+      U0[q] = U1[q];
+      U1[q] = U2[q];
+      U2[q] = U3[q];
+      s_cur[q] = s_next[q];
+      Gb[q] = Gt[q];
+    }
+  }
+
+  if (STAGE == 2 && MODE == 0) {
+    if (bad) {
+      if (atomicCAS(&run.status[inst], 0, 1) == 0) run.bad_cell[inst] = badc;
+    }
+    const T m = warp_min_t(wmin);
+    if (lane == 0) {
+      if (m > T(0) && m < T(1e30))
+        atomicMin(&run.wmin[inst], (unsigned long long)__double_as_longlong((double)m));
+      __threadfence();
+      const unsigned int nst = (unsigned int)(I.strip_end - I.strip_begin);
+      if (atomicAdd(&run.counter[inst], 1u) + 1u == nst) {
+        run.counter[inst] = 0u;
+        __threadfence();
+        const double dt = run.dtrec[(long long)inst * run.max_steps + n];
+        const double t = run.t[inst];
+        const double tn = I.nsteps > 0 ? t + dt : (dt >= I.T - t ? I.T : t + dt);
+        run.t[inst] = tn;
+        run.nstep[inst] = n + 1;
+        finish_step<T>(I, run, inst, n + 1, tn);
+      }
+    }
+  }
+  if (STAGE == 2 && MODE == 1 && x0 == 0 && y0 == 0 && lane == 0) run.nstep[inst] = n + 1;
+}
+
+// --------------------------------------------------------- stage (tile variant)
 // Shared memory (elements of T): primitive tile with 2 ghost layers, x-face
 // and y-face fluxes.
 constexpr int ST_EX = TX + 4, ST_EY = TY + 4;
 constexpr int ST_NFX = (TX + 1) * TY, ST_NFY = TX * (TY + 1);
 constexpr int ST_SMEM_ELEMS = 4 * ST_EX * ST_EY + 4 * ST_NFX + 4 * ST_NFY;
 
-// MODE 0: CFL control (the instance's last CTA records the next dt, advances
-// t and the step count); MODE 1: replay recorded steps, counting them;
-// MODE 2: replay without touching any run scalar (checkpoint recomputation).
+// Tile variant of the stage kernel: one CTA per 32 x 16 tile, primitive
+// states with 2 ghost layers in shared memory, one thread per face, then one
+// thread per cell for the update. Modes as for the sweep variant.
 template <class T, int STAGE, int MODE>
-__global__ void __launch_bounds__(NTH) k_stage(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,
+__global__ void __launch_bounds__(NTH) k_stage_tile(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,
                                                const T* __restrict__ src, const T* __restrict__ base,
                                                T* __restrict__ dst, RunDev run, int n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -341,21 +559,22 @@ __global__ void __launch_bounds__(NTH) k_stage(const InstDev* __restrict__ insts
 
 // ----------------------------------------------------------------- adjoint
 // Shared memory (elements of T): primitive tile with 3 ghost layers,
-// cotangent tile with 2, and 16 contributions per x face and per y face.
+// cotangent tile with 2, and one face buffer (16 contributions per face)
+// used first by the x faces and then by the y faces.
 constexpr int ADJ_AX = TX + 6, ADJ_AY = TY + 6, ADJ_KX = TX + 4, ADJ_KY = TY + 4;
 constexpr int ADJ_NFX = (TX + 3) * TY, ADJ_NFY = TX * (TY + 3);
-constexpr int ADJ_SMEM_ELEMS = 4 * ADJ_AX * ADJ_AY + 4 * ADJ_KX * ADJ_KY + 16 * ADJ_NFX + 16 * ADJ_NFY;
+constexpr int ADJ_FACES = ADJ_NFX > ADJ_NFY ? ADJ_NFX : ADJ_NFY;
+constexpr int ADJ_SMEM_ELEMS = 4 * ADJ_AX * ADJ_AY + 4 * ADJ_KX * ADJ_KY + 16 * ADJ_FACES;
 
 template <class T>
-__global__ void __launch_bounds__(NTH) k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,
-                                                 const T* __restrict__ U, const T* __restrict__ K, T kscale,
-                                                 const T* __restrict__ E, T escale, T* __restrict__ out,
-                                                 RunDev run, int n) {
+__global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 3 : 1)
+k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, const T* __restrict__ U,
+          const T* __restrict__ K, T kscale, const T* __restrict__ E, T escale, T* __restrict__ out, RunDev run,
+          int n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sW = reinterpret_cast<T*>(smem_raw);  // [4][AY][AX]
   T* sK = sW + 4 * ADJ_AX * ADJ_AY;        // [4][KY][KX]
-  T* sBx = sK + 4 * ADJ_KX * ADJ_KY;       // [16][NFX]
-  T* sBy = sBx + 16 * ADJ_NFX;             // [16][NFY]
+  T* sB = sK + 4 * ADJ_KX * ADJ_KY;        // [16][ADJ_FACES]
   const int4 tl = tiles[blockIdx.x];
   const int inst = tl.x;
   const InstDev& I = insts[inst];
@@ -386,67 +605,78 @@ __global__ void __launch_bounds__(NTH) k_adjoint(const InstDev* __restrict__ ins
   }
   __syncthreads();
 
-  // every face once: x face fx of row fy is the left face of tile cell fx-1;
-  // y face fy of column fx is the bottom face of tile row fy-1 (global y0+fy-1)
-  for (int f = threadIdx.x; f < ADJ_NFX + ADJ_NFY; f += NTH) {
+  const int tx = threadIdx.x % TX;
+  constexpr int PASSES = TY / ROWS_PER_PASS;
+  T bW[PASSES][4];
+#pragma unroll
+  for (int pass = 0; pass < PASSES; ++pass)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) bW[pass][q] = T(0);
+
+  // x faces: fx of row fy is the left face of tile cell fx-1 (cells fx-3 .. fx)
+  for (int f = threadIdx.x; f < ADJ_NFX; f += NTH) {
+    const int fy = f / (TX + 3), fx = f - fy * (TX + 3);
+    T w[4][4], mu[4], o[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) w[p][q] = sW[(q * ADJ_AY + fy + 3) * ADJ_AX + fx + p];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      mu[q] = sc.dtdx * (sK[(q * ADJ_KY + fy + 2) * ADJ_KX + fx + 1] - sK[(q * ADJ_KY + fy + 2) * ADJ_KX + fx]);
+    face_vjp<T, 0>(w, mu, lim, P.gamma, P.gm1, o);
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sB[(p * 4 + q) * ADJ_FACES + f] = o[p][q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int pass = 0; pass < PASSES; ++pass) {
+    const int ty = threadIdx.x / TX + pass * ROWS_PER_PASS;
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) bW[pass][q] += sB[(p * 4 + q) * ADJ_FACES + ty * (TX + 3) + tx + 3 - p];
+  }
+  __syncthreads();
+
+  // y faces: fy of column fx is the bottom face of tile row fy-1 (global face y0+fy-1)
+  for (int f = threadIdx.x; f < ADJ_NFY; f += NTH) {
+    const int fy = f / TX, fx = f - fy * TX;
+    const int gf = y0 + fy - 1;
     T o[4][4];
-    if (f < ADJ_NFX) {
-      const int fy = f / (TX + 3), fx = f - fy * (TX + 3);
+    if (gf >= 0 && gf <= ny) {
       T w[4][4], mu[4];
 #pragma unroll
       for (int p = 0; p < 4; ++p)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) w[p][q] = sW[(q * ADJ_AY + fy + 3) * ADJ_AX + fx + p];
+        for (int q = 0; q < 4; ++q) w[p][q] = sW[(q * ADJ_AY + fy + p) * ADJ_AX + fx + 3];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        mu[q] = sc.dtdx * (sK[(q * ADJ_KY + fy + 2) * ADJ_KX + fx + 1] - sK[(q * ADJ_KY + fy + 2) * ADJ_KX + fx]);
-      face_vjp<T, 0>(w, mu, lim, P.gamma, P.gm1, o);
-#pragma unroll
-      for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) sBx[(p * 4 + q) * ADJ_NFX + f] = o[p][q];
+        mu[q] = sc.dtdy * (sK[(q * ADJ_KY + fy + 1) * ADJ_KX + fx + 2] - sK[(q * ADJ_KY + fy) * ADJ_KX + fx + 2]);
+      face_vjp<T, 1>(w, mu, lim, P.gamma, P.gm1, o);
     } else {
-      const int g = f - ADJ_NFX;
-      const int fy = g / TX, fx = g - fy * TX;
-      const int gf = y0 + fy - 1;
-      if (gf >= 0 && gf <= ny) {
-        T w[4][4], mu[4];
-#pragma unroll
-        for (int p = 0; p < 4; ++p)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) w[p][q] = sW[(q * ADJ_AY + fy + p) * ADJ_AX + fx + 3];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          mu[q] = sc.dtdy * (sK[(q * ADJ_KY + fy + 1) * ADJ_KX + fx + 2] - sK[(q * ADJ_KY + fy) * ADJ_KX + fx + 2]);
-        face_vjp<T, 1>(w, mu, lim, P.gamma, P.gm1, o);
-      } else {
-#pragma unroll
-        for (int p = 0; p < 4; ++p)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) o[p][q] = T(0);
-      }
 #pragma unroll
       for (int p = 0; p < 4; ++p)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) sBy[(p * 4 + q) * ADJ_NFY + g] = o[p][q];
+        for (int q = 0; q < 4; ++q) o[p][q] = T(0);
     }
-  }
-  __syncthreads();
-
-  const int tx = threadIdx.x % TX;
-#pragma unroll
-  for (int pass = 0; pass < TY / ROWS_PER_PASS; ++pass) {
-    const int ty = threadIdx.x / TX + pass * ROWS_PER_PASS;
-    const int gx = x0 + tx, gy = y0 + ty;
-    T bW[4] = {T(0), T(0), T(0), T(0)};
-    // face f touches tile cells f-3 .. f (position p = cell - f + 3)
 #pragma unroll
     for (int p = 0; p < 4; ++p)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        bW[q] += sBx[(p * 4 + q) * ADJ_NFX + ty * (TX + 3) + tx + 3 - p];
-        bW[q] += sBy[(p * 4 + q) * ADJ_NFY + (ty + 3 - p) * TX + tx];
-      }
+      for (int q = 0; q < 4; ++q) sB[(p * 4 + q) * ADJ_FACES + f] = o[p][q];
+  }
+  __syncthreads();
+
+#pragma unroll
+  for (int pass = 0; pass < PASSES; ++pass) {
+    const int ty = threadIdx.x / TX + pass * ROWS_PER_PASS;
+    const int gx = x0 + tx, gy = y0 + ty;
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) bW[pass][q] += sB[(p * 4 + q) * ADJ_FACES + (ty + 3 - p) * TX + tx];
     // ghost rows of the y boundary fold back onto the cells they mirror
     for (int side = 0; side < 2; ++side) {
       int k, gly;
@@ -457,27 +687,28 @@ __global__ void __launch_bounds__(NTH) k_adjoint(const InstDev* __restrict__ ins
       for (int fy = f_lo; fy <= f_hi; ++fy) {
         const int p = gly - fy + 3;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) gq[q] += sBy[(p * 4 + q) * ADJ_NFY + fy * TX + tx];
+        for (int q = 0; q < 4; ++q) gq[q] += sB[(p * 4 + q) * ADJ_FACES + fy * TX + tx];
       }
-      bW[0] += gq[0];
-      bW[1] += gq[1];
-      bW[2] -= gq[2];
-      bW[3] += gq[3];
+      bW[pass][0] += gq[0];
+      bW[pass][1] += gq[1];
+      bW[pass][2] -= gq[2];
+      bW[pass][3] += gq[3];
       if (I.bc_y == 1) {
         const T dyk = (T)((double)(2 * k + 1) * I.dy);
-        if (side == 0) bW[0] -= P.g * dyk * gq[3];
-        else bW[0] += P.g * dyk * gq[3];
+        if (side == 0) bW[pass][0] -= P.g * dyk * gq[3];
+        else bW[pass][0] += P.g * dyk * gq[3];
       }
     }
     if (gx < nx && gy < ny) {
       const long long c = (long long)gy * nx + gx;
       const T r = Ui[c], mx = Ui[cells + c], my = Ui[2 * cells + c];
       const T u = mx / r, v = my / r;
+      const T* b = bW[pass];
       T bU[4];
-      bU[0] = bW[0] - (u * bW[1] + v * bW[2]) / r + P.gm1 * T(0.5) * (u * u + v * v) * bW[3];
-      bU[1] = bW[1] / r - P.gm1 * u * bW[3];
-      bU[2] = bW[2] / r - P.gm1 * v * bW[3];
-      bU[3] = P.gm1 * bW[3];
+      bU[0] = b[0] - (u * b[1] + v * b[2]) / r + P.gm1 * T(0.5) * (u * u + v * v) * b[3];
+      bU[1] = b[1] / r - P.gm1 * u * b[3];
+      bU[2] = b[2] / r - P.gm1 * v * b[3];
+      bU[3] = P.gm1 * b[3];
       T kc[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) kc[q] = sK[(q * ADJ_KY + ty + 2) * ADJ_KX + tx + 2];

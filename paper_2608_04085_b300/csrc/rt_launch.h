@@ -11,10 +11,12 @@ namespace rt {
 template <class T>
 cudaError_t launch_inject(const InstDev* insts, const int4* tiles, int ntiles, const double* v, T* U,
                           const RunDev& run, int record, cudaStream_t s);
-// mode: 0 CFL control, 1 replay counting steps, 2 replay (recompute)
+// variant: STAGE_SWEEP or STAGE_TILE; mode: 0 CFL control, 1 replay counting
+// steps, 2 replay (recompute)
 template <class T>
-cudaError_t launch_stage(int stage, int mode, const InstDev* insts, const int4* tiles, int ntiles, const T* src,
-                         const T* base, T* dst, const RunDev& run, int n, cudaStream_t s);
+cudaError_t launch_stage(int variant, int stage, int mode, const InstDev* insts, const int4* strips, int nstrips,
+                         const int4* tiles, int ntiles, const T* src, const T* base, T* dst, const RunDev& run, int n,
+                         cudaStream_t s);
 template <class T>
 cudaError_t launch_adjoint(const InstDev* insts, const int4* tiles, int ntiles, const T* U, const T* K,
                            double kscale, const T* E, double escale, T* out, const RunDev& run, int n,

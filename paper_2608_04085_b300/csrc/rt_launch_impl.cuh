@@ -15,15 +15,31 @@ cudaError_t launch_inject(const InstDev* insts, const int4* tiles, int ntiles, c
 }
 
 template <class T>
-cudaError_t launch_stage(int stage, int mode, const InstDev* insts, const int4* tiles, int ntiles, const T* src,
-                         const T* base, T* dst, const RunDev& run, int n, cudaStream_t s) {
-  const size_t sm = ST_SMEM_ELEMS * sizeof(T);
-  if (stage == 1) {  // stage 1 reads the recorded step constants in every mode
-    k_stage<T, 1, 2><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
+cudaError_t launch_stage(int variant, int stage, int mode, const InstDev* insts, const int4* strips, int nstrips,
+                         const int4* tiles, int ntiles, const T* src, const T* base, T* dst, const RunDev& run, int n,
+                         cudaStream_t s) {
+  if (variant == STAGE_SWEEP) {
+    const int grid = (nstrips + STRIP_WARPS - 1) / STRIP_WARPS, block = 32 * STRIP_WARPS;
+    if (stage == 1) {  // stage 1 reads the recorded step constants in every mode
+      k_stage_sweep<T, 1, 2><<<grid, block, 0, s>>>(insts, strips, nstrips, src, base, dst, run, n);
+    } else if (mode == 0) {
+      k_stage_sweep<T, 2, 0><<<grid, block, 0, s>>>(insts, strips, nstrips, src, base, dst, run, n);
+    } else if (mode == 1) {
+      k_stage_sweep<T, 2, 1><<<grid, block, 0, s>>>(insts, strips, nstrips, src, base, dst, run, n);
+    } else {
+      k_stage_sweep<T, 2, 2><<<grid, block, 0, s>>>(insts, strips, nstrips, src, base, dst, run, n);
+    }
   } else {
-    if (mode == 0) k_stage<T, 2, 0><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
-    else if (mode == 1) k_stage<T, 2, 1><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
-    else k_stage<T, 2, 2><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
+    const size_t sm = ST_SMEM_ELEMS * sizeof(T);
+    if (stage == 1) {
+      k_stage_tile<T, 1, 2><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
+    } else if (mode == 0) {
+      k_stage_tile<T, 2, 0><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
+    } else if (mode == 1) {
+      k_stage_tile<T, 2, 1><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
+    } else {
+      k_stage_tile<T, 2, 2><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
+    }
   }
   return cudaGetLastError();
 }
@@ -55,21 +71,20 @@ cudaError_t launch_grad(const InstDev* insts, const int4* tiles, int ntiles, con
 template <class T>
 cudaError_t configure_kernels() {
   const int st = (int)(ST_SMEM_ELEMS * sizeof(T));
-  cudaError_t e = cudaFuncSetAttribute(k_stage<T, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, st);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage<T, 2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, st);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage<T, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, st);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage<T, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, st);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_adjoint<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(ADJ_SMEM_ELEMS * sizeof(T)));
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(k_stage_tile<T, 1, 2>, a, st);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage_tile<T, 2, 0>, a, st);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage_tile<T, 2, 1>, a, st);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage_tile<T, 2, 2>, a, st);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adjoint<T>, a, (int)(ADJ_SMEM_ELEMS * sizeof(T)));
   return e;
 }
 
 #define RT_INSTANTIATE_LAUNCHERS(T)                                                                              \
   template cudaError_t launch_inject<T>(const InstDev*, const int4*, int, const double*, T*, const RunDev&, int,  \
                                         cudaStream_t);                                                           \
-  template cudaError_t launch_stage<T>(int, int, const InstDev*, const int4*, int, const T*, const T*, T*,        \
-                                       const RunDev&, int, cudaStream_t);                                        \
+  template cudaError_t launch_stage<T>(int, int, int, const InstDev*, const int4*, int, const int4*, int,         \
+                                       const T*, const T*, T*, const RunDev&, int, cudaStream_t);                \
   template cudaError_t launch_adjoint<T>(const InstDev*, const int4*, int, const T*, const T*, double, const T*,  \
                                          double, T*, const RunDev&, int, cudaStream_t);                          \
   template cudaError_t launch_objective<T>(const InstDev*, const int4*, int, T* const*, int, const int*, double*, \

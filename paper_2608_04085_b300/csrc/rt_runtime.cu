@@ -33,6 +33,9 @@ struct rt_ctx {
   std::vector<int4> h_tiles;
   int4* d_tiles = nullptr;
   int ntiles = 0;
+  std::vector<int4> h_strips;  // sweep-kernel strips over all instances
+  int4* d_strips = nullptr;
+  int nstrips = 0;
   long long total_cells = 0;
   size_t total_v = 0;
   std::vector<long long> cell_off, v_off;
@@ -76,6 +79,9 @@ struct rt_ctx {
   std::vector<std::pair<int, int>> evused;  // (kind, index of the start event; end = index + 1)
   double kind_ms[3] = {0, 0, 0};
   long long kind_samples[3] = {0, 0, 0};
+  // stage-kernel variant in use and the autotuner's timings (ms per step)
+  int stage_variant = rt::STAGE_SWEEP;
+  double tune_ms[3] = {0, 0, 0};
 };
 
 namespace {
@@ -171,7 +177,8 @@ void timing_end(rt_ctx* c, int idx) {
 template <class T>
 cudaError_t stage(rt_ctx* c, int st, int mode, const T* src, const T* base, T* dst, int n) {
   const int ev = timing_begin(c, st - 1);
-  cudaError_t e = rt::launch_stage<T>(st, mode, c->d_inst, c->d_tiles, c->ntiles, src, base, dst, c->run, n, c->stream);
+  cudaError_t e = rt::launch_stage<T>(c->stage_variant, st, mode, c->d_inst, c->d_strips, c->nstrips, c->d_tiles,
+                                      c->ntiles, src, base, dst, c->run, n, c->stream);
   timing_end(c, ev);
   return e;
 }
@@ -560,6 +567,39 @@ rt_status baseline(rt_ctx* c) {
   return RT_OK;
 }
 
+// Autotuner: time a few CFL steps of the unperturbed batch with each
+// stage-kernel variant and keep the faster (both give identical values).
+template <class T>
+rt_status autotune_stage(rt_ctx* c) {
+  CU(cudaMemsetAsync(c->d_v, 0, c->total_v * sizeof(double), c->stream));
+  const int variants[2] = {rt::STAGE_SWEEP, rt::STAGE_TILE};
+  const int warm = 2, timed = 4;
+  double best = 1e300;
+  int best_v = rt::STAGE_SWEEP;
+  for (int v : variants) {
+    c->stage_variant = v;
+    CHK(inject<T>(c, c->d_v, c->sA));
+    for (int n = 0; n < warm + timed; ++n) {
+      if (n == warm) CU(cudaEventRecord(c->ev0, c->stream));
+      void* src = (n & 1) ? c->sB : c->sA;
+      void* dst = (n & 1) ? c->sA : c->sB;
+      CU(rt::launch_stage<T>(v, 1, 0, c->d_inst, c->d_strips, c->nstrips, c->d_tiles, c->ntiles, slotp<T>(src),
+                             nullptr, slotp<T>(c->sU1), c->run, n, c->stream));
+      CU(rt::launch_stage<T>(v, 2, 0, c->d_inst, c->d_strips, c->nstrips, c->d_tiles, c->ntiles,
+                             slotp<T>(c->sU1), slotp<T>(src), slotp<T>(dst), c->run, n, c->stream));
+    }
+    CU(cudaEventRecord(c->ev1, c->stream));
+    CU(cudaEventSynchronize(c->ev1));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    c->tune_ms[v] = ms / timed;
+    if (ms < best) { best = ms; best_v = v; }
+  }
+  c->stage_variant = best_v;
+  c->have_run = false;
+  return RT_OK;
+}
+
 struct Timer {
   rt_ctx* c;
   explicit Timer(rt_ctx* cc) : c(cc) { cudaEventRecord(c->ev0, c->stream); }
@@ -778,10 +818,15 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
     for (int y0 = 0; y0 < P.ny; y0 += rt::TILE_Y)
       for (int x0 = 0; x0 < P.nx; x0 += rt::TILE_X) c->h_tiles.push_back(make_int4(i, x0, y0, 0));
     I.tile_end = (int)c->h_tiles.size();
+    I.strip_begin = (int)c->h_strips.size();
+    for (int y0 = 0; y0 < P.ny; y0 += rt::STRIP_H)
+      for (int x0 = 0; x0 < P.nx; x0 += rt::STRIP_W) c->h_strips.push_back(make_int4(i, x0, y0, 0));
+    I.strip_end = (int)c->h_strips.size();
     I.ek0 = nullptr;
     roff += P.ny;
   }
   c->ntiles = (int)c->h_tiles.size();
+  c->nstrips = (int)c->h_strips.size();
   const int N = n_instances;
 #define INIT_CU(call)                                                                            \
   do {                                                                                           \
@@ -804,6 +849,8 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
   INIT_CU(cudaMemcpy(c->d_inst, c->h_inst.data(), N * sizeof(InstDev), cudaMemcpyHostToDevice));
   INIT_CU(cudaMalloc(&c->d_tiles, c->ntiles * sizeof(int4)));
   INIT_CU(cudaMemcpy(c->d_tiles, c->h_tiles.data(), c->ntiles * sizeof(int4), cudaMemcpyHostToDevice));
+  INIT_CU(cudaMalloc(&c->d_strips, c->nstrips * sizeof(int4)));
+  INIT_CU(cudaMemcpy(c->d_strips, c->h_strips.data(), c->nstrips * sizeof(int4), cudaMemcpyHostToDevice));
   void** bufs[6] = {&c->sA, &c->sB, &c->sU1, &c->lA, &c->lB, &c->l1};
   for (void** b : bufs) INIT_CU(cudaMalloc(b, c->slot_bytes));
   c->run.n_inst = N;
@@ -835,6 +882,16 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
     if (s == RT_OK) s = c->esz == 8 ? baseline<double>(c) : baseline<float>(c);
     if (s != RT_OK) return bail(s);
   }
+  if (c->opt.stage_kernel == RT_STAGE_SWEEP || c->opt.stage_kernel == RT_STAGE_TILE) {
+    c->stage_variant = c->opt.stage_kernel;
+  } else if (c->opt.stage_kernel == RT_STAGE_AUTO) {
+    rt_status s = ensure_fields(c, false);
+    if (s == RT_OK) s = c->esz == 8 ? autotune_stage<double>(c) : autotune_stage<float>(c);
+    if (s != RT_OK) return bail(s);
+  } else {
+    fail(c, RT_EINVAL, "stage_kernel");
+    return bail(RT_EINVAL);
+  }
 #undef INIT_CU
   *out = c;
   return RT_OK;
@@ -842,7 +899,7 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
 
 void rt_destroy(rt_ctx* c) {
   if (!c) return;
-  void* ptrs[] = {c->d_inst, c->d_tiles, c->d_base, c->d_ek0, c->d_ek, c->sA, c->sB, c->sU1, c->lA, c->lB,
+  void* ptrs[] = {c->d_inst, c->d_tiles, c->d_strips, c->d_base, c->d_ek0, c->d_ek, c->sA, c->sB, c->sU1, c->lA, c->lB,
                   c->l1, c->d_tab, c->run.dtrec, c->run.dtc, c->run.counter, c->run.t, c->run.nstep, c->run.wmin, c->run.status,
                   c->run.bad_cell, c->d_partials, c->d_sums, c->d_scal, c->d_v, c->d_g, c->d_w1, c->d_w2,
                   c->d_w3, c->d_w4};
@@ -968,6 +1025,15 @@ rt_status rt_set_kernel_timing(rt_ctx* c, int every) {
     for (auto& e : c->evpool) CU(cudaEventCreate(&e));
   }
   return RT_OK;
+}
+
+int rt_stage_kernel(const rt_ctx* c, double* tuned_ms) {
+  if (!c) return 0;
+  if (tuned_ms) {
+    tuned_ms[0] = c->tune_ms[rt::STAGE_SWEEP];
+    tuned_ms[1] = c->tune_ms[rt::STAGE_TILE];
+  }
+  return c->stage_variant;
 }
 
 rt_status rt_kernel_times(rt_ctx* c, double* mean_ms, long long* samples, long long* launches) {

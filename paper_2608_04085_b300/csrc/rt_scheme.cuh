@@ -210,6 +210,19 @@ __device__ __forceinline__ void hllc_vjp(T rL, T uL, T vL, T pL, T rR, T uR, T v
   bRs[0] = brR; bRs[1] = buR; bRs[2] = bvR; bRs[3] = bpR;
 }
 
+// Flux through a face along DIR (0: x, 1: y) from the reconstructed face
+// states WL = W_a + s_a/2 and WR = W_b - s_b/2 (primitive, unrotated).
+template <class T, int DIR>
+__device__ __forceinline__ void face_flux_states(const T WL[4], const T WR[4], T gamma, T gm1, T F[4]) {
+  constexpr int n = 1 + DIR, t = 2 - DIR;
+  T f[4];
+  hllc(WL[0], WL[n], WL[t], WL[3], WR[0], WR[n], WR[t], WR[3], gamma, gm1, f);
+  F[0] = f[0];
+  F[n] = f[1];
+  F[t] = f[2];
+  F[3] = f[3];
+}
+
 // Flux through the face between cells a and b along DIR (0: x, 1: y), from
 // the primitive states w[0..3] of cells a-1, a, b, b+1 (index [cell][var]).
 template <class T, int DIR>
@@ -222,13 +235,7 @@ __device__ __forceinline__ void face_flux(const T w[4][4], int lim, T gamma, T g
     WL[q] = w[1][q] + T(0.5) * sa;
     WR[q] = w[2][q] - T(0.5) * sb;
   }
-  constexpr int n = 1 + DIR, t = 2 - DIR;
-  T f[4];
-  hllc(WL[0], WL[n], WL[t], WL[3], WR[0], WR[n], WR[t], WR[3], gamma, gm1, f);
-  F[0] = f[0];
-  F[n] = f[1];
-  F[t] = f[2];
-  F[3] = f[3];
+  face_flux_states<T, DIR>(WL, WR, gamma, gm1, F);
 }
 
 // Transposed face flux: out[cell][var] = (dF/dW_cell,var)^T mu for the four

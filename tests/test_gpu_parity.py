@@ -37,14 +37,17 @@ FWD_CASES = {
 
 
 @pytest.mark.parametrize("name", sorted(FWD_CASES))
-def test_fp64_forward_bitwise(name):
+@pytest.mark.parametrize("variant", ["sweep", "tile"])
+def test_fp64_forward_bitwise(name, variant):
     import oracle
     w, seed = FWD_CASES[name]
     v = _v(w, seed)
     ek0 = oracle.baseline_ek(w) if w.objective == I.OBJ_EK_ANOMALY_L2 else None
     ref = oracle.forward(w, v, ek0=ek0)
     rt = _rt()
-    with rt.Context([w], precision=rt.RT_FP64) as ctx:
+    sk = rt.RT_STAGE_SWEEP if variant == "sweep" else rt.RT_STAGE_TILE
+    with rt.Context([w], precision=rt.RT_FP64, stage_kernel=sk) as ctx:
+        assert ctx.stage_kernel()[0] == sk
         J, Jke, st = ctx.forward(v.ravel())
         dt = ctx.dt(0)
         U = ctx.state(0)
@@ -55,7 +58,8 @@ def test_fp64_forward_bitwise(name):
     assert J[0] == pytest.approx(oracle.objective_value(w, ref), rel=1e-12)
 
 
-def test_fp64_batch_of_uneven_grids_matches_single_runs():
+@pytest.mark.parametrize("variant", ["sweep", "tile"])
+def test_fp64_batch_of_uneven_grids_matches_single_runs(variant):
     """One batched launch over uneven instances gives each instance the same
     bits as running it alone."""
     import oracle
@@ -63,7 +67,8 @@ def test_fp64_batch_of_uneven_grids_matches_single_runs():
           I.rt_box(8, 96, nsteps=0, T=0.03, ncomp=I.PERT_VY)]
     vs = [_v(w, 10 + k) for k, w in enumerate(ws)]
     rt = _rt()
-    with rt.Context(ws, precision=rt.RT_FP64) as ctx:
+    sk = rt.RT_STAGE_SWEEP if variant == "sweep" else rt.RT_STAGE_TILE
+    with rt.Context(ws, precision=rt.RT_FP64, stage_kernel=sk) as ctx:
         J, Jke, st = ctx.forward(np.concatenate([v.ravel() for v in vs]))
         for k, w in enumerate(ws):
             ref = oracle.forward(w, vs[k])
@@ -192,6 +197,26 @@ def test_nonfinite_state_is_reported():
         with pytest.raises(rt.RtError) as e:
             ctx.forward(v)
         assert e.value.status == rt.RT_ENONFINITE
+
+
+def test_autotuner_picks_a_variant_and_matches_forced_ones():
+    w = I.rt_box(96, 160, nsteps=20)
+    v = _v(w, 4).ravel()
+    rt = _rt()
+    out = {}
+    for sk in (rt.RT_STAGE_AUTO, rt.RT_STAGE_SWEEP, rt.RT_STAGE_TILE):
+        with rt.Context([w], precision=rt.RT_FP32_STATE, stage_kernel=sk) as ctx:
+            var, tuned = ctx.stage_kernel()
+            out[sk] = (ctx.forward(v)[0][0], ctx.state(0))
+            if sk == rt.RT_STAGE_AUTO:
+                assert var in (rt.RT_STAGE_SWEEP, rt.RT_STAGE_TILE)
+                assert tuned["sweep"] > 0 and tuned["tile"] > 0
+                assert tuned["sweep" if var == rt.RT_STAGE_SWEEP else "tile"] == min(tuned.values())
+    # FP32 with FMA contraction: the two schedules may fuse products differently,
+    # so they agree to FP32 rounding (the FP64 path is bitwise in both)
+    a, b = out[rt.RT_STAGE_SWEEP], out[rt.RT_STAGE_TILE]
+    assert abs(a[0] - b[0]) <= 1e-5 * abs(a[0])
+    assert np.max(np.abs(a[1] - b[1])) <= 1e-5 * np.max(np.abs(a[1]))
 
 
 def test_invalid_problem_rejected():
