@@ -236,7 +236,9 @@ __device__ __forceinline__ void load_prim(const T* __restrict__ Ui, const InstDe
 
 // ------------------------------------------------------------------- stage
 // Two variants of one stage kernel compute the same values bit for bit; the
-// runtime's autotuner picks the faster for the batch at hand.
+// runtime's autotuner picks the faster for the batch at hand. LIM >= 0 fixes
+// the limiter at compile time (every instance of the batch uses it); -1
+// reads each instance's limiter.
 //
 // Sweep variant: each warp advances one strip of STRIP_W x STRIP_H cells,
 // marching up the rows. Lane L holds column x0 - 2 + L; the y direction keeps
@@ -292,7 +294,7 @@ __device__ __forceinline__ void raw_to_prim(const T u[4], const InstDev& I, int 
   }
 }
 
-template <class T, int STAGE, int MODE>
+template <class T, int STAGE, int MODE, int LIM>
 __global__ void __launch_bounds__(32 * STRIP_WARPS, 6) k_stage_sweep(const InstDev* __restrict__ insts,
                                                             const int4* __restrict__ strips, int nstrips,
                                                             const T* __restrict__ src, const T* __restrict__ base,
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS, 6) k_stage_sweep(const InstD
   if (!(sc.dt > T(0))) return;  // instance inactive at this step (uniform over the warp)
 
   const Phys<T> P = phys<T>(I);
-  const int nx = I.nx, ny = I.ny, lim = I.limiter;
+  const int nx = I.nx, ny = I.ny, lim = LIM >= 0 ? LIM : I.limiter;
   const long long cells = (long long)nx * ny;
   const T* Si = src + 4 * I.cell_off;
   const T* Bi = base + 4 * I.cell_off;
@@ -454,7 +456,7 @@ constexpr int ST_SMEM_ELEMS = 4 * ST_EX * ST_EY + 4 * ST_NFX + 4 * ST_NFY;
 // Tile variant of the stage kernel: one CTA per 32 x 16 tile, primitive
 // states with 2 ghost layers in shared memory, one thread per face, then one
 // thread per cell for the update. Modes as for the sweep variant.
-template <class T, int STAGE, int MODE>
+template <class T, int STAGE, int MODE, int LIM>
 __global__ void __launch_bounds__(NTH) k_stage_tile(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,
                                                const T* __restrict__ src, const T* __restrict__ base,
                                                T* __restrict__ dst, RunDev run, int n) {
@@ -473,7 +475,7 @@ __global__ void __launch_bounds__(NTH) k_stage_tile(const InstDev* __restrict__ 
   const long long cells = (long long)I.nx * I.ny;
   const T* Si = src + 4 * I.cell_off;
   const int x0 = tl.y, y0 = tl.z;
-  const int lim = I.limiter;
+  const int lim = LIM >= 0 ? LIM : I.limiter;
   for (int e = threadIdx.x; e < ST_EX * ST_EY; e += NTH) {
     const int ey = e / ST_EX, ex = e - ey * ST_EX;
     T W[4];
@@ -566,7 +568,7 @@ constexpr int ADJ_NFX = (TX + 3) * TY, ADJ_NFY = TX * (TY + 3);
 constexpr int ADJ_FACES = ADJ_NFX > ADJ_NFY ? ADJ_NFX : ADJ_NFY;
 constexpr int ADJ_SMEM_ELEMS = 4 * ADJ_AX * ADJ_AY + 4 * ADJ_KX * ADJ_KY + 16 * ADJ_FACES;
 
-template <class T>
+template <class T, int LIM>
 __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 3 : 1)
 k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, const T* __restrict__ U,
           const T* __restrict__ K, T kscale, const T* __restrict__ E, T escale, T* __restrict__ out, RunDev run,
@@ -585,7 +587,7 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
   const T* Ui = U + 4 * I.cell_off;
   const T* Ki = K + 4 * I.cell_off;
   const int x0 = tl.y, y0 = tl.z, nx = I.nx, ny = I.ny;
-  const int lim = I.limiter;
+  const int lim = LIM >= 0 ? LIM : I.limiter;
 
   for (int e = threadIdx.x; e < ADJ_AX * ADJ_AY; e += NTH) {
     const int ey = e / ADJ_AX, ex = e - ey * ADJ_AX;

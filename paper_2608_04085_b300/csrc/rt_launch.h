@@ -13,12 +13,13 @@ cudaError_t launch_inject(const InstDev* insts, const int4* tiles, int ntiles, c
                           const RunDev& run, int record, cudaStream_t s);
 // variant: STAGE_SWEEP or STAGE_TILE; mode: 0 CFL control, 1 replay counting
 // steps, 2 replay (recompute)
+// lim: the batch's common limiter (compile-time specialised kernels), or -1
 template <class T>
-cudaError_t launch_stage(int variant, int stage, int mode, const InstDev* insts, const int4* strips, int nstrips,
-                         const int4* tiles, int ntiles, const T* src, const T* base, T* dst, const RunDev& run, int n,
-                         cudaStream_t s);
+cudaError_t launch_stage(int variant, int lim, int stage, int mode, const InstDev* insts, const int4* strips,
+                         int nstrips, const int4* tiles, int ntiles, const T* src, const T* base, T* dst,
+                         const RunDev& run, int n, cudaStream_t s);
 template <class T>
-cudaError_t launch_adjoint(const InstDev* insts, const int4* tiles, int ntiles, const T* U, const T* K,
+cudaError_t launch_adjoint(int lim, const InstDev* insts, const int4* tiles, int ntiles, const T* U, const T* K,
                            double kscale, const T* E, double escale, T* out, const RunDev& run, int n,
                            cudaStream_t s);
 template <class T>

@@ -14,42 +14,56 @@ cudaError_t launch_inject(const InstDev* insts, const int4* tiles, int ntiles, c
   return cudaGetLastError();
 }
 
-template <class T>
-cudaError_t launch_stage(int variant, int stage, int mode, const InstDev* insts, const int4* strips, int nstrips,
-                         const int4* tiles, int ntiles, const T* src, const T* base, T* dst, const RunDev& run, int n,
-                         cudaStream_t s) {
+template <class T, int LIM>
+cudaError_t launch_stage_lim(int variant, int stage, int mode, const InstDev* insts, const int4* strips, int nstrips,
+                             const int4* tiles, int ntiles, const T* src, const T* base, T* dst, const RunDev& run,
+                             int n, cudaStream_t s) {
   if (variant == STAGE_SWEEP) {
     const int grid = (nstrips + STRIP_WARPS - 1) / STRIP_WARPS, block = 32 * STRIP_WARPS;
     if (stage == 1) {  // stage 1 reads the recorded step constants in every mode
-      k_stage_sweep<T, 1, 2><<<grid, block, 0, s>>>(insts, strips, nstrips, src, base, dst, run, n);
+      k_stage_sweep<T, 1, 2, LIM><<<grid, block, 0, s>>>(insts, strips, nstrips, src, base, dst, run, n);
     } else if (mode == 0) {
-      k_stage_sweep<T, 2, 0><<<grid, block, 0, s>>>(insts, strips, nstrips, src, base, dst, run, n);
+      k_stage_sweep<T, 2, 0, LIM><<<grid, block, 0, s>>>(insts, strips, nstrips, src, base, dst, run, n);
     } else if (mode == 1) {
-      k_stage_sweep<T, 2, 1><<<grid, block, 0, s>>>(insts, strips, nstrips, src, base, dst, run, n);
+      k_stage_sweep<T, 2, 1, LIM><<<grid, block, 0, s>>>(insts, strips, nstrips, src, base, dst, run, n);
     } else {
-      k_stage_sweep<T, 2, 2><<<grid, block, 0, s>>>(insts, strips, nstrips, src, base, dst, run, n);
+      k_stage_sweep<T, 2, 2, LIM><<<grid, block, 0, s>>>(insts, strips, nstrips, src, base, dst, run, n);
     }
   } else {
     const size_t sm = ST_SMEM_ELEMS * sizeof(T);
     if (stage == 1) {
-      k_stage_tile<T, 1, 2><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
+      k_stage_tile<T, 1, 2, LIM><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
     } else if (mode == 0) {
-      k_stage_tile<T, 2, 0><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
+      k_stage_tile<T, 2, 0, LIM><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
     } else if (mode == 1) {
-      k_stage_tile<T, 2, 1><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
+      k_stage_tile<T, 2, 1, LIM><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
     } else {
-      k_stage_tile<T, 2, 2><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
+      k_stage_tile<T, 2, 2, LIM><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
     }
   }
   return cudaGetLastError();
 }
 
 template <class T>
-cudaError_t launch_adjoint(const InstDev* insts, const int4* tiles, int ntiles, const T* U, const T* K,
+cudaError_t launch_stage(int variant, int lim, int stage, int mode, const InstDev* insts, const int4* strips,
+                         int nstrips, const int4* tiles, int ntiles, const T* src, const T* base, T* dst,
+                         const RunDev& run, int n, cudaStream_t s) {
+  if (lim == LIM_MINMOD)
+    return launch_stage_lim<T, LIM_MINMOD>(variant, stage, mode, insts, strips, nstrips, tiles, ntiles, src, base,
+                                           dst, run, n, s);
+  return launch_stage_lim<T, -1>(variant, stage, mode, insts, strips, nstrips, tiles, ntiles, src, base, dst, run,
+                                 n, s);
+}
+
+template <class T>
+cudaError_t launch_adjoint(int lim, const InstDev* insts, const int4* tiles, int ntiles, const T* U, const T* K,
                            double kscale, const T* E, double escale, T* out, const RunDev& run, int n,
                            cudaStream_t s) {
-  k_adjoint<T><<<ntiles, NTH, ADJ_SMEM_ELEMS * sizeof(T), s>>>(insts, tiles, U, K, (T)kscale, E, (T)escale, out,
-                                                                 run, n);
+  const size_t sm = ADJ_SMEM_ELEMS * sizeof(T);
+  if (lim == LIM_MINMOD)
+    k_adjoint<T, LIM_MINMOD><<<ntiles, NTH, sm, s>>>(insts, tiles, U, K, (T)kscale, E, (T)escale, out, run, n);
+  else
+    k_adjoint<T, -1><<<ntiles, NTH, sm, s>>>(insts, tiles, U, K, (T)kscale, E, (T)escale, out, run, n);
   return cudaGetLastError();
 }
 
@@ -68,25 +82,32 @@ cudaError_t launch_grad(const InstDev* insts, const int4* tiles, int ntiles, con
   return cudaGetLastError();
 }
 
-template <class T>
-cudaError_t configure_kernels() {
+template <class T, int LIM>
+cudaError_t configure_lim() {
   const int st = (int)(ST_SMEM_ELEMS * sizeof(T));
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(k_stage_tile<T, 1, 2>, a, st);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage_tile<T, 2, 0>, a, st);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage_tile<T, 2, 1>, a, st);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage_tile<T, 2, 2>, a, st);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adjoint<T>, a, (int)(ADJ_SMEM_ELEMS * sizeof(T)));
+  cudaError_t e = cudaFuncSetAttribute(k_stage_tile<T, 1, 2, LIM>, a, st);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage_tile<T, 2, 0, LIM>, a, st);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage_tile<T, 2, 1, LIM>, a, st);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage_tile<T, 2, 2, LIM>, a, st);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adjoint<T, LIM>, a, (int)(ADJ_SMEM_ELEMS * sizeof(T)));
+  return e;
+}
+
+template <class T>
+cudaError_t configure_kernels() {
+  cudaError_t e = configure_lim<T, LIM_MINMOD>();
+  if (e == cudaSuccess) e = configure_lim<T, -1>();
   return e;
 }
 
 #define RT_INSTANTIATE_LAUNCHERS(T)                                                                              \
   template cudaError_t launch_inject<T>(const InstDev*, const int4*, int, const double*, T*, const RunDev&, int,  \
                                         cudaStream_t);                                                           \
-  template cudaError_t launch_stage<T>(int, int, int, const InstDev*, const int4*, int, const int4*, int,         \
+  template cudaError_t launch_stage<T>(int, int, int, int, const InstDev*, const int4*, int, const int4*, int,    \
                                        const T*, const T*, T*, const RunDev&, int, cudaStream_t);                \
-  template cudaError_t launch_adjoint<T>(const InstDev*, const int4*, int, const T*, const T*, double, const T*,  \
-                                         double, T*, const RunDev&, int, cudaStream_t);                          \
+  template cudaError_t launch_adjoint<T>(int, const InstDev*, const int4*, int, const T*, const T*, double,       \
+                                         const T*, double, T*, const RunDev&, int, cudaStream_t);                \
   template cudaError_t launch_objective<T>(const InstDev*, const int4*, int, T* const*, int, const int*, double*, \
                                            T*, T*, double*, cudaStream_t);                                       \
   template cudaError_t launch_grad<T>(const InstDev*, const int4*, int, const T*, const double*, double*,         \

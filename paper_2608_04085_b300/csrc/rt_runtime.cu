@@ -81,6 +81,7 @@ struct rt_ctx {
   long long kind_samples[3] = {0, 0, 0};
   // stage-kernel variant in use and the autotuner's timings (ms per step)
   int stage_variant = rt::STAGE_SWEEP;
+  int lim = -1;  // limiter shared by every instance (compile-time specialised kernels), or -1
   double tune_ms[3] = {0, 0, 0};
 };
 
@@ -177,8 +178,8 @@ void timing_end(rt_ctx* c, int idx) {
 template <class T>
 cudaError_t stage(rt_ctx* c, int st, int mode, const T* src, const T* base, T* dst, int n) {
   const int ev = timing_begin(c, st - 1);
-  cudaError_t e = rt::launch_stage<T>(c->stage_variant, st, mode, c->d_inst, c->d_strips, c->nstrips, c->d_tiles,
-                                      c->ntiles, src, base, dst, c->run, n, c->stream);
+  cudaError_t e = rt::launch_stage<T>(c->stage_variant, c->lim, st, mode, c->d_inst, c->d_strips, c->nstrips,
+                                      c->d_tiles, c->ntiles, src, base, dst, c->run, n, c->stream);
   timing_end(c, ev);
   return e;
 }
@@ -186,7 +187,8 @@ cudaError_t stage(rt_ctx* c, int st, int mode, const T* src, const T* base, T* d
 template <class T>
 cudaError_t adjoint(rt_ctx* c, const T* U, const T* K, double ks, const T* E, double es, T* out, int n) {
   const int ev = timing_begin(c, 2);
-  cudaError_t e = rt::launch_adjoint<T>(c->d_inst, c->d_tiles, c->ntiles, U, K, ks, E, es, out, c->run, n, c->stream);
+  cudaError_t e =
+      rt::launch_adjoint<T>(c->lim, c->d_inst, c->d_tiles, c->ntiles, U, K, ks, E, es, out, c->run, n, c->stream);
   timing_end(c, ev);
   return e;
 }
@@ -583,9 +585,9 @@ rt_status autotune_stage(rt_ctx* c) {
       if (n == warm) CU(cudaEventRecord(c->ev0, c->stream));
       void* src = (n & 1) ? c->sB : c->sA;
       void* dst = (n & 1) ? c->sA : c->sB;
-      CU(rt::launch_stage<T>(v, 1, 0, c->d_inst, c->d_strips, c->nstrips, c->d_tiles, c->ntiles, slotp<T>(src),
-                             nullptr, slotp<T>(c->sU1), c->run, n, c->stream));
-      CU(rt::launch_stage<T>(v, 2, 0, c->d_inst, c->d_strips, c->nstrips, c->d_tiles, c->ntiles,
+      CU(rt::launch_stage<T>(v, c->lim, 1, 0, c->d_inst, c->d_strips, c->nstrips, c->d_tiles, c->ntiles,
+                             slotp<T>(src), nullptr, slotp<T>(c->sU1), c->run, n, c->stream));
+      CU(rt::launch_stage<T>(v, c->lim, 2, 0, c->d_inst, c->d_strips, c->nstrips, c->d_tiles, c->ntiles,
                              slotp<T>(c->sU1), slotp<T>(src), slotp<T>(dst), c->run, n, c->stream));
     }
     CU(cudaEventRecord(c->ev1, c->stream));
@@ -827,6 +829,10 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
   }
   c->ntiles = (int)c->h_tiles.size();
   c->nstrips = (int)c->h_strips.size();
+  c->lim = c->prob[0].limiter;
+  for (int i = 1; i < n_instances; ++i)
+    if (c->prob[i].limiter != c->lim) c->lim = -1;
+  if (c->lim != RT_LIM_MINMOD) c->lim = -1;  // only minmod has specialised kernels
   const int N = n_instances;
 #define INIT_CU(call)                                                                            \
   do {                                                                                           \
