@@ -46,7 +46,7 @@ WORKLOAD = "rt-box 256x768 x32 instances, T=2.0, FP32 state + FP64 reductions, r
 # U1, lam^{n+1}, writes lam1 (12 s); stage-1 adjoint reads U^n, lam1,
 # lam^{n+1}, writes lam^n (16 s); s = 4 bytes; launches alternate.
 ADJ_BYTES_PER_CELL = {"stage2_adjoint": 12 * 4, "stage1_adjoint": 16 * 4, "mean": 14 * 4}
-STEP_BYTES_PER_CELL_UPDATE = 76 * 4  # forward 20s + recompute 20s + adjoint 36s (sqrt checkpointing)
+STEP_BYTES_PER_CELL_UPDATE = 68 * 4  # forward 20s + segment recompute 20s (U1 kept) + adjoint 12s + 16s (sqrt checkpointing)
 
 
 def dist_env():

@@ -51,6 +51,7 @@ struct rt_ctx {
   void* lB = nullptr;
   void* l1 = nullptr;        // stage-1 cotangent
   std::vector<void*> pool;   // checkpoint / stored-state slots
+  std::vector<void*> pool1;  // stored stage-1 states (U1) of the steps the reverse sweep walks
   void** d_tab = nullptr;    // device table of slot pointers
   int tab_cap = 0;
   RunDev run{};
@@ -234,6 +235,18 @@ rt_status ensure_pool(rt_ctx* c, size_t n) {
   return RT_OK;
 }
 
+rt_status ensure_pool1(rt_ctx* c, size_t n) {
+  while (c->pool1.size() < n) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, c->slot_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, RT_ENOMEM, "cannot allocate stage-1 slot %zu (%zu bytes)", c->pool1.size(), c->slot_bytes);
+    }
+    c->pool1.push_back(p);
+  }
+  return RT_OK;
+}
+
 rt_status upload_tab(rt_ctx* c, const std::vector<void*>& tab) {
   if ((int)tab.size() > c->tab_cap) {
     if (c->d_tab) cudaFree(c->d_tab);
@@ -332,11 +345,12 @@ rt_status march(rt_ctx* c, const Plan& plan, int mode, int n_est, int replay_ste
   for (;;) {
     for (; n < target; ++n) {
       if (n >= c->opt.max_steps) return fail(c, RT_EINVAL, "step limit %d reached", c->opt.max_steps);
-      void *src, *dst;
+      void *src, *dst, *u1 = c->sU1;
       if (plan.kind == 2) {
         if (n + 1 >= plan.slots) return fail(c, RT_ENOMEM, "stored-state plan ran out of slots at step %d", n);
         src = c->pool[n];
         dst = c->pool[n + 1];
+        u1 = c->pool1[n];
       } else {
         src = (n & 1) ? c->sB : c->sA;
         dst = (n & 1) ? c->sA : c->sB;
@@ -346,8 +360,8 @@ rt_status march(rt_ctx* c, const Plan& plan, int mode, int n_est, int replay_ste
           CU(cudaMemcpyAsync(c->pool[plan.S + k], src, c->slot_bytes, cudaMemcpyDeviceToDevice, c->stream));
         }
       }
-      CU(stage<T>(c, 1, smode == 1 ? 2 : 0, slotp<T>(src), nullptr, slotp<T>(c->sU1), n));
-      CU(stage<T>(c, 2, smode, slotp<T>(c->sU1), slotp<T>(src), slotp<T>(dst), n));
+      CU(stage<T>(c, 1, smode == 1 ? 2 : 0, slotp<T>(src), nullptr, slotp<T>(u1), n));
+      CU(stage<T>(c, 2, smode, slotp<T>(u1), slotp<T>(src), slotp<T>(dst), n));
     }
     CHK(read_run(c, nstep, t, status));
     CHK(nonfinite(c, status, nullptr));
@@ -448,18 +462,20 @@ rt_status gradient_impl(rt_ctx* c, const double* d_v, double* J_out, double* d_g
   int n_est = 1;
   CHK(estimate_steps(c, &n_est));
   Plan plan;
-  const double need_all = ((double)n_est * 1.1 + 16.0) * (double)c->slot_bytes;
+  const double need_all = (2.0 * ((double)n_est * 1.1 + 16.0)) * (double)c->slot_bytes;
   int mode = c->opt.ckpt;
   if (mode == RT_CKPT_AUTO) mode = need_all <= c->mem_cap ? RT_CKPT_STORE_ALL : RT_CKPT_SQRT;
   if (mode == RT_CKPT_STORE_ALL) {
     plan.kind = 2;
     plan.slots = (int)(n_est * 1.1 + 16);
     CHK(ensure_pool(c, plan.slots));
+    CHK(ensure_pool1(c, plan.slots));
     CHK(inject<T>(c, d_v, c->pool[0]));
   } else {
     plan.kind = 1;
     plan.S = std::max(1, (int)std::ceil(std::sqrt((double)n_est)));
     CHK(ensure_pool(c, plan.S + n_est / plan.S + 2));
+    CHK(ensure_pool1(c, plan.S));
   }
   int n_done = 0;
   rt_status s = march<T>(c, plan, 0, n_est, 0, &n_done);
@@ -468,6 +484,7 @@ rt_status gradient_impl(rt_ctx* c, const double* d_v, double* J_out, double* d_g
     plan.kind = 1;
     plan.S = std::max(1, (int)std::ceil(std::sqrt((double)n_est * 1.5)));
     CHK(ensure_pool(c, plan.S + 2 * n_est / plan.S + 2));
+    CHK(ensure_pool1(c, plan.S));
     CHK(inject<T>(c, d_v, c->sA));
     s = march<T>(c, plan, 0, n_est, 0, &n_done);
   }
@@ -475,29 +492,30 @@ rt_status gradient_impl(rt_ctx* c, const double* d_v, double* J_out, double* d_g
   CHK(objective<T>(c, plan, true, nullptr));
   CHK(read_J(c, J_out, nullptr));
   const int N = c->last_steps;
-  T* U1 = slotp<T>(c->sU1);
   T* lam[2] = {slotp<T>(c->lA), slotp<T>(c->lB)};
   T* l1 = slotp<T>(c->l1);
-  auto reverse_step = [&](int n, T* Un) -> rt_status {
-    CU(stage<T>(c, 1, 2, Un, nullptr, U1, n));
+  // lam1 = (dStage2/dU1)^T lam^{n+1};  lam^n = lam^{n+1}/2 + (dStage1/dU^n)^T lam1
+  auto reverse_step = [&](int n, T* Un, T* U1) -> rt_status {
     CU(adjoint<T>(c, U1, lam[(n + 1) & 1], 0.5, nullptr, 0.0, l1, n));
     CU(adjoint<T>(c, Un, l1, 1.0, lam[(n + 1) & 1], 0.5, lam[n & 1], n));
     return RT_OK;
   };
   int segments = 1;
   if (plan.kind == 2) {
-    for (int n = N - 1; n >= 0; --n) CHK(reverse_step(n, slotp<T>(c->pool[n])));
+    for (int n = N - 1; n >= 0; --n) CHK(reverse_step(n, slotp<T>(c->pool[n]), slotp<T>(c->pool1[n])));
   } else {
     const int S = plan.S;
     segments = (N + S - 1) / S;
     for (int k = segments - 1; k >= 0; --k) {
       const int n0 = k * S, n1 = std::min(N, n0 + S);
       auto seg = [&](int n) -> T* { return n == n0 ? slotp<T>(c->pool[S + k]) : slotp<T>(c->pool[n - n0]); };
-      for (int n = n0; n < n1 - 1; ++n) {
-        CU(stage<T>(c, 1, 2, seg(n), nullptr, U1, n));
-        CU(stage<T>(c, 2, 2, U1, seg(n), seg(n + 1), n));
+      auto seg1 = [&](int n) -> T* { return slotp<T>(c->pool1[n - n0]); };
+      // recompute the segment from its checkpoint, keeping U^n and U1 of every step
+      for (int n = n0; n < n1; ++n) {
+        CU(stage<T>(c, 1, 2, seg(n), nullptr, seg1(n), n));
+        if (n < n1 - 1) CU(stage<T>(c, 2, 2, seg1(n), seg(n), seg(n + 1), n));
       }
-      for (int n = n1 - 1; n >= n0; --n) CHK(reverse_step(n, seg(n)));
+      for (int n = n1 - 1; n >= n0; --n) CHK(reverse_step(n, seg(n), seg1(n)));
     }
   }
   CU(rt::launch_grad<T>(c->d_inst, c->d_tiles, c->ntiles, lam[0], d_v, d_g, c->stream));
@@ -912,6 +930,7 @@ void rt_destroy(rt_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : c->pool) cudaFree(p);
+  for (void* p : c->pool1) cudaFree(p);
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
