@@ -60,7 +60,7 @@ enum { RT_BC_REFLECT = 0, RT_BC_HYDROSTATIC = 1 };
 enum { RT_LIM_MINMOD = 0, RT_LIM_MC = 1, RT_LIM_NONE = 2 };
 enum { RT_OBJ_KE = 0, RT_OBJ_EK_ANOMALY_L2 = 1 };
 enum { RT_FP64 = 0, RT_FP32_STATE = 1 };
-enum { RT_CKPT_AUTO = 0, RT_CKPT_STORE_ALL = 1, RT_CKPT_SQRT = 2 };
+enum { RT_CKPT_AUTO = 0, RT_CKPT_STORE_ALL = 1, RT_CKPT_SQRT = 2, RT_CKPT_REVOLVE = 3 };
 enum { RT_STAGE_AUTO = 0, RT_STAGE_SWEEP = 1, RT_STAGE_TILE = 2 };
 
 /* flags for rt_forward / rt_gradient / rt_constraint / rt_project */
@@ -89,8 +89,10 @@ typedef struct {
 
 typedef struct {
   int precision;            /* RT_FP64, or RT_FP32_STATE: FP32 state with FP64 reductions */
-  int ckpt;                 /* RT_CKPT_AUTO | RT_CKPT_STORE_ALL | RT_CKPT_SQRT */
-  double ckpt_hbm_cap_bytes;/* cap on checkpoint + segment memory; 0 = 60% of free memory */
+  int ckpt;                 /* RT_CKPT_AUTO | RT_CKPT_STORE_ALL | RT_CKPT_SQRT | RT_CKPT_REVOLVE;
+                               AUTO takes the first that fits the cap in that order */
+  double ckpt_hbm_cap_bytes;/* cap on checkpoint + segment memory; 0 = 60% of free memory.
+                               REVOLVE uses cap / slot size - 4 binomial checkpoint slots */
   int max_steps;            /* upper bound on steps per run (sizes the dt record); 0 = 200000 */
   int stage_kernel;         /* RT_STAGE_AUTO (time both at rt_init, keep the faster),
                                RT_STAGE_SWEEP or RT_STAGE_TILE; both give identical values */
@@ -98,7 +100,8 @@ typedef struct {
 
 typedef struct {
   int steps;                /* largest step count over instances in the last run */
-  int segments;             /* checkpoint segments used by the last gradient */
+  int segments;             /* checkpoint segments of the last gradient (sqrt: > 1;
+                               store-all: 1; revolve: minus the recomputed steps) */
   int bad_instance;         /* first instance with a non-finite state, or -1 */
   long long bad_cell;       /* its cell index (j*nx + i), or -1 */
   double cell_updates;      /* sum over instances of cells x steps advanced */
@@ -141,8 +144,9 @@ rt_status rt_forward(rt_ctx* ctx, const double* v0, int flags, double* J_out,
 
 /* Exact discrete gradient dJ/dv0 (Sec. 3.4) of the same map, dt sequence
  * frozen at the one the forward pass chose, by a hand-written adjoint of the
- * time stepper with sqrt(N) (or store-all) checkpointing. grad_out has the
- * layout of v0. Errors as rt_forward. */
+ * time stepper with store-all, sqrt(N) or binomial (revolve) checkpointing
+ * (Sec. 3.4 uses binomial checkpointing). grad_out has the layout of v0.
+ * Errors as rt_forward. */
 rt_status rt_gradient(rt_ctx* ctx, const double* v0, int flags, double* J_out,
                       double* grad_out, rt_run_stats* st);
 

@@ -23,7 +23,7 @@ RT_BC_REFLECT, RT_BC_HYDROSTATIC = 0, 1
 RT_LIM_MINMOD, RT_LIM_MC, RT_LIM_NONE = 0, 1, 2
 RT_OBJ_KE, RT_OBJ_EK_ANOMALY_L2 = 0, 1
 RT_FP64, RT_FP32_STATE = 0, 1
-RT_CKPT_AUTO, RT_CKPT_STORE_ALL, RT_CKPT_SQRT = 0, 1, 2
+RT_CKPT_AUTO, RT_CKPT_STORE_ALL, RT_CKPT_SQRT, RT_CKPT_REVOLVE = 0, 1, 2, 3
 RT_STAGE_AUTO, RT_STAGE_SWEEP, RT_STAGE_TILE = 0, 1, 2
 RT_DEVICE_PTRS, RT_REPLAY_DT = 1, 2
 

@@ -281,7 +281,9 @@ rt_status nonfinite(rt_ctx* c, const std::vector<int>& status, rt_run_stats* st)
 }
 
 // Forward plan: kind 0 = ping-pong sA/sB; kind 1 = ping-pong plus a copy of
-// every S-th state into pool[k]; kind 2 = every state n stored in pool[n].
+// every S-th state into pool[k]; kind 2 = every state n stored in pool[n];
+// kind 3 = plain forward, then binomial (revolve) recomputation from U^0
+// with `slots` checkpoint slots.
 struct Plan {
   int kind = 0;
   int S = 0;
@@ -453,6 +455,75 @@ rt_status forward_impl(rt_ctx* c, const double* d_v, int flags, double* J_out, d
   return RT_OK;
 }
 
+// beta(s, t) = C(s + t, s): steps reversible with s checkpoints and t
+// forward repetitions (binomial checkpointing, Griewank & Walther).
+double binom_beta(int s, int t) {
+  double b = 1.0;
+  for (int i = 1; i <= s; ++i) b = b * (t + i) / i;
+  return b;
+}
+
+// Binomial-checkpointing reverse sweep over steps [l, r) given U^l in `Ul`,
+// with `free_slots` checkpoint slots left in `slots`. Every step's adjoint
+// needs U^n and its stage-1 state, recomputed from the nearest checkpoint.
+template <class T>
+struct Revolve {
+  rt_ctx* c;
+  std::vector<void*> free;  // unused checkpoint slots
+  void* scratch[2];         // ping-pong for intermediate states while advancing
+  void* leaf_state;         // target of the slot-free (quadratic) recomputation
+  T* lam[2];
+  T* l1;
+  long long recomputed = 0;
+
+  // advance U from step a (in src) to step b, result in dst; src and dst are
+  // never scratch slots, intermediates alternate between the two scratch slots
+  rt_status advance(int a, int b, void* src, void* dst) {
+    void* cur = src;
+    for (int k = a; k < b; ++k) {
+      void* out = (k == b - 1) ? dst : (cur == scratch[0] ? scratch[1] : scratch[0]);
+      CU(stage<T>(c, 1, 2, slotp<T>(cur), nullptr, slotp<T>(c->sU1), k));
+      CU(stage<T>(c, 2, 2, slotp<T>(c->sU1), slotp<T>(cur), slotp<T>(out), k));
+      cur = out;
+      ++recomputed;
+    }
+    return RT_OK;
+  }
+  rt_status leaf(int n, void* Un) {
+    CU(stage<T>(c, 1, 2, slotp<T>(Un), nullptr, slotp<T>(c->sU1), n));
+    CU(adjoint<T>(c, slotp<T>(c->sU1), lam[(n + 1) & 1], 0.5, nullptr, 0.0, l1, n));
+    CU(adjoint<T>(c, slotp<T>(Un), l1, 1.0, lam[(n + 1) & 1], 0.5, lam[n & 1], n));
+    return RT_OK;
+  }
+  rt_status reverse(int l, int r, void* Ul) {
+    const int n = r - l;
+    if (n == 1) return leaf(l, Ul);
+    const int s = (int)free.size();
+    if (s == 0) {  // no slot left: recompute from l for every step
+      for (int k = r - 1; k >= l; --k) {
+        if (k == l) {
+          CHK(leaf(l, Ul));
+        } else {
+          CHK(advance(l, k, Ul, leaf_state));
+          CHK(leaf(k, leaf_state));
+        }
+      }
+      return RT_OK;
+    }
+    int t = 1;
+    while (binom_beta(s, t) < n) ++t;
+    int left = (int)std::min<double>(binom_beta(s, t - 1), (double)(n - 1));
+    if (left < 1) left = 1;
+    const int m = l + left;
+    void* Um = free.back();
+    free.pop_back();
+    CHK(advance(l, m, Ul, Um));
+    CHK(reverse(m, r, Um));
+    free.push_back(Um);
+    return reverse(l, m, Ul);
+  }
+};
+
 // Gradient: forward with checkpoints, terminal cotangent, then for each step
 // in reverse: recompute U1 = stage1(U^n), lam1 = (dStage2/dU1)^T lam^{n+1},
 // lam^n = lam^{n+1}/2 + lam1 + (dL/dU^n)^T lam1 dt (SSP-RK2 transposed).
@@ -464,8 +535,15 @@ rt_status gradient_impl(rt_ctx* c, const double* d_v, double* J_out, double* d_g
   Plan plan;
   const double need_all = (2.0 * ((double)n_est * 1.1 + 16.0)) * (double)c->slot_bytes;
   int mode = c->opt.ckpt;
-  if (mode == RT_CKPT_AUTO) mode = need_all <= c->mem_cap ? RT_CKPT_STORE_ALL : RT_CKPT_SQRT;
-  if (mode == RT_CKPT_STORE_ALL) {
+  const double S_est = std::ceil(std::sqrt((double)n_est));
+  const double need_sqrt = (2.0 * S_est + (double)n_est / S_est + 4.0) * (double)c->slot_bytes;
+  if (mode == RT_CKPT_AUTO)
+    mode = need_all <= c->mem_cap ? RT_CKPT_STORE_ALL : (need_sqrt <= c->mem_cap ? RT_CKPT_SQRT : RT_CKPT_REVOLVE);
+  if (mode == RT_CKPT_REVOLVE) {
+    plan.kind = 3;
+    plan.slots = std::max(0, (int)(c->mem_cap / (double)c->slot_bytes) - 4);
+    CHK(ensure_pool(c, plan.slots + 4));  // + U^0 slot, 2 scratch, 1 leaf state
+  } else if (mode == RT_CKPT_STORE_ALL) {
     plan.kind = 2;
     plan.slots = (int)(n_est * 1.1 + 16);
     CHK(ensure_pool(c, plan.slots));
@@ -478,7 +556,9 @@ rt_status gradient_impl(rt_ctx* c, const double* d_v, double* J_out, double* d_g
     CHK(ensure_pool1(c, plan.S));
   }
   int n_done = 0;
-  rt_status s = march<T>(c, plan, 0, n_est, 0, &n_done);
+  Plan fplan = plan;
+  if (plan.kind == 3) fplan = Plan();  // revolve: plain forward first, recomputation from U^0 later
+  rt_status s = march<T>(c, fplan, 0, n_est, 0, &n_done);
   if (s == RT_ENOMEM && plan.kind == 2) {  // the run outgrew the stored-state plan: redo it checkpointed
     plan = Plan();
     plan.kind = 1;
@@ -489,7 +569,7 @@ rt_status gradient_impl(rt_ctx* c, const double* d_v, double* J_out, double* d_g
     s = march<T>(c, plan, 0, n_est, 0, &n_done);
   }
   if (s != RT_OK) return s;
-  CHK(objective<T>(c, plan, true, nullptr));
+  CHK(objective<T>(c, fplan, true, nullptr));
   CHK(read_J(c, J_out, nullptr));
   const int N = c->last_steps;
   T* lam[2] = {slotp<T>(c->lA), slotp<T>(c->lB)};
@@ -501,7 +581,20 @@ rt_status gradient_impl(rt_ctx* c, const double* d_v, double* J_out, double* d_g
     return RT_OK;
   };
   int segments = 1;
-  if (plan.kind == 2) {
+  if (plan.kind == 3) {
+    Revolve<T> rv;
+    rv.c = c;
+    for (int k = 0; k < plan.slots; ++k) rv.free.push_back(c->pool[4 + k]);
+    rv.scratch[0] = c->pool[1];
+    rv.scratch[1] = c->pool[2];
+    rv.leaf_state = c->pool[3];
+    rv.lam[0] = lam[0];
+    rv.lam[1] = lam[1];
+    rv.l1 = l1;
+    CHK(inject<T>(c, d_v, c->pool[0], true));  // U^0 again; keeps the recorded dt sequence
+    if (N > 0) CHK(rv.reverse(0, N, c->pool[0]));
+    segments = -(int)std::min<long long>(rv.recomputed, 2000000000LL);  // reported as minus the recomputed steps
+  } else if (plan.kind == 2) {
     for (int n = N - 1; n >= 0; --n) CHK(reverse_step(n, slotp<T>(c->pool[n]), slotp<T>(c->pool1[n])));
   } else {
     const int S = plan.S;

@@ -107,15 +107,27 @@ def test_fp64_gradient_matches_oracle(name, ckpt):
         assert st["segments"] > 1
 
 
-def test_checkpoint_schedules_agree_bitwise():
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_checkpoint_schedules_agree_bitwise(prec):
+    """Store-all, sqrt(N) and binomial checkpointing (with 0, 2 and 7 slots,
+    forcing deep recomputation) give bitwise identical gradients."""
     w = I.rt_box(24, 36, nsteps=40)
     v = _v(w, 7, 1e-3).ravel()
     rt = _rt()
-    out = {}
-    for mode in (rt.RT_CKPT_STORE_ALL, rt.RT_CKPT_SQRT):
-        with rt.Context([w], precision=rt.RT_FP64, ckpt=mode) as ctx:
-            out[mode] = ctx.gradient(v)[1]
-    assert np.array_equal(out[rt.RT_CKPT_STORE_ALL], out[rt.RT_CKPT_SQRT])
+    p = rt.RT_FP64 if prec == "fp64" else rt.RT_FP32_STATE
+    slot = 4 * w.nx * w.ny * (8 if prec == "fp64" else 4)
+    runs = [(rt.RT_CKPT_STORE_ALL, 0.0), (rt.RT_CKPT_SQRT, 0.0)]
+    runs += [(rt.RT_CKPT_REVOLVE, (k + 4) * slot) for k in (0, 2, 7)]
+    out = []
+    for mode, cap in runs:
+        with rt.Context([w], precision=p, ckpt=mode, ckpt_cap_bytes=cap) as ctx:
+            J, g, st = ctx.gradient(v)
+            out.append((J[0], g))
+            if mode == rt.RT_CKPT_REVOLVE:
+                assert st["segments"] < -40  # steps were recomputed
+    for J, g in out[1:]:
+        assert J == out[0][0]
+        assert np.array_equal(g, out[0][1])
 
 
 def test_fp64_gradient_deterministic_and_batch_invariant():
