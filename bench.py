@@ -118,6 +118,21 @@ def bench_inputs(rank):
     return I.gaussian_batch(seeds, 2, NY, NX).reshape(-1)
 
 
+def reduce_timing(ms_total, cells_total, world, device=None):
+    """(max over ranks of the timed milliseconds, sum over ranks of the cell
+    updates); identity on one rank. Weak scaling: every rank advances its
+    own batch, so the only collective is this reduction of two scalars."""
+    if world <= 1:
+        return ms_total, cells_total
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_total, cells_total], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(t[1])
+
+
 def workload_problems():
     return [I.single_256().replace(T=T_HORIZON) for _ in range(BATCH)]
 
@@ -215,15 +230,7 @@ def run_ours(args):
         e2e_cells = st_h["cell_updates"]
     e2e_rate = e2e_cells / (e2e_ms / max(1, min(args.steps, 2)) * 1e-3)
 
-    t_max = ms_total
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms_total, cells_total], dtype=torch.float64, device=dev)
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        t_max = float(mx[0])
-        cells_total = float(tt[1])
+    t_max, cells_total = reduce_timing(ms_total, cells_total, world, dev)
 
     # FP64 single-instance comparison (same grid and seed-0 input, bounded horizon)
     fp64 = None
