@@ -46,6 +46,10 @@ WORKLOAD = "rt-box 256x768 x32 instances, T=2.0, FP32 state + FP64 reductions, r
 # U1, lam^{n+1}, writes lam1 (12 s); stage-1 adjoint reads U^n, lam1,
 # lam^{n+1}, writes lam^n (16 s); s = 4 bytes; launches alternate.
 ADJ_BYTES_PER_CELL = {"stage2_adjoint": 12 * 4, "stage1_adjoint": 16 * 4, "mean": 14 * 4}
+# DRAM traffic of k_adjoint<float, minmod> per cell per launch (read + write),
+# from the ncu capture summarised in profiles/k_adjoint_fp32_rtbox256x768x16_dram.md
+# (16 instances of the same grid; traffic grows in proportion to the cells).
+ADJ_TRAFFIC_BYTES_PER_CELL = 48.67
 STEP_BYTES_PER_CELL_UPDATE = 68 * 4  # forward 20s + segment recompute 20s (U1 kept) + adjoint 12s + 16s (sqrt checkpointing)
 
 
@@ -266,7 +270,8 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clk,
             "roofline": {"bound": "hbm", "kernel": "k_adjoint<float>", "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": ADJ_TRAFFIC_BYTES_PER_CELL * cells_per_launch,
                          "peak_source": peak_kind + " hbm_gbs",
                          "algorithmic_bytes_per_cell": ADJ_BYTES_PER_CELL["mean"],
                          "mean_launch_ms": {"adjoint": adj_ms, "stage1": st1_ms, "stage2": st2_ms}},
@@ -290,13 +295,14 @@ def run_ours(args):
 
 def run_profile_case(args):
     """Small case for ncu captures: 16 instances of the benchmark grid with a
-    short horizon (T = 0.01, about 25 RK2 steps) and store-all checkpointing;
-    about 1.5 GB on the device, each kernel's working set (4 x 50 MB) still
-    larger than L2."""
+    short horizon (T = 0.01, about 25 RK2 steps) and the benchmark's sqrt(N)
+    checkpointing, so one gradient launches the same kernel mix as a
+    benchmark step (about 130 launches instead of about 29,000); about 1 GB on
+    the device, each kernel's working set (4 x 50 MB) still larger than L2."""
     import paper_2608_04085_b300 as rt
     nb = 16
     probs = [I.single_256().replace(T=0.01) for _ in range(nb)]
-    with rt.Context(probs, precision=rt.RT_FP32_STATE, ckpt=rt.RT_CKPT_STORE_ALL) as ctx:
+    with rt.Context(probs, precision=rt.RT_FP32_STATE, ckpt=rt.RT_CKPT_SQRT) as ctx:
         v = ctx.project(I.gaussian_batch(range(nb), 2, NY, NX).reshape(-1), DELTA, to_budget=True)
         for k in range(3):
             ctx.set_kernel_timing(1 if k == 2 else 0)
