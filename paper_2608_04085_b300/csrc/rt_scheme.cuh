@@ -84,15 +84,15 @@ __device__ __forceinline__ void hllc(T rL, T uL, T vL, T pL, T rR, T uR, T vR, T
   const T SL = aL <= aR ? aL : aR;
   const T bL = uL + cL, bR = uR + cR;
   const T SR = bL >= bR ? bL : bR;
-  const T EL = pL / gm1 + T(0.5) * rL * (uL * uL + vL * vL);
-  const T ER = pR / gm1 + T(0.5) * rR * (uR * uR + vR * vR);
   const T dL = SL - uL, dR = SR - uR;
   const T mL = rL * dL, mR = rR * dR;
   const T Ss = ((pR - pL) + uL * mL - uR * mR) / (mL - mR);
   const bool left = (SL >= T(0)) || (Ss >= T(0));
   const bool star = left ? !(SL >= T(0)) : (SR >= T(0));
   const T r = left ? rL : rR, u = left ? uL : uR, v = left ? vL : vR, p = left ? pL : pR;
-  const T E = left ? EL : ER, S = left ? SL : SR, m = left ? mL : mR;
+  const T S = left ? SL : SR, m = left ? mL : mR;
+  // total energy of the side whose flux is taken (the other side's is not needed)
+  const T E = p / gm1 + T(0.5) * r * (u * u + v * v);
   const T f0 = r * u;
   F[0] = f0;
   F[1] = f0 * u + p;
@@ -121,8 +121,6 @@ __device__ __forceinline__ void hllc_vjp(T rL, T uL, T vL, T pL, T rR, T uR, T v
   const T bL = uL + cL, bR = uR + cR;
   const bool srL = bL >= bR;
   const T SR = srL ? bL : bR;
-  const T EL = pL / gm1 + T(0.5) * rL * (uL * uL + vL * vL);
-  const T ER = pR / gm1 + T(0.5) * rR * (uR * uR + vR * vR);
   const T dL = SL - uL, dR = SR - uR;
   const T mL = rL * dL, mR = rR * dR;
   const T den = mL - mR;
@@ -130,7 +128,8 @@ __device__ __forceinline__ void hllc_vjp(T rL, T uL, T vL, T pL, T rR, T uR, T v
   const bool left = (SL >= T(0)) || (Ss >= T(0));
   const bool star = left ? !(SL >= T(0)) : (SR >= T(0));
   const T r = left ? rL : rR, u = left ? uL : uR, v = left ? vL : vR, p = left ? pL : pR;
-  const T E = left ? EL : ER, S = left ? SL : SR, m = left ? mL : mR;
+  const T S = left ? SL : SR, m = left ? mL : mR;
+  const T E = p / gm1 + T(0.5) * r * (u * u + v * v);
   const T f0 = r * u;
 
   // physical-flux part of the chosen side
