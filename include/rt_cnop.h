@@ -20,9 +20,13 @@
  *   * Every call returns rt_status; no C++ exception crosses the ABI. On
  *     failure rt_last_error(ctx) returns a message owned by the context.
  *   * A context owns all device memory (states, checkpoints, dt records) and
- *     runs on the CUDA stream given to rt_init (NULL = legacy default
- *     stream). Calls are synchronous with respect to the host: they return
- *     after their device work has finished.
+ *     a CUDA stream of its own; each call first orders that stream after the
+ *     stream given to rt_init (NULL = legacy default stream), so device
+ *     inputs produced there are complete before they are read. Calls are
+ *     synchronous with respect to the host: they return after their device
+ *     work has finished. The time loop and the checkpoint segments of the
+ *     reverse sweep run as CUDA graphs captured on first use and replayed
+ *     from a per-context cache (environment RT_CNOP_GRAPHS=0 disables them).
  *   * Perturbations and gradients are FP64, layout [instance][component][ny][nx]
  *     (C-contiguous, x fastest); instances are concatenated in order, each
  *     with perturb_ncomp components (1: u_y only; 2: u_x then u_y).

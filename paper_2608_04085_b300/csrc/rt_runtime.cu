@@ -10,7 +10,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -22,10 +24,29 @@
 using rt::InstDev;
 using rt::RunDev;
 
+// Instantiated CUDA graph of a chunk of time-step launches, keyed by
+// everything that is baked into its kernel arguments.
+struct GraphKey {
+  int what, kind, mode, variant, lim, S, a, b;
+  bool operator<(const GraphKey& o) const {
+    return std::tie(what, kind, mode, variant, lim, S, a, b) <
+           std::tie(o.what, o.kind, o.mode, o.variant, o.lim, o.S, o.a, o.b);
+  }
+};
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  long long launches = 0;
+  long long kind_launches[3] = {0, 0, 0};
+};
+
 struct rt_ctx {
   int n_inst = 0;
   rt_options opt{};
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;       // the context's own stream (capturable)
+  cudaStream_t user_stream = nullptr;  // the caller's stream; work is ordered after it
+  cudaEvent_t ev_in = nullptr;
+  bool graphs = true;
+  std::map<GraphKey, GraphEntry> gcache;
   int device = 0;
   std::vector<rt_problem> prob;
   std::vector<InstDev> h_inst;
@@ -194,6 +215,53 @@ cudaError_t adjoint(rt_ctx* c, const T* U, const T* K, double ks, const T* E, do
   return e;
 }
 
+// Steps per captured chunk of the time loop.
+constexpr int kGraphChunk = 64;
+
+// Run `enqueue` (a fixed sequence of launches) as a cached CUDA graph: the
+// first call captures and instantiates it, later calls with the same key
+// replay it. Sampled kernel timing bypasses the graphs.
+template <class F>
+rt_status run_graph(rt_ctx* c, const GraphKey& key, F&& enqueue) {
+  if (!c->graphs || c->time_every > 0) return enqueue();
+  auto it = c->gcache.find(key);
+  if (it == c->gcache.end()) {
+    const long long l0 = c->launches;
+    long long k0[3];
+    for (int k = 0; k < 3; ++k) k0[k] = c->kind_launches[k];
+    CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    const rt_status s = enqueue();
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (s != RT_OK) {
+      if (e == cudaSuccess && g) cudaGraphDestroy(g);
+      return s;
+    }
+    CU(e);
+    GraphEntry ent;
+    const cudaError_t ei = cudaGraphInstantiate(&ent.exec, g, 0);
+    cudaGraphDestroy(g);
+    CU(ei);
+    ent.launches = c->launches - l0;
+    for (int k = 0; k < 3; ++k) ent.kind_launches[k] = c->kind_launches[k] - k0[k];
+    c->launches = l0;  // counted below, when the graph runs
+    for (int k = 0; k < 3; ++k) c->kind_launches[k] = k0[k];
+    it = c->gcache.emplace(key, ent).first;
+  }
+  CU(cudaGraphLaunch(it->second.exec, c->stream));
+  c->launches += it->second.launches;
+  for (int k = 0; k < 3; ++k) c->kind_launches[k] += it->second.kind_launches[k];
+  return RT_OK;
+}
+
+// Order the context's stream after the caller's stream (device inputs the
+// caller produced there are complete before the library reads them).
+rt_status enter(rt_ctx* c) {
+  CU(cudaEventRecord(c->ev_in, c->user_stream));
+  CU(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
+  return RT_OK;
+}
+
 void reset_accounting(rt_ctx* c) {
   c->launches = 0;
   for (int k = 0; k < 3; ++k) { c->kind_launches[k] = 0; c->kind_ms[k] = 0.0; c->kind_samples[k] = 0; }
@@ -344,26 +412,35 @@ rt_status march(rt_ctx* c, const Plan& plan, int mode, int n_est, int replay_ste
   const int smode = mode == 1 ? 1 : 0;
   std::vector<int> nstep, status;
   std::vector<double> t;
-  for (;;) {
-    for (; n < target; ++n) {
-      if (n >= c->opt.max_steps) return fail(c, RT_EINVAL, "step limit %d reached", c->opt.max_steps);
+  auto steps = [&](int a, int b) -> rt_status {
+    for (int k = a; k < b; ++k) {
       void *src, *dst, *u1 = c->sU1;
       if (plan.kind == 2) {
-        if (n + 1 >= plan.slots) return fail(c, RT_ENOMEM, "stored-state plan ran out of slots at step %d", n);
-        src = c->pool[n];
-        dst = c->pool[n + 1];
-        u1 = c->pool1[n];
+        src = c->pool[k];
+        dst = c->pool[k + 1];
+        u1 = c->pool1[k];
       } else {
-        src = (n & 1) ? c->sB : c->sA;
-        dst = (n & 1) ? c->sA : c->sB;
-        if (plan.kind == 1 && n % plan.S == 0) {
-          const size_t k = n / plan.S;
-          CHK(ensure_pool(c, plan.S + k + 1));
-          CU(cudaMemcpyAsync(c->pool[plan.S + k], src, c->slot_bytes, cudaMemcpyDeviceToDevice, c->stream));
-        }
+        src = (k & 1) ? c->sB : c->sA;
+        dst = (k & 1) ? c->sA : c->sB;
+        if (plan.kind == 1 && k % plan.S == 0)
+          CU(cudaMemcpyAsync(c->pool[plan.S + k / plan.S], src, c->slot_bytes, cudaMemcpyDeviceToDevice,
+                             c->stream));
       }
-      CU(stage<T>(c, 1, smode == 1 ? 2 : 0, slotp<T>(src), nullptr, slotp<T>(u1), n));
-      CU(stage<T>(c, 2, smode, slotp<T>(u1), slotp<T>(src), slotp<T>(dst), n));
+      CU(stage<T>(c, 1, smode == 1 ? 2 : 0, slotp<T>(src), nullptr, slotp<T>(u1), k));
+      CU(stage<T>(c, 2, smode, slotp<T>(u1), slotp<T>(src), slotp<T>(dst), k));
+    }
+    return RT_OK;
+  };
+  for (;;) {
+    while (n < target) {
+      const int b = std::min(target, (n / kGraphChunk + 1) * kGraphChunk);
+      if (b > c->opt.max_steps) return fail(c, RT_EINVAL, "step limit %d reached", c->opt.max_steps);
+      if (plan.kind == 2 && b >= plan.slots)
+        return fail(c, RT_ENOMEM, "stored-state plan ran out of slots at step %d", b);
+      if (plan.kind == 1) CHK(ensure_pool(c, plan.S + (b - 1) / plan.S + 1));  // no allocation inside a capture
+      const GraphKey key{0, plan.kind, smode, c->stage_variant, c->lim, plan.S, n, b};
+      CHK(run_graph(c, key, [&] { return steps(n, b); }));
+      n = b;
     }
     CHK(read_run(c, nstep, t, status));
     CHK(nonfinite(c, status, nullptr));
@@ -581,7 +658,7 @@ rt_status gradient_impl(rt_ctx* c, const double* d_v, double* J_out, double* d_g
     return RT_OK;
   };
   int segments = 1;
-  if (plan.kind == 3) {
+  if (plan.kind == 3) {  // dynamic recursion: launched directly
     Revolve<T> rv;
     rv.c = c;
     for (int k = 0; k < plan.slots; ++k) rv.free.push_back(c->pool[4 + k]);
@@ -595,7 +672,15 @@ rt_status gradient_impl(rt_ctx* c, const double* d_v, double* J_out, double* d_g
     if (N > 0) CHK(rv.reverse(0, N, c->pool[0]));
     segments = -(int)std::min<long long>(rv.recomputed, 2000000000LL);  // reported as minus the recomputed steps
   } else if (plan.kind == 2) {
-    for (int n = N - 1; n >= 0; --n) CHK(reverse_step(n, slotp<T>(c->pool[n]), slotp<T>(c->pool1[n])));
+    for (int hi = N; hi > 0;) {
+      const int lo = ((hi - 1) / kGraphChunk) * kGraphChunk;
+      const GraphKey key{1, 2, 0, c->stage_variant, c->lim, 0, lo, hi};
+      CHK(run_graph(c, key, [&]() -> rt_status {
+        for (int n = hi - 1; n >= lo; --n) CHK(reverse_step(n, slotp<T>(c->pool[n]), slotp<T>(c->pool1[n])));
+        return RT_OK;
+      }));
+      hi = lo;
+    }
   } else {
     const int S = plan.S;
     segments = (N + S - 1) / S;
@@ -604,11 +689,15 @@ rt_status gradient_impl(rt_ctx* c, const double* d_v, double* J_out, double* d_g
       auto seg = [&](int n) -> T* { return n == n0 ? slotp<T>(c->pool[S + k]) : slotp<T>(c->pool[n - n0]); };
       auto seg1 = [&](int n) -> T* { return slotp<T>(c->pool1[n - n0]); };
       // recompute the segment from its checkpoint, keeping U^n and U1 of every step
-      for (int n = n0; n < n1; ++n) {
-        CU(stage<T>(c, 1, 2, seg(n), nullptr, seg1(n), n));
-        if (n < n1 - 1) CU(stage<T>(c, 2, 2, seg1(n), seg(n), seg(n + 1), n));
-      }
-      for (int n = n1 - 1; n >= n0; --n) CHK(reverse_step(n, seg(n), seg1(n)));
+      const GraphKey key{2, 1, 0, c->stage_variant, c->lim, S, n0, n1};
+      CHK(run_graph(c, key, [&]() -> rt_status {
+        for (int n = n0; n < n1; ++n) {
+          CU(stage<T>(c, 1, 2, seg(n), nullptr, seg1(n), n));
+          if (n < n1 - 1) CU(stage<T>(c, 2, 2, seg1(n), seg(n), seg(n + 1), n));
+        }
+        for (int n = n1 - 1; n >= n0; --n) CHK(reverse_step(n, seg(n), seg1(n)));
+        return RT_OK;
+      }));
     }
   }
   CU(rt::launch_grad<T>(c->d_inst, c->d_tiles, c->ntiles, lam[0], d_v, d_g, c->stream));
@@ -867,7 +956,7 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
     return bail(RT_EINVAL);
   }
   c->esz = c->opt.precision == RT_FP64 ? sizeof(double) : sizeof(float);
-  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->user_stream = static_cast<cudaStream_t>(cuda_stream);
   c->prob.assign(problems, problems + n_instances);
   for (int i = 0; i < n_instances; ++i) {
     rt_status s = validate(c, c->prob[i], i);
@@ -986,8 +1075,14 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
   INIT_CU(cudaMalloc(&c->d_sums, (size_t)N * 2 * sizeof(double)));
   INIT_CU(cudaMalloc(&c->d_scal, (size_t)N * 4 * sizeof(double)));
   INIT_CU(cudaMalloc(&c->d_ek, c->total_cells * sizeof(double)));
+  INIT_CU(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
   INIT_CU(cudaEventCreate(&c->ev0));
   INIT_CU(cudaEventCreate(&c->ev1));
+  INIT_CU(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+  {
+    const char* g = getenv("RT_CNOP_GRAPHS");
+    c->graphs = !(g && g[0] == '0');
+  }
   INIT_CU(c->esz == 8 ? rt::configure_kernels<double>() : rt::configure_kernels<float>());
   size_t freeb = 0, totb = 0;
   INIT_CU(cudaMemGetInfo(&freeb, &totb));
@@ -1024,7 +1119,13 @@ void rt_destroy(rt_ctx* c) {
     if (p) cudaFree(p);
   for (void* p : c->pool) cudaFree(p);
   for (void* p : c->pool1) cudaFree(p);
+  for (auto& kv : c->gcache) cudaGraphExecDestroy(kv.second.exec);
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->stream) {
+    cudaStreamSynchronize(c->stream);
+    cudaStreamDestroy(c->stream);
+  }
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   delete c;
@@ -1044,6 +1145,7 @@ rt_status rt_forward(rt_ctx* c, const double* v0, int flags, double* J_out, doub
   if (!c || !v0 || !J_out) return fail(c, RT_EINVAL, "null argument");
   c->err.clear();
   CHK(ensure_fields(c, false));
+  CHK(enter(c));
   reset_accounting(c);
   Timer tm(c);
   CHK(copy_in(c, v0, flags, c->d_v));
@@ -1061,6 +1163,7 @@ rt_status rt_gradient(rt_ctx* c, const double* v0, int flags, double* J_out, dou
   if (flags & RT_REPLAY_DT) return fail(c, RT_EINVAL, "rt_gradient always freezes its own dt sequence");
   c->err.clear();
   CHK(ensure_fields(c, false));
+  CHK(enter(c));
   reset_accounting(c);
   Timer tm(c);
   CHK(copy_in(c, v0, flags, c->d_v));
@@ -1077,6 +1180,7 @@ rt_status rt_gradient(rt_ctx* c, const double* v0, int flags, double* J_out, dou
 rt_status rt_constraint(rt_ctx* c, const double* v, int flags, double* C_out) {
   if (!c || !v || !C_out) return fail(c, RT_EINVAL, "null argument");
   CHK(ensure_fields(c, false));
+  CHK(enter(c));
   CHK(copy_in(c, v, flags, c->d_v));
   std::vector<double> C;
   CHK(field_sums(c, 0, c->d_v, nullptr, C));
@@ -1087,6 +1191,7 @@ rt_status rt_constraint(rt_ctx* c, const double* v, int flags, double* C_out) {
 rt_status rt_project(rt_ctx* c, double* v, int flags, const double* eps, int to_budget) {
   if (!c || !v || !eps) return fail(c, RT_EINVAL, "null argument");
   CHK(ensure_fields(c, false));
+  CHK(enter(c));
   CHK(copy_in(c, v, flags, c->d_v));
   std::vector<double> C;
   CHK(field_sums(c, 0, c->d_v, nullptr, C));
@@ -1169,6 +1274,7 @@ rt_status cnop_solve(rt_ctx* c, const cnop_params* prm, double* v_inout, int fla
   if (!c || !prm || !v_inout || !prm->eps) return fail(c, RT_EINVAL, "null argument");
   if (prm->max_iter < 0) return fail(c, RT_EINVAL, "max_iter < 0");
   c->err.clear();
+  CHK(enter(c));
   Timer tm(c);
   rt_status s = c->esz == 8 ? cnop_impl<double>(c, prm, v_inout, flags, J_out, res)
                             : cnop_impl<float>(c, prm, v_inout, flags, J_out, res);
