@@ -294,6 +294,39 @@ __device__ __forceinline__ void raw_to_prim(const T u[4], const InstDev& I, int 
   }
 }
 
+// Load a tile of primitive states into shared memory (layout [4][EY][EX],
+// origin (gx0, gy0)), issuing every global load of this thread's cells before
+// converting any of them, so that they are in flight together.
+template <class T, int EX, int EY>
+__device__ __forceinline__ void load_prim_tile(const T* __restrict__ Ui, const InstDev& I, long long cells, int gx0,
+                                               int gy0, const Phys<T>& P, T* __restrict__ sW) {
+  constexpr int N = EX * EY;
+  constexpr int PER = (N + NTH - 1) / NTH;
+  T u[PER][4];
+  int rr[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int e = threadIdx.x + k * NTH;
+    rr[k] = 0;
+    if (e < N) {
+      const int ey = e / EX, ex = e - ey * EX;
+      rr[k] = gy0 + ey;
+      load_raw(Ui, I.nx, I.ny, cells, wrap_x(gx0 + ex, I.nx), rr[k], u[k]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int e = threadIdx.x + k * NTH;
+    if (e < N) {
+      const int ey = e / EX, ex = e - ey * EX;
+      T W[4];
+      raw_to_prim(u[k], I, rr[k], P, W);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sW[(q * EY + ey) * EX + ex] = W[q];
+    }
+  }
+}
+
 template <class T, int STAGE, int MODE, int LIM>
 __global__ void __launch_bounds__(32 * STRIP_WARPS, 6) k_stage_sweep(const InstDev* __restrict__ insts,
                                                             const int4* __restrict__ strips, int nstrips,
@@ -476,13 +509,7 @@ __global__ void __launch_bounds__(NTH) k_stage_tile(const InstDev* __restrict__ 
   const T* Si = src + 4 * I.cell_off;
   const int x0 = tl.y, y0 = tl.z;
   const int lim = LIM >= 0 ? LIM : I.limiter;
-  for (int e = threadIdx.x; e < ST_EX * ST_EY; e += NTH) {
-    const int ey = e / ST_EX, ex = e - ey * ST_EX;
-    T W[4];
-    load_prim(Si, I, cells, x0 + ex - 2, y0 + ey - 2, P, W);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) sW[(q * ST_EY + ey) * ST_EX + ex] = W[q];
-  }
+  load_prim_tile<T, ST_EX, ST_EY>(Si, I, cells, x0 - 2, y0 - 2, P, sW);
   __syncthreads();
   for (int f = threadIdx.x; f < ST_NFX + ST_NFY; f += NTH) {
     T w[4][4], F[4];
@@ -589,21 +616,29 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
   const int x0 = tl.y, y0 = tl.z, nx = I.nx, ny = I.ny;
   const int lim = LIM >= 0 ? LIM : I.limiter;
 
-  for (int e = threadIdx.x; e < ADJ_AX * ADJ_AY; e += NTH) {
-    const int ey = e / ADJ_AX, ex = e - ey * ADJ_AX;
-    T W[4];
-    load_prim(Ui, I, cells, x0 + ex - 3, y0 + ey - 3, P, W);
+  {  // cotangent tile: all loads first
+    constexpr int N = ADJ_KX * ADJ_KY, PER = (N + NTH - 1) / NTH;
+    T kv[PER][4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) sW[(q * ADJ_AY + ey) * ADJ_AX + ex] = W[q];
-  }
-  for (int e = threadIdx.x; e < ADJ_KX * ADJ_KY; e += NTH) {
-    const int ey = e / ADJ_KX, ex = e - ey * ADJ_KX;
-    const int gy = y0 + ey - 2;
-    const int gx = wrap_x(x0 + ex - 2, nx);
-    const bool in = gy >= 0 && gy < ny;
-    const long long c = (long long)(in ? gy : 0) * nx + gx;
+    for (int k = 0; k < PER; ++k) {
+      const int e = threadIdx.x + k * NTH;
+      const int ey = e / ADJ_KX, ex = e - ey * ADJ_KX;
+      const int gy = y0 + ey - 2;
+      const bool in = e < N && gy >= 0 && gy < ny;
+      const long long c = in ? (long long)gy * nx + wrap_x(x0 + ex - 2, nx) : 0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) sK[(q * ADJ_KY + ey) * ADJ_KX + ex] = in ? kscale * Ki[q * cells + c] : T(0);
+      for (int q = 0; q < 4; ++q) kv[k][q] = in ? Ki[q * cells + c] : T(0);
+    }
+    load_prim_tile<T, ADJ_AX, ADJ_AY>(Ui, I, cells, x0 - 3, y0 - 3, P, sW);
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int e = threadIdx.x + k * NTH;
+      if (e < N) {
+        const int ey = e / ADJ_KX, ex = e - ey * ADJ_KX;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sK[(q * ADJ_KY + ey) * ADJ_KX + ex] = kscale * kv[k][q];
+      }
+    }
   }
   __syncthreads();
 
@@ -703,8 +738,10 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
     }
     if (gx < nx && gy < ny) {
       const long long c = (long long)gy * nx + gx;
-      const T r = Ui[c], mx = Ui[cells + c], my = Ui[2 * cells + c];
-      const T u = mx / r, v = my / r;
+      // rho, u_x, u_y of the cell from the primitive tile (the values mx/rho, my/rho)
+      const T r = sW[(0 * ADJ_AY + ty + 3) * ADJ_AX + tx + 3];
+      const T u = sW[(1 * ADJ_AY + ty + 3) * ADJ_AX + tx + 3];
+      const T v = sW[(2 * ADJ_AY + ty + 3) * ADJ_AX + tx + 3];
       const T* b = bW[pass];
       T bU[4];
       bU[0] = b[0] - (u * b[1] + v * b[2]) / r + P.gm1 * T(0.5) * (u * u + v * v) * b[3];
