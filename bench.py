@@ -49,7 +49,7 @@ ADJ_BYTES_PER_CELL = {"stage2_adjoint": 12 * 4, "stage1_adjoint": 16 * 4, "mean"
 # DRAM traffic of k_adjoint<float, minmod> per cell per launch (read + write),
 # from the ncu capture summarised in profiles/k_adjoint_fp32_rtbox256x768x16_dram.md
 # (16 instances of the same grid; traffic grows in proportion to the cells).
-ADJ_TRAFFIC_BYTES_PER_CELL = 48.67
+ADJ_TRAFFIC_BYTES_PER_CELL = 48.06
 STEP_BYTES_PER_CELL_UPDATE = 68 * 4  # forward 20s + segment recompute 20s (U1 kept) + adjoint 12s + 16s (sqrt checkpointing)
 
 
