@@ -9,15 +9,17 @@ plain parameter values).
 The time stepper, its tangent and its reverse sweep live in ``rt_oracle.cpp``
 (plain C++, FP64, built with ``-O2 -ffp-contract=off``); the CNOP pieces that
 act on whole fields (constraint, projection, random start, spectral projected
-gradient with a non-monotone line search, 1D Fourier spectrum, five-mode
-reconstruction) are plain NumPy here. Each function names the paper passage it
+gradient and projected L-BFGS with a non-monotone line search, 1D Fourier
+spectrum, five-mode reconstruction) are plain NumPy here. Each function names the paper passage it
 follows.
 
 Parity status: every function below is pinned by a ``-m "not gpu"`` test
 (``tests/test_oracle_*.py``) against closed forms, textbook solutions,
-invariants or brute force, except ``spg`` at finite amplitude, whose result has
-no closed form; it is pinned only in the small-amplitude limit, where it must
-reproduce the leading eigenvector of the tangent-linear problem.
+invariants or brute force, except ``spg`` and ``lbfgs`` at finite amplitude,
+whose results have no closed form (parity unpinned there); they are pinned in
+the small-amplitude limit, where they must reproduce the leading eigenvector of
+the tangent-linear problem, and ``projected_lbfgs`` / ``lbfgs_direction`` are
+pinned on analytic objectives and against the dense BFGS update.
 """
 from __future__ import annotations
 
@@ -296,6 +298,115 @@ def spg(w, v_start, eps, iters, memory=10, armijo=1e-4, alpha_min=1e-30, alpha_m
         if log is not None:
             log(records[-1])
     return {"v": v, "J": J, "history": hist, "records": records, "evals": evals, "grads": grads}
+
+
+# ------------------------------------- projected L-BFGS, Sec. 3.4 (Eq. projection)
+def lbfgs_direction(g, pairs, gamma):
+    """Two-loop recursion (Nocedal & Wright, Numerical Optimization, Alg. 7.4)
+    for the ascent direction p = H g, H the limited-memory inverse-Hessian
+    estimate of -J. ``pairs`` lists (s, y, rho) from oldest to newest, with
+    y = -(g_new - g_old) and rho = 1 / <s, y>; a pair with rho = 0 (one that
+    failed the curvature test) takes no part. The initial matrix is gamma I."""
+    q = np.array(g, dtype=np.float64, copy=True)
+    a = [0.0] * len(pairs)
+    for j in range(len(pairs) - 1, -1, -1):
+        s, y, rho = pairs[j]
+        a[j] = rho * float(np.sum(s * q))
+        q = q - a[j] * y
+    r = gamma * q
+    for j in range(len(pairs)):
+        s, y, rho = pairs[j]
+        b = rho * float(np.sum(y * r))
+        r = r + (a[j] - b) * s
+    return r
+
+
+def projected_lbfgs(value, value_and_grad, proj, v_start, iters, m=10, memory=10, armijo=1e-4,
+                    max_backtracks=30, log=None):
+    """Projected L-BFGS ascent with a non-monotone Armijo line search
+    (Sec. 3.4), on any objective: ``value(v)`` -> J, ``value_and_grad(v)`` ->
+    (J, dJ/dv), ``proj`` the projection P onto the feasible set.
+
+    Iteration k, from the feasible v with gradient g:
+      - p = H g by ``lbfgs_direction`` over the pairs of the last m
+        iterations; H0 = gamma I with gamma = <s, y> / <y, y> of the newest
+        stored pair, or ||v|| / ||g|| when none is stored;
+      - if <g, P(v + p) - v> <= 0 while pairs are stored, every pair is
+        dropped and p = (||v|| / ||g||) g (steepest-ascent restart);
+      - trial points v(lam) = P(v + lam p), lam = 1, 1/2, 1/4, ...; the first
+        with J(v(lam)) >= max(last ``memory`` accepted J) + armijo <g, v(lam) - v>
+        is taken (Grippo-Lampariello-Lucidi non-monotone rule). None within
+        ``max_backtracks`` trials ends the run;
+      - the pair (s, y) = (v_new - v, -(g_new - g)) is stored with
+        rho = 1 / <s, y> if <s, y> > 0 and rho = 0 otherwise; the memory
+        keeps the pairs of the last m iterations.
+    Returns a dict with v, J, the accepted J history, per-iteration records
+    and evaluation counts."""
+    v = np.array(v_start, dtype=np.float64, copy=True)
+    J, g = value_and_grad(v)
+    evals, grads = 1, 1
+    hist = [J]
+    pairs = []
+    records = []
+
+    def steepest_gamma(v, g):
+        return float(np.linalg.norm(v) / max(np.linalg.norm(g), 1e-300))
+
+    for k in range(iters):
+        stored = [pr for pr in pairs if pr[2] > 0.0]
+        if stored:
+            s, y, _ = stored[-1]
+            gamma = float(np.sum(s * y)) / float(np.sum(y * y))
+        else:
+            gamma = steepest_gamma(v, g)
+        p = lbfgs_direction(g, pairs, gamma)
+        restart = False
+        if stored and float(np.sum(g * (proj(v + p) - v))) <= 0.0:
+            pairs = [(s, y, 0.0) for s, y, _ in pairs]
+            p = steepest_gamma(v, g) * g
+            restart = True
+        Jref = max(hist[-memory:])
+        lam = 1.0
+        accepted = False
+        for _ in range(max_backtracks):
+            vt = proj(v + lam * p)
+            Jt = value(vt)
+            evals += 1
+            if Jt >= Jref + armijo * float(np.sum(g * (vt - v))):
+                accepted = True
+                break
+            lam *= 0.5
+        if not accepted:
+            break
+        Jn, gn = value_and_grad(vt)
+        grads += 1
+        s = vt - v
+        y = -(gn - g)
+        sy = float(np.sum(s * y))
+        pairs.append((s, y, 1.0 / sy if sy > 0.0 else 0.0))
+        if len(pairs) > m:
+            pairs.pop(0)
+        v, J, g = vt, Jn, gn
+        hist.append(J)
+        records.append({"iter": k, "J": J, "lam": lam, "gamma": gamma, "restart": restart, "sy": sy})
+        if log is not None:
+            log(records[-1])
+    return {"v": v, "J": J, "history": hist, "records": records, "evals": evals, "grads": grads}
+
+
+def lbfgs(w, v_start, eps, iters, m=10, memory=10, armijo=1e-4, max_backtracks=30, ek0=None, log=None):
+    """The CNOP by projected L-BFGS (Sec. 3.4): ``projected_lbfgs`` on the
+    workload's objective with the radial projection P onto {C <= eps}
+    (Eq. projection), starting from P(v_start)."""
+    def value(v):
+        return objective_value(w, forward(w, v, ek0=ek0))
+
+    def value_and_grad(v):
+        J, g, _ = value_and_gradient(w, v, ek0)
+        return J, g
+
+    return projected_lbfgs(value, value_and_grad, lambda v: project(w, v, eps), project(w, v_start, eps),
+                           iters, m=m, memory=memory, armijo=armijo, max_backtracks=max_backtracks, log=log)
 
 
 # ------------------------------------------------- spectra, Sec. 4.2 Eq. fourier_coeff

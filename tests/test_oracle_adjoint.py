@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 import rt_inputs as I
+from tests import tlm_eigen
 
 CASES = {
     "box_minmod_ke": I.rt_box(12, 36, nsteps=30),
@@ -131,44 +132,14 @@ def test_five_modes_keeps_a_five_mode_field(oracle_lib):
 
 
 # --------------------------------------------- CNOP in the tangent-linear limit
-def _steady_case():
-    # stratified, g = 0: the unperturbed state is exactly steady, so J_KE is a
-    # pure quadratic form at small amplitude and its maximiser on {C = eps} is
-    # the leading generalised eigenvector of (M^T W_T M, W_0).
-    return I.rt_box(8, 24, g_y=0.0, nsteps=30, limiter=I.LIM_NONE)
-
-
-def _tlm_eigen(o, w):
-    nv = w.ncomp * w.ny * w.nx
-    zero = np.zeros((w.ncomp, w.ny, w.nx))
-    base = o.forward(w, zero)
-    dt = base["dt"]
-    rho_T = base["U"][0]
-    dx, dy = o.grid_spacing(w)
-    cols = []
-    for c in range(nv):
-        e = np.zeros(nv)
-        e[c] = 1.0
-        _, dU = o.tangent_state(w, zero, e.reshape(zero.shape), dt)
-        cols.append(dU[1:3].ravel())
-    M = np.array(cols).T
-    wT = np.tile((dx * dy / rho_T).ravel(), 2)
-    rho0, _ = o.base_state(w)
-    w0 = np.tile(np.repeat(rho0 * dx * dy, w.nx), w.ncomp)
-    H = M.T @ (wT[:, None] * M)
-    s = 1.0 / np.sqrt(w0)
-    lam, V = np.linalg.eigh(s[:, None] * H * s[None, :])
-    return lam[::-1], (s[:, None] * V)[:, ::-1], w0, dt
-
-
 def test_cnop_small_amplitude_matches_tangent_linear_eigenvector(oracle_lib):
     """SPG CNOP at delta = 1e-12 puts >= 99% of its W0-energy in the leading
     eigenspace of the brute-force tangent-linear problem, and 2 J / (2 C)
     matches the top eigenvalue to 1e-3. Power iteration through the reverse
     sweep (v <- W0^-1 grad J) reaches the same eigenvalue."""
     o = oracle_lib
-    w = _steady_case()
-    lam, V, w0, dt = _tlm_eigen(o, w)
+    w = tlm_eigen.steady_case()
+    lam, V, w0, dt = tlm_eigen.tlm_eigen(o, w)
     nlead = int(np.sum(lam >= lam[0] * (1 - 1e-6)))
     lead = V[:, :nlead]
     eps = 1e-12
@@ -194,7 +165,7 @@ def test_objective_is_quadratic_at_small_amplitude(oracle_lib):
     """J_KE(s v) / J_KE(v) -> s^2 when the unperturbed state is steady (dt
     sequence frozen at the unperturbed one; the ratio's error is O(|v|))."""
     o = oracle_lib
-    w = _steady_case()
+    w = tlm_eigen.steady_case()
     dt = o.forward(w, np.zeros((w.ncomp, w.ny, w.nx)))["dt"]
     for amp, tol in ((1e-10, 1e-4), (1e-14, 1e-6)):
         v = o.scale_to_budget(w, I.gaussian_field(3, w.ncomp, w.ny, w.nx), amp)
