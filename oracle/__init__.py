@@ -322,36 +322,60 @@ def lbfgs_direction(g, pairs, gamma):
 
 
 def projected_lbfgs(value, value_and_grad, proj, v_start, iters, m=10, memory=10, armijo=1e-4,
-                    max_backtracks=30, log=None):
+                    max_backtracks=30, normal=None, active=None, log=None):
     """Projected L-BFGS ascent with a non-monotone Armijo line search
     (Sec. 3.4), on any objective: ``value(v)`` -> J, ``value_and_grad(v)`` ->
-    (J, dJ/dv), ``proj`` the projection P onto the feasible set.
+    (J, dJ/dv), ``proj`` the radial projection P onto {C <= eps} of a
+    constraint C homogeneous of degree 2, ``normal(v)`` = dC/dv and
+    ``active(v)`` true when v lies on C = eps (both may be None: no
+    constraint surface).
 
-    Iteration k, from the feasible v with gradient g:
-      - p = H g by ``lbfgs_direction`` over the pairs of the last m
+    At an iterate on the surface the search runs on it:
+      - the model gradient is the gradient of J o P there,
+        gh = g - (<g, v> / <n, v>) n, n = normal(v) (elsewhere gh = g);
+      - the direction is made tangent to the surface,
+        p <- p - (<n, p> / <n, n>) n, so that C(v + lam p) >= eps and P puts
+        every trial point back on the surface.
+    Iteration k, from v with model gradient gh:
+      - p = H gh by ``lbfgs_direction`` over the pairs of the last m
         iterations; H0 = gamma I with gamma = <s, y> / <y, y> of the newest
-        stored pair, or ||v|| / ||g|| when none is stored;
-      - if <g, P(v + p) - v> <= 0 while pairs are stored, every pair is
-        dropped and p = (||v|| / ||g||) g (steepest-ascent restart);
+        stored pair, or ||v|| / ||gh|| when none is stored; then tangent;
+      - if <gh, p> <= 0 while pairs are stored, every pair is dropped and
+        p = (||v|| / ||gh||) gh, then tangent (steepest-ascent restart);
       - trial points v(lam) = P(v + lam p), lam = 1, 1/2, 1/4, ...; the first
-        with J(v(lam)) >= max(last ``memory`` accepted J) + armijo <g, v(lam) - v>
+        with J(v(lam)) >= max(last ``memory`` accepted J) + armijo <gh, v(lam) - v>
         is taken (Grippo-Lampariello-Lucidi non-monotone rule). None within
         ``max_backtracks`` trials ends the run;
-      - the pair (s, y) = (v_new - v, -(g_new - g)) is stored with
+      - the pair (s, y) = (v_new - v, -(gh_new - gh)) is stored with
         rho = 1 / <s, y> if <s, y> > 0 and rho = 0 otherwise; the memory
         keeps the pairs of the last m iterations.
     Returns a dict with v, J, the accepted J history, per-iteration records
     and evaluation counts."""
-    v = np.array(v_start, dtype=np.float64, copy=True)
-    J, g = value_and_grad(v)
-    evals, grads = 1, 1
-    hist = [J]
-    pairs = []
-    records = []
+    def on_surface(v):
+        return normal is not None and active is not None and active(v)
+
+    def model_gradient(v, g):
+        if not on_surface(v):
+            return g
+        n = normal(v)
+        return g - (float(np.sum(g * v)) / float(np.sum(n * v))) * n
+
+    def tangent(v, p):
+        if not on_surface(v):
+            return p
+        n = normal(v)
+        return p - (float(np.sum(n * p)) / float(np.sum(n * n))) * n
 
     def steepest_gamma(v, g):
         return float(np.linalg.norm(v) / max(np.linalg.norm(g), 1e-300))
 
+    v = np.array(v_start, dtype=np.float64, copy=True)
+    J, g = value_and_grad(v)
+    g = model_gradient(v, g)
+    evals, grads = 1, 1
+    hist = [J]
+    pairs = []
+    records = []
     for k in range(iters):
         stored = [pr for pr in pairs if pr[2] > 0.0]
         if stored:
@@ -359,11 +383,11 @@ def projected_lbfgs(value, value_and_grad, proj, v_start, iters, m=10, memory=10
             gamma = float(np.sum(s * y)) / float(np.sum(y * y))
         else:
             gamma = steepest_gamma(v, g)
-        p = lbfgs_direction(g, pairs, gamma)
+        p = tangent(v, lbfgs_direction(g, pairs, gamma))
         restart = False
-        if stored and float(np.sum(g * (proj(v + p) - v))) <= 0.0:
+        if stored and float(np.sum(g * p)) <= 0.0:
             pairs = [(s, y, 0.0) for s, y, _ in pairs]
-            p = steepest_gamma(v, g) * g
+            p = tangent(v, steepest_gamma(v, g) * g)
             restart = True
         Jref = max(hist[-memory:])
         lam = 1.0
@@ -379,6 +403,7 @@ def projected_lbfgs(value, value_and_grad, proj, v_start, iters, m=10, memory=10
         if not accepted:
             break
         Jn, gn = value_and_grad(vt)
+        gn = model_gradient(vt, gn)
         grads += 1
         s = vt - v
         y = -(gn - g)
@@ -394,10 +419,20 @@ def projected_lbfgs(value, value_and_grad, proj, v_start, iters, m=10, memory=10
     return {"v": v, "J": J, "history": hist, "records": records, "evals": evals, "grads": grads}
 
 
+def constraint_normal(w, v):
+    """dC/dv of Eq. constraint: rho0 v dx dy per perturbed component."""
+    rho0, _ = base_state(w)
+    dx, dy = grid_spacing(w)
+    v = np.asarray(v, dtype=np.float64).reshape(w.ncomp, w.ny, w.nx)
+    return rho0[None, :, None] * v * dx * dy
+
+
 def lbfgs(w, v_start, eps, iters, m=10, memory=10, armijo=1e-4, max_backtracks=30, ek0=None, log=None):
     """The CNOP by projected L-BFGS (Sec. 3.4): ``projected_lbfgs`` on the
     workload's objective with the radial projection P onto {C <= eps}
-    (Eq. projection), starting from P(v_start)."""
+    (Eq. projection), starting from P(v_start). The iterate counts as on the
+    budget surface when C(v) >= eps (1 - 1e-10), i.e. P placed it there up
+    to rounding."""
     def value(v):
         return objective_value(w, forward(w, v, ek0=ek0))
 
@@ -406,7 +441,9 @@ def lbfgs(w, v_start, eps, iters, m=10, memory=10, armijo=1e-4, max_backtracks=3
         return J, g
 
     return projected_lbfgs(value, value_and_grad, lambda v: project(w, v, eps), project(w, v_start, eps),
-                           iters, m=m, memory=memory, armijo=armijo, max_backtracks=max_backtracks, log=log)
+                           iters, m=m, memory=memory, armijo=armijo, max_backtracks=max_backtracks,
+                           normal=lambda v: constraint_normal(w, v),
+                           active=lambda v: constraint(w, v) >= eps * (1.0 - 1e-10), log=log)
 
 
 # ------------------------------------------------- spectra, Sec. 4.2 Eq. fourier_coeff

@@ -101,11 +101,21 @@ def test_sphere_quadratic_reaches_leading_eigenvector(oracle_lib):
         return value(v), 2.0 * (A @ v)
 
     v0 = proj(rng.standard_normal(n) * 10)
-    res = oracle_lib.projected_lbfgs(value, vg, proj, v0, iters=300)
+    kw = dict(normal=lambda v: 2.0 * v, active=lambda v: float(v @ v) >= r * (1 - 1e-10))
+    res = oracle_lib.projected_lbfgs(value, vg, proj, v0, iters=300, **kw)
     v = res["v"]
     cos = abs(v @ V[:, -1]) / np.linalg.norm(v)
     assert cos >= 1 - 1e-10, cos
     assert res["J"] == pytest.approx(lam[-1] * r, rel=1e-10)
+    # on the sphere the pairs carry the (positive) curvature of -J o P, and the
+    # quasi-Newton model converges far faster than scaled steepest ascent
+    n_it = 20
+    qn = oracle_lib.projected_lbfgs(value, vg, proj, v0, iters=n_it, **kw)
+    sd = oracle_lib.projected_lbfgs(value, vg, proj, v0, iters=n_it, m=0, **kw)
+    assert sum(rec["sy"] > 0 for rec in qn["records"]) >= n_it - 2
+    gap = lambda out: lam[-1] * r - out["J"]
+    assert gap(sd) > 1e-8
+    assert gap(qn) <= 1e-3 * gap(sd), (gap(qn), gap(sd))
 
 
 def test_monotone_memory_gives_nondecreasing_J(oracle_lib):
@@ -116,6 +126,7 @@ def test_monotone_memory_gives_nondecreasing_J(oracle_lib):
     h = res["history"]
     assert len(h) == 7
     assert all(b >= a for a, b in zip(h, h[1:])), h
+    assert sum(rec["sy"] > 0 for rec in res["records"]) >= 4
     assert o.constraint(w, res["v"]) == pytest.approx(1e-4, rel=1e-12)
 
 
