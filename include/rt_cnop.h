@@ -66,6 +66,7 @@ enum { RT_OBJ_KE = 0, RT_OBJ_EK_ANOMALY_L2 = 1 };
 enum { RT_FP64 = 0, RT_FP32_STATE = 1 };
 enum { RT_CKPT_AUTO = 0, RT_CKPT_STORE_ALL = 1, RT_CKPT_SQRT = 2, RT_CKPT_REVOLVE = 3 };
 enum { RT_STAGE_AUTO = 0, RT_STAGE_SWEEP = 1, RT_STAGE_TILE = 2 };
+enum { RT_CNOP_SPG = 0, RT_CNOP_LBFGS = 1 };
 
 /* flags for rt_forward / rt_gradient / rt_constraint / rt_project */
 enum { RT_DEVICE_PTRS = 1, RT_REPLAY_DT = 2 };
@@ -196,6 +197,8 @@ typedef struct {
   double alpha_min, alpha_max; /* spectral step safeguards */
   double h_loc;          /* > 0: multiply v_inout by exp(-(y-y_int)^2/(2 h_loc^2)) first */
   const double* eps;     /* budget per instance */
+  int method;            /* RT_CNOP_SPG or RT_CNOP_LBFGS */
+  int lbfgs_memory;      /* L-BFGS: pairs of the last m iterations; 0 = 10 (Sec. 3.4) */
 } cnop_params;
 
 typedef struct {
@@ -205,15 +208,26 @@ typedef struct {
   double ms;             /* device time of the whole solve */
 } cnop_result;
 
-/* CNOP by spectral projected gradient ascent (Sec. 3.4): every instance
- * starts from v_inout (a seeded random field; optionally localised by h_loc),
- * scaled onto C = eps, then iterates d = P(v + alpha g) - v, a non-monotone
- * Armijo backtracking line search along d, and the Barzilai-Borwein step
- * alpha = <s,s>/<s,y'> with y' = -(g_new - g_old). All instances advance in
- * lockstep through batched forward and gradient runs. On return v_inout
- * holds the CNOP of every instance and J_out[i] (nullable) its objective.
- * Errors: as rt_gradient; RT_ENOTCONVERGED when an instance found no
- * acceptable step (its last accepted iterate is returned). */
+/* CNOP search (Sec. 3.4, Eq. projection). Every instance starts from
+ * v_inout (a seeded random field; optionally localised by h_loc), scaled onto
+ * C = eps (a start with C = 0 is RT_EINVAL), and all instances advance in
+ * lockstep through batched forward and gradient runs; an instance that has
+ * stopped is switched off in those runs. Two methods:
+ *  RT_CNOP_LBFGS (the paper's): the ascent direction p = H g from the
+ *    two-loop recursion over the (s, y) pairs of the last lbfgs_memory
+ *    iterations, y = -(g_new - g_old), a pair with <s, y> <= 0 skipped,
+ *    H0 = <s, y>/<y, y> of the newest stored pair (||v||/||g|| when none);
+ *    if <g, P(v + p) - v> <= 0 the pairs are dropped and p = (||v||/||g||) g;
+ *    trial points P(v + lam p), lam = 1, 1/2, ..., accepted once
+ *    J >= max(last gll_memory J) + armijo_c <g, P(v + lam p) - v>.
+ *  RT_CNOP_SPG: d = P(v + alpha g) - v, trial points v + lam d accepted once
+ *    J >= max(last gll_memory J) + armijo_c lam <g, d>, and the
+ *    Barzilai-Borwein step alpha = <s,s>/<s,y> clipped to
+ *    [alpha_min, alpha_max] (alpha_max when <s,y> <= 0).
+ * On return v_inout holds the CNOP of every instance and J_out[i] (nullable)
+ * its objective. Errors: as rt_gradient; RT_EINVAL for an unknown method;
+ * RT_ENOTCONVERGED when an instance found no acceptable step within
+ * max_backtracks trials (its last accepted iterate is returned). */
 rt_status cnop_solve(rt_ctx* ctx, const cnop_params* prm, double* v_inout, int flags,
                      double* J_out, cnop_result* res);
 

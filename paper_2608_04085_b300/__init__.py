@@ -26,6 +26,7 @@ RT_FP64, RT_FP32_STATE = 0, 1
 RT_CKPT_AUTO, RT_CKPT_STORE_ALL, RT_CKPT_SQRT, RT_CKPT_REVOLVE = 0, 1, 2, 3
 RT_STAGE_AUTO, RT_STAGE_SWEEP, RT_STAGE_TILE = 0, 1, 2
 RT_DEVICE_PTRS, RT_REPLAY_DT = 1, 2
+RT_CNOP_SPG, RT_CNOP_LBFGS = 0, 1
 
 _STATUS = {1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENONFINITE", 5: "RT_ETIMEOUT",
            6: "RT_ENOTCONVERGED", 7: "RT_ESTATE"}
@@ -75,7 +76,8 @@ class RtRunStats(ctypes.Structure):
 class CnopParams(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int), ("gll_memory", ctypes.c_int), ("max_backtracks", ctypes.c_int),
                 ("armijo_c", ctypes.c_double), ("alpha_min", ctypes.c_double), ("alpha_max", ctypes.c_double),
-                ("h_loc", ctypes.c_double), ("eps", ctypes.POINTER(ctypes.c_double))]
+                ("h_loc", ctypes.c_double), ("eps", ctypes.POINTER(ctypes.c_double)),
+                ("method", ctypes.c_int), ("lbfgs_memory", ctypes.c_int)]
 
 
 class CnopResult(ctypes.Structure):
@@ -307,9 +309,10 @@ class Context:
         self._check(library().rt_kernel_times(self._h, _dptr(ms), sa, la))
         return {k: (ms[i], sa[i], la[i]) for i, k in enumerate(("stage1", "stage2", "adjoint"))}
 
-    def cnop(self, v_start, eps, iters, gll_memory=10, armijo_c=1e-4, alpha_min=1e-30, alpha_max=1e30,
-             max_backtracks=30, h_loc=0.0, raise_on_stall=False):
-        """CNOP by projected spectral gradient (cnop_solve). Returns (v, J, result)."""
+    def cnop(self, v_start, eps, iters, method=RT_CNOP_LBFGS, lbfgs_memory=10, gll_memory=10, armijo_c=1e-4,
+             alpha_min=1e-30, alpha_max=1e30, max_backtracks=30, h_loc=0.0, raise_on_stall=False):
+        """CNOP search (cnop_solve): projected L-BFGS (the default) or spectral
+        projected gradient. Returns (v, J, result)."""
         if hasattr(v_start, "clone"):
             v = v_start.clone()
         else:
@@ -317,7 +320,7 @@ class Context:
         p, flags, keep = self._arg(v)
         e = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, dtype=np.float64), (self.n,)))
         prm = CnopParams(int(iters), int(gll_memory), int(max_backtracks), float(armijo_c), float(alpha_min),
-                         float(alpha_max), float(h_loc), _dptr(e))
+                         float(alpha_max), float(h_loc), _dptr(e), int(method), int(lbfgs_memory))
         J = np.zeros(self.n)
         res = CnopResult()
         st = library().cnop_solve(self._h, ctypes.byref(prm), p, flags, _dptr(J), ctypes.byref(res))

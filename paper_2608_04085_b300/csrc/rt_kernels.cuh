@@ -902,6 +902,25 @@ __global__ void __launch_bounds__(NTH) k_field_axpby(const InstDev* __restrict__
   }
 }
 
+// out = rho0(y) dA a on perturbation fields: the gradient of the constraint
+// C (Eq. constraint) at a, the normal of the budget surface.
+__global__ void __launch_bounds__(NTH) k_field_weight(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,
+                                                      double* __restrict__ out, const double* __restrict__ a) {
+  const int4 tl = tiles[blockIdx.x];
+  const InstDev& I = insts[tl.x];
+  const long long cells = (long long)I.nx * I.ny;
+  for (int e = threadIdx.x; e < TX * TY; e += NTH) {
+    const int gx = tl.y + e % TX, gy = tl.z + e / TX;
+    if (gx >= I.nx || gy >= I.ny) continue;
+    const long long c = (long long)gy * I.nx + gx;
+    const double w = I.rho0[gy];
+    for (int k = 0; k < I.ncomp; ++k) {
+      const long long idx = I.v_off + k * cells + c;
+      out[idx] = w * a[idx] * I.dA;
+    }
+  }
+}
+
 // Multiply each perturbation field by the interface envelope
 // exp(-(y - y_int)^2 / (2 h_loc^2)) (Sec. 3.4, localised random start).
 __global__ void __launch_bounds__(NTH) k_localise(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,

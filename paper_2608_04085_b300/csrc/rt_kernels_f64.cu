@@ -27,6 +27,12 @@ cudaError_t launch_field_axpby(const InstDev* insts, const int4* tiles, int ntil
   return cudaGetLastError();
 }
 
+cudaError_t launch_field_weight(const InstDev* insts, const int4* tiles, int ntiles, double* out, const double* a,
+                                cudaStream_t s) {
+  k_field_weight<<<ntiles, NTH, 0, s>>>(insts, tiles, out, a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_localise(const InstDev* insts, const int4* tiles, int ntiles, double h_loc, double* v,
                             cudaStream_t s) {
   k_localise<<<ntiles, NTH, 0, s>>>(insts, tiles, h_loc, v);

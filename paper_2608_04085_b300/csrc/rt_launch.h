@@ -40,6 +40,9 @@ cudaError_t launch_field_reduce(int mode, const InstDev* insts, const int4* tile
 cudaError_t launch_field_axpby(const InstDev* insts, const int4* tiles, int ntiles, double* out,
                                const double* alpha, const double* a, const double* beta, const double* b,
                                cudaStream_t s);
+// out = rho0(y) dA a (gradient of the constraint C at a)
+cudaError_t launch_field_weight(const InstDev* insts, const int4* tiles, int ntiles, double* out, const double* a,
+                                cudaStream_t s);
 cudaError_t launch_localise(const InstDev* insts, const int4* tiles, int ntiles, double h_loc, double* v,
                             cudaStream_t s);
 

@@ -21,6 +21,12 @@
 #include "rt_internal.h"
 #include "rt_launch.h"
 
+// The Python binding mirrors these layouts with ctypes.
+static_assert(sizeof(rt_problem) == 144, "rt_problem layout");
+static_assert(sizeof(rt_options) == 24, "rt_options layout");
+static_assert(sizeof(cnop_params) == 64, "cnop_params layout");
+static_assert(sizeof(cnop_result) == 24, "cnop_result layout");
+
 using rt::InstDev;
 using rt::RunDev;
 
@@ -85,6 +91,8 @@ struct rt_ctx {
   double* d_w2 = nullptr;
   double* d_w3 = nullptr;
   double* d_w4 = nullptr;
+  double* d_pairs = nullptr;     // L-BFGS (s, y) ring: 2 * pairs_m fields
+  int pairs_m = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::string err;
   // last run
@@ -730,16 +738,17 @@ rt_status axpby(rt_ctx* c, double* out, const std::vector<double>& alpha, const 
   return RT_OK;
 }
 
+// Perturbation-sized fields, zeroed once when allocated: a CNOP search leaves
+// the fields of a stopped instance untouched, and a zero coefficient on a
+// never-written (zero) field keeps its iterate finite.
 rt_status ensure_fields(rt_ctx* c, bool cnop) {
   const size_t bytes = c->total_v * sizeof(double);
-  if (!c->d_v) CU(cudaMalloc(&c->d_v, bytes));
-  if (!c->d_g) CU(cudaMalloc(&c->d_g, bytes));
-  if (cnop) {
-    if (!c->d_w1) CU(cudaMalloc(&c->d_w1, bytes));
-    if (!c->d_w2) CU(cudaMalloc(&c->d_w2, bytes));
-    if (!c->d_w3) CU(cudaMalloc(&c->d_w3, bytes));
-    if (!c->d_w4) CU(cudaMalloc(&c->d_w4, bytes));
-  }
+  double** f[] = {&c->d_v, &c->d_g, &c->d_w1, &c->d_w2, &c->d_w3, &c->d_w4};
+  for (int k = 0; k < (cnop ? 6 : 2); ++k)
+    if (!*f[k]) {
+      CU(cudaMalloc(f[k], bytes));
+      CU(cudaMemsetAsync(*f[k], 0, bytes, c->stream));
+    }
   return RT_OK;
 }
 
@@ -814,23 +823,47 @@ struct Timer {
   }
 };
 
+// Every instance switched back on when a CNOP search returns, on any path.
+struct EnableAllOnExit {
+  rt_ctx* c;
+  ~EnableAllOnExit() {
+    std::vector<char> en(c->n_inst, 1);
+    set_enabled(c, en);
+  }
+};
+
+// Start of a CNOP search (Sec. 3.4): v_inout into c->d_v, optionally
+// localised at the interface, then scaled onto C = eps.
+rt_status cnop_start(rt_ctx* c, const cnop_params* prm, const double* v_inout, int flags, std::vector<double>& eps) {
+  const int N = c->n_inst;
+  eps.assign(prm->eps, prm->eps + N);
+  for (int i = 0; i < N; ++i)
+    if (!(eps[i] > 0.0) || !std::isfinite(eps[i])) return fail(c, RT_EINVAL, "eps[%d] must be positive", i);
+  CHK(copy_in(c, v_inout, flags, c->d_v));
+  if (prm->h_loc > 0.0) CU(rt::launch_localise(c->d_inst, c->d_tiles, c->ntiles, prm->h_loc, c->d_v, c->stream));
+  std::vector<double> C, sc(N);
+  CHK(field_sums(c, 0, c->d_v, nullptr, C));
+  for (int i = 0; i < N; ++i) {
+    if (!(C[i] > 0.0) || !std::isfinite(C[i]))
+      return fail(c, RT_EINVAL, "start field of instance %d has C = %g (needs 0 < C < inf)", i, C[i]);
+    sc[i] = std::sqrt(eps[i] / C[i]);
+  }
+  return axpby(c, c->d_v, sc, c->d_v, nullptr, nullptr);
+}
+
 template <class T>
 rt_status cnop_impl(rt_ctx* c, const cnop_params* prm, double* v_inout, int flags, double* J_out, cnop_result* res) {
   const int N = c->n_inst;
   CHK(ensure_fields(c, true));
+  EnableAllOnExit guard{c};
+  std::vector<double> eps, C, dots, ones(N, 1.0), mones(N, -1.0), sc(N);
+  CHK(cnop_start(c, prm, v_inout, flags, eps));
   double* v = c->d_v;
   double* g = c->d_g;
   double* vt = c->d_w1;
   double* gt = c->d_w2;
   double* d = c->d_w3;
   double* tmp = c->d_w4;
-  CHK(copy_in(c, v_inout, flags, v));
-  std::vector<double> eps(prm->eps, prm->eps + N), C, dots, ones(N, 1.0), mones(N, -1.0);
-  if (prm->h_loc > 0.0) CU(rt::launch_localise(c->d_inst, c->d_tiles, c->ntiles, prm->h_loc, v, c->stream));
-  CHK(field_sums(c, 0, v, nullptr, C));
-  std::vector<double> sc(N);
-  for (int i = 0; i < N; ++i) sc[i] = std::sqrt(eps[i] / C[i]);
-  CHK(axpby(c, v, sc, v, nullptr, nullptr));
   std::vector<char> en(N, 1), stuck(N, 0);
   CHK(set_enabled(c, en));
   std::vector<double> J(N), Jt(N), Jn(N);
@@ -917,6 +950,232 @@ rt_status cnop_impl(rt_ctx* c, const cnop_params* prm, double* v_inout, int flag
   }
   std::fill(en.begin(), en.end(), 1);
   CHK(set_enabled(c, en));
+  CHK(copy_out(c, v, flags, v_inout));
+  CU(cudaStreamSynchronize(c->stream));
+  if (J_out)
+    for (int i = 0; i < N; ++i) J_out[i] = J[i];
+  if (res) {
+    res->iterations = iters;
+    res->forward_evals = fevals;
+    res->gradient_evals = gevals;
+  }
+  if (any_stuck) return fail(c, RT_ENOTCONVERGED, "an instance found no acceptable step");
+  return RT_OK;
+}
+
+// L-BFGS work fields: the (s, y) ring of m pairs plus the constraint normal.
+rt_status ensure_pairs(rt_ctx* c, int m) {
+  if (c->d_pairs && c->pairs_m >= m) return RT_OK;
+  if (c->d_pairs) cudaFree(c->d_pairs);
+  c->d_pairs = nullptr;
+  c->pairs_m = 0;
+  const size_t bytes = (size_t)(2 * m + 1) * c->total_v * sizeof(double);
+  CU(cudaMalloc(&c->d_pairs, bytes));
+  CU(cudaMemsetAsync(c->d_pairs, 0, bytes, c->stream));
+  c->pairs_m = m;
+  return RT_OK;
+}
+
+// Projected L-BFGS ascent with the non-monotone Armijo search (Sec. 3.4, Eq.
+// projection); the rule is stated at cnop_solve in the C header. On the
+// budget surface C = eps the model gradient is that of J o P,
+// gh = g - (<g, v> / <n, v>) n with n = dC/dv, and every direction is made
+// tangent, p <- p - (<n, p> / <n, n>) n, so P puts each trial point back on
+// the surface. The (s, y) pairs of the last m iterations live in a ring of
+// device fields shared by all instances; an instance whose pair failed the
+// curvature test, or that restarted, holds rho = 0 there, which makes the
+// pair a no-op in the two-loop recursion (Nocedal & Wright Alg. 7.4). Dot
+// products and the scalars of the recursion are FP64, reduced per instance.
+template <class T>
+rt_status lbfgs_impl(rt_ctx* c, const cnop_params* prm, double* v_inout, int flags, double* J_out, cnop_result* res) {
+  const int N = c->n_inst;
+  const int m = prm->lbfgs_memory > 0 ? prm->lbfgs_memory : 10;
+  CHK(ensure_fields(c, true));
+  CHK(ensure_pairs(c, m));
+  EnableAllOnExit guard{c};
+  std::vector<double> eps, C, ones(N, 1.0), mones(N, -1.0), sc(N);
+  CHK(cnop_start(c, prm, v_inout, flags, eps));
+  double* v = c->d_v;
+  double* g = c->d_g;    // model gradient gh at v
+  double* vt = c->d_w1;
+  double* gt = c->d_w2;  // model gradient at vt
+  double* p = c->d_w3;
+  double* tmp = c->d_w4;
+  double* nrm = c->d_pairs + (size_t)(2 * m) * c->total_v;  // dC/dv at the current point
+  auto S = [&](int j) { return c->d_pairs + (size_t)(2 * j) * c->total_v; };
+  auto Y = [&](int j) { return c->d_pairs + (size_t)(2 * j + 1) * c->total_v; };
+  std::vector<char> en(N, 1), stuck(N, 0), on_surf(N, 0);
+  CHK(set_enabled(c, en));
+  // on_surf[i] = C(x_i) >= eps (1 - 1e-10): x was put on the surface by P
+  // (up to rounding). Then nrm = dC/dx and gx <- gx - (<gx, x> / <nrm, x>) nrm.
+  auto model_gradient = [&](const double* x, double* gx) -> rt_status {
+    CHK(field_sums(c, 0, x, nullptr, C));
+    for (int i = 0; i < N; ++i) on_surf[i] = C[i] >= eps[i] * (1.0 - 1e-10);
+    CU(rt::launch_field_weight(c->d_inst, c->d_tiles, c->ntiles, nrm, x, c->stream));
+    std::vector<double> gx_x, n_x, coef(N, 0.0);
+    CHK(field_sums(c, 1, gx, x, gx_x));
+    CHK(field_sums(c, 1, nrm, x, n_x));
+    for (int i = 0; i < N; ++i)
+      if (on_surf[i] && !stuck[i]) coef[i] = -(gx_x[i] / n_x[i]);
+    return axpby(c, gx, ones, gx, &coef, nrm);
+  };
+  // p <- p - (<nrm, p> / <nrm, nrm>) nrm for the instances flagged in `sel`
+  auto tangent = [&](const std::vector<char>& sel) -> rt_status {
+    std::vector<double> np_, nn, coef(N, 0.0);
+    CHK(field_sums(c, 1, nrm, p, np_));
+    CHK(field_sums(c, 1, nrm, nrm, nn));
+    for (int i = 0; i < N; ++i)
+      if (sel[i] && on_surf[i] && !stuck[i]) coef[i] = -(np_[i] / nn[i]);
+    return axpby(c, p, ones, p, &coef, nrm);
+  };
+  std::vector<double> J(N), Jt(N), Jn(N);
+  int fevals = 0, gevals = 0, iters = 0;
+  CHK(gradient_impl<T>(c, v, J.data(), g, nullptr));
+  ++gevals;
+  CHK(model_gradient(v, g));
+  std::vector<std::vector<double>> rho(m, std::vector<double>(N, 0.0)), gam(m, std::vector<double>(N, 0.0)),
+      a(m, std::vector<double>(N, 0.0));
+  int stored_iters = 0;  // pairs written so far; the ring holds the last min(stored_iters, m)
+  std::vector<std::vector<double>> hist(N);
+  for (int i = 0; i < N; ++i) hist[i].push_back(J[i]);
+  const int M = prm->gll_memory > 0 ? prm->gll_memory : 10;
+  const int maxbt = prm->max_backtracks > 0 ? prm->max_backtracks : 30;
+  bool any_stuck = false;
+  // slot of the t-th newest pair in the ring (t = 0: newest)
+  auto slot = [&](int t) { return (stored_iters - 1 - t) % m; };
+  // vt = P(v + lam p) (Eq. projection), then tmp = vt - v and gd = <gh, tmp>;
+  // stopped instances keep vt = v.
+  auto trial = [&](const std::vector<double>& lam, std::vector<double>& gd) -> rt_status {
+    CHK(axpby(c, vt, ones, v, &lam, p));
+    CHK(field_sums(c, 0, vt, nullptr, C));
+    for (int i = 0; i < N; ++i) sc[i] = (stuck[i] || C[i] <= eps[i]) ? 1.0 : std::sqrt(eps[i] / C[i]);
+    CHK(axpby(c, vt, sc, vt, nullptr, nullptr));
+    CHK(axpby(c, tmp, ones, vt, &mones, v));
+    return field_sums(c, 1, g, tmp, gd);
+  };
+  for (int k = 0; k < prm->max_iter; ++k) {
+    const int npairs = std::min(stored_iters, m);
+    // H0 = gamma I: <s,y>/<y,y> of the newest stored pair, else ||v|| / ||gh||
+    std::vector<double> vv, gg, g0(N), gamma(N);
+    std::vector<char> has_pair(N, 0);
+    CHK(field_sums(c, 1, v, v, vv));
+    CHK(field_sums(c, 1, g, g, gg));
+    for (int i = 0; i < N; ++i) {
+      g0[i] = std::sqrt(vv[i]) / std::max(std::sqrt(gg[i]), 1e-300);
+      gamma[i] = g0[i];
+      for (int t = 0; t < npairs; ++t)
+        if (rho[slot(t)][i] > 0.0) {
+          gamma[i] = gam[slot(t)][i];
+          has_pair[i] = 1;
+          break;
+        }
+    }
+    // two-loop recursion on p (starts as gh)
+    CHK(axpby(c, p, ones, g, nullptr, nullptr));
+    auto slot_used = [&](int j) {
+      for (int i = 0; i < N; ++i)
+        if (rho[j][i] != 0.0) return true;
+      return false;
+    };
+    for (int t = 0; t < npairs; ++t) {
+      const int j = slot(t);
+      if (!slot_used(j)) continue;
+      std::vector<double> sq, na(N);
+      CHK(field_sums(c, 1, S(j), p, sq));
+      for (int i = 0; i < N; ++i) {
+        a[j][i] = rho[j][i] * sq[i];
+        na[i] = -a[j][i];
+      }
+      CHK(axpby(c, p, ones, p, &na, Y(j)));
+    }
+    CHK(axpby(c, p, gamma, p, nullptr, nullptr));
+    for (int t = npairs - 1; t >= 0; --t) {
+      const int j = slot(t);
+      if (!slot_used(j)) continue;
+      std::vector<double> yr, coef(N);
+      CHK(field_sums(c, 1, Y(j), p, yr));
+      for (int i = 0; i < N; ++i) coef[i] = a[j][i] - rho[j][i] * yr[i];
+      CHK(axpby(c, p, ones, p, &coef, S(j)));
+    }
+    CHK(tangent(en));
+    // ascent check; a failed check drops the pairs and restarts from the
+    // scaled model gradient
+    std::vector<double> gp, keep(N, 1.0), gcoef(N, 0.0);
+    CHK(field_sums(c, 1, g, p, gp));
+    std::vector<char> restart(N, 0);
+    bool any_restart = false;
+    for (int i = 0; i < N; ++i)
+      if (!stuck[i] && has_pair[i] && gp[i] <= 0.0) {
+        restart[i] = 1;
+        any_restart = true;
+        keep[i] = 0.0;
+        gcoef[i] = g0[i];
+        for (int j = 0; j < m; ++j) rho[j][i] = 0.0;
+      }
+    if (any_restart) {
+      CHK(axpby(c, p, keep, p, &gcoef, g));
+      CHK(tangent(restart));
+    }
+    std::vector<double> Jref(N), lam(N, 1.0), gd;
+    for (int i = 0; i < N; ++i) {
+      const size_t h0 = hist[i].size() > (size_t)M ? hist[i].size() - M : 0;
+      Jref[i] = *std::max_element(hist[i].begin() + h0, hist[i].end());
+    }
+    std::vector<char> acc(N, 0);
+    for (int i = 0; i < N; ++i) acc[i] = stuck[i];
+    for (int bt = 0; bt < maxbt; ++bt) {
+      CHK(trial(lam, gd));
+      std::vector<char> e(N);
+      for (int i = 0; i < N; ++i) e[i] = !acc[i];
+      CHK(set_enabled(c, e));
+      int steps = 0;
+      CHK(forward_impl<T>(c, vt, RT_DEVICE_PTRS, Jt.data(), nullptr, &steps));
+      ++fevals;
+      bool all = true;
+      for (int i = 0; i < N; ++i) {
+        if (acc[i]) continue;
+        if (Jt[i] >= Jref[i] + prm->armijo_c * gd[i]) acc[i] = 1;
+        else { lam[i] *= 0.5; all = false; }
+      }
+      if (all) break;
+    }
+    for (int i = 0; i < N; ++i)
+      if (!acc[i]) { stuck[i] = 1; any_stuck = true; }
+    for (int i = 0; i < N; ++i)
+      if (stuck[i]) lam[i] = 0.0;
+    CHK(trial(lam, gd));  // the accepted point (v itself for stopped instances)
+    std::vector<char> e(N);
+    bool any_live = false;
+    for (int i = 0; i < N; ++i) { e[i] = !stuck[i]; any_live = any_live || e[i]; }
+    if (!any_live) break;
+    CHK(set_enabled(c, e));
+    CHK(gradient_impl<T>(c, vt, Jn.data(), gt, nullptr));
+    ++gevals;
+    CHK(model_gradient(vt, gt));
+    // new pair: s = vt - v (already in tmp), y = -(gh_new - gh) = gh - gh_new
+    const int h = stored_iters % m;
+    CHK(axpby(c, S(h), ones, tmp, nullptr, nullptr));
+    CHK(axpby(c, Y(h), ones, g, &mones, gt));
+    std::vector<double> sy, yy;
+    CHK(field_sums(c, 1, S(h), Y(h), sy));
+    CHK(field_sums(c, 1, Y(h), Y(h), yy));
+    for (int i = 0; i < N; ++i) {
+      const bool ok = !stuck[i] && sy[i] > 0.0;
+      rho[h][i] = ok ? 1.0 / sy[i] : 0.0;
+      gam[h][i] = ok ? sy[i] / yy[i] : 0.0;
+      if (stuck[i]) continue;
+      J[i] = Jn[i];
+      hist[i].push_back(J[i]);
+    }
+    ++stored_iters;
+    std::swap(c->d_v, c->d_w1);  // v <- vt
+    std::swap(c->d_g, c->d_w2);  // gh <- gh_new
+    v = c->d_v;
+    g = c->d_g;
+    vt = c->d_w1;
+    gt = c->d_w2;
+    ++iters;
+  }
   CHK(copy_out(c, v, flags, v_inout));
   CU(cudaStreamSynchronize(c->stream));
   if (J_out)
@@ -1114,7 +1373,7 @@ void rt_destroy(rt_ctx* c) {
   void* ptrs[] = {c->d_inst, c->d_tiles, c->d_strips, c->d_base, c->d_ek0, c->d_ek, c->sA, c->sB, c->sU1, c->lA, c->lB,
                   c->l1, c->d_tab, c->run.dtrec, c->run.dtc, c->run.counter, c->run.t, c->run.nstep, c->run.wmin, c->run.status,
                   c->run.bad_cell, c->d_partials, c->d_sums, c->d_scal, c->d_v, c->d_g, c->d_w1, c->d_w2,
-                  c->d_w3, c->d_w4};
+                  c->d_w3, c->d_w4, c->d_pairs};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : c->pool) cudaFree(p);
@@ -1273,11 +1532,19 @@ rt_status cnop_solve(rt_ctx* c, const cnop_params* prm, double* v_inout, int fla
                      cnop_result* res) {
   if (!c || !prm || !v_inout || !prm->eps) return fail(c, RT_EINVAL, "null argument");
   if (prm->max_iter < 0) return fail(c, RT_EINVAL, "max_iter < 0");
+  if (prm->lbfgs_memory < 0) return fail(c, RT_EINVAL, "lbfgs_memory < 0");
   c->err.clear();
   CHK(enter(c));
   Timer tm(c);
-  rt_status s = c->esz == 8 ? cnop_impl<double>(c, prm, v_inout, flags, J_out, res)
-                            : cnop_impl<float>(c, prm, v_inout, flags, J_out, res);
+  rt_status s;
+  if (prm->method == RT_CNOP_LBFGS)
+    s = c->esz == 8 ? lbfgs_impl<double>(c, prm, v_inout, flags, J_out, res)
+                    : lbfgs_impl<float>(c, prm, v_inout, flags, J_out, res);
+  else if (prm->method == RT_CNOP_SPG)
+    s = c->esz == 8 ? cnop_impl<double>(c, prm, v_inout, flags, J_out, res)
+                    : cnop_impl<float>(c, prm, v_inout, flags, J_out, res);
+  else
+    s = fail(c, RT_EINVAL, "unknown CNOP method %d", prm->method);
   const float ms = tm.stop();
   if (res) res->ms = ms;
   return s;

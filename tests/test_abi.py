@@ -34,6 +34,8 @@ def test_struct_sizes_match_header_layout():
     # rt_problem: 2 ints, 12 doubles, 2 ints, 2 doubles, 3 ints (+ padding)
     assert ctypes.sizeof(rt.RtProblem) == 8 + 12 * 8 + 8 + 16 + 16
     assert ctypes.sizeof(rt.RtOptions) == 24
+    # cnop_params: 3 ints (+ pad), 4 doubles, a pointer, 2 ints
+    assert ctypes.sizeof(rt.CnopParams) == 16 + 32 + 8 + 8
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
@@ -42,3 +44,13 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(rt, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         rt.library()
+
+
+def test_header_enums_match_binding_constants():
+    import paper_2608_04085_b300 as rt
+    src = open(os.path.join(ROOT, "include", "rt_cnop.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    consts = dict((k, int(v)) for k, v in re.findall(r"\b(RT_[A-Z0-9_]+)\s*=\s*(\d+)", src))
+    assert len(consts) >= 25
+    for name, value in consts.items():
+        assert getattr(rt, name) == value, name
