@@ -57,7 +57,8 @@ typedef enum {
   RT_ENONFINITE = 4,    /* non-positive density/pressure or NaN in a state */
   RT_ETIMEOUT = 5,      /* a bounded device wait gave up */
   RT_ENOTCONVERGED = 6, /* optimiser stopped without an accepted step */
-  RT_ESTATE = 7         /* call out of order (e.g. replay before any run) */
+  RT_ESTATE = 7,        /* call out of order (e.g. replay before any run) */
+  RT_EIO = 8            /* reading or writing a file failed */
 } rt_status;
 
 enum { RT_BC_REFLECT = 0, RT_BC_HYDROSTATIC = 1 };
@@ -190,22 +191,41 @@ int rt_stage_kernel(const rt_ctx* ctx, double* tuned_ms);
 rt_status rt_kernel_times(rt_ctx* ctx, double* mean_ms, long long* samples, long long* launches);
 
 typedef struct {
-  int max_iter;          /* outer iterations */
-  int gll_memory;        /* non-monotone memory M (max of the last M values) */
+  int max_iter;          /* total iterations (a resumed run continues up to it) */
+  int gll_memory;        /* non-monotone memory M (max of the last M values); 0 = 10 */
   int max_backtracks;    /* per iteration; 0 = 30 */
   double armijo_c;       /* sufficient-increase constant, e.g. 1e-4 */
-  double alpha_min, alpha_max; /* spectral step safeguards */
+  double alpha_min, alpha_max; /* SPG step safeguards; 0 = 1e-30, 1e30 */
   double h_loc;          /* > 0: multiply v_inout by exp(-(y-y_int)^2/(2 h_loc^2)) first */
   const double* eps;     /* budget per instance */
   int method;            /* RT_CNOP_SPG or RT_CNOP_LBFGS */
   int lbfgs_memory;      /* L-BFGS: pairs of the last m iterations; 0 = 10 (Sec. 3.4) */
+  double chi_tol;        /* > 0: an instance stops once chi <= chi_tol (App. A) */
+  const char* log_path;  /* nullable: one text line per instance and iteration
+                            (iter instance J C chi grad_norm lambda forward_evals
+                            gradient_evals); truncated on a fresh start, appended on resume */
+  const char* checkpoint_path; /* nullable: the whole optimiser state (iterate, gradient,
+                            L-BFGS pairs, step and J histories) is written here every
+                            checkpoint_every iterations and on return */
+  int checkpoint_every;  /* 0 = only on return */
+  int resume;            /* nonzero: continue from checkpoint_path if that file exists
+                            (v_inout and h_loc are then ignored) */
 } cnop_params;
 
 typedef struct {
-  int iterations;        /* accepted iterations (minimum over instances) */
+  int iterations;        /* iterations run, counting those before a resume (lockstep batch) */
   int forward_evals;     /* batched forward runs (line-search trials) */
   int gradient_evals;    /* batched gradient runs */
   double ms;             /* device time of the whole solve */
+  /* Per-instance outputs: caller-owned arrays, each NULL or n_instances long
+   * (J_history: (max_iter + 1) * n_instances, row k = J after k iterations,
+   * rows after the last iteration left untouched). Zero the struct, then set
+   * the ones wanted. */
+  double* C;             /* C of the returned iterate (Eq. constraint) */
+  double* chi;           /* chi = ||P(v + dJ/dv) - v||_inf at the returned iterate (App. A) */
+  double* grad_norm;     /* ||dJ/dv||_2 there */
+  int* stop;             /* 0 iteration limit, 1 no acceptable step, 2 chi <= chi_tol */
+  double* J_history;
 } cnop_result;
 
 /* CNOP search (Sec. 3.4, Eq. projection). Every instance starts from
@@ -213,19 +233,23 @@ typedef struct {
  * C = eps (a start with C = 0 is RT_EINVAL), and all instances advance in
  * lockstep through batched forward and gradient runs; an instance that has
  * stopped is switched off in those runs. Two methods:
- *  RT_CNOP_LBFGS (the paper's): the ascent direction p = H g from the
- *    two-loop recursion over the (s, y) pairs of the last lbfgs_memory
- *    iterations, y = -(g_new - g_old), a pair with <s, y> <= 0 skipped,
- *    H0 = <s, y>/<y, y> of the newest stored pair (||v||/||g|| when none);
- *    if <g, P(v + p) - v> <= 0 the pairs are dropped and p = (||v||/||g||) g;
- *    trial points P(v + lam p), lam = 1, 1/2, ..., accepted once
- *    J >= max(last gll_memory J) + armijo_c <g, P(v + lam p) - v>.
+ *  RT_CNOP_LBFGS (the paper's): on the budget surface C = eps the model
+ *    gradient is that of J o P, gh = g - (<g,v>/<n,v>) n with n = dC/dv, and
+ *    the direction is made tangent, p <- p - (<n,p>/<n,n>) n (off the surface
+ *    gh = g). p = H gh from the two-loop recursion over the (s, y) pairs of
+ *    the last lbfgs_memory iterations, y = -(gh_new - gh_old), a pair with
+ *    <s, y> <= 0 skipped, H0 = <s, y>/<y, y> of the newest stored pair
+ *    (||v||/||gh|| when none); if <gh, p> <= 0 the pairs are dropped and
+ *    p = (||v||/||gh||) gh; trial points P(v + lam p), lam = 1, 1/2, ...,
+ *    accepted once J >= max(last gll_memory J) + armijo_c <gh, P(v + lam p) - v>.
  *  RT_CNOP_SPG: d = P(v + alpha g) - v, trial points v + lam d accepted once
  *    J >= max(last gll_memory J) + armijo_c lam <g, d>, and the
  *    Barzilai-Borwein step alpha = <s,s>/<s,y> clipped to
  *    [alpha_min, alpha_max] (alpha_max when <s,y> <= 0).
  * On return v_inout holds the CNOP of every instance and J_out[i] (nullable)
- * its objective. Errors: as rt_gradient; RT_EINVAL for an unknown method;
+ * its objective. Errors: as rt_gradient; RT_EINVAL for an unknown method, or
+ * a checkpoint written for another context, method, memory, precision or
+ * eps; RT_EIO when the log or checkpoint cannot be written or read;
  * RT_ENOTCONVERGED when an instance found no acceptable step within
  * max_backtracks trials (its last accepted iterate is returned). */
 rt_status cnop_solve(rt_ctx* ctx, const cnop_params* prm, double* v_inout, int flags,

@@ -294,7 +294,8 @@ def spg(w, v_start, eps, iters, memory=10, armijo=1e-4, alpha_min=1e-30, alpha_m
         v, J, g = vt, Jn, gn
         hist.append(J)
         chi = float(np.max(np.abs(project(w, v + g, eps) - v)))
-        records.append({"iter": k, "J": J, "lam": lam, "alpha": alpha, "chi": chi})
+        records.append({"iter": k, "J": J, "lam": lam, "alpha": alpha, "chi": chi,
+                        "grad_norm": float(np.linalg.norm(g))})
         if log is not None:
             log(records[-1])
     return {"v": v, "J": J, "history": hist, "records": records, "evals": evals, "grads": grads}
@@ -369,8 +370,13 @@ def projected_lbfgs(value, value_and_grad, proj, v_start, iters, m=10, memory=10
     def steepest_gamma(v, g):
         return float(np.linalg.norm(v) / max(np.linalg.norm(g), 1e-300))
 
+    def stationarity(v, g):
+        # App. A: chi = ||P(v + dJ/dv) - v||_inf, with the gradient of J itself
+        return float(np.max(np.abs(proj(v + g) - v))), float(np.linalg.norm(g))
+
     v = np.array(v_start, dtype=np.float64, copy=True)
     J, g = value_and_grad(v)
+    chi0 = stationarity(v, g)
     g = model_gradient(v, g)
     evals, grads = 1, 1
     hist = [J]
@@ -403,6 +409,7 @@ def projected_lbfgs(value, value_and_grad, proj, v_start, iters, m=10, memory=10
         if not accepted:
             break
         Jn, gn = value_and_grad(vt)
+        chi, gnorm = stationarity(vt, gn)
         gn = model_gradient(vt, gn)
         grads += 1
         s = vt - v
@@ -413,10 +420,12 @@ def projected_lbfgs(value, value_and_grad, proj, v_start, iters, m=10, memory=10
             pairs.pop(0)
         v, J, g = vt, Jn, gn
         hist.append(J)
-        records.append({"iter": k, "J": J, "lam": lam, "gamma": gamma, "restart": restart, "sy": sy})
+        records.append({"iter": k, "J": J, "lam": lam, "gamma": gamma, "restart": restart, "sy": sy,
+                        "chi": chi, "grad_norm": gnorm})
         if log is not None:
             log(records[-1])
-    return {"v": v, "J": J, "history": hist, "records": records, "evals": evals, "grads": grads}
+    return {"v": v, "J": J, "history": hist, "records": records, "evals": evals, "grads": grads,
+            "chi0": chi0[0], "grad_norm0": chi0[1]}
 
 
 def constraint_normal(w, v):

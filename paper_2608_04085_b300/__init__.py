@@ -18,7 +18,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librt_cnop.so")
 
-RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENONFINITE, RT_ETIMEOUT, RT_ENOTCONVERGED, RT_ESTATE = range(8)
+RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENONFINITE, RT_ETIMEOUT, RT_ENOTCONVERGED, RT_ESTATE, RT_EIO = range(9)
 RT_BC_REFLECT, RT_BC_HYDROSTATIC = 0, 1
 RT_LIM_MINMOD, RT_LIM_MC, RT_LIM_NONE = 0, 1, 2
 RT_OBJ_KE, RT_OBJ_EK_ANOMALY_L2 = 0, 1
@@ -29,7 +29,7 @@ RT_DEVICE_PTRS, RT_REPLAY_DT = 1, 2
 RT_CNOP_SPG, RT_CNOP_LBFGS = 0, 1
 
 _STATUS = {1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENONFINITE", 5: "RT_ETIMEOUT",
-           6: "RT_ENOTCONVERGED", 7: "RT_ESTATE"}
+           6: "RT_ENOTCONVERGED", 7: "RT_ESTATE", 8: "RT_EIO"}
 
 #: every entry point declared in include/rt_cnop.h
 EXPORTS = ("rt_init", "rt_destroy", "rt_last_error", "rt_num_instances", "rt_field_offset",
@@ -77,12 +77,17 @@ class CnopParams(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int), ("gll_memory", ctypes.c_int), ("max_backtracks", ctypes.c_int),
                 ("armijo_c", ctypes.c_double), ("alpha_min", ctypes.c_double), ("alpha_max", ctypes.c_double),
                 ("h_loc", ctypes.c_double), ("eps", ctypes.POINTER(ctypes.c_double)),
-                ("method", ctypes.c_int), ("lbfgs_memory", ctypes.c_int)]
+                ("method", ctypes.c_int), ("lbfgs_memory", ctypes.c_int), ("chi_tol", ctypes.c_double),
+                ("log_path", ctypes.c_char_p), ("checkpoint_path", ctypes.c_char_p),
+                ("checkpoint_every", ctypes.c_int), ("resume", ctypes.c_int)]
 
 
 class CnopResult(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("forward_evals", ctypes.c_int),
-                ("gradient_evals", ctypes.c_int), ("ms", ctypes.c_double)]
+                ("gradient_evals", ctypes.c_int), ("ms", ctypes.c_double),
+                ("C", ctypes.POINTER(ctypes.c_double)), ("chi", ctypes.POINTER(ctypes.c_double)),
+                ("grad_norm", ctypes.POINTER(ctypes.c_double)), ("stop", ctypes.POINTER(ctypes.c_int)),
+                ("J_history", ctypes.POINTER(ctypes.c_double))]
 
 
 _lib = None
@@ -310,23 +315,35 @@ class Context:
         return {k: (ms[i], sa[i], la[i]) for i, k in enumerate(("stage1", "stage2", "adjoint"))}
 
     def cnop(self, v_start, eps, iters, method=RT_CNOP_LBFGS, lbfgs_memory=10, gll_memory=10, armijo_c=1e-4,
-             alpha_min=1e-30, alpha_max=1e30, max_backtracks=30, h_loc=0.0, raise_on_stall=False):
+             alpha_min=1e-30, alpha_max=1e30, max_backtracks=30, h_loc=0.0, chi_tol=0.0, log_path=None,
+             checkpoint_path=None, checkpoint_every=0, resume=False, raise_on_stall=False):
         """CNOP search (cnop_solve): projected L-BFGS (the default) or spectral
-        projected gradient. Returns (v, J, result)."""
+        projected gradient. Returns (v, J, result); result holds the counts,
+        the status and per-instance C, chi, grad_norm, stop and J_history
+        (iterations + 1 rows)."""
         if hasattr(v_start, "clone"):
             v = v_start.clone()
         else:
             v = np.array(v_start, dtype=np.float64, copy=True).ravel()
         p, flags, keep = self._arg(v)
         e = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, dtype=np.float64), (self.n,)))
+        enc = lambda path: None if path is None else os.fsencode(path)
         prm = CnopParams(int(iters), int(gll_memory), int(max_backtracks), float(armijo_c), float(alpha_min),
-                         float(alpha_max), float(h_loc), _dptr(e), int(method), int(lbfgs_memory))
+                         float(alpha_max), float(h_loc), _dptr(e), int(method), int(lbfgs_memory),
+                         float(chi_tol), enc(log_path), enc(checkpoint_path), int(checkpoint_every), int(bool(resume)))
         J = np.zeros(self.n)
+        C, chi, gnorm = np.zeros(self.n), np.zeros(self.n), np.zeros(self.n)
+        stop = np.zeros(self.n, dtype=np.int32)
+        hist = np.full((int(iters) + 1, self.n), np.nan)
         res = CnopResult()
+        res.C, res.chi, res.grad_norm, res.J_history = _dptr(C), _dptr(chi), _dptr(gnorm), _dptr(hist)
+        res.stop = stop.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
         st = library().cnop_solve(self._h, ctypes.byref(prm), p, flags, _dptr(J), ctypes.byref(res))
         if st != RT_OK and (raise_on_stall or st != RT_ENOTCONVERGED):
             self._check(st)
-        return v, J, {k: getattr(res, k) for k, _ in CnopResult._fields_} | {"status": st}
+        out = {k: getattr(res, k) for k in ("iterations", "forward_evals", "gradient_evals", "ms")}
+        return v, J, out | {"status": st, "C": C, "chi": chi, "grad_norm": gnorm, "stop": stop,
+                            "J_history": hist[:res.iterations + 1]}
 
 
 def field_layout(problems):

@@ -67,6 +67,19 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
+// Block-wide maximum of non-negative values (result in thread 0).
+__device__ __forceinline__ double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = fmax(s, red[w]);
+  return s;
+}
+
 // Physics constants of an instance in the state precision (no conversion
 // instructions in the kernels).
 template <class T>
@@ -855,8 +868,20 @@ __global__ void __launch_bounds__(NTH) k_finalize(const InstDev* __restrict__ in
   }
 }
 
+// Per-instance maximum of per-tile partial maxima (instance = block).
+__global__ void __launch_bounds__(NTH) k_finalize_max(const InstDev* __restrict__ insts,
+                                                      const double* __restrict__ partials, double* __restrict__ out) {
+  __shared__ double red[NTH / 32];
+  const InstDev& I = insts[blockIdx.x];
+  double s = 0.0;
+  for (int t = I.tile_begin + threadIdx.x; t < I.tile_end; t += NTH) s = fmax(s, partials[t]);
+  s = block_max(s, red);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
 // Per-tile partial sums over perturbation fields: MODE 0: C(a) / dA =
-// sum rho0 a^2 / 2 (Eq. constraint without the cell area); MODE 1: <a, b>.
+// sum rho0 a^2 / 2 (Eq. constraint without the cell area); MODE 1: <a, b>;
+// MODE 2: max |a| (a partial maximum, not a sum).
 template <int MODE>
 __global__ void __launch_bounds__(NTH) k_field_reduce(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,
                                                       const double* __restrict__ a, const double* __restrict__ b,
@@ -873,10 +898,11 @@ __global__ void __launch_bounds__(NTH) k_field_reduce(const InstDev* __restrict_
     for (int k = 0; k < I.ncomp; ++k) {
       const double x = a[I.v_off + k * cells + c];
       if (MODE == 0) s += 0.5 * I.rho0[gy] * x * x;
-      else s += x * b[I.v_off + k * cells + c];
+      else if (MODE == 1) s += x * b[I.v_off + k * cells + c];
+      else s = fmax(s, fabs(x));
     }
   }
-  s = block_sum(s, red);
+  s = MODE == 2 ? block_max(s, red) : block_sum(s, red);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 

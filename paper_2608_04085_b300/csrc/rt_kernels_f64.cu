@@ -16,7 +16,14 @@ cudaError_t launch_finalize(const InstDev* insts, int n_inst, const double* part
 cudaError_t launch_field_reduce(int mode, const InstDev* insts, const int4* tiles, int ntiles, const double* a,
                                 const double* b, double* partials, cudaStream_t s) {
   if (mode == 0) k_field_reduce<0><<<ntiles, NTH, 0, s>>>(insts, tiles, a, b, partials);
-  else k_field_reduce<1><<<ntiles, NTH, 0, s>>>(insts, tiles, a, b, partials);
+  else if (mode == 1) k_field_reduce<1><<<ntiles, NTH, 0, s>>>(insts, tiles, a, b, partials);
+  else k_field_reduce<2><<<ntiles, NTH, 0, s>>>(insts, tiles, a, b, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_max(const InstDev* insts, int n_inst, const double* partials, double* out,
+                                cudaStream_t s) {
+  k_finalize_max<<<n_inst, NTH, 0, s>>>(insts, partials, out);
   return cudaGetLastError();
 }
 

@@ -34,7 +34,10 @@ cudaError_t configure_kernels();
 
 cudaError_t launch_finalize(const InstDev* insts, int n_inst, const double* partials, int width, int scale_by_dA,
                             double* out, cudaStream_t s);
-// mode 0: C(a)/dA partials; mode 1: <a, b> partials
+// per-instance maximum of the mode-2 partials
+cudaError_t launch_finalize_max(const InstDev* insts, int n_inst, const double* partials, double* out,
+                                cudaStream_t s);
+// mode 0: C(a)/dA partials; mode 1: <a, b> partials; mode 2: max |a| partials
 cudaError_t launch_field_reduce(int mode, const InstDev* insts, const int4* tiles, int ntiles, const double* a,
                                 const double* b, double* partials, cudaStream_t s);
 cudaError_t launch_field_axpby(const InstDev* insts, const int4* tiles, int ntiles, double* out,

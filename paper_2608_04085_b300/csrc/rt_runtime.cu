@@ -24,8 +24,8 @@
 // The Python binding mirrors these layouts with ctypes.
 static_assert(sizeof(rt_problem) == 144, "rt_problem layout");
 static_assert(sizeof(rt_options) == 24, "rt_options layout");
-static_assert(sizeof(cnop_params) == 64, "cnop_params layout");
-static_assert(sizeof(cnop_result) == 24, "cnop_result layout");
+static_assert(sizeof(cnop_params) == 96, "cnop_params layout");
+static_assert(sizeof(cnop_result) == 64, "cnop_result layout");
 
 using rt::InstDev;
 using rt::RunDev;
@@ -823,6 +823,7 @@ struct Timer {
   }
 };
 
+// ------------------------------------------------------------------ CNOP search
 // Every instance switched back on when a CNOP search returns, on any path.
 struct EnableAllOnExit {
   rt_ctx* c;
@@ -834,11 +835,9 @@ struct EnableAllOnExit {
 
 // Start of a CNOP search (Sec. 3.4): v_inout into c->d_v, optionally
 // localised at the interface, then scaled onto C = eps.
-rt_status cnop_start(rt_ctx* c, const cnop_params* prm, const double* v_inout, int flags, std::vector<double>& eps) {
+rt_status cnop_start(rt_ctx* c, const cnop_params* prm, const double* v_inout, int flags,
+                     const std::vector<double>& eps) {
   const int N = c->n_inst;
-  eps.assign(prm->eps, prm->eps + N);
-  for (int i = 0; i < N; ++i)
-    if (!(eps[i] > 0.0) || !std::isfinite(eps[i])) return fail(c, RT_EINVAL, "eps[%d] must be positive", i);
   CHK(copy_in(c, v_inout, flags, c->d_v));
   if (prm->h_loc > 0.0) CU(rt::launch_localise(c->d_inst, c->d_tiles, c->ntiles, prm->h_loc, c->d_v, c->stream));
   std::vector<double> C, sc(N);
@@ -849,118 +848,6 @@ rt_status cnop_start(rt_ctx* c, const cnop_params* prm, const double* v_inout, i
     sc[i] = std::sqrt(eps[i] / C[i]);
   }
   return axpby(c, c->d_v, sc, c->d_v, nullptr, nullptr);
-}
-
-template <class T>
-rt_status cnop_impl(rt_ctx* c, const cnop_params* prm, double* v_inout, int flags, double* J_out, cnop_result* res) {
-  const int N = c->n_inst;
-  CHK(ensure_fields(c, true));
-  EnableAllOnExit guard{c};
-  std::vector<double> eps, C, dots, ones(N, 1.0), mones(N, -1.0), sc(N);
-  CHK(cnop_start(c, prm, v_inout, flags, eps));
-  double* v = c->d_v;
-  double* g = c->d_g;
-  double* vt = c->d_w1;
-  double* gt = c->d_w2;
-  double* d = c->d_w3;
-  double* tmp = c->d_w4;
-  std::vector<char> en(N, 1), stuck(N, 0);
-  CHK(set_enabled(c, en));
-  std::vector<double> J(N), Jt(N), Jn(N);
-  int fevals = 0, gevals = 0, iters = 0;
-  CHK(gradient_impl<T>(c, v, J.data(), g, nullptr));
-  ++gevals;
-  std::vector<double> vv, gg;
-  CHK(field_sums(c, 1, v, v, vv));
-  CHK(field_sums(c, 1, g, g, gg));
-  const double amin = prm->alpha_min > 0 ? prm->alpha_min : 1e-30;
-  const double amax = prm->alpha_max > 0 ? prm->alpha_max : 1e30;
-  std::vector<double> alpha(N);
-  for (int i = 0; i < N; ++i)
-    alpha[i] = std::min(std::max(std::sqrt(vv[i]) / std::max(std::sqrt(gg[i]), 1e-300), amin), amax);
-  std::vector<std::vector<double>> hist(N);
-  for (int i = 0; i < N; ++i) hist[i].push_back(J[i]);
-  const int M = prm->gll_memory > 0 ? prm->gll_memory : 10;
-  const int maxbt = prm->max_backtracks > 0 ? prm->max_backtracks : 30;
-  bool any_stuck = false;
-  for (int k = 0; k < prm->max_iter; ++k) {
-    // d = P(v + alpha g) - v
-    CHK(axpby(c, vt, ones, v, &alpha, g));
-    CHK(field_sums(c, 0, vt, nullptr, C));
-    for (int i = 0; i < N; ++i) sc[i] = C[i] <= eps[i] ? 1.0 : std::sqrt(eps[i] / C[i]);
-    CHK(axpby(c, vt, sc, vt, nullptr, nullptr));
-    CHK(axpby(c, d, ones, vt, &mones, v));
-    std::vector<double> gd;
-    CHK(field_sums(c, 1, g, d, gd));
-    std::vector<double> Jref(N), lam(N, 1.0);
-    for (int i = 0; i < N; ++i) {
-      const size_t h0 = hist[i].size() > (size_t)M ? hist[i].size() - M : 0;
-      Jref[i] = *std::max_element(hist[i].begin() + h0, hist[i].end());
-    }
-    std::vector<char> acc(N, 0);
-    for (int i = 0; i < N; ++i) acc[i] = stuck[i];
-    for (int bt = 0; bt < maxbt; ++bt) {
-      CHK(axpby(c, vt, ones, v, &lam, d));
-      std::vector<char> e(N);
-      for (int i = 0; i < N; ++i) e[i] = !acc[i];
-      CHK(set_enabled(c, e));
-      int steps = 0;
-      CHK(forward_impl<T>(c, vt, RT_DEVICE_PTRS, Jt.data(), nullptr, &steps));
-      ++fevals;
-      bool all = true;
-      for (int i = 0; i < N; ++i) {
-        if (acc[i]) continue;
-        if (Jt[i] >= Jref[i] + prm->armijo_c * lam[i] * gd[i]) acc[i] = 1;
-        else { lam[i] *= 0.5; all = false; }
-      }
-      if (all) break;
-    }
-    for (int i = 0; i < N; ++i)
-      if (!acc[i]) { stuck[i] = 1; any_stuck = true; }
-    for (int i = 0; i < N; ++i)
-      if (stuck[i]) lam[i] = 0.0;
-    CHK(axpby(c, vt, ones, v, &lam, d));
-    std::vector<char> e(N);
-    bool any_live = false;
-    for (int i = 0; i < N; ++i) { e[i] = !stuck[i]; any_live = any_live || e[i]; }
-    if (!any_live) break;
-    CHK(set_enabled(c, e));
-    CHK(gradient_impl<T>(c, vt, Jn.data(), gt, nullptr));
-    ++gevals;
-    // s = vt - v; y' = -(gt - g); alpha = <s,s>/<s,y'>
-    CHK(axpby(c, tmp, ones, vt, &mones, v));
-    std::vector<double> ss, sg, sgt;
-    CHK(field_sums(c, 1, tmp, tmp, ss));
-    CHK(field_sums(c, 1, tmp, g, sg));
-    CHK(field_sums(c, 1, tmp, gt, sgt));
-    for (int i = 0; i < N; ++i) {
-      if (stuck[i]) continue;
-      const double sy = sg[i] - sgt[i];
-      alpha[i] = sy <= 0.0 ? amax : std::min(std::max(ss[i] / sy, amin), amax);
-      J[i] = Jn[i];
-      hist[i].push_back(J[i]);
-    }
-    std::swap(c->d_v, c->d_w1);  // v <- vt
-    std::swap(c->d_g, c->d_w2);  // g <- gt
-    v = c->d_v;
-    g = c->d_g;
-    vt = c->d_w1;
-    gt = c->d_w2;
-    ++iters;
-  }
-  std::fill(en.begin(), en.end(), 1);
-  CHK(set_enabled(c, en));
-  CHK(copy_out(c, v, flags, v_inout));
-  CU(cudaStreamSynchronize(c->stream));
-  if (J_out)
-    for (int i = 0; i < N; ++i) J_out[i] = J[i];
-  if (res) {
-    res->iterations = iters;
-    res->forward_evals = fevals;
-    res->gradient_evals = gevals;
-  }
-  if (any_stuck) return fail(c, RT_ENOTCONVERGED, "an instance found no acceptable step");
-  return RT_OK;
 }
 
 // L-BFGS work fields: the (s, y) ring of m pairs plus the constraint normal.
@@ -976,38 +863,220 @@ rt_status ensure_pairs(rt_ctx* c, int m) {
   return RT_OK;
 }
 
-// Projected L-BFGS ascent with the non-monotone Armijo search (Sec. 3.4, Eq.
-// projection); the rule is stated at cnop_solve in the C header. On the
-// budget surface C = eps the model gradient is that of J o P,
-// gh = g - (<g, v> / <n, v>) n with n = dC/dv, and every direction is made
-// tangent, p <- p - (<n, p> / <n, n>) n, so P puts each trial point back on
-// the surface. The (s, y) pairs of the last m iterations live in a ring of
-// device fields shared by all instances; an instance whose pair failed the
-// curvature test, or that restarted, holds rho = 0 there, which makes the
-// pair a no-op in the two-loop recursion (Nocedal & Wright Alg. 7.4). Dot
-// products and the scalars of the recursion are FP64, reduced per instance.
-template <class T>
-rt_status lbfgs_impl(rt_ctx* c, const cnop_params* prm, double* v_inout, int flags, double* J_out, cnop_result* res) {
+// max |a| per instance
+rt_status field_max_abs(rt_ctx* c, const double* a, std::vector<double>& out) {
+  CU(rt::launch_field_reduce(2, c->d_inst, c->d_tiles, c->ntiles, a, nullptr, c->d_partials, c->stream));
+  CU(rt::launch_finalize_max(c->d_inst, c->n_inst, c->d_partials, c->d_sums, c->stream));
+  out.resize(c->n_inst);
+  CU(cudaMemcpyAsync(out.data(), c->d_sums, c->n_inst * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return RT_OK;
+}
+
+// Host side of a CNOP search: everything, besides the device fields v, g and
+// the L-BFGS pair ring, that the iterations after k depend on. Kept whole so
+// a run can be checkpointed and resumed.
+struct CnopState {
+  int k = 0, fevals = 0, gevals = 0, stored_iters = 0;
+  std::vector<int> stop;                      // 0 running, 1 no acceptable step, 2 chi <= chi_tol
+  std::vector<double> J, alpha, chi, gnorm;   // alpha: SPG step
+  std::vector<std::vector<double>> hist;      // accepted J per instance
+  std::vector<std::vector<double>> rho, gam;  // L-BFGS: [m][N]
+};
+
+const char kCkptMagic[8] = {'R', 'T', 'C', 'N', 'O', 'P', 'C', '1'};
+
+// Checkpoint file: magic, sizes and method, eps, the host state, then the
+// device fields v, g (and the L-BFGS ring) as FP64. Written to <path>.tmp and
+// renamed, so a crash leaves the previous checkpoint intact.
+rt_status save_checkpoint(rt_ctx* c, const char* path, int method, int m, const std::vector<double>& eps,
+                          const CnopState& st) {
   const int N = c->n_inst;
-  const int m = prm->lbfgs_memory > 0 ? prm->lbfgs_memory : 10;
+  std::vector<double> field(c->total_v);
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = fopen(tmp.c_str(), "wb");
+  if (!f) return fail(c, RT_EIO, "cannot write checkpoint %s", tmp.c_str());
+  bool ok = true;
+  auto put = [&](const void* p, size_t n) { ok = ok && fwrite(p, 1, n, f) == n; };
+  const long long hdr[9] = {N, (long long)c->total_v, method, m, (long long)c->esz, st.k, st.fevals, st.gevals,
+                            st.stored_iters};
+  put(kCkptMagic, sizeof(kCkptMagic));
+  put(hdr, sizeof(hdr));
+  put(eps.data(), N * sizeof(double));
+  put(st.stop.data(), N * sizeof(int));
+  put(st.J.data(), N * sizeof(double));
+  put(st.alpha.data(), N * sizeof(double));
+  put(st.chi.data(), N * sizeof(double));
+  put(st.gnorm.data(), N * sizeof(double));
+  for (int i = 0; i < N; ++i) {
+    const long long n = (long long)st.hist[i].size();
+    put(&n, sizeof(n));
+    put(st.hist[i].data(), n * sizeof(double));
+  }
+  for (int j = 0; j < m; ++j) {
+    put(st.rho[j].data(), N * sizeof(double));
+    put(st.gam[j].data(), N * sizeof(double));
+  }
+  std::vector<const double*> dev = {c->d_v, c->d_g};
+  for (int j = 0; j < 2 * m + 1 && method == RT_CNOP_LBFGS; ++j) dev.push_back(c->d_pairs + (size_t)j * c->total_v);
+  for (const double* d : dev) {
+    if (cudaMemcpyAsync(field.data(), d, c->total_v * sizeof(double), cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+      fclose(f);
+      return fail(c, RT_ECUDA, "checkpoint copy");
+    }
+    put(field.data(), c->total_v * sizeof(double));
+  }
+  ok = (fclose(f) == 0) && ok;
+  if (!ok || rename(tmp.c_str(), path) != 0) return fail(c, RT_EIO, "cannot write checkpoint %s", path);
+  return RT_OK;
+}
+
+// Loads a checkpoint written by save_checkpoint for the same context,
+// method, memory, precision and budgets. *found = false (and RT_OK) when the
+// file does not exist.
+rt_status load_checkpoint(rt_ctx* c, const char* path, int method, int m, const std::vector<double>& eps,
+                          CnopState& st, bool* found) {
+  const int N = c->n_inst;
+  *found = false;
+  FILE* f = fopen(path, "rb");
+  if (!f) return RT_OK;
+  *found = true;
+  bool ok = true;
+  auto get = [&](void* p, size_t n) { ok = ok && fread(p, 1, n, f) == n; };
+  char magic[8];
+  long long hdr[9];
+  get(magic, sizeof(magic));
+  get(hdr, sizeof(hdr));
+  if (!ok || memcmp(magic, kCkptMagic, sizeof(magic)) != 0) {
+    fclose(f);
+    return fail(c, RT_EIO, "%s is not a CNOP checkpoint", path);
+  }
+  if (hdr[0] != N || hdr[1] != (long long)c->total_v || hdr[2] != method || hdr[3] != m || hdr[4] != (long long)c->esz) {
+    fclose(f);
+    return fail(c, RT_EINVAL, "checkpoint %s was written for another context, method, memory or precision", path);
+  }
+  std::vector<double> e(N);
+  get(e.data(), N * sizeof(double));
+  if (!ok || e != eps) {
+    fclose(f);
+    return fail(c, RT_EINVAL, "checkpoint %s was written for other budgets eps", path);
+  }
+  st.k = (int)hdr[5];
+  st.fevals = (int)hdr[6];
+  st.gevals = (int)hdr[7];
+  st.stored_iters = (int)hdr[8];
+  get(st.stop.data(), N * sizeof(int));
+  get(st.J.data(), N * sizeof(double));
+  get(st.alpha.data(), N * sizeof(double));
+  get(st.chi.data(), N * sizeof(double));
+  get(st.gnorm.data(), N * sizeof(double));
+  for (int i = 0; i < N && ok; ++i) {
+    long long n = 0;
+    get(&n, sizeof(n));
+    if (!ok || n < 0 || n > (1LL << 31)) { ok = false; break; }
+    st.hist[i].resize(n);
+    get(st.hist[i].data(), n * sizeof(double));
+  }
+  for (int j = 0; j < m; ++j) {
+    get(st.rho[j].data(), N * sizeof(double));
+    get(st.gam[j].data(), N * sizeof(double));
+  }
+  std::vector<double*> dev = {c->d_v, c->d_g};
+  for (int j = 0; j < 2 * m + 1 && method == RT_CNOP_LBFGS; ++j) dev.push_back(c->d_pairs + (size_t)j * c->total_v);
+  std::vector<double> field(c->total_v);
+  for (double* d : dev) {
+    get(field.data(), c->total_v * sizeof(double));
+    if (!ok) break;
+    if (cudaMemcpyAsync(d, field.data(), c->total_v * sizeof(double), cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+      fclose(f);
+      return fail(c, RT_ECUDA, "checkpoint copy");
+    }
+  }
+  fclose(f);
+  if (!ok) return fail(c, RT_EIO, "checkpoint %s is truncated", path);
+  return RT_OK;
+}
+
+// The CNOP search of cnop_solve (Sec. 3.4, Eq. projection, App. A); the two
+// methods' rules are stated at cnop_solve in the C header.
+//
+// Projected L-BFGS: on the budget surface C = eps the model gradient is that
+// of J o P, gh = g - (<g, v> / <n, v>) n with n = dC/dv, and every direction
+// is made tangent, p <- p - (<n, p> / <n, n>) n, so P puts each trial point
+// back on the surface. The (s, y) pairs of the last m iterations live in a
+// ring of device fields shared by all instances; an instance whose pair
+// failed the curvature test, or that restarted, holds rho = 0 there, which
+// makes the pair a no-op in the two-loop recursion (Nocedal & Wright
+// Alg. 7.4).
+//
+// All instances advance in lockstep; dot products and the scalars of both
+// methods are FP64, reduced per instance on the device.
+template <class T>
+rt_status cnop_run(rt_ctx* c, const cnop_params* prm, double* v_inout, int flags, double* J_out, cnop_result* res) {
+  const int N = c->n_inst;
+  const bool lbfgs = prm->method == RT_CNOP_LBFGS;
+  const int m = lbfgs ? (prm->lbfgs_memory > 0 ? prm->lbfgs_memory : 10) : 0;
+  std::vector<double> eps(prm->eps, prm->eps + N);
+  for (int i = 0; i < N; ++i)
+    if (!(eps[i] > 0.0) || !std::isfinite(eps[i])) return fail(c, RT_EINVAL, "eps[%d] must be positive", i);
   CHK(ensure_fields(c, true));
-  CHK(ensure_pairs(c, m));
+  if (lbfgs) CHK(ensure_pairs(c, m));
   EnableAllOnExit guard{c};
-  std::vector<double> eps, C, ones(N, 1.0), mones(N, -1.0), sc(N);
-  CHK(cnop_start(c, prm, v_inout, flags, eps));
+  std::vector<double> C, ones(N, 1.0), mones(N, -1.0), sc(N);
   double* v = c->d_v;
-  double* g = c->d_g;    // model gradient gh at v
+  double* g = c->d_g;  // dJ/dv at v (SPG) or the model gradient gh (L-BFGS)
   double* vt = c->d_w1;
-  double* gt = c->d_w2;  // model gradient at vt
-  double* p = c->d_w3;
+  double* gt = c->d_w2;
+  double* p = c->d_w3;  // search direction (L-BFGS p, SPG d); scratch once the step is taken
   double* tmp = c->d_w4;
-  double* nrm = c->d_pairs + (size_t)(2 * m) * c->total_v;  // dC/dv at the current point
+  double* nrm = lbfgs ? c->d_pairs + (size_t)(2 * m) * c->total_v : nullptr;  // dC/dv at v
   auto S = [&](int j) { return c->d_pairs + (size_t)(2 * j) * c->total_v; };
   auto Y = [&](int j) { return c->d_pairs + (size_t)(2 * j + 1) * c->total_v; };
-  std::vector<char> en(N, 1), stuck(N, 0), on_surf(N, 0);
-  CHK(set_enabled(c, en));
-  // on_surf[i] = C(x_i) >= eps (1 - 1e-10): x was put on the surface by P
-  // (up to rounding). Then nrm = dC/dx and gx <- gx - (<gx, x> / <nrm, x>) nrm.
+  const double amin = prm->alpha_min > 0 ? prm->alpha_min : 1e-30;
+  const double amax = prm->alpha_max > 0 ? prm->alpha_max : 1e30;
+  const int M = prm->gll_memory > 0 ? prm->gll_memory : 10;
+  const int maxbt = prm->max_backtracks > 0 ? prm->max_backtracks : 30;
+
+  CnopState st;
+  st.stop.assign(N, 0);
+  st.J.assign(N, 0.0);
+  st.alpha.assign(N, 0.0);
+  st.chi.assign(N, 0.0);
+  st.gnorm.assign(N, 0.0);
+  st.hist.assign(N, {});
+  st.rho.assign(m, std::vector<double>(N, 0.0));
+  st.gam.assign(m, std::vector<double>(N, 0.0));
+  std::vector<char> on_surf(N, 0);
+  auto running = [&](int i) { return st.stop[i] == 0; };
+  auto set_running = [&]() -> rt_status {
+    std::vector<char> e(N);
+    for (int i = 0; i < N; ++i) e[i] = running(i);
+    return set_enabled(c, e);
+  };
+
+  // chi = ||P(x + g) - x||_inf with g = dJ/dx (App. A), and ||g||; p is scratch
+  auto stationarity = [&](const double* x, const double* gx) -> rt_status {
+    std::vector<double> gg, chi;
+    CHK(axpby(c, p, ones, x, &ones, gx));
+    CHK(field_sums(c, 0, p, nullptr, C));
+    for (int i = 0; i < N; ++i) sc[i] = C[i] <= eps[i] ? 1.0 : std::sqrt(eps[i] / C[i]);
+    CHK(axpby(c, p, sc, p, nullptr, nullptr));
+    CHK(axpby(c, p, ones, p, &mones, x));
+    CHK(field_max_abs(c, p, chi));
+    CHK(field_sums(c, 1, gx, gx, gg));
+    for (int i = 0; i < N; ++i)
+      if (running(i)) {
+        st.chi[i] = chi[i];
+        st.gnorm[i] = std::sqrt(gg[i]);
+      }
+    return RT_OK;
+  };
+  // on_surf[i] = C(x_i) >= eps (1 - 1e-10): x was put on the surface by P (up
+  // to rounding). Then nrm = dC/dx and gx <- gx - (<gx, x> / <nrm, x>) nrm.
   auto model_gradient = [&](const double* x, double* gx) -> rt_status {
     CHK(field_sums(c, 0, x, nullptr, C));
     for (int i = 0; i < N; ++i) on_surf[i] = C[i] >= eps[i] * (1.0 - 1e-10);
@@ -1016,7 +1085,7 @@ rt_status lbfgs_impl(rt_ctx* c, const cnop_params* prm, double* v_inout, int fla
     CHK(field_sums(c, 1, gx, x, gx_x));
     CHK(field_sums(c, 1, nrm, x, n_x));
     for (int i = 0; i < N; ++i)
-      if (on_surf[i] && !stuck[i]) coef[i] = -(gx_x[i] / n_x[i]);
+      if (on_surf[i] && running(i)) coef[i] = -(gx_x[i] / n_x[i]);
     return axpby(c, gx, ones, gx, &coef, nrm);
   };
   // p <- p - (<nrm, p> / <nrm, nrm>) nrm for the instances flagged in `sel`
@@ -1025,165 +1094,266 @@ rt_status lbfgs_impl(rt_ctx* c, const cnop_params* prm, double* v_inout, int fla
     CHK(field_sums(c, 1, nrm, p, np_));
     CHK(field_sums(c, 1, nrm, nrm, nn));
     for (int i = 0; i < N; ++i)
-      if (sel[i] && on_surf[i] && !stuck[i]) coef[i] = -(np_[i] / nn[i]);
+      if (sel[i] && on_surf[i] && running(i)) coef[i] = -(np_[i] / nn[i]);
     return axpby(c, p, ones, p, &coef, nrm);
   };
-  std::vector<double> J(N), Jt(N), Jn(N);
-  int fevals = 0, gevals = 0, iters = 0;
-  CHK(gradient_impl<T>(c, v, J.data(), g, nullptr));
-  ++gevals;
-  CHK(model_gradient(v, g));
-  std::vector<std::vector<double>> rho(m, std::vector<double>(N, 0.0)), gam(m, std::vector<double>(N, 0.0)),
-      a(m, std::vector<double>(N, 0.0));
-  int stored_iters = 0;  // pairs written so far; the ring holds the last min(stored_iters, m)
-  std::vector<std::vector<double>> hist(N);
-  for (int i = 0; i < N; ++i) hist[i].push_back(J[i]);
-  const int M = prm->gll_memory > 0 ? prm->gll_memory : 10;
-  const int maxbt = prm->max_backtracks > 0 ? prm->max_backtracks : 30;
-  bool any_stuck = false;
-  // slot of the t-th newest pair in the ring (t = 0: newest)
-  auto slot = [&](int t) { return (stored_iters - 1 - t) % m; };
-  // vt = P(v + lam p) (Eq. projection), then tmp = vt - v and gd = <gh, tmp>;
-  // stopped instances keep vt = v.
-  auto trial = [&](const std::vector<double>& lam, std::vector<double>& gd) -> rt_status {
-    CHK(axpby(c, vt, ones, v, &lam, p));
-    CHK(field_sums(c, 0, vt, nullptr, C));
-    for (int i = 0; i < N; ++i) sc[i] = (stuck[i] || C[i] <= eps[i]) ? 1.0 : std::sqrt(eps[i] / C[i]);
-    CHK(axpby(c, vt, sc, vt, nullptr, nullptr));
-    CHK(axpby(c, tmp, ones, vt, &mones, v));
-    return field_sums(c, 1, g, tmp, gd);
-  };
-  for (int k = 0; k < prm->max_iter; ++k) {
-    const int npairs = std::min(stored_iters, m);
-    // H0 = gamma I: <s,y>/<y,y> of the newest stored pair, else ||v|| / ||gh||
-    std::vector<double> vv, gg, g0(N), gamma(N);
-    std::vector<char> has_pair(N, 0);
+  auto spg_alpha0 = [&]() -> rt_status {
+    std::vector<double> vv, gg;
     CHK(field_sums(c, 1, v, v, vv));
     CHK(field_sums(c, 1, g, g, gg));
-    for (int i = 0; i < N; ++i) {
-      g0[i] = std::sqrt(vv[i]) / std::max(std::sqrt(gg[i]), 1e-300);
-      gamma[i] = g0[i];
-      for (int t = 0; t < npairs; ++t)
-        if (rho[slot(t)][i] > 0.0) {
-          gamma[i] = gam[slot(t)][i];
-          has_pair[i] = 1;
-          break;
-        }
-    }
-    // two-loop recursion on p (starts as gh)
-    CHK(axpby(c, p, ones, g, nullptr, nullptr));
-    auto slot_used = [&](int j) {
-      for (int i = 0; i < N; ++i)
-        if (rho[j][i] != 0.0) return true;
-      return false;
-    };
-    for (int t = 0; t < npairs; ++t) {
-      const int j = slot(t);
-      if (!slot_used(j)) continue;
-      std::vector<double> sq, na(N);
-      CHK(field_sums(c, 1, S(j), p, sq));
-      for (int i = 0; i < N; ++i) {
-        a[j][i] = rho[j][i] * sq[i];
-        na[i] = -a[j][i];
-      }
-      CHK(axpby(c, p, ones, p, &na, Y(j)));
-    }
-    CHK(axpby(c, p, gamma, p, nullptr, nullptr));
-    for (int t = npairs - 1; t >= 0; --t) {
-      const int j = slot(t);
-      if (!slot_used(j)) continue;
-      std::vector<double> yr, coef(N);
-      CHK(field_sums(c, 1, Y(j), p, yr));
-      for (int i = 0; i < N; ++i) coef[i] = a[j][i] - rho[j][i] * yr[i];
-      CHK(axpby(c, p, ones, p, &coef, S(j)));
-    }
-    CHK(tangent(en));
-    // ascent check; a failed check drops the pairs and restarts from the
-    // scaled model gradient
-    std::vector<double> gp, keep(N, 1.0), gcoef(N, 0.0);
-    CHK(field_sums(c, 1, g, p, gp));
-    std::vector<char> restart(N, 0);
-    bool any_restart = false;
     for (int i = 0; i < N; ++i)
-      if (!stuck[i] && has_pair[i] && gp[i] <= 0.0) {
-        restart[i] = 1;
-        any_restart = true;
-        keep[i] = 0.0;
-        gcoef[i] = g0[i];
-        for (int j = 0; j < m; ++j) rho[j][i] = 0.0;
-      }
-    if (any_restart) {
-      CHK(axpby(c, p, keep, p, &gcoef, g));
-      CHK(tangent(restart));
+      st.alpha[i] = std::min(std::max(std::sqrt(vv[i]) / std::max(std::sqrt(gg[i]), 1e-300), amin), amax);
+    return RT_OK;
+  };
+
+  FILE* log = nullptr;
+  bool resumed = false;
+  if (prm->resume && prm->checkpoint_path) CHK(load_checkpoint(c, prm->checkpoint_path, prm->method, m, eps, st, &resumed));
+  if (prm->log_path) {
+    log = fopen(prm->log_path, resumed ? "a" : "w");
+    if (!log) return fail(c, RT_EIO, "cannot open log %s", prm->log_path);
+    if (!resumed) fprintf(log, "# iter instance J C chi grad_norm lambda forward_evals gradient_evals\n");
+  }
+  struct CloseLog {
+    FILE*& f;
+    ~CloseLog() {
+      if (f) fclose(f);
     }
-    std::vector<double> Jref(N), lam(N, 1.0), gd;
+  } close_log{log};
+  auto record = [&](int iter, const std::vector<double>& lam) -> rt_status {
+    if (res && res->J_history)
+      for (int i = 0; i < N; ++i) res->J_history[(size_t)iter * N + i] = st.J[i];
+    if (!log) return RT_OK;
+    CHK(field_sums(c, 0, v, nullptr, C));
+    for (int i = 0; i < N; ++i)
+      fprintf(log, "%d %d %.17g %.17g %.17g %.17g %.17g %d %d\n", iter, i, st.J[i], C[i], st.chi[i], st.gnorm[i],
+              lam.empty() ? 0.0 : lam[i], st.fevals, st.gevals);
+    fflush(log);
+    return RT_OK;
+  };
+  auto check_chi = [&]() {
+    for (int i = 0; i < N; ++i)
+      if (running(i) && prm->chi_tol > 0.0 && st.chi[i] <= prm->chi_tol) st.stop[i] = 2;
+  };
+
+  if (resumed) {
+    if (lbfgs) {
+      // on_surf and nrm at v, as the last model_gradient left them
+      CHK(field_sums(c, 0, v, nullptr, C));
+      for (int i = 0; i < N; ++i) on_surf[i] = C[i] >= eps[i] * (1.0 - 1e-10);
+      CU(rt::launch_field_weight(c->d_inst, c->d_tiles, c->ntiles, nrm, v, c->stream));
+    }
+  } else {
+    CHK(cnop_start(c, prm, v_inout, flags, eps));
+    CHK(set_running());
+    CHK(gradient_impl<T>(c, v, st.J.data(), g, nullptr));
+    ++st.gevals;
+    CHK(stationarity(v, g));
+    if (lbfgs) CHK(model_gradient(v, g));
+    else CHK(spg_alpha0());
+    for (int i = 0; i < N; ++i) st.hist[i].push_back(st.J[i]);
+    check_chi();
+    CHK(record(0, {}));
+  }
+
+  auto slot = [&](int t) { return (st.stored_iters - 1 - t) % m; };  // t = 0: newest pair
+  auto slot_used = [&](int j) {
+    for (int i = 0; i < N; ++i)
+      if (st.rho[j][i] != 0.0) return true;
+    return false;
+  };
+  bool any_live = false;
+  for (int i = 0; i < N; ++i) any_live = any_live || running(i);
+  while (st.k < prm->max_iter && any_live) {
+    const int k = st.k;
+    std::vector<double> gd, lam(N, 1.0), Jref(N), Jt(N), Jn(N);
+    if (lbfgs) {
+      // H0 = gamma I: <s,y>/<y,y> of the newest stored pair, else ||v|| / ||gh||
+      const int npairs = std::min(st.stored_iters, m);
+      std::vector<double> vv, gg, g0(N), gamma(N);
+      std::vector<char> has_pair(N, 0), all(N, 1);
+      CHK(field_sums(c, 1, v, v, vv));
+      CHK(field_sums(c, 1, g, g, gg));
+      for (int i = 0; i < N; ++i) {
+        g0[i] = std::sqrt(vv[i]) / std::max(std::sqrt(gg[i]), 1e-300);
+        gamma[i] = g0[i];
+        for (int t = 0; t < npairs; ++t)
+          if (st.rho[slot(t)][i] > 0.0) {
+            gamma[i] = st.gam[slot(t)][i];
+            has_pair[i] = 1;
+            break;
+          }
+      }
+      // two-loop recursion on p (starts as gh)
+      std::vector<std::vector<double>> a(m, std::vector<double>(N, 0.0));
+      CHK(axpby(c, p, ones, g, nullptr, nullptr));
+      for (int t = 0; t < npairs; ++t) {
+        const int j = slot(t);
+        if (!slot_used(j)) continue;
+        std::vector<double> sq, na(N);
+        CHK(field_sums(c, 1, S(j), p, sq));
+        for (int i = 0; i < N; ++i) {
+          a[j][i] = st.rho[j][i] * sq[i];
+          na[i] = -a[j][i];
+        }
+        CHK(axpby(c, p, ones, p, &na, Y(j)));
+      }
+      CHK(axpby(c, p, gamma, p, nullptr, nullptr));
+      for (int t = npairs - 1; t >= 0; --t) {
+        const int j = slot(t);
+        if (!slot_used(j)) continue;
+        std::vector<double> yr, coef(N);
+        CHK(field_sums(c, 1, Y(j), p, yr));
+        for (int i = 0; i < N; ++i) coef[i] = a[j][i] - st.rho[j][i] * yr[i];
+        CHK(axpby(c, p, ones, p, &coef, S(j)));
+      }
+      CHK(tangent(all));
+      // ascent check; a failed check drops the pairs and restarts from the
+      // scaled model gradient
+      std::vector<double> gp, keep(N, 1.0), gcoef(N, 0.0);
+      CHK(field_sums(c, 1, g, p, gp));
+      std::vector<char> restart(N, 0);
+      bool any_restart = false;
+      for (int i = 0; i < N; ++i)
+        if (running(i) && has_pair[i] && gp[i] <= 0.0) {
+          restart[i] = 1;
+          any_restart = true;
+          keep[i] = 0.0;
+          gcoef[i] = g0[i];
+          for (int j = 0; j < m; ++j) st.rho[j][i] = 0.0;
+        }
+      if (any_restart) {
+        CHK(axpby(c, p, keep, p, &gcoef, g));
+        CHK(tangent(restart));
+      }
+    } else {
+      // d = P(v + alpha g) - v and <g, d>
+      CHK(axpby(c, vt, ones, v, &st.alpha, g));
+      CHK(field_sums(c, 0, vt, nullptr, C));
+      for (int i = 0; i < N; ++i) sc[i] = C[i] <= eps[i] ? 1.0 : std::sqrt(eps[i] / C[i]);
+      CHK(axpby(c, vt, sc, vt, nullptr, nullptr));
+      CHK(axpby(c, p, ones, vt, &mones, v));
+      CHK(field_sums(c, 1, g, p, gd));
+    }
+    // trial point for the step lam and its sufficient-increase term: L-BFGS
+    // vt = P(v + lam p), c <gh, vt - v>; SPG vt = v + lam d, c lam <g, d>.
+    // Stopped instances keep vt = v.
+    std::vector<double> term(N);
+    auto trial = [&]() -> rt_status {
+      CHK(axpby(c, vt, ones, v, &lam, p));
+      if (!lbfgs) {
+        for (int i = 0; i < N; ++i) term[i] = prm->armijo_c * lam[i] * gd[i];
+        return RT_OK;
+      }
+      std::vector<double> gs;
+      CHK(field_sums(c, 0, vt, nullptr, C));
+      for (int i = 0; i < N; ++i) sc[i] = (!running(i) || C[i] <= eps[i]) ? 1.0 : std::sqrt(eps[i] / C[i]);
+      CHK(axpby(c, vt, sc, vt, nullptr, nullptr));
+      CHK(axpby(c, tmp, ones, vt, &mones, v));
+      CHK(field_sums(c, 1, g, tmp, gs));
+      for (int i = 0; i < N; ++i) term[i] = prm->armijo_c * gs[i];
+      return RT_OK;
+    };
     for (int i = 0; i < N; ++i) {
-      const size_t h0 = hist[i].size() > (size_t)M ? hist[i].size() - M : 0;
-      Jref[i] = *std::max_element(hist[i].begin() + h0, hist[i].end());
+      const size_t h0 = st.hist[i].size() > (size_t)M ? st.hist[i].size() - M : 0;
+      Jref[i] = *std::max_element(st.hist[i].begin() + h0, st.hist[i].end());
     }
     std::vector<char> acc(N, 0);
-    for (int i = 0; i < N; ++i) acc[i] = stuck[i];
+    for (int i = 0; i < N; ++i) acc[i] = !running(i);
     for (int bt = 0; bt < maxbt; ++bt) {
-      CHK(trial(lam, gd));
+      CHK(trial());
       std::vector<char> e(N);
       for (int i = 0; i < N; ++i) e[i] = !acc[i];
       CHK(set_enabled(c, e));
       int steps = 0;
       CHK(forward_impl<T>(c, vt, RT_DEVICE_PTRS, Jt.data(), nullptr, &steps));
-      ++fevals;
+      ++st.fevals;
       bool all = true;
       for (int i = 0; i < N; ++i) {
         if (acc[i]) continue;
-        if (Jt[i] >= Jref[i] + prm->armijo_c * gd[i]) acc[i] = 1;
+        if (Jt[i] >= Jref[i] + term[i]) acc[i] = 1;
         else { lam[i] *= 0.5; all = false; }
       }
       if (all) break;
     }
     for (int i = 0; i < N; ++i)
-      if (!acc[i]) { stuck[i] = 1; any_stuck = true; }
+      if (!acc[i]) st.stop[i] = 1;
     for (int i = 0; i < N; ++i)
-      if (stuck[i]) lam[i] = 0.0;
-    CHK(trial(lam, gd));  // the accepted point (v itself for stopped instances)
-    std::vector<char> e(N);
-    bool any_live = false;
-    for (int i = 0; i < N; ++i) { e[i] = !stuck[i]; any_live = any_live || e[i]; }
+      if (!running(i)) lam[i] = 0.0;
+    CHK(trial());  // the accepted point (v itself for stopped instances)
+    any_live = false;
+    for (int i = 0; i < N; ++i) any_live = any_live || running(i);
     if (!any_live) break;
-    CHK(set_enabled(c, e));
+    CHK(set_running());
     CHK(gradient_impl<T>(c, vt, Jn.data(), gt, nullptr));
-    ++gevals;
-    CHK(model_gradient(vt, gt));
-    // new pair: s = vt - v (already in tmp), y = -(gh_new - gh) = gh - gh_new
-    const int h = stored_iters % m;
-    CHK(axpby(c, S(h), ones, tmp, nullptr, nullptr));
-    CHK(axpby(c, Y(h), ones, g, &mones, gt));
-    std::vector<double> sy, yy;
-    CHK(field_sums(c, 1, S(h), Y(h), sy));
-    CHK(field_sums(c, 1, Y(h), Y(h), yy));
-    for (int i = 0; i < N; ++i) {
-      const bool ok = !stuck[i] && sy[i] > 0.0;
-      rho[h][i] = ok ? 1.0 / sy[i] : 0.0;
-      gam[h][i] = ok ? sy[i] / yy[i] : 0.0;
-      if (stuck[i]) continue;
-      J[i] = Jn[i];
-      hist[i].push_back(J[i]);
+    ++st.gevals;
+    CHK(stationarity(vt, gt));
+    CHK(axpby(c, tmp, ones, vt, &mones, v));  // s = vt - v
+    if (lbfgs) {
+      CHK(model_gradient(vt, gt));
+      // new pair: s, y = -(gh_new - gh) = gh - gh_new
+      const int h = st.stored_iters % m;
+      CHK(axpby(c, S(h), ones, tmp, nullptr, nullptr));
+      CHK(axpby(c, Y(h), ones, g, &mones, gt));
+      std::vector<double> sy, yy;
+      CHK(field_sums(c, 1, S(h), Y(h), sy));
+      CHK(field_sums(c, 1, Y(h), Y(h), yy));
+      for (int i = 0; i < N; ++i) {
+        const bool ok = running(i) && sy[i] > 0.0;
+        st.rho[h][i] = ok ? 1.0 / sy[i] : 0.0;
+        st.gam[h][i] = ok ? sy[i] / yy[i] : 0.0;
+      }
+      ++st.stored_iters;
+    } else {
+      // alpha = <s,s>/<s,y'>, y' = -(g_new - g)
+      std::vector<double> ss, sg, sgt;
+      CHK(field_sums(c, 1, tmp, tmp, ss));
+      CHK(field_sums(c, 1, tmp, g, sg));
+      CHK(field_sums(c, 1, tmp, gt, sgt));
+      for (int i = 0; i < N; ++i) {
+        if (!running(i)) continue;
+        const double sy = sg[i] - sgt[i];
+        st.alpha[i] = sy <= 0.0 ? amax : std::min(std::max(ss[i] / sy, amin), amax);
+      }
     }
-    ++stored_iters;
+    for (int i = 0; i < N; ++i) {
+      if (!running(i)) continue;
+      st.J[i] = Jn[i];
+      st.hist[i].push_back(st.J[i]);
+    }
     std::swap(c->d_v, c->d_w1);  // v <- vt
-    std::swap(c->d_g, c->d_w2);  // gh <- gh_new
+    std::swap(c->d_g, c->d_w2);  // g <- g_new
     v = c->d_v;
     g = c->d_g;
     vt = c->d_w1;
     gt = c->d_w2;
-    ++iters;
+    st.k = k + 1;
+    check_chi();
+    CHK(record(st.k, lam));
+    any_live = false;
+    for (int i = 0; i < N; ++i) any_live = any_live || running(i);
+    if (prm->checkpoint_path && prm->checkpoint_every > 0 && st.k % prm->checkpoint_every == 0)
+      CHK(save_checkpoint(c, prm->checkpoint_path, prm->method, m, eps, st));
   }
+  if (prm->checkpoint_path) CHK(save_checkpoint(c, prm->checkpoint_path, prm->method, m, eps, st));
   CHK(copy_out(c, v, flags, v_inout));
   CU(cudaStreamSynchronize(c->stream));
   if (J_out)
-    for (int i = 0; i < N; ++i) J_out[i] = J[i];
+    for (int i = 0; i < N; ++i) J_out[i] = st.J[i];
+  bool any_stuck = false;
+  for (int i = 0; i < N; ++i) any_stuck = any_stuck || st.stop[i] == 1;
   if (res) {
-    res->iterations = iters;
-    res->forward_evals = fevals;
-    res->gradient_evals = gevals;
+    res->iterations = st.k;
+    res->forward_evals = st.fevals;
+    res->gradient_evals = st.gevals;
+    std::vector<double> Cf;
+    if (res->C) CHK(field_sums(c, 0, v, nullptr, Cf));
+    for (int i = 0; i < N; ++i) {
+      if (res->C) res->C[i] = Cf[i];
+      if (res->chi) res->chi[i] = st.chi[i];
+      if (res->grad_norm) res->grad_norm[i] = st.gnorm[i];
+      if (res->stop) res->stop[i] = st.stop[i];
+    }
   }
   if (any_stuck) return fail(c, RT_ENOTCONVERGED, "an instance found no acceptable step");
   return RT_OK;
@@ -1537,12 +1707,9 @@ rt_status cnop_solve(rt_ctx* c, const cnop_params* prm, double* v_inout, int fla
   CHK(enter(c));
   Timer tm(c);
   rt_status s;
-  if (prm->method == RT_CNOP_LBFGS)
-    s = c->esz == 8 ? lbfgs_impl<double>(c, prm, v_inout, flags, J_out, res)
-                    : lbfgs_impl<float>(c, prm, v_inout, flags, J_out, res);
-  else if (prm->method == RT_CNOP_SPG)
-    s = c->esz == 8 ? cnop_impl<double>(c, prm, v_inout, flags, J_out, res)
-                    : cnop_impl<float>(c, prm, v_inout, flags, J_out, res);
+  if (prm->method == RT_CNOP_LBFGS || prm->method == RT_CNOP_SPG)
+    s = c->esz == 8 ? cnop_run<double>(c, prm, v_inout, flags, J_out, res)
+                    : cnop_run<float>(c, prm, v_inout, flags, J_out, res);
   else
     s = fail(c, RT_EINVAL, "unknown CNOP method %d", prm->method);
   const float ms = tm.stop();

@@ -34,8 +34,10 @@ def test_struct_sizes_match_header_layout():
     # rt_problem: 2 ints, 12 doubles, 2 ints, 2 doubles, 3 ints (+ padding)
     assert ctypes.sizeof(rt.RtProblem) == 8 + 12 * 8 + 8 + 16 + 16
     assert ctypes.sizeof(rt.RtOptions) == 24
-    # cnop_params: 3 ints (+ pad), 4 doubles, a pointer, 2 ints
-    assert ctypes.sizeof(rt.CnopParams) == 16 + 32 + 8 + 8
+    # cnop_params: 3 ints (+ pad), 4 doubles, a pointer, 2 ints, a double, 2 pointers, 2 ints
+    # cnop_result: 3 ints (+ pad), a double, 5 pointers
+    assert ctypes.sizeof(rt.CnopParams) == 16 + 32 + 8 + 8 + 8 + 16 + 8
+    assert ctypes.sizeof(rt.CnopResult) == 16 + 8 + 40
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

@@ -114,6 +114,60 @@ def test_lbfgs_fp64_matches_oracle():
         assert err <= 1e-8, err
         assert oracle.constraint(w, v.reshape(v0.shape)) == pytest.approx(eps, rel=1e-12)
         assert J[0] > ref["history"][0]
+        assert np.allclose(res["J_history"][:, 0], ref["history"], rtol=1e-10, atol=0)
+        assert res["chi"][0] == pytest.approx(ref["records"][-1]["chi"], rel=1e-6)
+        assert res["grad_norm"][0] == pytest.approx(ref["records"][-1]["grad_norm"], rel=1e-8)
+        assert res["C"][0] == pytest.approx(eps, rel=1e-12)
+        assert res["stop"][0] == 0
+
+
+def test_cnop_checkpoint_resume_log_and_chi_stop(tmp_path):
+    """A run of 6 iterations equals, bitwise, 3 iterations + checkpoint +
+    resume to 6 in a fresh context (both methods, batch of two instances);
+    the log has one line per instance and iteration; a chi tolerance stops
+    an instance at the first iteration whose chi is below it."""
+    import paper_2608_04085_b300 as rt
+    ws = [I.rt_box(16, 32, nsteps=12), I.rt_box(12, 40, nsteps=10, limiter=I.LIM_MC)]
+    eps = [1e-4, 3e-4]
+    xi = np.concatenate([I.gaussian_field(30 + k, 2, w.ny, w.nx).ravel() for k, w in enumerate(ws)])
+    for method in (rt.RT_CNOP_LBFGS, rt.RT_CNOP_SPG):
+        log = tmp_path / f"log{method}.txt"
+        with rt.Context(ws, precision=rt.RT_FP64) as ctx:
+            v6, J6, r6 = ctx.cnop(xi, eps, 6, method=method, log_path=str(log))
+        lines = [l.split() for l in log.read_text().splitlines() if not l.startswith("#")]
+        assert len(lines) == 7 * 2
+        assert [int(l[0]) for l in lines] == [k for k in range(7) for _ in range(2)]
+        assert np.allclose([float(l[2]) for l in lines], r6["J_history"].ravel(), rtol=1e-15, atol=0)
+        ck = tmp_path / f"ck{method}.bin"
+        with rt.Context(ws, precision=rt.RT_FP64) as ctx:
+            _, _, r3 = ctx.cnop(xi, eps, 3, method=method, checkpoint_path=str(ck), checkpoint_every=1)
+        assert r3["iterations"] == 3 and ck.exists()
+        with rt.Context(ws, precision=rt.RT_FP64) as ctx:
+            vr, Jr, rr = ctx.cnop(np.zeros_like(xi), eps, 6, method=method, checkpoint_path=str(ck), resume=True)
+        assert rr["iterations"] == 6
+        assert (rr["forward_evals"], rr["gradient_evals"]) == (r6["forward_evals"], r6["gradient_evals"])
+        assert np.array_equal(vr, v6) and np.array_equal(Jr, J6)
+        assert np.array_equal(rr["chi"], r6["chi"])
+        # chi tolerance: each instance stops at its first iteration whose chi
+        # is at most the tolerance; the others run on unchanged
+        chis = np.array([float(l[4]) for l in lines]).reshape(7, 2)
+        tol = float(np.min(chis[1:, 0]))
+        with rt.Context(ws, precision=rt.RT_FP64) as ctx:
+            _, Jc, rc = ctx.cnop(xi, eps, 6, method=method, chi_tol=tol)
+        assert rc["status"] == rt.RT_OK
+        last = 0
+        for i in range(2):
+            hits = np.nonzero(chis[:, i] <= tol)[0]
+            k_i = int(hits[0]) if hits.size else 6
+            last = max(last, k_i)
+            assert rc["stop"][i] == (2 if hits.size else 0)
+            assert Jc[i] == r6["J_history"][k_i, i]
+        assert rc["stop"][0] == 2
+        assert rc["iterations"] == last
+    # a checkpoint of one method does not resume the other
+    with rt.Context(ws, precision=rt.RT_FP64) as ctx:
+        with pytest.raises(RuntimeError, match="another context, method"):
+            ctx.cnop(xi, eps, 6, method=rt.RT_CNOP_SPG, checkpoint_path=str(tmp_path / "ck1.bin"), resume=True)
 
 
 def test_lbfgs_fp32_cosine_against_fp64_and_beats_spg():

@@ -107,6 +107,9 @@ def test_sphere_quadratic_reaches_leading_eigenvector(oracle_lib):
     cos = abs(v @ V[:, -1]) / np.linalg.norm(v)
     assert cos >= 1 - 1e-10, cos
     assert res["J"] == pytest.approx(lam[-1] * r, rel=1e-10)
+    # App. A stationarity: at the maximiser g = 2 lambda v, so P(v + g) = v
+    assert res["records"][-1]["chi"] <= 1e-7 * np.max(np.abs(v))
+    assert res["chi0"] > 1e-2 * np.max(np.abs(v0))
     # on the sphere the pairs carry the (positive) curvature of -J o P, and the
     # quasi-Newton model converges far faster than scaled steepest ascent
     n_it = 20
