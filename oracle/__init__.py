@@ -455,6 +455,48 @@ def lbfgs(w, v_start, eps, iters, m=10, memory=10, armijo=1e-4, max_backtracks=3
                            active=lambda v: constraint(w, v) >= eps * (1.0 - 1e-10), log=log)
 
 
+# ------------------------------- comparison diagnostics, Sec. 4.3 (Eqs. ke, hmix, hmix-f)
+def kinetic_energy(w, U):
+    """Total kinetic energy: sum over cells of e_k = rho |u|^2 / 2 = |m|^2 / (2 rho), times dx dy (Eq. ke)."""
+    U = np.asarray(U, dtype=np.float64).reshape(4, w.ny, w.nx)
+    dx, dy = grid_spacing(w)
+    return float(np.sum(0.5 * (U[1] * U[1] + U[2] * U[2]) / U[0]) * dx * dy)
+
+
+def mixing_width(w, U):
+    """Eqs. hmix, hmix-f: f(y) = clip((<rho>_x - rho_l) / (rho_h - rho_l), 0, 1) and
+    h_mix = integral of 4 f (1 - f) dy, the integral a midpoint sum over the rows."""
+    U = np.asarray(U, dtype=np.float64).reshape(4, w.ny, w.nx)
+    _, dy = grid_spacing(w)
+    rho_mean = np.mean(U[0], axis=1)
+    f = np.clip((rho_mean - w.rho_light) / (w.rho_heavy - w.rho_light), 0.0, 1.0)
+    return float(np.sum(4.0 * f * (1.0 - f)) * dy)
+
+
+def series(w, v, every):
+    """KE(t) and h_mix(t) of the forward run from v, sampled at steps 0, every,
+    2 every, ... and at the last step (Sec. 4.3, Figs. ek_growth, mixing_width).
+    The state after k steps is the forward run replaying the first k time
+    steps. Returns arrays step, t, KE, h_mix."""
+    full = forward(w, v)
+    dt = full["dt"]
+    n = len(dt)
+    steps = list(range(0, n, every))
+    if steps[-1] != n:
+        steps.append(n)
+    out = {"step": [], "t": [], "KE": [], "h_mix": []}
+    for k in steps:
+        U = inject(w, v) if k == 0 else forward(w, v, dt_replay=dt[:k])["U"]
+        t = 0.0
+        for d in dt[:k]:
+            t += d
+        out["step"].append(k)
+        out["t"].append(t)
+        out["KE"].append(kinetic_energy(w, U))
+        out["h_mix"].append(mixing_width(w, U))
+    return {key: np.array(val) for key, val in out.items()}
+
+
 # ------------------------------------------------- spectra, Sec. 4.2 Eq. fourier_coeff
 def spectrum(vy):
     """Row y_peak of largest rms along x (ties: lowest row), its DFT u_n and the

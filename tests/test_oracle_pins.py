@@ -234,3 +234,53 @@ def test_linear_rayleigh_taylor_growth_rate(oracle_lib):
     A = (w.rho_heavy - w.rho_light) / (w.rho_heavy + w.rho_light)
     ideal = math.sqrt(A * abs(w.g_y) * k)
     assert 0.8 * ideal <= sigma <= 1.02 * ideal, (sigma, ideal)
+
+
+# ------------------------------------------ comparison diagnostics (Sec. 4.3)
+def test_mixing_width_of_the_tanh_profile_is_twice_h_s(oracle_lib):
+    """Eqs. hmix, hmix-f on the base state: f = (1 + tanh(y / h_s)) / 2, so
+    4 f (1 - f) = sech^2(y / h_s), whose integral over the line is 2 h_s."""
+    o = oracle_lib
+    w = I.rt_box(4, 6000)
+    rho0, p0 = o.base_state(w)
+    U = np.zeros((4, w.ny, w.nx))
+    U[0] = rho0[:, None]
+    U[3] = (p0 / (w.gamma - 1.0))[:, None]
+    assert o.mixing_width(w, U) == pytest.approx(2.0 * w.h_s, rel=1e-6)
+    assert o.kinetic_energy(w, U) == 0.0
+
+
+def test_mixing_width_limits_and_kinetic_energy_of_uniform_flow(oracle_lib):
+    o = oracle_lib
+    w = I.rt_box(8, 24)
+    U = np.zeros((4, w.ny, w.nx))
+    U[3] = 2.5
+    # fully mixed: f = 1/2 everywhere, h_mix = L_y
+    U[0] = 0.5 * (w.rho_heavy + w.rho_light)
+    assert o.mixing_width(w, U) == pytest.approx(w.y1 - w.y0, rel=1e-14)
+    # sharp interface on a cell boundary: no mixed row
+    U[0] = np.where(np.arange(w.ny) >= w.ny // 2, w.rho_heavy, w.rho_light)[:, None]
+    assert o.mixing_width(w, U) == 0.0
+    # densities beyond the pure values are clipped
+    U[0, :3] = 3.0
+    U[0, 3:6] = 0.5
+    assert o.mixing_width(w, U) == 0.0
+    # uniform flow: KE = rho |u|^2 / 2 times the area
+    U[0] = 1.7
+    U[1] = 1.7 * 0.3
+    U[2] = 1.7 * -0.4
+    area = (w.x1 - w.x0) * (w.y1 - w.y0)
+    assert o.kinetic_energy(w, U) == pytest.approx(0.5 * 1.7 * 0.25 * area, rel=1e-13)
+
+
+def test_series_ends_at_the_objective_and_starts_at_the_injected_state(oracle_lib):
+    o = oracle_lib
+    w = I.rt_box(12, 36, nsteps=25)
+    v = o.scale_to_budget(w, I.gaussian_field(2, 2, w.ny, w.nx), 1e-4)
+    s = o.series(w, v, 7)
+    assert list(s["step"]) == [0, 7, 14, 21, 25]
+    ref = o.forward(w, v)
+    assert s["KE"][-1] == pytest.approx(ref["J_ke"], rel=1e-13)
+    assert s["t"][-1] == pytest.approx(np.sum(ref["dt"]), rel=1e-15)
+    # at t = 0 the kinetic energy is the perturbation's, sum rho0 |v|^2 / 2 dA = C(v)
+    assert s["KE"][0] == pytest.approx(o.constraint(w, v), rel=1e-13)
