@@ -148,6 +148,20 @@ size_t rt_field_total(const rt_ctx* ctx);
 rt_status rt_forward(rt_ctx* ctx, const double* v0, int flags, double* J_out,
                      double* J_ke_out, rt_run_stats* st);
 
+/* Comparison diagnostics of one forward run (Sec. 4.3, Figs. ek_growth and
+ * mixing_width): for every instance, samples of the time t, the total kinetic
+ * energy KE(t) = sum e_k dx dy (Eq. ke) and the mixing width
+ * h_mix(t) = sum over rows of 4 f (1 - f) dy with
+ * f = clip((<rho>_x - rho_light) / (rho_heavy - rho_light), 0, 1)
+ * (Eqs. hmix, hmix-f), taken at step 0, every `every` steps, and at the
+ * instance's last step. Outputs are [n_instances][max_samples] row-major
+ * (instance i's samples start at i * max_samples); n_out[i] = samples
+ * written (samples beyond max_samples are dropped). flags as rt_forward; the
+ * run counts as the previous run for RT_REPLAY_DT.
+ * Errors: RT_EINVAL (null output, every < 1, max_samples < 1), as rt_forward. */
+rt_status rt_forward_series(rt_ctx* ctx, const double* v0, int flags, int every, int max_samples,
+                            double* t_out, double* ke_out, double* hmix_out, int* n_out);
+
 /* Exact discrete gradient dJ/dv0 (Sec. 3.4) of the same map, dt sequence
  * frozen at the one the forward pass chose, by a hand-written adjoint of the
  * time stepper with store-all, sqrt(N) or binomial (revolve) checkpointing

@@ -35,7 +35,7 @@ _STATUS = {1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENONFINITE", 5:
 EXPORTS = ("rt_init", "rt_destroy", "rt_last_error", "rt_num_instances", "rt_field_offset",
            "rt_field_size", "rt_field_total", "rt_forward", "rt_gradient", "rt_constraint",
            "rt_project", "rt_get_state", "rt_get_dt", "rt_set_kernel_timing", "rt_kernel_times", "rt_stage_kernel",
-           "cnop_solve", "rt_objective_noalloc")
+           "cnop_solve", "rt_objective_noalloc", "rt_forward_series")
 
 
 class RtError(RuntimeError):
@@ -134,6 +134,8 @@ def library():
         llp = ctypes.POINTER(ctypes.c_longlong)
         L.rt_kernel_times.argtypes = [vp, dp, llp, llp]
         L.rt_kernel_times.restype = ip
+        L.rt_forward_series.argtypes = [vp, vp, ip, ip, ip, dp, dp, dp, ctypes.POINTER(ip)]
+        L.rt_forward_series.restype = ip
         L.cnop_solve.argtypes = [vp, ctypes.POINTER(CnopParams), vp, ip, dp, ctypes.POINTER(CnopResult)]
         L.cnop_solve.restype = ip
         _lib = L
@@ -313,6 +315,20 @@ class Context:
         la = (ctypes.c_longlong * 3)()
         self._check(library().rt_kernel_times(self._h, _dptr(ms), sa, la))
         return {k: (ms[i], sa[i], la[i]) for i, k in enumerate(("stage1", "stage2", "adjoint"))}
+
+    def series(self, v, every, max_samples=4096, replay=False):
+        """KE(t) and h_mix(t) sampled every `every` steps of one forward run
+        (rt_forward_series; at most max_samples per instance). Returns one
+        dict per instance with arrays t, KE, h_mix."""
+        p, flags, keep = self._arg(v)
+        if replay:
+            flags |= RT_REPLAY_DT
+        shape = (self.n, int(max_samples))
+        t, ke, h = np.zeros(shape), np.zeros(shape), np.zeros(shape)
+        n = (ctypes.c_int * self.n)()
+        self._check(library().rt_forward_series(self._h, p, flags, int(every), int(max_samples), _dptr(t),
+                                                _dptr(ke), _dptr(h), n))
+        return [{"t": t[i, :n[i]], "KE": ke[i, :n[i]], "h_mix": h[i, :n[i]]} for i in range(self.n)]
 
     def cnop(self, v_start, eps, iters, method=RT_CNOP_LBFGS, lbfgs_memory=10, gll_memory=10, armijo_c=1e-4,
              alpha_min=1e-30, alpha_max=1e30, max_backtracks=30, h_loc=0.0, chi_tol=0.0, log_path=None,

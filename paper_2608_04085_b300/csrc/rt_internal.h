@@ -39,6 +39,8 @@ struct InstDev {
   int strip_begin, strip_end;  // this instance's strips in the sweep list
   double dx, dy, dA;
   double y0, y_int;          // domain bottom and interface height
+  double rho_l, rho_h;       // light and heavy densities (mixing width, Eq. hmix-f)
+  long long row_off;         // first row of this instance in the all-instance row list
   double gamma, gm1, g_y;
   double cfl, T;
   float gamma_f, gm1_f, g_f, dx_f, dy_f;  // the same constants rounded once for FP32 kernels

@@ -826,6 +826,29 @@ __global__ void __launch_bounds__(NTH) k_objective(const InstDev* __restrict__ i
   }
 }
 
+// Row sums over x for the comparison diagnostics (Sec. 4.3): sum rho and sum
+// e_k = |m|^2 / (2 rho) (Eq. ke) along row y of one instance; one CTA per
+// (instance, row). The instance's current state is slot_tab[nstep % 2].
+template <class T>
+__global__ void __launch_bounds__(NTH) k_row_sums(const InstDev* __restrict__ insts, const int2* __restrict__ rows,
+                                                  T* const* __restrict__ slot_tab, const int* __restrict__ nstep,
+                                                  double2* __restrict__ out) {
+  __shared__ double red[NTH / 32];
+  const int2 r = rows[blockIdx.x];
+  const InstDev& I = insts[r.x];
+  const long long cells = (long long)I.nx * I.ny;
+  const T* U = slot_tab[nstep[r.x] & 1] + 4 * I.cell_off + (long long)r.y * I.nx;
+  double sr = 0.0, sk = 0.0;
+  for (int x = threadIdx.x; x < I.nx; x += NTH) {
+    const double rho = U[x], mx = U[cells + x], my = U[2 * cells + x];
+    sr += rho;
+    sk += 0.5 * (mx * mx + my * my) / rho;
+  }
+  sr = block_sum(sr, red);
+  sk = block_sum(sk, red);
+  if (threadIdx.x == 0) out[blockIdx.x] = make_double2(sr, sk);
+}
+
 // dJ/dv from dJ/dU0 (transpose of k_inject).
 template <class T>
 __global__ void __launch_bounds__(NTH) k_grad(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,
@@ -865,6 +888,34 @@ __global__ void __launch_bounds__(NTH) k_finalize(const InstDev* __restrict__ in
     for (int t = I.tile_begin + threadIdx.x; t < I.tile_end; t += NTH) s += partials[(long long)t * width + wc];
     s = block_sum(s, red);
     if (threadIdx.x == 0) out[blockIdx.x * width + wc] = scale_by_dA ? s * I.dA : s;
+  }
+}
+
+// One sample per instance (one CTA each) from the row sums: t, total kinetic
+// energy (Eq. ke) and mixing width h_mix = sum over rows of 4 f (1 - f) dy
+// with f = clip((<rho>_x - rho_l) / (rho_h - rho_l), 0, 1) (Eqs. hmix,
+// hmix-f), and the step count. Rows are summed in a fixed order.
+__global__ void __launch_bounds__(NTH) k_series_sample(const InstDev* __restrict__ insts,
+                                                       const double2* __restrict__ rowsum,
+                                                       const double* __restrict__ t, const int* __restrict__ nstep,
+                                                       double* __restrict__ out) {
+  __shared__ double red[NTH / 32];
+  const InstDev& I = insts[blockIdx.x];
+  double h = 0.0, ke = 0.0;
+  for (int y = threadIdx.x; y < I.ny; y += NTH) {
+    const double2 s = rowsum[I.row_off + y];
+    const double f = fmin(fmax((s.x / I.nx - I.rho_l) / (I.rho_h - I.rho_l), 0.0), 1.0);
+    h += 4.0 * f * (1.0 - f);
+    ke += s.y;
+  }
+  h = block_sum(h, red);
+  ke = block_sum(ke, red);
+  if (threadIdx.x == 0) {
+    double* o = out + 4 * (long long)blockIdx.x;
+    o[0] = t[blockIdx.x];
+    o[1] = ke * I.dA;
+    o[2] = h * I.dy;
+    o[3] = (double)nstep[blockIdx.x];
   }
 }
 

@@ -21,6 +21,12 @@ cudaError_t launch_field_reduce(int mode, const InstDev* insts, const int4* tile
   return cudaGetLastError();
 }
 
+cudaError_t launch_series_sample(const InstDev* insts, int n_inst, const double2* rowsum, const double* t,
+                                 const int* nstep, double* out, cudaStream_t s) {
+  k_series_sample<<<n_inst, NTH, 0, s>>>(insts, rowsum, t, nstep, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finalize_max(const InstDev* insts, int n_inst, const double* partials, double* out,
                                 cudaStream_t s) {
   k_finalize_max<<<n_inst, NTH, 0, s>>>(insts, partials, out);

@@ -27,6 +27,12 @@ cudaError_t launch_objective(const InstDev* insts, const int4* tiles, int ntiles
                              const int* nstep, double* ek_out, T* lamA, T* lamB, double* partials,
                              cudaStream_t s);
 template <class T>
+cudaError_t launch_row_sums(const InstDev* insts, const int2* rows, int nrows, T* const* slot_tab, const int* nstep,
+                            double2* out, cudaStream_t s);
+// one diagnostics sample per instance: out[i] = {t, KE, h_mix, nstep}
+cudaError_t launch_series_sample(const InstDev* insts, int n_inst, const double2* rowsum, const double* t,
+                                 const int* nstep, double* out, cudaStream_t s);
+template <class T>
 cudaError_t launch_grad(const InstDev* insts, const int4* tiles, int ntiles, const T* lam, const double* v,
                         double* g, cudaStream_t s);
 template <class T>

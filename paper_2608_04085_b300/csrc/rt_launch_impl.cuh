@@ -76,6 +76,13 @@ cudaError_t launch_objective(const InstDev* insts, const int4* tiles, int ntiles
 }
 
 template <class T>
+cudaError_t launch_row_sums(const InstDev* insts, const int2* rows, int nrows, T* const* slot_tab, const int* nstep,
+                            double2* out, cudaStream_t s) {
+  k_row_sums<T><<<nrows, NTH, 0, s>>>(insts, rows, slot_tab, nstep, out);
+  return cudaGetLastError();
+}
+
+template <class T>
 cudaError_t launch_grad(const InstDev* insts, const int4* tiles, int ntiles, const T* lam, const double* v,
                         double* g, cudaStream_t s) {
   k_grad<T><<<ntiles, NTH, 0, s>>>(insts, tiles, lam, v, g);
@@ -112,6 +119,8 @@ cudaError_t configure_kernels() {
                                            T*, T*, double*, cudaStream_t);                                       \
   template cudaError_t launch_grad<T>(const InstDev*, const int4*, int, const T*, const double*, double*,         \
                                       cudaStream_t);                                                             \
+  template cudaError_t launch_row_sums<T>(const InstDev*, const int2*, int, T* const*, const int*, double2*,       \
+                                          cudaStream_t);                                                         \
   template cudaError_t configure_kernels<T>();
 
 }  // namespace rt

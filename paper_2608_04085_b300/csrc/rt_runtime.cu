@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <string>
 #include <tuple>
@@ -92,6 +93,10 @@ struct rt_ctx {
   double* d_w3 = nullptr;
   double* d_w4 = nullptr;
   double* d_pairs = nullptr;     // L-BFGS (s, y) ring: 2 * pairs_m fields
+  int2* d_rows = nullptr;        // (instance, y) of every row of every instance (diagnostics)
+  double2* d_rowsum = nullptr;   // per-row sums of rho and e_k
+  double* d_sample = nullptr;    // [n_inst][4] one diagnostics sample
+  int total_rows = 0;
   int pairs_m = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::string err;
@@ -414,7 +419,8 @@ bool all_done(rt_ctx* c, const std::vector<int>& nstep, const std::vector<double
 // March every instance from the injected state to its horizon. mode 0: CFL
 // control; mode 1: replay the recorded dt sequence for `replay_steps` steps.
 template <class T>
-rt_status march(rt_ctx* c, const Plan& plan, int mode, int n_est, int replay_steps, int* n_done) {
+rt_status march(rt_ctx* c, const Plan& plan, int mode, int n_est, int replay_steps, int* n_done,
+                int sample_every = 0, const std::function<rt_status(int)>* sampler = nullptr) {
   int n = 0;
   int target = mode == 1 ? replay_steps : n_est;
   const int smode = mode == 1 ? 1 : 0;
@@ -441,7 +447,8 @@ rt_status march(rt_ctx* c, const Plan& plan, int mode, int n_est, int replay_ste
   };
   for (;;) {
     while (n < target) {
-      const int b = std::min(target, (n / kGraphChunk + 1) * kGraphChunk);
+      int b = std::min(target, (n / kGraphChunk + 1) * kGraphChunk);
+      if (sample_every > 0) b = std::min(b, (n / sample_every + 1) * sample_every);
       if (b > c->opt.max_steps) return fail(c, RT_EINVAL, "step limit %d reached", c->opt.max_steps);
       if (plan.kind == 2 && b >= plan.slots)
         return fail(c, RT_ENOMEM, "stored-state plan ran out of slots at step %d", b);
@@ -449,6 +456,7 @@ rt_status march(rt_ctx* c, const Plan& plan, int mode, int n_est, int replay_ste
       const GraphKey key{0, plan.kind, smode, c->stage_variant, c->lim, plan.S, n, b};
       CHK(run_graph(c, key, [&] { return steps(n, b); }));
       n = b;
+      if (sampler && n % sample_every == 0) CHK((*sampler)(n));
     }
     CHK(read_run(c, nstep, t, status));
     CHK(nonfinite(c, status, nullptr));
@@ -538,6 +546,50 @@ rt_status forward_impl(rt_ctx* c, const double* d_v, int flags, double* J_out, d
   CHK(read_J(c, J_out, J_ke_out));
   if (steps) *steps = n_done;
   return RT_OK;
+}
+
+// Forward run that samples t, KE and h_mix of every instance after step 0,
+// every `every` steps and at the end (Sec. 4.3). samples receives one
+// [n_inst][4] block {t, KE, h_mix, nstep} per sampling point; an instance that
+// has reached its horizon repeats its final values, which the caller drops.
+template <class T>
+rt_status series_impl(rt_ctx* c, const double* d_v, int flags, int every, std::vector<double>& samples) {
+  const bool replay = (flags & RT_REPLAY_DT) != 0;
+  if (replay && !c->have_run) return fail(c, RT_ESTATE, "RT_REPLAY_DT needs a previous run");
+  if (!c->d_rows) {
+    std::vector<int2> rows;
+    for (int i = 0; i < c->n_inst; ++i)
+      for (int y = 0; y < c->prob[i].ny; ++y) rows.push_back(make_int2(i, y));
+    c->total_rows = (int)rows.size();
+    CU(cudaMalloc(&c->d_rows, rows.size() * sizeof(int2)));
+    CU(cudaMalloc(&c->d_rowsum, rows.size() * sizeof(double2)));
+    CU(cudaMalloc(&c->d_sample, (size_t)c->n_inst * 4 * sizeof(double)));
+    CU(cudaMemcpyAsync(c->d_rows, rows.data(), rows.size() * sizeof(int2), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+  }
+  const int replay_steps = c->last_steps;
+  Plan plan;
+  CHK(inject<T>(c, d_v, c->sA, replay));
+  int n_est = replay_steps;
+  if (!replay) CHK(estimate_steps(c, &n_est));
+  std::function<rt_status(int)> take = [&](int) -> rt_status {
+    const std::vector<void*> tab = {c->sA, c->sB};
+    CHK(upload_tab(c, tab));
+    CU(rt::launch_row_sums<T>(c->d_inst, c->d_rows, c->total_rows, reinterpret_cast<T* const*>(c->d_tab),
+                              c->run.nstep, c->d_rowsum, c->stream));
+    CU(rt::launch_series_sample(c->d_inst, c->n_inst, c->d_rowsum, c->run.t, c->run.nstep, c->d_sample, c->stream));
+    c->launches += 2;
+    const size_t at = samples.size();
+    samples.resize(at + 4 * c->n_inst);
+    CU(cudaMemcpyAsync(samples.data() + at, c->d_sample, 4 * c->n_inst * sizeof(double), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return RT_OK;
+  };
+  CHK(take(0));
+  int n_done = 0;
+  CHK(march<T>(c, plan, replay ? 1 : 0, n_est, replay_steps, &n_done, every, &take));
+  return take(n_done);
 }
 
 // beta(s, t) = C(s + t, s): steps reversible with s checkpoints and t
@@ -1435,6 +1487,9 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
     I.dA = I.dx * I.dy;
     I.y0 = P.y0;
     I.y_int = P.y_int;
+    I.rho_l = P.rho_light;
+    I.rho_h = P.rho_heavy;
+    I.row_off = roff;  // advanced at the end of this loop body
     I.gamma = P.gamma;
     I.gm1 = P.gamma - 1.0;
     I.g_y = P.g_y;
@@ -1543,7 +1598,7 @@ void rt_destroy(rt_ctx* c) {
   void* ptrs[] = {c->d_inst, c->d_tiles, c->d_strips, c->d_base, c->d_ek0, c->d_ek, c->sA, c->sB, c->sU1, c->lA, c->lB,
                   c->l1, c->d_tab, c->run.dtrec, c->run.dtc, c->run.counter, c->run.t, c->run.nstep, c->run.wmin, c->run.status,
                   c->run.bad_cell, c->d_partials, c->d_sums, c->d_scal, c->d_v, c->d_g, c->d_w1, c->d_w2,
-                  c->d_w3, c->d_w4, c->d_pairs};
+                  c->d_w3, c->d_w4, c->d_pairs, c->d_rows, c->d_rowsum, c->d_sample};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : c->pool) cudaFree(p);
@@ -1584,6 +1639,37 @@ rt_status rt_forward(rt_ctx* c, const double* v0, int flags, double* J_out, doub
   const float ms = tm.stop();
   collect_timing(c);
   fill_stats(c, st, ms, 0);
+  return RT_OK;
+}
+
+rt_status rt_forward_series(rt_ctx* c, const double* v0, int flags, int every, int max_samples, double* t_out,
+                            double* ke_out, double* hmix_out, int* n_out) {
+  if (!c || !v0 || !t_out || !ke_out || !hmix_out || !n_out) return fail(c, RT_EINVAL, "null argument");
+  if (every < 1 || max_samples < 1) return fail(c, RT_EINVAL, "every and max_samples must be >= 1");
+  c->err.clear();
+  CHK(ensure_fields(c, false));
+  CHK(enter(c));
+  reset_accounting(c);
+  CHK(copy_in(c, v0, flags, c->d_v));
+  std::vector<double> smp;
+  CHK(c->esz == 8 ? series_impl<double>(c, c->d_v, flags, every, smp)
+                  : series_impl<float>(c, c->d_v, flags, every, smp));
+  const int N = c->n_inst;
+  const size_t npts = smp.size() / (4 * (size_t)N);
+  for (int i = 0; i < N; ++i) {
+    int k = 0;
+    double last = -1.0;
+    for (size_t s = 0; s < npts && k < max_samples; ++s) {
+      const double* q = smp.data() + (s * N + i) * 4;
+      if (q[3] <= last) continue;  // no step since the previous sample
+      last = q[3];
+      t_out[(size_t)i * max_samples + k] = q[0];
+      ke_out[(size_t)i * max_samples + k] = q[1];
+      hmix_out[(size_t)i * max_samples + k] = q[2];
+      ++k;
+    }
+    n_out[i] = k;
+  }
   return RT_OK;
 }
 

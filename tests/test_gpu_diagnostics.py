@@ -1,0 +1,64 @@
+"""Comparison diagnostics on the GPU (Sec. 4.3): KE(t) and the mixing width
+h_mix(t) sampled during one forward run (rt_forward_series), against the
+oracle's series, which rebuilds each sampled state by replaying the first k
+time steps."""
+import numpy as np
+import pytest
+
+import rt_inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    return [I.rt_box(16, 48, nsteps=25), I.rt_box(24, 40, T=0.2, limiter=I.LIM_MC),
+            I.paper_unit_square(20, 0.06)]
+
+
+def test_series_fp64_matches_oracle():
+    import oracle
+    import paper_2608_04085_b300 as rt
+    ws = _cases()
+    vs = [oracle.scale_to_budget(w, I.gaussian_field(40 + k, w.ncomp, w.ny, w.nx), 1e-3).ravel()
+          for k, w in enumerate(ws)]
+    every = 4
+    with rt.Context(ws, precision=rt.RT_FP64) as ctx:
+        got = ctx.series(np.concatenate(vs), every)
+        J, Jke, _ = ctx.forward(np.concatenate(vs))
+    for k, w in enumerate(ws):
+        ref = oracle.series(w, vs[k].reshape(w.ncomp, w.ny, w.nx), every)
+        g = got[k]
+        assert len(g["t"]) == len(ref["t"]), (len(g["t"]), ref["step"])
+        assert np.allclose(g["t"], ref["t"], rtol=1e-14, atol=0)
+        assert np.allclose(g["KE"], ref["KE"], rtol=1e-12, atol=0)
+        assert np.allclose(g["h_mix"], ref["h_mix"], rtol=1e-12, atol=1e-15)
+        assert g["KE"][-1] == pytest.approx(Jke[k], rel=1e-13)
+        # singles equal the batch bitwise
+        with rt.Context([w], precision=rt.RT_FP64) as c1:
+            s1 = c1.series(vs[k], every)[0]
+        for key in ("t", "KE", "h_mix"):
+            assert np.array_equal(s1[key], g[key])
+
+
+def test_series_fp32_and_limits():
+    """FP32 state: KE(t) and h_mix(t) within 1e-4 of FP64; max_samples
+    truncates; the unperturbed box keeps h_mix at its initial value to
+    within the scheme's drift."""
+    import paper_2608_04085_b300 as rt
+    w = I.rt_box(32, 96, T=0.3)
+    v = I.gaussian_field(3, 2, w.ny, w.nx).ravel()
+    out = {}
+    for prec in (rt.RT_FP64, rt.RT_FP32_STATE):
+        with rt.Context([w], precision=prec) as ctx:
+            v1 = ctx.project(v, 1e-4, to_budget=True)
+            out[prec] = ctx.series(v1, 10)[0]
+            short = ctx.series(v1, 10, max_samples=3)[0]
+            assert len(short["t"]) == 3 and np.array_equal(short["KE"], out[prec]["KE"][:3])
+    a, b = out[rt.RT_FP64], out[rt.RT_FP32_STATE]
+    assert np.allclose(a["t"], b["t"], rtol=1e-6)
+    assert np.allclose(b["KE"], a["KE"], rtol=1e-4)
+    assert np.allclose(b["h_mix"], a["h_mix"], rtol=1e-4)
+    with rt.Context([w], precision=rt.RT_FP64) as ctx:
+        z = ctx.series(np.zeros(2 * w.nx * w.ny), 25)[0]
+    assert z["KE"][0] == 0.0
+    assert np.all(np.abs(z["h_mix"] - z["h_mix"][0]) <= 1e-2 * z["h_mix"][0])
