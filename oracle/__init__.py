@@ -513,6 +513,53 @@ def spectrum(vy):
     return y_peak, n, pw / np.sum(pw)
 
 
+def dft_matrix(n, sign=-1.0):
+    """W[k, j] = exp(sign 2 pi i k j / n), the phase reduced exactly as (k j mod n)."""
+    k = np.arange(n)
+    return np.exp(sign * 2j * np.pi * (np.outer(k, k) % n) / n)
+
+
+def spectrum2d(vy):
+    """App. B: normalised two-dimensional spectral energy of a field [ny][nx]:
+    F = sum_{l,j} u(x_j, y_l) exp(-2 pi i (n_x j / N_x + n_y l / N_y)) and
+    E[n_y, n_x] = |F|^2 / sum |F|^2 over all modes (reading: the DFT runs over
+    the whole grid, and the energies are normalised over every mode)."""
+    vy = np.asarray(vy, dtype=np.float64)
+    ny, nx = vy.shape
+    F = dft_matrix(ny) @ vy @ dft_matrix(nx).T
+    pw = np.abs(F) ** 2
+    return pw / np.sum(pw)
+
+
+def power_reconstruct(w, v, eps, frac=0.9):
+    """App. B: the reconstruction that keeps the two-dimensional Fourier modes
+    holding `frac` of the spectral energy of u_y. Reading: modes are ranked in
+    conjugate pairs {(n_x, n_y), (-n_x, -n_y)} by the pair's energy, so the
+    field stays real; the pairs are kept from the largest down until the kept
+    energy reaches frac of the total, together with every pair whose energy
+    ties the last one kept. That mode set is applied to every perturbed
+    component, the inverse DFT's real part is taken and the result rescaled to
+    C = eps. Returns (field, number of kept modes)."""
+    v = np.asarray(v, dtype=np.float64).reshape(w.ncomp, w.ny, w.nx)
+    ny, nx = w.ny, w.nx
+    E = spectrum2d(v[-1])
+    ky, kx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    cy, cx = (-ky) % ny, (-kx) % nx
+    pair = np.where((cy == ky) & (cx == kx), E, E + E[cy, cx])
+    rep = (ky * nx + kx) <= (cy * nx + cx)  # one representative per pair
+    vals = np.sort(pair[rep])[::-1]
+    csum = np.cumsum(vals)
+    tau = vals[int(np.nonzero(csum >= frac * csum[-1])[0][0])]
+    keep = pair >= tau
+    Wy, Wx = dft_matrix(ny), dft_matrix(nx)
+    iWy, iWx = dft_matrix(ny, +1.0) / ny, dft_matrix(nx, +1.0) / nx
+    out = np.empty_like(v)
+    for c in range(w.ncomp):
+        F = Wy @ v[c] @ Wx.T
+        out[c] = np.real(iWy @ (F * keep) @ iWx.T)
+    return scale_to_budget(w, out, eps), int(np.sum(keep))
+
+
 def five_modes(w, v, eps, count=5):
     """Sec. 3.5 / 4.2: keep the ``count`` positive horizontal modes with the
     largest E_n at y_peak (ties: lower n), apply that index set to every row

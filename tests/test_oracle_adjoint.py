@@ -172,3 +172,39 @@ def test_objective_is_quadratic_at_small_amplitude(oracle_lib):
         J1 = o.forward(w, v, dt_replay=dt)["J_ke"]
         J2 = o.forward(w, 2 * v, dt_replay=dt)["J_ke"]
         assert J2 / J1 == pytest.approx(4.0, rel=tol)
+
+
+# ------------------------------------------ two-dimensional spectra (App. B)
+def test_spectrum2d_matches_fft2_and_parseval(oracle_lib):
+    o = oracle_lib
+    f = I.gaussian_field(8, 1, 12, 20)[0]
+    E = o.spectrum2d(f)
+    F = np.fft.fft2(f)
+    assert np.allclose(E, np.abs(F) ** 2 / np.sum(np.abs(F) ** 2), rtol=1e-12, atol=1e-15)
+    assert np.sum(E) == pytest.approx(1.0, rel=1e-14)
+    # Parseval: sum |F|^2 = N sum f^2, and a real field has E(k) = E(-k)
+    assert np.sum(np.abs(F) ** 2) == pytest.approx(f.size * np.sum(f * f), rel=1e-12)
+    assert np.allclose(E, np.roll(np.flip(E), 1, axis=(0, 1)), rtol=1e-12, atol=1e-15)
+
+
+def test_power_reconstruct_keeps_the_dominant_pairs(oracle_lib):
+    """Three mode pairs with 62 / 30 / 8 % of the energy: 90 % keeps the first
+    two pairs (4 modes) exactly; 50 % keeps one pair; 100 % returns the field."""
+    o = oracle_lib
+    w = I.rt_box(16, 12, ncomp=I.PERT_VY)
+    j = np.arange(w.nx)[None, :]
+    l = np.arange(w.ny)[:, None]
+    a = np.sqrt([0.62, 0.30, 0.08])
+    m1 = a[0] * np.cos(2 * np.pi * (3 * j / w.nx + 1 * l / w.ny))
+    m2 = a[1] * np.sin(2 * np.pi * (5 * j / w.nx - 2 * l / w.ny))
+    m3 = a[2] * np.cos(2 * np.pi * (1 * j / w.nx + 4 * l / w.ny) + 0.3)
+    v = (m1 + m2 + m3)[None]
+    eps = 1e-4
+    r, kept = o.power_reconstruct(w, v, eps, 0.9)
+    assert kept == 4
+    assert np.allclose(r, o.scale_to_budget(w, (m1 + m2)[None], eps), rtol=1e-10, atol=1e-14)
+    r, kept = o.power_reconstruct(w, v, eps, 0.5)
+    assert kept == 2
+    assert np.allclose(r, o.scale_to_budget(w, m1[None], eps), rtol=1e-10, atol=1e-14)
+    r, kept = o.power_reconstruct(w, v, eps, 1.0)
+    assert np.allclose(r, o.scale_to_budget(w, v, eps), rtol=1e-10, atol=1e-14)
