@@ -269,6 +269,35 @@ typedef struct {
 rt_status cnop_solve(rt_ctx* ctx, const cnop_params* prm, double* v_inout, int flags,
                      double* J_out, cnop_result* res);
 
+/* Fourier analysis of perturbation fields and the reduced seeds built from
+ * it (Sec. 3.5, Sec. 4.2 Eq. fourier_coeff, App. B). v has the layout of v0
+ * (RT_DEVICE_PTRS: device pointer); the spectra are taken of u_y, the last
+ * perturbed component of an instance. Plain DFTs with exactly reduced
+ * phases, FP64; nx and ny at most 6144. E_out is a host array.
+ *
+ * rt_spectrum_x: y_peak = the row where the rms of u_y along x is largest
+ *   (ties: lowest row); u_n = sum_j u_y(x_j, y_peak) exp(-2 pi i n j / nx) and
+ *   E_out[n - 1] = |u_n|^2 / sum_m |u_m|^2 for n, m = 1 .. nx/2.
+ * rt_spectrum_2d: E_out[ky * nx + kx] = |F|^2 / sum |F|^2 over all modes,
+ *   F the two-dimensional DFT of u_y over the whole grid.
+ * rt_reconstruct: the reduced seed of every instance, rescaled to
+ *   C = eps[i] and written to out (layout of v0):
+ *   RT_RECON_X_MODES, param = count: the `count` horizontal modes n with the
+ *     largest E_n at y_peak (ties: lower n), with their mirrors -n, kept in
+ *     every row and component (the paper's five-mode seed, count = 5);
+ *   RT_RECON_2D_POWER, param = fraction in (0, 1]: the two-dimensional modes,
+ *     ranked in conjugate pairs by the pair's energy, that hold `fraction`
+ *     of the energy (the last pair's ties included), kept in every
+ *     component (the paper's 90%-power seed, fraction = 0.9).
+ *   kept_out[i] (nullable) = modes kept.
+ * Errors: RT_EINVAL (bad instance, kind, parameter or size; a
+ * reconstruction with C = 0), RT_ECUDA. */
+enum { RT_RECON_X_MODES = 0, RT_RECON_2D_POWER = 1 };
+rt_status rt_spectrum_x(rt_ctx* ctx, const double* v, int flags, int inst, double* E_out, int* y_peak_out);
+rt_status rt_spectrum_2d(rt_ctx* ctx, const double* v, int flags, int inst, double* E_out);
+rt_status rt_reconstruct(rt_ctx* ctx, const double* v, int flags, int kind, double param, const double* eps,
+                         double* out, int* kept_out);
+
 /* Allocation-free objective of one final state. The paper has no
  * counterpart: this exists for callers that must not let a library allocate
  * device memory (a host framework that owns all device memory through its

@@ -27,6 +27,7 @@ RT_CKPT_AUTO, RT_CKPT_STORE_ALL, RT_CKPT_SQRT, RT_CKPT_REVOLVE = 0, 1, 2, 3
 RT_STAGE_AUTO, RT_STAGE_SWEEP, RT_STAGE_TILE = 0, 1, 2
 RT_DEVICE_PTRS, RT_REPLAY_DT = 1, 2
 RT_CNOP_SPG, RT_CNOP_LBFGS = 0, 1
+RT_RECON_X_MODES, RT_RECON_2D_POWER = 0, 1
 
 _STATUS = {1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENONFINITE", 5: "RT_ETIMEOUT",
            6: "RT_ENOTCONVERGED", 7: "RT_ESTATE", 8: "RT_EIO"}
@@ -35,7 +36,8 @@ _STATUS = {1: "RT_EINVAL", 2: "RT_ENOMEM", 3: "RT_ECUDA", 4: "RT_ENONFINITE", 5:
 EXPORTS = ("rt_init", "rt_destroy", "rt_last_error", "rt_num_instances", "rt_field_offset",
            "rt_field_size", "rt_field_total", "rt_forward", "rt_gradient", "rt_constraint",
            "rt_project", "rt_get_state", "rt_get_dt", "rt_set_kernel_timing", "rt_kernel_times", "rt_stage_kernel",
-           "cnop_solve", "rt_objective_noalloc", "rt_forward_series")
+           "cnop_solve", "rt_objective_noalloc", "rt_forward_series", "rt_spectrum_x", "rt_spectrum_2d",
+           "rt_reconstruct")
 
 
 class RtError(RuntimeError):
@@ -136,6 +138,12 @@ def library():
         L.rt_kernel_times.restype = ip
         L.rt_forward_series.argtypes = [vp, vp, ip, ip, ip, dp, dp, dp, ctypes.POINTER(ip)]
         L.rt_forward_series.restype = ip
+        L.rt_spectrum_x.argtypes = [vp, vp, ip, ip, dp, ctypes.POINTER(ip)]
+        L.rt_spectrum_x.restype = ip
+        L.rt_spectrum_2d.argtypes = [vp, vp, ip, ip, dp]
+        L.rt_spectrum_2d.restype = ip
+        L.rt_reconstruct.argtypes = [vp, vp, ip, ip, ctypes.c_double, dp, vp, ctypes.POINTER(ip)]
+        L.rt_reconstruct.restype = ip
         L.cnop_solve.argtypes = [vp, ctypes.POINTER(CnopParams), vp, ip, dp, ctypes.POINTER(CnopResult)]
         L.cnop_solve.restype = ip
         _lib = L
@@ -329,6 +337,37 @@ class Context:
         self._check(library().rt_forward_series(self._h, p, flags, int(every), int(max_samples), _dptr(t),
                                                 _dptr(ke), _dptr(h), n))
         return [{"t": t[i, :n[i]], "KE": ke[i, :n[i]], "h_mix": h[i, :n[i]]} for i in range(self.n)]
+
+    def spectrum_x(self, v, inst=0):
+        """(y_peak, E_n for n = 1 .. nx/2) of u_y (rt_spectrum_x, Eq. fourier_coeff)."""
+        p, flags, keep = self._arg(v)
+        E = np.zeros(_field(self.problems[inst], "nx") // 2)
+        yp = ctypes.c_int()
+        self._check(library().rt_spectrum_x(self._h, p, flags, int(inst), _dptr(E), ctypes.byref(yp)))
+        return yp.value, E
+
+    def spectrum_2d(self, v, inst=0):
+        """Normalised 2D spectral energy E[ky, kx] of u_y (rt_spectrum_2d, App. B)."""
+        p, flags, keep = self._arg(v)
+        w = self.problems[inst]
+        E = np.zeros((_field(w, "ny"), _field(w, "nx")))
+        self._check(library().rt_spectrum_2d(self._h, p, flags, int(inst), _dptr(E)))
+        return E
+
+    def reconstruct(self, v, kind, param, eps):
+        """Reduced seeds (rt_reconstruct): RT_RECON_X_MODES with param = count
+        (five-mode seed) or RT_RECON_2D_POWER with param = energy fraction.
+        Returns (field, kept modes per instance)."""
+        p, flags, keep = self._arg(v)
+        if hasattr(v, "clone"):
+            out = v.clone()
+        else:
+            out = np.zeros(self.total)
+        po, _, keep2 = self._arg(out)
+        e = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, dtype=np.float64), (self.n,)))
+        kept = (ctypes.c_int * self.n)()
+        self._check(library().rt_reconstruct(self._h, p, flags, int(kind), float(param), _dptr(e), po, kept))
+        return out, list(kept)
 
     def cnop(self, v_start, eps, iters, method=RT_CNOP_LBFGS, lbfgs_memory=10, gll_memory=10, armijo_c=1e-4,
              alpha_min=1e-30, alpha_max=1e30, max_backtracks=30, h_loc=0.0, chi_tol=0.0, log_path=None,

@@ -23,6 +23,7 @@ UNITS = [
     ("rt_kernels_f32.cu", ["-use_fast_math"]),
     ("rt_runtime.cu", []),
     ("rt_noalloc.cu", []),
+    ("rt_spectra.cu", ["-fmad=false"]),
 ]
 
 

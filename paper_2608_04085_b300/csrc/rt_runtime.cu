@@ -21,6 +21,7 @@
 #include "../../include/rt_cnop.h"
 #include "rt_internal.h"
 #include "rt_launch.h"
+#include "rt_spectra.h"
 
 // The Python binding mirrors these layouts with ctypes.
 static_assert(sizeof(rt_problem) == 144, "rt_problem layout");
@@ -1414,6 +1415,50 @@ rt_status cnop_run(rt_ctx* c, const cnop_params* prm, double* v_inout, int flags
 }  // namespace
 
 // =================================================================== C ABI
+// ---------------------------------------------- spectra and reduced seeds
+namespace {
+// Work buffers of one spectral analysis, sized for the largest instance.
+struct SpecWork {
+  double2* a = nullptr;
+  double2* b = nullptr;
+  double* E = nullptr;
+  unsigned char* keep = nullptr;
+  int* ints = nullptr;   // [0] y_peak, [1] kept modes
+  double* dbl = nullptr; // [0] total energy
+  ~SpecWork() {
+    cudaFree(a);
+    cudaFree(b);
+    cudaFree(E);
+    cudaFree(keep);
+    cudaFree(ints);
+    cudaFree(dbl);
+  }
+};
+
+rt_status spec_alloc(rt_ctx* c, SpecWork& w) {
+  long long n = 0;
+  for (const rt_problem& P : c->prob) {
+    if (P.nx > rt::SPEC_MAX_N || P.ny > rt::SPEC_MAX_N)
+      return fail(c, RT_EINVAL, "spectra need nx, ny <= %d", rt::SPEC_MAX_N);
+    n = std::max(n, (long long)P.nx * P.ny);
+  }
+  CU(cudaMalloc(&w.a, n * sizeof(double2)));
+  CU(cudaMalloc(&w.b, n * sizeof(double2)));
+  CU(cudaMalloc(&w.E, n * sizeof(double)));
+  CU(cudaMalloc(&w.keep, n));
+  CU(cudaMalloc(&w.ints, 2 * sizeof(int)));
+  CU(cudaMalloc(&w.dbl, sizeof(double)));
+  CU(rt::spec_configure());
+  return RT_OK;
+}
+
+// u_y of instance i: the last perturbed component of v
+const double* uy_plane(rt_ctx* c, const double* v, int i) {
+  const rt_problem& P = c->prob[i];
+  return v + c->v_off[i] + (size_t)(P.perturb_ncomp - 1) * P.nx * P.ny;
+}
+}  // namespace
+
 extern "C" {
 
 rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options* opt, void* cuda_stream,
@@ -1670,6 +1715,118 @@ rt_status rt_forward_series(rt_ctx* c, const double* v0, int flags, int every, i
     }
     n_out[i] = k;
   }
+  return RT_OK;
+}
+
+
+rt_status rt_spectrum_x(rt_ctx* c, const double* v, int flags, int inst, double* E_out, int* y_peak_out) {
+  if (!c || !v || !E_out) return fail(c, RT_EINVAL, "null argument");
+  if (inst < 0 || inst >= c->n_inst) return fail(c, RT_EINVAL, "instance %d out of range", inst);
+  c->err.clear();
+  CHK(ensure_fields(c, false));
+  CHK(enter(c));
+  SpecWork w;
+  CHK(spec_alloc(c, w));
+  CHK(copy_in(c, v, flags, c->d_v));
+  const rt_problem& P = c->prob[inst];
+  const double* f = uy_plane(c, c->d_v, inst);
+  const long long n = (long long)P.nx * P.ny;
+  CU(rt::spec_real_to_complex(f, w.a, n, c->stream));
+  CU(rt::spec_dft_x(w.a, w.b, P.nx, P.ny, -1.0, c->stream));
+  CU(rt::spec_rms_peak(f, P.nx, P.ny, w.ints, c->stream));
+  CU(rt::spec_select_x(w.b, P.nx, w.ints, 0, w.E, w.keep, w.ints + 1, c->stream));
+  int yp = 0;
+  CU(cudaMemcpyAsync(E_out, w.E, (P.nx / 2) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(&yp, w.ints, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (y_peak_out) *y_peak_out = yp;
+  return RT_OK;
+}
+
+rt_status rt_spectrum_2d(rt_ctx* c, const double* v, int flags, int inst, double* E_out) {
+  if (!c || !v || !E_out) return fail(c, RT_EINVAL, "null argument");
+  if (inst < 0 || inst >= c->n_inst) return fail(c, RT_EINVAL, "instance %d out of range", inst);
+  c->err.clear();
+  CHK(ensure_fields(c, false));
+  CHK(enter(c));
+  SpecWork w;
+  CHK(spec_alloc(c, w));
+  CHK(copy_in(c, v, flags, c->d_v));
+  const rt_problem& P = c->prob[inst];
+  const long long n = (long long)P.nx * P.ny;
+  CU(rt::spec_real_to_complex(uy_plane(c, c->d_v, inst), w.a, n, c->stream));
+  CU(rt::spec_dft_x(w.a, w.b, P.nx, P.ny, -1.0, c->stream));
+  CU(rt::spec_dft_y(w.b, w.a, P.nx, P.ny, -1.0, c->stream));
+  CU(rt::spec_power(w.a, w.E, n, c->stream));
+  CU(rt::spec_select_pairs(w.E, P.nx, P.ny, 1.0, w.keep, w.ints + 1, w.dbl, c->stream));
+  CU(rt::spec_scale_by(w.E, n, w.dbl, c->stream));
+  CU(cudaMemcpyAsync(E_out, w.E, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return RT_OK;
+}
+
+rt_status rt_reconstruct(rt_ctx* c, const double* v, int flags, int kind, double param, const double* eps,
+                         double* out, int* kept_out) {
+  if (!c || !v || !eps || !out) return fail(c, RT_EINVAL, "null argument");
+  if (kind == RT_RECON_X_MODES ? !(param >= 1.0) : kind == RT_RECON_2D_POWER ? !(param > 0.0 && param <= 1.0) : true)
+    return fail(c, RT_EINVAL, "kind %d with parameter %g", kind, param);
+  c->err.clear();
+  CHK(ensure_fields(c, true));
+  CHK(enter(c));
+  SpecWork w;
+  CHK(spec_alloc(c, w));
+  CHK(copy_in(c, v, flags, c->d_v));
+  double* r = c->d_w1;
+  const int N = c->n_inst;
+  for (int i = 0; i < N; ++i) {
+    const rt_problem& P = c->prob[i];
+    const long long n = (long long)P.nx * P.ny;
+    const double* f = uy_plane(c, c->d_v, i);
+    // mode set from u_y
+    CU(rt::spec_real_to_complex(f, w.a, n, c->stream));
+    CU(rt::spec_dft_x(w.a, w.b, P.nx, P.ny, -1.0, c->stream));
+    if (kind == RT_RECON_X_MODES) {
+      CU(rt::spec_rms_peak(f, P.nx, P.ny, w.ints, c->stream));
+      const int count = (int)std::min(param, (double)(P.nx / 2));
+      CU(rt::spec_select_x(w.b, P.nx, w.ints, count, w.E, w.keep, w.ints + 1, c->stream));
+    } else {
+      CU(rt::spec_dft_y(w.b, w.a, P.nx, P.ny, -1.0, c->stream));
+      CU(rt::spec_power(w.a, w.E, n, c->stream));
+      CU(rt::spec_select_pairs(w.E, P.nx, P.ny, param, w.keep, w.ints + 1, w.dbl, c->stream));
+    }
+    // that set applied to every perturbed component
+    for (int k = 0; k < P.perturb_ncomp; ++k) {
+      const size_t off = c->v_off[i] + (size_t)k * n;
+      CU(rt::spec_real_to_complex(c->d_v + off, w.a, n, c->stream));
+      CU(rt::spec_dft_x(w.a, w.b, P.nx, P.ny, -1.0, c->stream));
+      if (kind == RT_RECON_X_MODES) {
+        CU(rt::spec_mask(w.b, w.keep, P.nx, P.ny, 0, c->stream));
+        CU(rt::spec_dft_x(w.b, w.a, P.nx, P.ny, 1.0, c->stream));
+        CU(rt::spec_real_part(w.a, r + off, n, 1.0 / P.nx, c->stream));
+      } else {
+        CU(rt::spec_dft_y(w.b, w.a, P.nx, P.ny, -1.0, c->stream));
+        CU(rt::spec_mask(w.a, w.keep, P.nx, P.ny, 1, c->stream));
+        CU(rt::spec_dft_y(w.a, w.b, P.nx, P.ny, 1.0, c->stream));
+        CU(rt::spec_dft_x(w.b, w.a, P.nx, P.ny, 1.0, c->stream));
+        CU(rt::spec_real_part(w.a, r + off, n, 1.0 / ((double)P.nx * P.ny), c->stream));
+      }
+    }
+    int kept = 0;
+    CU(cudaMemcpyAsync(&kept, w.ints + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (kept_out) kept_out[i] = kept;
+  }
+  // rescale onto C = eps
+  std::vector<double> C, sc(N);
+  CHK(field_sums(c, 0, r, nullptr, C));
+  for (int i = 0; i < N; ++i) {
+    if (!(C[i] > 0.0) || !std::isfinite(C[i]))
+      return fail(c, RT_EINVAL, "reconstruction of instance %d has C = %g", i, C[i]);
+    sc[i] = std::sqrt(eps[i] / C[i]);
+  }
+  CHK(axpby(c, r, sc, r, nullptr, nullptr));
+  CHK(copy_out(c, r, flags, out));
+  CU(cudaStreamSynchronize(c->stream));
   return RT_OK;
 }
 
