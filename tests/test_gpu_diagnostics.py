@@ -62,3 +62,31 @@ def test_series_fp32_and_limits():
         z = ctx.series(np.zeros(2 * w.nx * w.ny), 25)[0]
     assert z["KE"][0] == 0.0
     assert np.all(np.abs(z["h_mix"] - z["h_mix"][0]) <= 1e-2 * z["h_mix"][0])
+
+
+def test_comparison_runs_on_the_paper_configuration():
+    """Sec. 3.5 / 4.3 on a small paper configuration: a few L-BFGS iterations
+    from the localised random start, then the four comparison seeds in one
+    batch. The CNOP's J beats the random seed it started from; every seed
+    sits on the budget; each series ends at its forward's KE."""
+    import oracle
+    import paper_2608_04085_b300 as rt
+    from paper_2608_04085_b300.experiments import comparison_runs, SEEDS
+    w = I.paper_unit_square(24, 0.1)
+    eps = 1e-6
+    xi = I.gaussian_field(77, w.ncomp, w.ny, w.nx).ravel()
+    with rt.Context([w], precision=rt.RT_FP64) as ctx:
+        v_rand = ctx.project(xi, eps, to_budget=True)
+        v_loc, _, _ = ctx.cnop(xi, eps, 0, h_loc=0.1)
+        v_cnop, J_cnop, res = ctx.cnop(xi, eps, 4, h_loc=0.1)
+    assert res["iterations"] == 4
+    out = comparison_runs(w, v_cnop, v_loc, eps, 3)
+    assert set(out) == set(SEEDS)
+    assert out["CNOP"]["J"] == pytest.approx(J_cnop[0], rel=1e-12)
+    assert out["CNOP"]["J"] > out["Random"]["J"]
+    for name in SEEDS:
+        o = out[name]
+        assert oracle.constraint(w, o["v"]) == pytest.approx(eps, rel=1e-12)
+        assert o["KE"][-1] == pytest.approx(o["J_ke"], rel=1e-13)
+        assert o["t"][-1] == pytest.approx(w.T, rel=1e-15)
+        assert np.all(np.diff(o["t"]) > 0)
