@@ -310,7 +310,14 @@ __device__ __forceinline__ void raw_to_prim(const T u[4], const InstDev& I, int 
 // Load a tile of primitive states into shared memory (layout [4][EY][EX],
 // origin (gx0, gy0)), issuing every global load of this thread's cells before
 // converting any of them, so that they are in flight together.
-template <class T, int EX, int EY>
+// Four values of one cell held together (one 16-byte shared-memory access
+// for FP32, two for FP64).
+template <class T>
+struct __align__(16) Q4 {
+  T v[4];
+};
+
+template <class T, int EX, int EY, bool AOS = false>
 __device__ __forceinline__ void load_prim_tile(const T* __restrict__ Ui, const InstDev& I, long long cells, int gx0,
                                                int gy0, const Phys<T>& P, T* __restrict__ sW) {
   constexpr int N = EX * EY;
@@ -334,8 +341,15 @@ __device__ __forceinline__ void load_prim_tile(const T* __restrict__ Ui, const I
       const int ey = e / EX, ex = e - ey * EX;
       T W[4];
       raw_to_prim(u[k], I, rr[k], P, W);
+      if (AOS) {
+        Q4<T> c;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) sW[(q * EY + ey) * EX + ex] = W[q];
+        for (int q = 0; q < 4; ++q) c.v[q] = W[q];
+        reinterpret_cast<Q4<T>*>(sW)[ey * EX + ex] = c;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sW[(q * EY + ey) * EX + ex] = W[q];
+      }
     }
   }
 }
@@ -600,9 +614,10 @@ __global__ void __launch_bounds__(NTH) k_stage_tile(const InstDev* __restrict__ 
 }
 
 // ----------------------------------------------------------------- adjoint
-// Shared memory (elements of T): primitive tile with 3 ghost layers,
-// cotangent tile with 2, and one face buffer (16 contributions per face)
-// used first by the x faces and then by the y faces.
+// Shared memory, cell-major (the 4 values of a cell together, Q4): primitive
+// tile with 3 ghost layers, cotangent tile with 2, and one face buffer (the
+// 4 variables of each of the face's 4 cells) used first by the x faces and
+// then by the y faces.
 constexpr int ADJ_AX = TX + 6, ADJ_AY = TY + 6, ADJ_KX = TX + 4, ADJ_KY = TY + 4;
 constexpr int ADJ_NFX = (TX + 3) * TY, ADJ_NFY = TX * (TY + 3);
 constexpr int ADJ_FACES = ADJ_NFX > ADJ_NFY ? ADJ_NFX : ADJ_NFY;
@@ -614,9 +629,9 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
           const T* __restrict__ K, T kscale, const T* __restrict__ E, T escale, T* __restrict__ out, RunDev run,
           int n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sW = reinterpret_cast<T*>(smem_raw);  // [4][AY][AX]
-  T* sK = sW + 4 * ADJ_AX * ADJ_AY;        // [4][KY][KX]
-  T* sB = sK + 4 * ADJ_KX * ADJ_KY;        // [16][ADJ_FACES]
+  Q4<T>* sW = reinterpret_cast<Q4<T>*>(smem_raw);  // [AY][AX]
+  Q4<T>* sK = sW + ADJ_AX * ADJ_AY;                // [KY][KX]
+  Q4<T>* sB = sK + ADJ_KX * ADJ_KY;                // [4][ADJ_FACES]
   const int4 tl = tiles[blockIdx.x];
   const int inst = tl.x;
   const InstDev& I = insts[inst];
@@ -642,14 +657,15 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
 #pragma unroll
       for (int q = 0; q < 4; ++q) kv[k][q] = in ? Ki[q * cells + c] : T(0);
     }
-    load_prim_tile<T, ADJ_AX, ADJ_AY>(Ui, I, cells, x0 - 3, y0 - 3, P, sW);
+    load_prim_tile<T, ADJ_AX, ADJ_AY, true>(Ui, I, cells, x0 - 3, y0 - 3, P, reinterpret_cast<T*>(sW));
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       const int e = threadIdx.x + k * NTH;
       if (e < N) {
-        const int ey = e / ADJ_KX, ex = e - ey * ADJ_KX;
+        Q4<T> kc;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) sK[(q * ADJ_KY + ey) * ADJ_KX + ex] = kscale * kv[k][q];
+        for (int q = 0; q < 4; ++q) kc.v[q] = kscale * kv[k][q];
+        sK[e] = kc;
       }
     }
   }
@@ -668,26 +684,35 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
     const int fy = f / (TX + 3), fx = f - fy * (TX + 3);
     T w[4][4], mu[4], o[4][4];
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+    for (int p = 0; p < 4; ++p) {
+      const Q4<T> c = sW[(fy + 3) * ADJ_AX + fx + p];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) w[p][q] = sW[(q * ADJ_AY + fy + 3) * ADJ_AX + fx + p];
+      for (int q = 0; q < 4; ++q) w[p][q] = c.v[q];
+    }
+    {
+      const Q4<T> kr = sK[(fy + 2) * ADJ_KX + fx + 1], kl = sK[(fy + 2) * ADJ_KX + fx];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      mu[q] = sc.dtdx * (sK[(q * ADJ_KY + fy + 2) * ADJ_KX + fx + 1] - sK[(q * ADJ_KY + fy + 2) * ADJ_KX + fx]);
+      for (int q = 0; q < 4; ++q) mu[q] = sc.dtdx * (kr.v[q] - kl.v[q]);
+    }
     face_vjp<T, 0>(w, mu, lim, P.gamma, P.gm1, o);
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+    for (int p = 0; p < 4; ++p) {
+      Q4<T> c;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) sB[(p * 4 + q) * ADJ_FACES + f] = o[p][q];
+      for (int q = 0; q < 4; ++q) c.v[q] = o[p][q];
+      sB[p * ADJ_FACES + f] = c;
+    }
   }
   __syncthreads();
 #pragma unroll
   for (int pass = 0; pass < PASSES; ++pass) {
     const int ty = threadIdx.x / TX + pass * ROWS_PER_PASS;
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+    for (int p = 0; p < 4; ++p) {
+      const Q4<T> c = sB[p * ADJ_FACES + ty * (TX + 3) + tx + 3 - p];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) bW[pass][q] += sB[(p * 4 + q) * ADJ_FACES + ty * (TX + 3) + tx + 3 - p];
+      for (int q = 0; q < 4; ++q) bW[pass][q] += c.v[q];
+    }
   }
   __syncthreads();
 
@@ -699,12 +724,14 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
     if (gf >= 0 && gf <= ny) {
       T w[4][4], mu[4];
 #pragma unroll
-      for (int p = 0; p < 4; ++p)
+      for (int p = 0; p < 4; ++p) {
+        const Q4<T> c = sW[(fy + p) * ADJ_AX + fx + 3];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) w[p][q] = sW[(q * ADJ_AY + fy + p) * ADJ_AX + fx + 3];
+        for (int q = 0; q < 4; ++q) w[p][q] = c.v[q];
+      }
+      const Q4<T> ku = sK[(fy + 1) * ADJ_KX + fx + 2], kd = sK[fy * ADJ_KX + fx + 2];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        mu[q] = sc.dtdy * (sK[(q * ADJ_KY + fy + 1) * ADJ_KX + fx + 2] - sK[(q * ADJ_KY + fy) * ADJ_KX + fx + 2]);
+      for (int q = 0; q < 4; ++q) mu[q] = sc.dtdy * (ku.v[q] - kd.v[q]);
       face_vjp<T, 1>(w, mu, lim, P.gamma, P.gm1, o);
     } else {
 #pragma unroll
@@ -713,9 +740,12 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
         for (int q = 0; q < 4; ++q) o[p][q] = T(0);
     }
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+    for (int p = 0; p < 4; ++p) {
+      Q4<T> c;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) sB[(p * 4 + q) * ADJ_FACES + f] = o[p][q];
+      for (int q = 0; q < 4; ++q) c.v[q] = o[p][q];
+      sB[p * ADJ_FACES + f] = c;
+    }
   }
   __syncthreads();
 
@@ -724,9 +754,11 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
     const int ty = threadIdx.x / TX + pass * ROWS_PER_PASS;
     const int gx = x0 + tx, gy = y0 + ty;
 #pragma unroll
-    for (int p = 0; p < 4; ++p)
+    for (int p = 0; p < 4; ++p) {
+      const Q4<T> c = sB[p * ADJ_FACES + (ty + 3 - p) * TX + tx];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) bW[pass][q] += sB[(p * 4 + q) * ADJ_FACES + (ty + 3 - p) * TX + tx];
+      for (int q = 0; q < 4; ++q) bW[pass][q] += c.v[q];
+    }
     // ghost rows of the y boundary fold back onto the cells they mirror
     for (int side = 0; side < 2; ++side) {
       int k, gly;
@@ -736,8 +768,9 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
       const int f_lo = gly > 0 ? gly : 0, f_hi = (gly + 3) < (TY + 2) ? (gly + 3) : (TY + 2);
       for (int fy = f_lo; fy <= f_hi; ++fy) {
         const int p = gly - fy + 3;
+        const Q4<T> c = sB[p * ADJ_FACES + fy * TX + tx];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) gq[q] += sB[(p * 4 + q) * ADJ_FACES + fy * TX + tx];
+        for (int q = 0; q < 4; ++q) gq[q] += c.v[q];
       }
       bW[pass][0] += gq[0];
       bW[pass][1] += gq[1];
@@ -752,18 +785,18 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
     if (gx < nx && gy < ny) {
       const long long c = (long long)gy * nx + gx;
       // rho, u_x, u_y of the cell from the primitive tile (the values mx/rho, my/rho)
-      const T r = sW[(0 * ADJ_AY + ty + 3) * ADJ_AX + tx + 3];
-      const T u = sW[(1 * ADJ_AY + ty + 3) * ADJ_AX + tx + 3];
-      const T v = sW[(2 * ADJ_AY + ty + 3) * ADJ_AX + tx + 3];
+      const Q4<T> wc = sW[(ty + 3) * ADJ_AX + tx + 3];
+      const T r = wc.v[0], u = wc.v[1], v = wc.v[2];
       const T* b = bW[pass];
       T bU[4];
       bU[0] = b[0] - (u * b[1] + v * b[2]) / r + P.gm1 * T(0.5) * (u * u + v * v) * b[3];
       bU[1] = b[1] / r - P.gm1 * u * b[3];
       bU[2] = b[2] / r - P.gm1 * v * b[3];
       bU[3] = P.gm1 * b[3];
+      const Q4<T> kq = sK[(ty + 2) * ADJ_KX + tx + 2];
       T kc[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) kc[q] = sK[(q * ADJ_KY + ty + 2) * ADJ_KX + tx + 2];
+      for (int q = 0; q < 4; ++q) kc[q] = kq.v[q];
       T o[4];
       o[0] = kc[0] + bU[0] + sc.dtg * kc[2];
       o[1] = kc[1] + bU[1];
