@@ -507,8 +507,8 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS, 6) k_stage_sweep(const InstD
 }
 
 // --------------------------------------------------------- stage (tile variant)
-// Shared memory (elements of T): primitive tile with 2 ghost layers, x-face
-// and y-face fluxes.
+// Shared memory, cell-major (the 4 values of a cell or face together, Q4):
+// primitive tile with 2 ghost layers, x-face and y-face fluxes.
 constexpr int ST_EX = TX + 4, ST_EY = TY + 4;
 constexpr int ST_NFX = (TX + 1) * TY, ST_NFY = TX * (TY + 1);
 constexpr int ST_SMEM_ELEMS = 4 * ST_EX * ST_EY + 4 * ST_NFX + 4 * ST_NFY;
@@ -521,9 +521,9 @@ __global__ void __launch_bounds__(NTH) k_stage_tile(const InstDev* __restrict__ 
                                                const T* __restrict__ src, const T* __restrict__ base,
                                                T* __restrict__ dst, RunDev run, int n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sW = reinterpret_cast<T*>(smem_raw);  // [4][EY][EX]
-  T* sF = sW + 4 * ST_EX * ST_EY;          // [4][TY][TX+1]
-  T* sG = sF + 4 * ST_NFX;                 // [4][TY+1][TX]
+  Q4<T>* sW = reinterpret_cast<Q4<T>*>(smem_raw);  // [EY][EX]
+  Q4<T>* sF = sW + ST_EX * ST_EY;                  // [TY][TX+1]
+  Q4<T>* sG = sF + ST_NFX;                         // [TY+1][TX]
   __shared__ T red[NTH / 32];
   const int4 tl = tiles[blockIdx.x];
   const int inst = tl.x;
@@ -536,29 +536,37 @@ __global__ void __launch_bounds__(NTH) k_stage_tile(const InstDev* __restrict__ 
   const T* Si = src + 4 * I.cell_off;
   const int x0 = tl.y, y0 = tl.z;
   const int lim = LIM >= 0 ? LIM : I.limiter;
-  load_prim_tile<T, ST_EX, ST_EY>(Si, I, cells, x0 - 2, y0 - 2, P, sW);
+  load_prim_tile<T, ST_EX, ST_EY, true>(Si, I, cells, x0 - 2, y0 - 2, P, reinterpret_cast<T*>(sW));
   __syncthreads();
   for (int f = threadIdx.x; f < ST_NFX + ST_NFY; f += NTH) {
     T w[4][4], F[4];
     if (f < ST_NFX) {  // x face fx of row fy: between tile cells fx-1 and fx
       const int fy = f / (TX + 1), fx = f - fy * (TX + 1);
 #pragma unroll
-      for (int p = 0; p < 4; ++p)
+      for (int p = 0; p < 4; ++p) {
+        const Q4<T> c = sW[(fy + 2) * ST_EX + fx + p];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) w[p][q] = sW[(q * ST_EY + fy + 2) * ST_EX + fx + p];
+        for (int q = 0; q < 4; ++q) w[p][q] = c.v[q];
+      }
       face_flux<T, 0>(w, lim, P.gamma, P.gm1, F);
+      Q4<T> fq;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) sF[q * ST_NFX + f] = F[q];
+      for (int q = 0; q < 4; ++q) fq.v[q] = F[q];
+      sF[f] = fq;
     } else {  // y face fy of column fx: between tile rows fy-1 and fy
       const int g = f - ST_NFX;
       const int fy = g / TX, fx = g - fy * TX;
 #pragma unroll
-      for (int p = 0; p < 4; ++p)
+      for (int p = 0; p < 4; ++p) {
+        const Q4<T> c = sW[(fy + p) * ST_EX + fx + 2];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) w[p][q] = sW[(q * ST_EY + fy + p) * ST_EX + fx + 2];
+        for (int q = 0; q < 4; ++q) w[p][q] = c.v[q];
+      }
       face_flux<T, 1>(w, lim, P.gamma, P.gm1, F);
+      Q4<T> gq;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) sG[q * ST_NFY + g] = F[q];
+      for (int q = 0; q < 4; ++q) gq.v[q] = F[q];
+      sG[g] = gq;
     }
   }
   __syncthreads();
@@ -575,12 +583,12 @@ __global__ void __launch_bounds__(NTH) k_stage_tile(const InstDev* __restrict__ 
       const long long c = (long long)gy * I.nx + gx;
       const T u[4] = {Si[c], Si[cells + c], Si[2 * cells + c], Si[3 * cells + c]};
       T o[4];
+      const Q4<T> fl = sF[ty * (TX + 1) + tx], fr = sF[ty * (TX + 1) + tx + 1];
+      const Q4<T> gd = sG[ty * TX + tx], gu = sG[(ty + 1) * TX + tx];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const T* Fk = sF + k * ST_NFX + ty * (TX + 1);
-        const T* Gk = sG + k * ST_NFY;
-        T b = u[k] + sc.dtdx * (Fk[tx] - Fk[tx + 1]);
-        b = b + sc.dtdy * (Gk[ty * TX + tx] - Gk[(ty + 1) * TX + tx]);
+        T b = u[k] + sc.dtdx * (fl.v[k] - fr.v[k]);
+        b = b + sc.dtdy * (gd.v[k] - gu.v[k]);
         if (k == 2) b = b + sc.dt * (u[0] * P.g);
         if (k == 3) b = b + sc.dt * (u[2] * P.g);
         o[k] = b;
