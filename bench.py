@@ -49,7 +49,7 @@ ADJ_BYTES_PER_CELL = {"stage2_adjoint": 12 * 4, "stage1_adjoint": 16 * 4, "mean"
 # DRAM traffic of k_adjoint<float, minmod> per cell per launch (read + write),
 # from the ncu capture summarised in profiles/k_adjoint_fp32_rtbox256x768x16_dram.md
 # (16 instances of the same grid; traffic grows in proportion to the cells).
-ADJ_TRAFFIC_BYTES_PER_CELL = 48.06
+ADJ_TRAFFIC_BYTES_PER_CELL = 48.34
 STEP_BYTES_PER_CELL_UPDATE = 68 * 4  # forward 20s + segment recompute 20s (U1 kept) + adjoint 12s + 16s (sqrt checkpointing)
 
 
@@ -141,7 +141,7 @@ def workload_problems():
     return [I.single_256().replace(T=T_HORIZON) for _ in range(BATCH)]
 
 
-def cpu_oracle_sample(n_steps=3):
+def cpu_oracle_sample(n_steps=6):
     """FP64 CPU oracle on a bounded sample of the workload: one 256x768
     instance, n_steps CFL steps forward plus the reverse sweep. Returns
     (cell-updates/s, seconds, sample description)."""
@@ -282,7 +282,7 @@ def run_ours(args):
             "speedup_vs_fp64_single": grad_evals / world / fp64["grad_evals_per_s_at_T2"] if fp64 else None,
         }
         if not args.no_cpu:
-            rate, secs, desc = cpu_oracle_sample(3)
+            rate, secs, desc = cpu_oracle_sample(6)
             line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
                                     "seconds": secs}
         print(json.dumps(line), flush=True)
