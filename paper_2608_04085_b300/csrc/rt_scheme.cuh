@@ -39,6 +39,10 @@ __device__ __forceinline__ T limited_slope(T qm, T q0, T qp, int lim) {
   const T dm = q0 - qm, dp = qp - q0;
   if (lim == LIM_NONE) return T(0.5) * (dm + dp);
   if (lim == LIM_MINMOD) {
+    // FP32: "same strict sign" as dm dp > 0 and the smaller magnitude by |dm| <= |dp|
+    // (equal values; far fewer compare-and-select instructions). FP64 keeps the
+    // sign tests, which also hold when dm dp underflows.
+    if constexpr (sizeof(T) == 4) return (dm * dp > T(0)) ? (fabsf(dm) <= fabsf(dp) ? dm : dp) : T(0);
     if (dm > T(0) && dp > T(0)) return dm <= dp ? dm : dp;
     if (dm < T(0) && dp < T(0)) return dm >= dp ? dm : dp;
     return T(0);
@@ -237,12 +241,60 @@ __device__ __forceinline__ void face_flux(const T w[4][4], int lim, T gamma, T g
   face_flux_states<T, DIR>(WL, WR, gamma, gm1, F);
 }
 
+// Reverse of the HLLC part of a face: the cotangents of the reconstructed
+// face states WL, WR (primitive, unrotated) for the flux cotangent mu.
+template <class T, int DIR>
+__device__ __forceinline__ void face_states_vjp(const T WL[4], const T WR[4], const T mu[4], T gamma, T gm1,
+                                                T bWL[4], T bWR[4]) {
+  constexpr int n = 1 + DIR, t = 2 - DIR;
+  const T bf[4] = {mu[0], mu[n], mu[t], mu[3]};
+  T bl[4], br[4];
+  hllc_vjp(WL[0], WL[n], WL[t], WL[3], WR[0], WR[n], WR[t], WR[3], gamma, gm1, bf, bl, br);
+  bWL[0] = bl[0]; bWL[n] = bl[1]; bWL[t] = bl[2]; bWL[3] = bl[3];
+  bWR[0] = br[0]; bWR[n] = br[1]; bWR[t] = br[2]; bWR[3] = br[3];
+}
+
 // Transposed face flux: out[cell][var] = (dF/dW_cell,var)^T mu for the four
 // cells a-1, a, b, b+1.
 template <class T, int DIR>
 __device__ __forceinline__ void face_vjp(const T w[4][4], const T mu[4], int lim, T gamma, T gm1,
                                          T out[4][4]) {
-  T WL[4], WR[4], am[4], a0[4], ap[4], bm[4], b0[4], bp[4];
+  T WL[4], WR[4], bWL[4], bWR[4];
+  if constexpr (sizeof(T) == 4) {
+    if (lim == LIM_MINMOD) {
+      // FP32 minmod in the form of limited_slope: each slope is dm (cells
+      // a-1, a), dp (cells a, b) or 0, so its reverse passes the slope's
+      // cotangent to the two cells of the difference it picked.
+      bool ma[4], pa[4], mb[4], pb[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const T dma = w[1][q] - w[0][q], dpa = w[2][q] - w[1][q];
+        const T dmb = w[2][q] - w[1][q], dpb = w[3][q] - w[2][q];
+        const bool sa = dma * dpa > T(0), sb = dmb * dpb > T(0);
+        const bool ka = fabsf(dma) <= fabsf(dpa), kb = fabsf(dmb) <= fabsf(dpb);
+        ma[q] = sa && ka;
+        pa[q] = sa && !ka;
+        mb[q] = sb && kb;
+        pb[q] = sb && !kb;
+        WL[q] = w[1][q] + T(0.5) * (sa ? (ka ? dma : dpa) : T(0));
+        WR[q] = w[2][q] - T(0.5) * (sb ? (kb ? dmb : dpb) : T(0));
+      }
+      face_states_vjp<T, DIR>(WL, WR, mu, gamma, gm1, bWL, bWR);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const T bsa = T(0.5) * bWL[q];   // W_L = W_a + s_a / 2
+        const T bsb = T(-0.5) * bWR[q];  // W_R = W_b - s_b / 2
+        const T tam = ma[q] ? bsa : T(0), tap = pa[q] ? bsa : T(0);
+        const T tbm = mb[q] ? bsb : T(0), tbp = pb[q] ? bsb : T(0);
+        out[0][q] = -tam;
+        out[1][q] = bWL[q] + (tam - tap) - tbm;
+        out[2][q] = bWR[q] + tap + (tbm - tbp);
+        out[3][q] = tbp;
+      }
+      return;
+    }
+  }
+  T am[4], a0[4], ap[4], bm[4], b0[4], bp[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const T sa = limited_slope_d(w[0][q], w[1][q], w[2][q], lim, am[q], a0[q], ap[q]);
@@ -250,13 +302,7 @@ __device__ __forceinline__ void face_vjp(const T w[4][4], const T mu[4], int lim
     WL[q] = w[1][q] + T(0.5) * sa;
     WR[q] = w[2][q] - T(0.5) * sb;
   }
-  constexpr int n = 1 + DIR, t = 2 - DIR;
-  const T bf[4] = {mu[0], mu[n], mu[t], mu[3]};
-  T bl[4], br[4];
-  hllc_vjp(WL[0], WL[n], WL[t], WL[3], WR[0], WR[n], WR[t], WR[3], gamma, gm1, bf, bl, br);
-  T bWL[4], bWR[4];
-  bWL[0] = bl[0]; bWL[n] = bl[1]; bWL[t] = bl[2]; bWL[3] = bl[3];
-  bWR[0] = br[0]; bWR[n] = br[1]; bWR[t] = br[2]; bWR[3] = br[3];
+  face_states_vjp<T, DIR>(WL, WR, mu, gamma, gm1, bWL, bWR);
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const T bsa = T(0.5) * bWL[q];   // W_L = W_a + s_a / 2
