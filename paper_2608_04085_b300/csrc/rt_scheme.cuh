@@ -179,10 +179,10 @@ __device__ __forceinline__ void hllc_vjp(T rL, T uL, T vL, T pL, T rR, T uR, T v
   b_u += b_E * r * u;
   b_v += b_E * r * v;
 
-  T brL = T(0), buL = T(0), bvL = T(0), bpL = T(0), bSL = T(0), bmL = T(0);
-  T brR = T(0), buR = T(0), bvR = T(0), bpR = T(0), bSR = T(0), bmR = T(0);
-  if (left) { brL = b_r; buL = b_u; bvL = b_v; bpL = b_p; bSL = b_S; bmL = b_m; }
-  else      { brR = b_r; buR = b_u; bvR = b_v; bpR = b_p; bSR = b_S; bmR = b_m; }
+  // the chosen side takes the cotangents, the other side gets zero (x - x)
+  T brL = left ? b_r : T(0), buL = left ? b_u : T(0), bvL = left ? b_v : T(0);
+  T bpL = left ? b_p : T(0), bSL = left ? b_S : T(0), bmL = left ? b_m : T(0);
+  T brR = b_r - brL, buR = b_u - buL, bvR = b_v - bvL, bpR = b_p - bpL, bSR = b_S - bSL, bmR = b_m - bmL;
   // S* = num / den
   const T b_num = b_Ss / den;
   const T b_den = -b_Ss * Ss / den;
@@ -201,9 +201,13 @@ __device__ __forceinline__ void hllc_vjp(T rL, T uL, T vL, T pL, T rR, T uR, T v
   bSR += bdR;
   buR -= bdR;
   // Davis speeds
-  T bcL = T(0), bcR = T(0);
-  if (slL) { buL += bSL; bcL -= bSL; } else { buR += bSL; bcR -= bSL; }
-  if (srL) { buL += bSR; bcL += bSR; } else { buR += bSR; bcR += bSR; }
+  const T tL = slL ? bSL : T(0), tR = bSL - tL;  // S_L = u_L - c_L or u_R - c_R
+  const T sL = srL ? bSR : T(0), sR = bSR - sL;  // S_R = u_L + c_L or u_R + c_R
+  buL += tL;
+  buR += tR;
+  buL += sL;
+  buR += sR;
+  const T bcL = sL - tL, bcR = sR - tR;
   // c = sqrt(gamma p / rho)
   bpL += bcL * T(0.5) * cL / pL;
   brL -= bcL * T(0.5) * cL / rL;
@@ -265,17 +269,17 @@ __device__ __forceinline__ void face_vjp(const T w[4][4], const T mu[4], int lim
       // FP32 minmod in the form of limited_slope: each slope is dm (cells
       // a-1, a), dp (cells a, b) or 0, so its reverse passes the slope's
       // cotangent to the two cells of the difference it picked.
-      bool ma[4], pa[4], mb[4], pb[4];
+      bool nza[4], nzb[4], dma_[4], dmb_[4];  // slope nonzero; slope = dm
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const T dma = w[1][q] - w[0][q], dpa = w[2][q] - w[1][q];
         const T dmb = w[2][q] - w[1][q], dpb = w[3][q] - w[2][q];
         const bool sa = dma * dpa > T(0), sb = dmb * dpb > T(0);
         const bool ka = fabsf(dma) <= fabsf(dpa), kb = fabsf(dmb) <= fabsf(dpb);
-        ma[q] = sa && ka;
-        pa[q] = sa && !ka;
-        mb[q] = sb && kb;
-        pb[q] = sb && !kb;
+        nza[q] = sa;
+        nzb[q] = sb;
+        dma_[q] = ka;
+        dmb_[q] = kb;
         WL[q] = w[1][q] + T(0.5) * (sa ? (ka ? dma : dpa) : T(0));
         WR[q] = w[2][q] - T(0.5) * (sb ? (kb ? dmb : dpb) : T(0));
       }
@@ -284,8 +288,10 @@ __device__ __forceinline__ void face_vjp(const T w[4][4], const T mu[4], int lim
       for (int q = 0; q < 4; ++q) {
         const T bsa = T(0.5) * bWL[q];   // W_L = W_a + s_a / 2
         const T bsb = T(-0.5) * bWR[q];  // W_R = W_b - s_b / 2
-        const T tam = ma[q] ? bsa : T(0), tap = pa[q] ? bsa : T(0);
-        const T tbm = mb[q] ? bsb : T(0), tbp = pb[q] ? bsb : T(0);
+        // ta = bsa if the slope is nonzero; it goes to dm (tam) or dp (tap = ta - tam)
+        const T ta = nza[q] ? bsa : T(0), tb = nzb[q] ? bsb : T(0);
+        const T tam = dma_[q] ? ta : T(0), tbm = dmb_[q] ? tb : T(0);
+        const T tap = ta - tam, tbp = tb - tbm;
         out[0][q] = -tam;
         out[1][q] = bWL[q] + (tam - tap) - tbm;
         out[2][q] = bWR[q] + tap + (tbm - tbp);
