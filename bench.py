@@ -51,6 +51,14 @@ ADJ_BYTES_PER_CELL = {"stage2_adjoint": 12 * 4, "stage1_adjoint": 16 * 4, "mean"
 # (16 instances of the same grid; traffic grows in proportion to the cells).
 ADJ_TRAFFIC_BYTES_PER_CELL = 48.34
 STEP_BYTES_PER_CELL_UPDATE = 68 * 4  # forward 20s + segment recompute 20s (U1 kept) + adjoint 12s + 16s (sqrt checkpointing)
+# Warp instructions k_adjoint<float, minmod> executes per cell per launch
+# (ncu sm__inst_executed.sum / cells on 16 instances of the same grid, mean of
+# the two adjoint stages; profiles/k_adjoint_fp32_rtbox256x768x16_dram.md).
+# The kernel is bound by instruction issue, not by HBM: the issue roofline
+# divides its executed instructions per second by the issue peak of
+# 148 SMs x 4 schedulers x 1 warp instruction per clock at the sampled SM clock.
+ADJ_WARP_INSTR_PER_CELL = 38.0
+ISSUE_PER_SM_PER_CLK = 4
 
 
 def dist_env():
@@ -257,6 +265,8 @@ def run_ours(args):
         st1_ms = statistics.mean(k["stage1"][0] for k in ktimes)
         st2_ms = statistics.mean(k["stage2"][0] for k in ktimes)
         cells_per_launch = BATCH * NX * NY
+        sm_max = clk.get("sm_max_mhz") or 2032.0  # fallback: B300 maximum SM clock
+        issue_peak = 148 * ISSUE_PER_SM_PER_CLK * sm_max * 1e6
         achieved = ADJ_BYTES_PER_CELL["mean"] * cells_per_launch / (adj_ms * 1e-3) / 1e9
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -275,6 +285,12 @@ def run_ours(args):
                          "peak_source": peak_kind + " hbm_gbs",
                          "algorithmic_bytes_per_cell": ADJ_BYTES_PER_CELL["mean"],
                          "mean_launch_ms": {"adjoint": adj_ms, "stage1": st1_ms, "stage2": st2_ms}},
+            "issue_roofline": {"bound": "issue", "kernel": "k_adjoint<float>",
+                               "achieved": ADJ_WARP_INSTR_PER_CELL * cells_per_launch / (adj_ms * 1e-3),
+                               "peak": issue_peak, "unit": "warp-instr/s",
+                               "frac": ADJ_WARP_INSTR_PER_CELL * cells_per_launch / (adj_ms * 1e-3) / issue_peak,
+                               "warp_instr_per_cell": ADJ_WARP_INSTR_PER_CELL,
+                               "peak_source": "148 SMs x 4 issue/clk x %.0f MHz (sampled max SM clock)" % sm_max},
             "step_roofline": {"bytes_per_cell_update": STEP_BYTES_PER_CELL_UPDATE,
                               "achieved_gbs": value * STEP_BYTES_PER_CELL_UPDATE / 1e9,
                               "frac": value * STEP_BYTES_PER_CELL_UPDATE / 1e9 / peak},
