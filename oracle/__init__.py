@@ -6,7 +6,9 @@ CUDA library and its Python binding) never imports, loads or calls it, and the
 two share no code: the only common module is ``rt_inputs`` (seeded draws and
 plain parameter values).
 
-The time stepper, its tangent and its reverse sweep live in ``rt_oracle.cpp``
+The time stepper, its tangent and its reverse sweep (with the dt sequence
+frozen, and in a second form differentiated through the CFL step control) live
+in ``rt_oracle.cpp``
 (plain C++, FP64, built with ``-O2 -ffp-contract=off``); the CNOP pieces that
 act on whole fields (constraint, projection, random start, spectral projected
 gradient and projected L-BFGS with a non-monotone line search, 1D Fourier
@@ -87,6 +89,10 @@ def lib():
         L.o_tangent_state.argtypes = [pp, dp, dp, dp, ctypes.c_int, dp, dp]
         L.o_gradient.argtypes = [pp, dp, dp, ctypes.c_int, dp, dp, dp]
         L.o_step_vjp.argtypes = [pp, dp, ctypes.c_double, dp, dp]
+        L.o_tangent_dt.argtypes = [pp, dp, dp, ctypes.c_int, dp, dp, dp]
+        L.o_tangent_dt.restype = ctypes.c_int
+        L.o_gradient_dt.argtypes = [pp, dp, ctypes.c_int, dp, dp, dp]
+        L.o_gradient_dt.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -198,6 +204,29 @@ def gradient(w, v, dt, ek0=None):
     lib().o_gradient(ctypes.byref(_params(w)), _ptr(v), _ptr(_f64(dt)), len(dt),
                      _ptr(None if ek0 is None else _f64(ek0)), _ptr(J), _ptr(g))
     return (J[1] if w.objective == 1 else J[0]), g
+
+
+def tangent_dt(w, v, dv, ek0=None, max_steps=400000):
+    """J and its directional derivative along dv with the CFL step control
+    differentiated too (dt_n = cfl * min crossing time; the horizon-clipped
+    last step dt = T - t). Returns (J, dJ, steps)."""
+    J = np.zeros(2)
+    dJ = np.zeros(2)
+    n = lib().o_tangent_dt(ctypes.byref(_params(w)), _ptr(_f64(v)), _ptr(_f64(dv)), max_steps,
+                           _ptr(None if ek0 is None else _f64(ek0)), _ptr(J), _ptr(dJ))
+    k = 1 if w.objective == 1 else 0
+    return J[k], dJ[k], n
+
+
+def gradient_dt(w, v, ek0=None, max_steps=400000):
+    """The gradient of J through the step control as well (the reverse of
+    tangent_dt): readings in rt_oracle.cpp. Returns (J, grad, steps)."""
+    v = _f64(v)
+    J = np.zeros(2)
+    g = np.zeros_like(v)
+    n = lib().o_gradient_dt(ctypes.byref(_params(w)), _ptr(v), max_steps,
+                            _ptr(None if ek0 is None else _f64(ek0)), _ptr(J), _ptr(g))
+    return (J[1] if w.objective == 1 else J[0]), g, n
 
 
 def value_and_gradient(w, v, ek0=None):

@@ -277,8 +277,8 @@ template <class R> static void to_ext(const std::vector<R>& U, const Grid& G, co
 // One RK stage. out = b (stage 1) or 0.5*base + 0.5*b (stage 2) with
 // b = U + (dt/dx)(F_left - F_right) + (dt/dy)(G_bottom - G_top) + dt S(U),
 // S(U) = (0, 0, rho g_y, m_y g_y).                     [Eqs. mass/momentum/energy]
-template <class R> static void stage(const OParams& P, const std::vector<R>& U, double dt,
-                                     const std::vector<R>* base, std::vector<R>& out) {
+template <class R, class Q = double> static void stage(const OParams& P, const std::vector<R>& U, Q dt,
+                                                       const std::vector<R>* base, std::vector<R>& out) {
   const Grid G(P);
   const int nx = G.nx, ny = G.ny;
   Ext<R> X(nx, ny);
@@ -290,7 +290,7 @@ template <class R> static void stage(const OParams& P, const std::vector<R>& U, 
   for (int j = 0; j <= ny; ++j)
     for (int i = 0; i < nx; ++i)  // face j: bottom face of cell j
       face_flux(X.at(j - 2, i), X.at(j - 1, i), X.at(j, i), X.at(j + 1, i), 1, P, &Gy[((size_t)j * nx + i) * 4]);
-  const double dtdx = dt / G.dx, dtdy = dt / G.dy;
+  const Q dtdx = dt / G.dx, dtdy = dt / G.dy;
   out.resize(U.size());
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
@@ -309,7 +309,7 @@ template <class R> static void stage(const OParams& P, const std::vector<R>& U, 
 }
 
 // SSP-RK2 (Heun): U1 = U + dt L(U); U' = U/2 + (U1 + dt L(U1))/2.
-template <class R> static void rk2_step(const OParams& P, std::vector<R>& U, double dt) {
+template <class R, class Q = double> static void rk2_step(const OParams& P, std::vector<R>& U, Q dt) {
   std::vector<R> U1, Un;
   stage(P, U, dt, (const std::vector<R>*)nullptr, U1);
   stage(P, U1, dt, &U, Un);
@@ -654,4 +654,175 @@ extern "C" void o_step_vjp(const OParams* P, const double* U, double dt, const d
   stage_vjp(*P, U1, dt, kap, lam1);
   stage_vjp(*P, u, dt, lam1, lamn);
   std::memcpy(lam_out, lamn.data(), n * sizeof(double));
+}
+
+// ------------------------------------------- gradient through the step control
+// The frozen-dt gradient above treats each dt_n as a constant. This variant
+// also differentiates dt_n = cfl * min over cells and directions of the
+// crossing time d / (|u_d| + c) (Sec. 2.3 CFL rule), and, in horizon mode,
+// the last step dt = T - t with t = sum of the earlier steps. Readings:
+//   - the derivative of the minimum is shared equally by every candidate
+//     (cell, direction) whose value equals the minimum;
+//   - |u| has derivative sign(u) with sign(0) = 0;
+//   - the branch choices (which step is clipped) are those of the forward run.
+
+// |a| with derivative sign(a), sign(0) = 0.
+template <class R> static R abs0(const R& a) { return val(a) > 0.0 ? a : (val(a) < 0.0 ? -a : a * 0.0); }
+
+// The candidates' mean derivative, with the (common) value kept exactly.
+static double keep_value_mean(const std::vector<double>& c) { return c[0]; }
+template <int N> static Dual<N> keep_value_mean(const std::vector<Dual<N>>& c) {
+  Dual<N> r(c[0].v);
+  for (int i = 0; i < N; ++i) {
+    double s = 0.0;
+    for (const auto& x : c) s += x.d[i];
+    r.d[i] = s / (double)c.size();
+  }
+  return r;
+}
+
+// Crossing times of one cell, (d_x / (|u_x| + c), d_y / (|u_y| + c)).
+template <class R> static void crossing_pair(const OParams& P, const Grid& G, const R u[4], R& wx, R& wy) {
+  R W[4];
+  cons_to_prim(u, W, P.gamma - 1.0);
+  const R c = sqrt(P.gamma * W[3] / W[0]);
+  wx = G.dx / (abs0(W[1]) + c);
+  wy = G.dy / (abs0(W[2]) + c);
+}
+
+// min crossing time over the grid (its value equals cfl_wmin's).
+template <class R> static R cfl_wmin_shared(const OParams& P, const std::vector<R>& U) {
+  const Grid G(P);
+  double wmin = INFINITY;
+  std::vector<R> cand;
+  for (int j = 0; j < G.ny; ++j)
+    for (int i = 0; i < G.nx; ++i) {
+      const R u[4] = {U[G.at(0, j, i)], U[G.at(1, j, i)], U[G.at(2, j, i)], U[G.at(3, j, i)]};
+      R w[2];
+      crossing_pair(P, G, u, w[0], w[1]);
+      for (int d = 0; d < 2; ++d) {
+        if (val(w[d]) < wmin) { wmin = val(w[d]); cand.clear(); cand.push_back(w[d]); }
+        else if (val(w[d]) == wmin) cand.push_back(w[d]);
+      }
+    }
+  return keep_value_mean(cand);
+}
+
+// lam += coef * d(min crossing time)/dU (candidates share the derivative).
+static void add_wmin_gradient(const OParams& P, const std::vector<double>& U, double coef, std::vector<double>& lam) {
+  typedef Dual<4> D4;
+  const Grid G(P);
+  const double wmin = cfl_wmin(P, U);
+  std::vector<std::pair<size_t, D4>> cand;  // (cell index j*nx+i, crossing time with d/dU of that cell)
+  for (int j = 0; j < G.ny; ++j)
+    for (int i = 0; i < G.nx; ++i) {
+      D4 u[4];
+      for (int k = 0; k < 4; ++k) { u[k] = D4(U[G.at(k, j, i)]); u[k].d[k] = 1.0; }
+      D4 w[2];
+      crossing_pair(P, G, u, w[0], w[1]);
+      for (int d = 0; d < 2; ++d)
+        if (w[d].v == wmin) cand.push_back({(size_t)j * G.nx + i, w[d]});
+    }
+  const double share = coef / (double)cand.size();
+  for (const auto& c : cand) {
+    const int j = (int)(c.first / G.nx), i = (int)(c.first % G.nx);
+    for (int k = 0; k < 4; ++k) lam[G.at(k, j, i)] += share * c.second.d[k];
+  }
+}
+
+// Directional derivative of J along dv through the step control (forward
+// mode); returns the number of steps.
+extern "C" int o_tangent_dt(const OParams* P, const double* v, const double* dv, int max_steps, const double* ek0,
+                            double* J, double* dJ) {
+  typedef Dual<1> D;
+  const Grid G(*P);
+  std::vector<double> rho0(G.ny), p0(G.ny);
+  o_base_state(P, rho0.data(), p0.data());
+  const size_t nv = (size_t)P->ncomp * G.cells();
+  std::vector<D> vd(nv);
+  for (size_t c = 0; c < nv; ++c) { vd[c].v = v[c]; vd[c].d[0] = dv[c]; }
+  std::vector<D> U;
+  inject(*P, rho0.data(), p0.data(), vd.data(), U);
+  D t(0.0);
+  int n = 0;
+  for (; n < max_steps; ++n) {
+    if (P->nsteps > 0 ? n >= P->nsteps : t.v >= P->T) break;
+    D dt = P->cfl * cfl_wmin_shared(*P, U);
+    if (P->nsteps <= 0) {
+      const D rem = P->T - t;
+      if (dt.v >= rem.v) { dt = rem; t = D(P->T); } else { t = t + dt; }
+    }
+    rk2_step(*P, U, dt);
+  }
+  D jk, jp;
+  objectives(*P, U, ek0, jk, jp);
+  J[0] = jk.v; J[1] = jp.v;
+  dJ[0] = jk.d[0]; dJ[1] = jp.d[0];
+  return n;
+}
+
+// Reverse-mode gradient through the step control (all states stored). For
+// each step n, b_n = <lam^{n+1}, dU^{n+1}/d dt_n> comes from a one-step
+// forward-mode pass with dt_n as the seed; a clipped last step passes -b to
+// every earlier dt; an unclipped step adds (b_n - b_last) cfl dwmin/dU^n to
+// lam^n. Returns the number of steps.
+extern "C" int o_gradient_dt(const OParams* P, const double* v, int max_steps, const double* ek0, double* J,
+                             double* grad) {
+  typedef Dual<1> D;
+  const Grid G(*P);
+  std::vector<double> rho0(G.ny), p0(G.ny);
+  o_base_state(P, rho0.data(), p0.data());
+  std::vector<std::vector<double>> Us(1);
+  std::vector<double> dts;
+  std::vector<char> clipped;
+  inject(*P, rho0.data(), p0.data(), v, Us[0]);
+  double t = 0.0, dt = 0.0;
+  for (int n = 0; n < max_steps; ++n) {
+    const double t_before = t;
+    if (!next_dt(*P, n, t, Us[n], dt)) break;
+    // the branch next_dt took: the CFL step reached the horizon and was clipped
+    clipped.push_back(P->nsteps <= 0 && P->cfl * cfl_wmin(*P, Us[n]) >= P->T - t_before);
+    dts.push_back(dt);
+    Us.push_back(Us[n]);
+    rk2_step(*P, Us[n + 1], dt);
+  }
+  const int N = (int)dts.size();
+  objectives(*P, Us[N], ek0, J[0], J[1]);
+  std::vector<double> lam, lam1, lamn, U1, kap;
+  objective_cotangent(*P, Us[N], ek0, lam);
+  double b_last = 0.0;
+  for (int n = N - 1; n >= 0; --n) {
+    // b_n = <lam^{n+1}, dU^{n+1}/d dt_n>
+    std::vector<D> Ud(Us[n].begin(), Us[n].end());
+    D dtd(dts[n]);
+    dtd.d[0] = 1.0;
+    rk2_step(*P, Ud, dtd);
+    double b = 0.0;
+    for (size_t q = 0; q < lam.size(); ++q) b += lam[q] * Ud[q].d[0];
+    // frozen-dt pull-back of the step
+    stage(*P, Us[n], dts[n], (const std::vector<double>*)nullptr, U1);
+    kap.resize(lam.size());
+    for (size_t q = 0; q < lam.size(); ++q) kap[q] = 0.5 * lam[q];
+    lam1.assign(lam.size(), 0.0);
+    stage_vjp(*P, U1, dts[n], kap, lam1);
+    lamn.assign(lam.size(), 0.0);
+    for (size_t q = 0; q < lam.size(); ++q) lamn[q] = 0.5 * lam[q];
+    stage_vjp(*P, Us[n], dts[n], lam1, lamn);
+    // dt_n = T - t_n (clipped) or cfl * wmin(U^n)
+    if (clipped[n]) b_last = b;
+    else add_wmin_gradient(*P, Us[n], (b - b_last) * P->cfl, lamn);
+    lam.swap(lamn);
+  }
+  const size_t nc = G.cells();
+  for (int j = 0; j < G.ny; ++j)
+    for (int i = 0; i < G.nx; ++i) {
+      const size_t c = (size_t)j * G.nx + i;
+      if (P->ncomp == 2) {
+        grad[c] = rho0[j] * (lam[G.at(1, j, i)] + v[c] * lam[G.at(3, j, i)]);
+        grad[nc + c] = rho0[j] * (lam[G.at(2, j, i)] + v[nc + c] * lam[G.at(3, j, i)]);
+      } else {
+        grad[c] = rho0[j] * (lam[G.at(2, j, i)] + v[c] * lam[G.at(3, j, i)]);
+      }
+    }
+  return N;
 }

@@ -208,3 +208,52 @@ def test_power_reconstruct_keeps_the_dominant_pairs(oracle_lib):
     assert np.allclose(r, o.scale_to_budget(w, m1[None], eps), rtol=1e-10, atol=1e-14)
     r, kept = o.power_reconstruct(w, v, eps, 1.0)
     assert np.allclose(r, o.scale_to_budget(w, v, eps), rtol=1e-10, atol=1e-14)
+
+
+# ------------------------------- gradient through the step control (dt not frozen)
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_dt_reverse_matches_dt_tangent(oracle_lib, name):
+    """Dot-product test of the reverse sweep that also differentiates the CFL
+    step control against forward-mode duals through the same control."""
+    o = oracle_lib
+    w = CASES[name]
+    v = o.scale_to_budget(w, I.gaussian_field(3, w.ncomp, w.ny, w.nx), 1e-3)
+    ek0 = o.baseline_ek(w) if w.objective == I.OBJ_EK_ANOMALY_L2 else None
+    J, g, n = o.gradient_dt(w, v, ek0)
+    assert J == o.objective_value(w, o.forward(w, v, ek0=ek0))
+    for k in range(8):
+        d = I.gaussian_field(300 + k, w.ncomp, w.ny, w.nx)
+        Jt, dJ, nt = o.tangent_dt(w, v, d, ek0)
+        assert nt == n and Jt == J
+        assert np.sum(g * d) == pytest.approx(dJ, rel=1e-12)
+
+
+def test_dt_gradient_matches_differences_of_the_cfl_controlled_map(oracle_lib):
+    """Central differences of the forward map as a user runs it (CFL step
+    control, horizon clipping) agree with the dt-differentiated gradient to
+    1e-6, while the frozen-dt gradient misses the step-control part."""
+    o = oracle_lib
+    w = I.rt_box(10, 30, nsteps=0, T=0.15, limiter=I.LIM_NONE)
+    v = o.scale_to_budget(w, I.gaussian_field(3, w.ncomp, w.ny, w.nx), 1e-3)
+    J, g, n = o.gradient_dt(w, v)
+    gf = o.gradient(w, v, o.forward(w, v)["dt"])[1]
+    for k in range(4):
+        d = I.gaussian_field(400 + k, w.ncomp, w.ny, w.nx)
+        h = 1e-6 * np.linalg.norm(v) / np.linalg.norm(d)
+        fd = (o.forward(w, v + h * d)["J_ke"] - o.forward(w, v - h * d)["J_ke"]) / (2 * h)
+        assert np.sum(g * d) == pytest.approx(fd, rel=1e-6)
+        assert abs(np.sum(gf * d) - fd) > 10 * abs(np.sum(g * d) - fd)
+
+
+def test_dt_gradient_of_an_x_uniform_field_is_x_uniform(oracle_lib):
+    """x-uniform perturbations keep every row's crossing times tied along x;
+    the shared-minimum reading then gives an x-uniform gradient."""
+    o = oracle_lib
+    w = I.rt_box(8, 24, nsteps=12)
+    col = I.gaussian_field(5, w.ncomp, w.ny, 1)
+    v = o.scale_to_budget(w, np.repeat(col, w.nx, axis=2), 1e-3)
+    J, g, n = o.gradient_dt(w, v)
+    assert np.array_equal(g, np.repeat(g[:, :, :1], w.nx, axis=2))
+    d = I.gaussian_field(6, w.ncomp, w.ny, w.nx)
+    Jt, dJ, _ = o.tangent_dt(w, v, d)
+    assert np.sum(g * d) == pytest.approx(dJ, rel=1e-12)
