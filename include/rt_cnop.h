@@ -69,8 +69,12 @@ enum { RT_CKPT_AUTO = 0, RT_CKPT_STORE_ALL = 1, RT_CKPT_SQRT = 2, RT_CKPT_REVOLV
 enum { RT_STAGE_AUTO = 0, RT_STAGE_SWEEP = 1, RT_STAGE_TILE = 2 };
 enum { RT_CNOP_SPG = 0, RT_CNOP_LBFGS = 1 };
 
-/* flags for rt_forward / rt_gradient / rt_constraint / rt_project */
-enum { RT_DEVICE_PTRS = 1, RT_REPLAY_DT = 2 };
+/* flags for rt_forward / rt_gradient / rt_constraint / rt_project / cnop_solve:
+ * RT_DEVICE_PTRS  the v / grad / out pointers are device pointers;
+ * RT_REPLAY_DT    rt_forward replays the previous run's dt sequence;
+ * RT_GRAD_DT      rt_gradient (and cnop_solve's gradients) also differentiate
+ *                 the step control, see rt_gradient. */
+enum { RT_DEVICE_PTRS = 1, RT_REPLAY_DT = 2, RT_GRAD_DT = 4 };
 
 /* One RT problem (Sec. 2.1-2.3). Geometry: cells are (x1-x0)/nx by
  * (y1-y0)/ny. Base state: rho0(y) = (rho_heavy+rho_light)/2 +
@@ -166,6 +170,13 @@ rt_status rt_forward_series(rt_ctx* ctx, const double* v0, int flags, int every,
  * frozen at the one the forward pass chose, by a hand-written adjoint of the
  * time stepper with store-all, sqrt(N) or binomial (revolve) checkpointing
  * (Sec. 3.4 uses binomial checkpointing). grad_out has the layout of v0.
+ * With RT_GRAD_DT the step control is differentiated as well, as an automatic
+ * differentiation of the whole forward run would do: dt_n = cfl * (min over
+ * cells and directions of d / (|u_d| + c)) of U^n, its derivative shared
+ * equally by every (cell, direction) equal to the minimum (|u| has derivative
+ * sign(u), sign(0) = 0), and a horizon-clipped last step dt = T - t passes
+ * its sensitivity to every earlier dt. This costs one extra stage and three
+ * light launches per reverse step. RT_REPLAY_DT is not accepted.
  * Errors as rt_forward. */
 rt_status rt_gradient(rt_ctx* ctx, const double* v0, int flags, double* J_out,
                       double* grad_out, rt_run_stats* st);

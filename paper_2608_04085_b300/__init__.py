@@ -25,7 +25,7 @@ RT_OBJ_KE, RT_OBJ_EK_ANOMALY_L2 = 0, 1
 RT_FP64, RT_FP32_STATE = 0, 1
 RT_CKPT_AUTO, RT_CKPT_STORE_ALL, RT_CKPT_SQRT, RT_CKPT_REVOLVE = 0, 1, 2, 3
 RT_STAGE_AUTO, RT_STAGE_SWEEP, RT_STAGE_TILE = 0, 1, 2
-RT_DEVICE_PTRS, RT_REPLAY_DT = 1, 2
+RT_DEVICE_PTRS, RT_REPLAY_DT, RT_GRAD_DT = 1, 2, 4
 RT_CNOP_SPG, RT_CNOP_LBFGS = 0, 1
 RT_RECON_X_MODES, RT_RECON_2D_POWER = 0, 1
 
@@ -258,8 +258,9 @@ class Context:
         del keep
         return J, Jke, st.as_dict()
 
-    def gradient(self, v0, out=None):
-        """(J[n], dJ/dv0, stats) (rt_gradient). For a CUDA tensor input the
+    def gradient(self, v0, out=None, dt_grad=False):
+        """(J[n], dJ/dv0, stats) (rt_gradient; dt_grad adds RT_GRAD_DT, the
+        derivative through the step control). For a CUDA tensor input the
         gradient is a CUDA tensor, else a NumPy array."""
         p, flags, keep = self._arg(v0)
         if out is None:
@@ -272,7 +273,8 @@ class Context:
         assert gflags == flags, "v0 and the gradient must both be host or both be device arrays"
         J = np.zeros(self.n)
         st = RtRunStats()
-        self._check(library().rt_gradient(self._h, p, flags, _dptr(J), gp, ctypes.byref(st)))
+        self._check(library().rt_gradient(self._h, p, flags | (RT_GRAD_DT if dt_grad else 0), _dptr(J), gp,
+                                          ctypes.byref(st)))
         del keep, gkeep
         return J, out, st.as_dict()
 
@@ -371,7 +373,7 @@ class Context:
 
     def cnop(self, v_start, eps, iters, method=RT_CNOP_LBFGS, lbfgs_memory=10, gll_memory=10, armijo_c=1e-4,
              alpha_min=1e-30, alpha_max=1e30, max_backtracks=30, h_loc=0.0, chi_tol=0.0, log_path=None,
-             checkpoint_path=None, checkpoint_every=0, resume=False, raise_on_stall=False):
+             checkpoint_path=None, checkpoint_every=0, resume=False, dt_grad=False, raise_on_stall=False):
         """CNOP search (cnop_solve): projected L-BFGS (the default) or spectral
         projected gradient. Returns (v, J, result); result holds the counts,
         the status and per-instance C, chi, grad_norm, stop and J_history
@@ -381,6 +383,8 @@ class Context:
         else:
             v = np.array(v_start, dtype=np.float64, copy=True).ravel()
         p, flags, keep = self._arg(v)
+        if dt_grad:
+            flags |= RT_GRAD_DT
         e = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, dtype=np.float64), (self.n,)))
         enc = lambda path: None if path is None else os.fsencode(path)
         prm = CnopParams(int(iters), int(gll_memory), int(max_backtracks), float(armijo_c), float(alpha_min),

@@ -55,6 +55,7 @@ struct InstDev {
 // FP64 (dtrec) and the per-step constants in the state precision (dtc).
 struct RunDev {
   double* dtrec;             // [n_inst][max_steps] dt of every step (0 = inactive)
+  double* wrec;              // [n_inst][max_steps] min crossing time behind dt (-1: step clipped to T; 0: inactive)
   void* dtc;                 // [n_inst][max_steps] StepC<T>: dt, dt/dx, dt/dy, dt*g_y in T
   double* t;                 // simulated time
   int* nstep;                // steps taken

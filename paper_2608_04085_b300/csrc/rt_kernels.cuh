@@ -134,14 +134,19 @@ __device__ void finish_step(const InstDev& I, const RunDev& run, int inst, int n
   const bool ok = atomicAdd(&run.status[inst], 0) == 0 && bits != ~0ull;
   const bool active = ok && I.enabled && (I.nsteps > 0 ? n_next < I.nsteps : t < I.T);
   double dt = I.cfl * wmin;
+  bool clipped = false;
   if (I.nsteps <= 0) {
     const double rem = I.T - t;
-    if (dt >= rem) dt = rem;
+    if (dt >= rem) {
+      dt = rem;
+      clipped = true;
+    }
   }
   if (!active) dt = 0.0;
   if (n_next < run.max_steps) {
     const long long k = (long long)inst * run.max_steps + n_next;
     run.dtrec[k] = dt;
+    run.wrec[k] = !active ? 0.0 : (clipped ? -1.0 : wmin);
     StepC<T> c;
     c.dt = (T)dt;
     c.dtdx = (T)(dt / I.dx);
@@ -822,6 +827,110 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
   }
 }
 
+// ------------------------------------------- gradient through the step control
+// dt_n = cfl * (min over cells and directions of d / (|u_d| + c)) of U^n, or
+// T - t_n when the step was clipped to the horizon. Its derivative is shared
+// equally by every (cell, direction) whose crossing time equals the recorded
+// minimum; |u| has derivative sign(u) with sign(0) = 0.
+
+// Crossing times (x, y) of one conserved state, as crossing_time() computes them.
+template <class T>
+__device__ __forceinline__ void crossing_pair(T r, T mx, T my, T E, const Phys<T>& P, T& wx, T& wy) {
+  T W[4];
+  cons_to_prim(r, mx, my, E, P.gm1, W);
+  const T c = sqrt(P.gamma * W[3] / W[0]);
+  wx = P.dx / (fabs(W[1]) + c);
+  wy = P.dy / (fabs(W[2]) + c);
+}
+
+// Per-tile partial sums for b_n dt_n = <lam^{n+1}, dU^{n+1}/d dt_n> dt_n =
+// <lam1, U1 - U^n> + <lam^{n+1}, U^{n+1} - U^n/2 - U1/2> (SSP-RK2, with
+// lam1 = lam^{n+1}/2 + (d(dt L)/dU1)^T lam^{n+1}/2), and the number of
+// candidates of the minimum.
+template <class T>
+__global__ void __launch_bounds__(NTH) k_dt_partials(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,
+                                                     const T* __restrict__ U, const T* __restrict__ U1,
+                                                     const T* __restrict__ Un1, const T* __restrict__ lam,
+                                                     const T* __restrict__ lam1, RunDev run, int n,
+                                                     double* __restrict__ partials) {
+  __shared__ double red[NTH / 32];
+  const int4 tl = tiles[blockIdx.x];
+  const InstDev& I = insts[tl.x];
+  const long long k = (long long)tl.x * run.max_steps + n;
+  const double dt = run.dtrec[k], wmin = run.wrec[k];
+  const Phys<T> P = phys<T>(I);
+  const long long cells = (long long)I.nx * I.ny, off = 4 * I.cell_off;
+  double s = 0.0, cnt = 0.0;
+  if (dt > 0.0) {
+    for (int e = threadIdx.x; e < TX * TY; e += NTH) {
+      const int gx = tl.y + e % TX, gy = tl.z + e / TX;
+      if (gx >= I.nx || gy >= I.ny) continue;
+      const long long c = off + (long long)gy * I.nx + gx;
+      T u[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        u[q] = U[c + q * cells];
+        const double a = (double)U1[c + q * cells], b = (double)Un1[c + q * cells];
+        s += (double)lam1[c + q * cells] * (a - (double)u[q]) +
+             (double)lam[c + q * cells] * (b - 0.5 * (double)u[q] - 0.5 * a);
+      }
+      if (wmin > 0.0) {
+        T wx, wy;
+        crossing_pair<T>(u[0], u[1], u[2], u[3], P, wx, wy);
+        cnt += ((double)wx == wmin ? 1.0 : 0.0) + ((double)wy == wmin ? 1.0 : 0.0);
+      }
+    }
+  }
+  s = block_sum(s, red);
+  cnt = block_sum(cnt, red);
+  if (threadIdx.x == 0) {
+    partials[2 * (long long)blockIdx.x] = s;
+    partials[2 * (long long)blockIdx.x + 1] = cnt;
+  }
+}
+
+// lam^n += coef[inst] * d(crossing time)/dU^n at every candidate of the minimum.
+template <class T>
+__global__ void __launch_bounds__(NTH) k_dt_apply(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,
+                                                  const T* __restrict__ U, T* __restrict__ lam, RunDev run, int n,
+                                                  const double* __restrict__ coef) {
+  const int4 tl = tiles[blockIdx.x];
+  const InstDev& I = insts[tl.x];
+  const long long k = (long long)tl.x * run.max_steps + n;
+  const double wmin = run.wrec[k], cf = coef[tl.x];
+  if (!(run.dtrec[k] > 0.0) || !(wmin > 0.0) || cf == 0.0) return;
+  const Phys<T> P = phys<T>(I);
+  const long long cells = (long long)I.nx * I.ny, off = 4 * I.cell_off;
+  for (int e = threadIdx.x; e < TX * TY; e += NTH) {
+    const int gx = tl.y + e % TX, gy = tl.z + e / TX;
+    if (gx >= I.nx || gy >= I.ny) continue;
+    const long long c = off + (long long)gy * I.nx + gx;
+    const T r = U[c], mx = U[c + cells], my = U[c + 2 * cells], E = U[c + 3 * cells];
+    T wx, wy;
+    crossing_pair<T>(r, mx, my, E, P, wx, wy);
+    const bool hx = (double)wx == wmin, hy = (double)wy == wmin;
+    if (!hx && !hy) continue;
+    // w = d / (|u_d| + c): dw = -d / (|u_d| + c)^2 (sign(u_d) du_d + dc), with
+    // dc = gamma / (2 c rho) (dp - (p / rho) drho), p = (gamma-1)(E - |m|^2 / (2 rho))
+    const double rho = r, u = (double)mx / rho, v = (double)my / rho, gm1 = I.gm1;
+    const double p = gm1 * ((double)E - 0.5 * ((double)mx * u + (double)my * v));
+    const double cs = sqrt(I.gamma * p / rho), q = I.gamma / (2.0 * cs * rho);
+    double g[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int d = 0; d < 2; ++d) {
+      if (d == 0 ? !hx : !hy) continue;
+      const double ud = d == 0 ? u : v, s = ud > 0.0 ? 1.0 : (ud < 0.0 ? -1.0 : 0.0);
+      const double a = fabs(ud), h = d == 0 ? I.dx : I.dy;
+      const double K = -h / ((a + cs) * (a + cs));
+      g[0] += K * (s * (-ud / rho) + q * (gm1 * 0.5 * (u * u + v * v) - p / rho));
+      g[1] += K * ((d == 0 ? s / rho : 0.0) - q * gm1 * u);
+      g[2] += K * ((d == 1 ? s / rho : 0.0) - q * gm1 * v);
+      g[3] += K * q * gm1;
+    }
+#pragma unroll
+    for (int qv = 0; qv < 4; ++qv) lam[c + qv * cells] = (T)((double)lam[c + qv * cells] + cf * g[qv]);
+  }
+}
+
 // --------------------------------------------------------------- objective
 // Final state of instance i: slot_tab[nstep[i] % tab_mod] (tab_mod 2: the
 // forward ping-pong pair) or slot_tab[nstep[i]] (tab_mod 0: stored states).
@@ -957,6 +1066,35 @@ __global__ void __launch_bounds__(NTH) k_series_sample(const InstDev* __restrict
     o[1] = ke * I.dA;
     o[2] = h * I.dy;
     o[3] = (double)nstep[blockIdx.x];
+  }
+}
+
+// Coefficient of the step-control term of step n, one CTA per instance:
+// b = (tile partials) / dt; a clipped step stores b in blast (its dt is T
+// minus the sum of the earlier ones) and adds nothing; otherwise
+// coef = (b - blast) cfl / (number of candidates of the minimum).
+__global__ void __launch_bounds__(NTH) k_dt_coef(const InstDev* __restrict__ insts, const double* __restrict__ partials,
+                                                 RunDev run, int n, double* __restrict__ blast,
+                                                 double* __restrict__ coef) {
+  __shared__ double red[NTH / 32];
+  const InstDev& I = insts[blockIdx.x];
+  double s = 0.0, cnt = 0.0;
+  for (int t = I.tile_begin + threadIdx.x; t < I.tile_end; t += NTH) {
+    s += partials[2 * (long long)t];
+    cnt += partials[2 * (long long)t + 1];
+  }
+  s = block_sum(s, red);
+  cnt = block_sum(cnt, red);
+  if (threadIdx.x == 0) {
+    const long long k = (long long)blockIdx.x * run.max_steps + n;
+    const double dt = run.dtrec[k], w = run.wrec[k];
+    double cf = 0.0;
+    if (dt > 0.0) {
+      const double b = s / dt;
+      if (w < 0.0) blast[blockIdx.x] = b;
+      else if (cnt > 0.0) cf = (b - blast[blockIdx.x]) * I.cfl / cnt;
+    }
+    coef[blockIdx.x] = cf;
   }
 }
 

@@ -27,6 +27,12 @@ cudaError_t launch_series_sample(const InstDev* insts, int n_inst, const double2
   return cudaGetLastError();
 }
 
+cudaError_t launch_dt_coef(const InstDev* insts, int n_inst, const double* partials, const RunDev& run, int n,
+                           double* blast, double* coef, cudaStream_t s) {
+  k_dt_coef<<<n_inst, NTH, 0, s>>>(insts, partials, run, n, blast, coef);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finalize_max(const InstDev* insts, int n_inst, const double* partials, double* out,
                                 cudaStream_t s) {
   k_finalize_max<<<n_inst, NTH, 0, s>>>(insts, partials, out);

@@ -32,6 +32,16 @@ cudaError_t launch_row_sums(const InstDev* insts, const int2* rows, int nrows, T
 // one diagnostics sample per instance: out[i] = {t, KE, h_mix, nstep}
 cudaError_t launch_series_sample(const InstDev* insts, int n_inst, const double2* rowsum, const double* t,
                                  const int* nstep, double* out, cudaStream_t s);
+// gradient through the step control (see k_dt_partials / k_dt_coef / k_dt_apply)
+template <class T>
+cudaError_t launch_dt_partials(const InstDev* insts, const int4* tiles, int ntiles, const T* U, const T* U1,
+                               const T* Un1, const T* lam, const T* lam1, const RunDev& run, int n, double* partials,
+                               cudaStream_t s);
+cudaError_t launch_dt_coef(const InstDev* insts, int n_inst, const double* partials, const RunDev& run, int n,
+                           double* blast, double* coef, cudaStream_t s);
+template <class T>
+cudaError_t launch_dt_apply(const InstDev* insts, const int4* tiles, int ntiles, const T* U, T* lam, const RunDev& run,
+                            int n, const double* coef, cudaStream_t s);
 template <class T>
 cudaError_t launch_grad(const InstDev* insts, const int4* tiles, int ntiles, const T* lam, const double* v,
                         double* g, cudaStream_t s);

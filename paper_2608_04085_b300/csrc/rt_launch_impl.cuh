@@ -83,6 +83,21 @@ cudaError_t launch_row_sums(const InstDev* insts, const int2* rows, int nrows, T
 }
 
 template <class T>
+cudaError_t launch_dt_partials(const InstDev* insts, const int4* tiles, int ntiles, const T* U, const T* U1,
+                               const T* Un1, const T* lam, const T* lam1, const RunDev& run, int n, double* partials,
+                               cudaStream_t s) {
+  k_dt_partials<T><<<ntiles, NTH, 0, s>>>(insts, tiles, U, U1, Un1, lam, lam1, run, n, partials);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_dt_apply(const InstDev* insts, const int4* tiles, int ntiles, const T* U, T* lam, const RunDev& run,
+                            int n, const double* coef, cudaStream_t s) {
+  k_dt_apply<T><<<ntiles, NTH, 0, s>>>(insts, tiles, U, lam, run, n, coef);
+  return cudaGetLastError();
+}
+
+template <class T>
 cudaError_t launch_grad(const InstDev* insts, const int4* tiles, int ntiles, const T* lam, const double* v,
                         double* g, cudaStream_t s) {
   k_grad<T><<<ntiles, NTH, 0, s>>>(insts, tiles, lam, v, g);
@@ -121,6 +136,10 @@ cudaError_t configure_kernels() {
                                       cudaStream_t);                                                             \
   template cudaError_t launch_row_sums<T>(const InstDev*, const int2*, int, T* const*, const int*, double2*,       \
                                           cudaStream_t);                                                         \
+  template cudaError_t launch_dt_partials<T>(const InstDev*, const int4*, int, const T*, const T*, const T*,      \
+                                             const T*, const T*, const RunDev&, int, double*, cudaStream_t);      \
+  template cudaError_t launch_dt_apply<T>(const InstDev*, const int4*, int, const T*, T*, const RunDev&, int,     \
+                                          const double*, cudaStream_t);                                          \
   template cudaError_t configure_kernels<T>();
 
 }  // namespace rt

@@ -94,6 +94,8 @@ struct rt_ctx {
   double* d_w3 = nullptr;
   double* d_w4 = nullptr;
   double* d_pairs = nullptr;     // L-BFGS (s, y) ring: 2 * pairs_m fields
+  double* d_blast = nullptr;     // [n_inst] step-control cotangent of the horizon-clipped last step
+  double* d_coef = nullptr;      // [n_inst] coefficient of the step-control term of the current step
   int2* d_rows = nullptr;        // (instance, y) of every row of every instance (diagnostics)
   double2* d_rowsum = nullptr;   // per-row sums of rho and e_k
   double* d_sample = nullptr;    // [n_inst][4] one diagnostics sample
@@ -379,6 +381,7 @@ template <class T>
 rt_status inject(rt_ctx* c, const double* d_v, void* U0, bool replay = false) {
   if (!replay) {
     CU(cudaMemsetAsync(c->run.dtrec, 0, (size_t)c->n_inst * c->opt.max_steps * sizeof(double), c->stream));
+    CU(cudaMemsetAsync(c->run.wrec, 0, (size_t)c->n_inst * c->opt.max_steps * sizeof(double), c->stream));
     CU(cudaMemsetAsync(c->run.dtc, 0, (size_t)c->n_inst * c->opt.max_steps * sizeof(rt::StepC<T>), c->stream));
   }
   CU(cudaMemsetAsync(c->run.wmin, 0xff, c->n_inst * sizeof(unsigned long long), c->stream));
@@ -612,6 +615,7 @@ struct Revolve {
   void* leaf_state;         // target of the slot-free (quadratic) recomputation
   T* lam[2];
   T* l1;
+  std::function<rt_status(int, T*, T*)> post;  // after each step's pull-back (n, U^n, U1), if set
   long long recomputed = 0;
 
   // advance U from step a (in src) to step b, result in dst; src and dst are
@@ -631,7 +635,7 @@ struct Revolve {
     CU(stage<T>(c, 1, 2, slotp<T>(Un), nullptr, slotp<T>(c->sU1), n));
     CU(adjoint<T>(c, slotp<T>(c->sU1), lam[(n + 1) & 1], 0.5, nullptr, 0.0, l1, n));
     CU(adjoint<T>(c, slotp<T>(Un), l1, 1.0, lam[(n + 1) & 1], 0.5, lam[n & 1], n));
-    return RT_OK;
+    return post ? post(n, slotp<T>(Un), slotp<T>(c->sU1)) : RT_OK;
   }
   rt_status reverse(int l, int r, void* Ul) {
     const int n = r - l;
@@ -666,7 +670,8 @@ struct Revolve {
 // in reverse: recompute U1 = stage1(U^n), lam1 = (dStage2/dU1)^T lam^{n+1},
 // lam^n = lam^{n+1}/2 + lam1 + (dL/dU^n)^T lam1 dt (SSP-RK2 transposed).
 template <class T>
-rt_status gradient_impl(rt_ctx* c, const double* d_v, double* J_out, double* d_g, int* segments_out) {
+rt_status gradient_impl(rt_ctx* c, const double* d_v, double* J_out, double* d_g, int* segments_out,
+                        bool dt_grad = false) {
   CHK(inject<T>(c, d_v, c->sA));
   int n_est = 1;
   CHK(estimate_steps(c, &n_est));
@@ -713,10 +718,25 @@ rt_status gradient_impl(rt_ctx* c, const double* d_v, double* J_out, double* d_g
   T* lam[2] = {slotp<T>(c->lA), slotp<T>(c->lB)};
   T* l1 = slotp<T>(c->l1);
   // lam1 = (dStage2/dU1)^T lam^{n+1};  lam^n = lam^{n+1}/2 + (dStage1/dU^n)^T lam1
+  // With dt_grad, the step-control term of step n (after its frozen-dt
+  // pull-back): U^{n+1} is recomputed into sA (free during the reverse
+  // sweep), b_n = <lam^{n+1}, dU^{n+1}/d dt_n> is reduced per instance, and
+  // lam^n gains the derivative of dt_n at the candidates of the minimum.
+  auto dt_term = [&](int n, T* Un, T* U1) -> rt_status {
+    if (!dt_grad) return RT_OK;
+    CU(stage<T>(c, 2, 2, U1, Un, slotp<T>(c->sA), n));
+    CU(rt::launch_dt_partials<T>(c->d_inst, c->d_tiles, c->ntiles, Un, U1, slotp<T>(c->sA), lam[(n + 1) & 1], l1,
+                                 c->run, n, c->d_partials, c->stream));
+    CU(rt::launch_dt_coef(c->d_inst, c->n_inst, c->d_partials, c->run, n, c->d_blast, c->d_coef, c->stream));
+    CU(rt::launch_dt_apply<T>(c->d_inst, c->d_tiles, c->ntiles, Un, lam[n & 1], c->run, n, c->d_coef, c->stream));
+    c->launches += 3;
+    return RT_OK;
+  };
+  if (dt_grad) CU(cudaMemsetAsync(c->d_blast, 0, c->n_inst * sizeof(double), c->stream));
   auto reverse_step = [&](int n, T* Un, T* U1) -> rt_status {
     CU(adjoint<T>(c, U1, lam[(n + 1) & 1], 0.5, nullptr, 0.0, l1, n));
     CU(adjoint<T>(c, Un, l1, 1.0, lam[(n + 1) & 1], 0.5, lam[n & 1], n));
-    return RT_OK;
+    return dt_term(n, Un, U1);
   };
   int segments = 1;
   if (plan.kind == 3) {  // dynamic recursion: launched directly
@@ -729,13 +749,14 @@ rt_status gradient_impl(rt_ctx* c, const double* d_v, double* J_out, double* d_g
     rv.lam[0] = lam[0];
     rv.lam[1] = lam[1];
     rv.l1 = l1;
+    rv.post = dt_term;
     CHK(inject<T>(c, d_v, c->pool[0], true));  // U^0 again; keeps the recorded dt sequence
     if (N > 0) CHK(rv.reverse(0, N, c->pool[0]));
     segments = -(int)std::min<long long>(rv.recomputed, 2000000000LL);  // reported as minus the recomputed steps
   } else if (plan.kind == 2) {
     for (int hi = N; hi > 0;) {
       const int lo = ((hi - 1) / kGraphChunk) * kGraphChunk;
-      const GraphKey key{1, 2, 0, c->stage_variant, c->lim, 0, lo, hi};
+      const GraphKey key{1, 2, dt_grad ? 1 : 0, c->stage_variant, c->lim, 0, lo, hi};
       CHK(run_graph(c, key, [&]() -> rt_status {
         for (int n = hi - 1; n >= lo; --n) CHK(reverse_step(n, slotp<T>(c->pool[n]), slotp<T>(c->pool1[n])));
         return RT_OK;
@@ -750,7 +771,7 @@ rt_status gradient_impl(rt_ctx* c, const double* d_v, double* J_out, double* d_g
       auto seg = [&](int n) -> T* { return n == n0 ? slotp<T>(c->pool[S + k]) : slotp<T>(c->pool[n - n0]); };
       auto seg1 = [&](int n) -> T* { return slotp<T>(c->pool1[n - n0]); };
       // recompute the segment from its checkpoint, keeping U^n and U1 of every step
-      const GraphKey key{2, 1, 0, c->stage_variant, c->lim, S, n0, n1};
+      const GraphKey key{2, 1, dt_grad ? 1 : 0, c->stage_variant, c->lim, S, n0, n1};
       CHK(run_graph(c, key, [&]() -> rt_status {
         for (int n = n0; n < n1; ++n) {
           CU(stage<T>(c, 1, 2, seg(n), nullptr, seg1(n), n));
@@ -1199,7 +1220,7 @@ rt_status cnop_run(rt_ctx* c, const cnop_params* prm, double* v_inout, int flags
   } else {
     CHK(cnop_start(c, prm, v_inout, flags, eps));
     CHK(set_running());
-    CHK(gradient_impl<T>(c, v, st.J.data(), g, nullptr));
+    CHK(gradient_impl<T>(c, v, st.J.data(), g, nullptr, (flags & RT_GRAD_DT) != 0));
     ++st.gevals;
     CHK(stationarity(v, g));
     if (lbfgs) CHK(model_gradient(v, g));
@@ -1338,7 +1359,7 @@ rt_status cnop_run(rt_ctx* c, const cnop_params* prm, double* v_inout, int flags
     for (int i = 0; i < N; ++i) any_live = any_live || running(i);
     if (!any_live) break;
     CHK(set_running());
-    CHK(gradient_impl<T>(c, vt, Jn.data(), gt, nullptr));
+    CHK(gradient_impl<T>(c, vt, Jn.data(), gt, nullptr, (flags & RT_GRAD_DT) != 0));
     ++st.gevals;
     CHK(stationarity(vt, gt));
     CHK(axpby(c, tmp, ones, vt, &mones, v));  // s = vt - v
@@ -1591,6 +1612,10 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
   c->run.n_inst = N;
   c->run.max_steps = c->opt.max_steps;
   INIT_CU(cudaMalloc(&c->run.dtrec, (size_t)N * c->opt.max_steps * sizeof(double)));
+  INIT_CU(cudaMalloc(&c->run.wrec, (size_t)N * c->opt.max_steps * sizeof(double)));
+  INIT_CU(cudaMemset(c->run.wrec, 0, (size_t)N * c->opt.max_steps * sizeof(double)));
+  INIT_CU(cudaMalloc(&c->d_blast, (size_t)N * sizeof(double)));
+  INIT_CU(cudaMalloc(&c->d_coef, (size_t)N * sizeof(double)));
   INIT_CU(cudaMalloc(&c->run.t, N * sizeof(double)));
   INIT_CU(cudaMalloc(&c->run.nstep, N * sizeof(int)));
   INIT_CU(cudaMalloc(&c->run.wmin, N * sizeof(unsigned long long)));
@@ -1641,7 +1666,7 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
 void rt_destroy(rt_ctx* c) {
   if (!c) return;
   void* ptrs[] = {c->d_inst, c->d_tiles, c->d_strips, c->d_base, c->d_ek0, c->d_ek, c->sA, c->sB, c->sU1, c->lA, c->lB,
-                  c->l1, c->d_tab, c->run.dtrec, c->run.dtc, c->run.counter, c->run.t, c->run.nstep, c->run.wmin, c->run.status,
+                  c->l1, c->d_tab, c->run.dtrec, c->run.wrec, c->d_blast, c->d_coef, c->run.dtc, c->run.counter, c->run.t, c->run.nstep, c->run.wmin, c->run.status,
                   c->run.bad_cell, c->d_partials, c->d_sums, c->d_scal, c->d_v, c->d_g, c->d_w1, c->d_w2,
                   c->d_w3, c->d_w4, c->d_pairs, c->d_rows, c->d_rowsum, c->d_sample};
   for (void* p : ptrs)
@@ -1832,7 +1857,7 @@ rt_status rt_reconstruct(rt_ctx* c, const double* v, int flags, int kind, double
 
 rt_status rt_gradient(rt_ctx* c, const double* v0, int flags, double* J_out, double* grad_out, rt_run_stats* st) {
   if (!c || !v0 || !J_out || !grad_out) return fail(c, RT_EINVAL, "null argument");
-  if (flags & RT_REPLAY_DT) return fail(c, RT_EINVAL, "rt_gradient always freezes its own dt sequence");
+  if (flags & RT_REPLAY_DT) return fail(c, RT_EINVAL, "rt_gradient runs its own step control (RT_REPLAY_DT is not accepted)");
   c->err.clear();
   CHK(ensure_fields(c, false));
   CHK(enter(c));
@@ -1840,8 +1865,9 @@ rt_status rt_gradient(rt_ctx* c, const double* v0, int flags, double* J_out, dou
   Timer tm(c);
   CHK(copy_in(c, v0, flags, c->d_v));
   int segments = 0;
-  CHK(c->esz == 8 ? gradient_impl<double>(c, c->d_v, J_out, c->d_g, &segments)
-                  : gradient_impl<float>(c, c->d_v, J_out, c->d_g, &segments));
+  const bool dtg = (flags & RT_GRAD_DT) != 0;
+  CHK(c->esz == 8 ? gradient_impl<double>(c, c->d_v, J_out, c->d_g, &segments, dtg)
+                  : gradient_impl<float>(c, c->d_v, J_out, c->d_g, &segments, dtg));
   CHK(copy_out(c, c->d_g, flags, grad_out));
   const float ms = tm.stop();
   collect_timing(c);
