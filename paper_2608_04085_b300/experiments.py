@@ -8,7 +8,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import (RT_FP64, RT_RECON_2D_POWER, RT_RECON_X_MODES, Context)
+from . import (RT_FP32_STATE, RT_FP64, RT_RECON_2D_POWER, RT_RECON_X_MODES, Context)
 
 SEEDS = ("CNOP", "Random", "5modes", "90%Power-2D")
 
@@ -28,3 +28,55 @@ def comparison_runs(problem, v_cnop, v_random, eps, every, precision=RT_FP64, mo
         J, J_ke, _ = ctx.forward(flat)
         series = ctx.series(flat, every)
     return {name: {"v": seeds[k], "J": J[k], "J_ke": J_ke[k], **series[k]} for k, name in enumerate(SEEDS)}
+
+
+# The paper's three CNOP runs (Tab. runs): label -> (N, t*, iteration budget).
+PAPER_RUNS = {"T2_N128": (128, 2.0, 200), "T2_N256": (256, 2.0, 3000), "T3_N128": (128, 3.0, 5800)}
+
+
+def paper_run(label, seeds=(0, 1, 2, 3), iters=None, eps=1e-6, h_loc=0.1, precision=RT_FP32_STATE, every=20):
+    """One of the paper's CNOP runs on the unit-square configuration (Sec. 2-3,
+    Tabs. params and runs), from localised random starts with the given seeds
+    (all seeds in one batch): projected L-BFGS to the iteration budget, then
+    the comparison seeds of comparison_runs for each. Returns a dict with, per
+    seed, the CNOP objective, the kinetic energy at t* of every seed kind, the
+    CNOP's KE amplification over its random start and its dominant horizontal
+    modes at y_peak."""
+    import time
+    import rt_inputs
+    N, t_star, budget = PAPER_RUNS[label]
+    iters = budget if iters is None else iters
+    w = rt_inputs.paper_unit_square(N, t_star)
+    xi = np.concatenate([rt_inputs.gaussian_field(s, w.ncomp, w.ny, w.nx).ravel() for s in seeds])
+    t0 = time.perf_counter()
+    with Context([w] * len(seeds), precision=precision) as ctx:
+        v0, _, _ = ctx.cnop(xi, eps, 0, h_loc=h_loc)            # the localised random starts
+        v, J, res = ctx.cnop(xi, eps, iters, h_loc=h_loc)       # the CNOPs
+    solve_s = time.perf_counter() - t0
+    n = w.ncomp * w.nx * w.ny
+    out = {"label": label, "N": N, "t_star": t_star, "iterations": res["iterations"], "eps": eps,
+           "solve_seconds": solve_s, "seeds": []}
+    for k, s in enumerate(seeds):
+        cmp = comparison_runs(w, v[k * n:(k + 1) * n], v0[k * n:(k + 1) * n], eps, every, precision=precision)
+        with Context([w], precision=precision) as one:
+            y_peak, E = one.spectrum_x(v[k * n:(k + 1) * n])
+        top = [int(m) + 1 for m in np.argsort(-E, kind="stable")[:5]]
+        out["seeds"].append({
+            "seed": int(s), "J_cnop": float(J[k]), "J_start": float(res["J_history"][0, k]),
+            "KE_t_star": {name: float(cmp[name]["J_ke"]) for name in SEEDS},
+            "h_mix_t_star": {name: float(cmp[name]["h_mix"][-1]) for name in SEEDS},
+            "KE_amplification_vs_random": float(cmp["CNOP"]["J_ke"] / cmp["Random"]["J_ke"]),
+            "dominant_modes": top, "y_peak": int(y_peak), "stop": int(res["stop"][k]),
+            "chi": float(res["chi"][k])})
+    return out
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="the paper's CNOP runs on synthetic random starts")
+    ap.add_argument("--run", default="T2_N128", choices=sorted(PAPER_RUNS))
+    ap.add_argument("--iters", type=int, default=None)
+    ap.add_argument("--seeds", type=int, default=4)
+    a = ap.parse_args()
+    print(json.dumps(paper_run(a.run, seeds=tuple(range(a.seeds)), iters=a.iters)), flush=True)
