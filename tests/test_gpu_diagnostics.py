@@ -90,3 +90,16 @@ def test_comparison_runs_on_the_paper_configuration():
         assert o["KE"][-1] == pytest.approx(o["J_ke"], rel=1e-13)
         assert o["t"][-1] == pytest.approx(w.T, rel=1e-15)
         assert np.all(np.diff(o["t"]) > 0)
+
+
+def test_paper_run_driver_short():
+    """The paper-run driver on a cut-down budget: a batch of two seeds of the
+    T2_N128 configuration, three L-BFGS iterations; every seed ends on the
+    budget with J above its start and a finite KE amplification."""
+    from paper_2608_04085_b300.experiments import paper_run
+    out = paper_run("T2_N128", seeds=(0, 1), iters=3)
+    assert out["iterations"] == 3 and out["N"] == 128
+    for s in out["seeds"]:
+        assert s["J_cnop"] > s["J_start"]
+        assert np.isfinite(s["KE_amplification_vs_random"]) and s["KE_amplification_vs_random"] > 1.0
+        assert len(s["dominant_modes"]) == 5 and all(1 <= n <= 64 for n in s["dominant_modes"])
