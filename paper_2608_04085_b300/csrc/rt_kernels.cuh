@@ -542,6 +542,21 @@ __global__ void __launch_bounds__(NTH) k_stage_tile(const InstDev* __restrict__ 
   const int x0 = tl.y, y0 = tl.z;
   const int lim = LIM >= 0 ? LIM : I.limiter;
   load_prim_tile<T, ST_EX, ST_EY, true>(Si, I, cells, x0 - 2, y0 - 2, P, reinterpret_cast<T*>(sW));
+  // stage 2 also needs U^n of this thread's cells in the update; their loads
+  // are issued here so that the face work hides their latency
+  constexpr int PASSES = TY / ROWS_PER_PASS;
+  T bpre[PASSES][4];
+  if (STAGE == 2) {
+    const T* Bi = base + 4 * I.cell_off;
+#pragma unroll
+    for (int pass = 0; pass < PASSES; ++pass) {
+      const int gx = x0 + threadIdx.x % TX, gy = y0 + threadIdx.x / TX + pass * ROWS_PER_PASS;
+      const bool in = gx < I.nx && gy < I.ny;
+      const long long c = in ? (long long)gy * I.nx + gx : 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) bpre[pass][k] = in ? Bi[k * cells + c] : T(0);
+    }
+  }
   __syncthreads();
   for (int f = threadIdx.x; f < ST_NFX + ST_NFY; f += NTH) {
     T w[4][4], F[4];
@@ -581,7 +596,7 @@ __global__ void __launch_bounds__(NTH) k_stage_tile(const InstDev* __restrict__ 
   bool bad = false;
   long long badc = 0;
 #pragma unroll
-  for (int pass = 0; pass < TY / ROWS_PER_PASS; ++pass) {
+  for (int pass = 0; pass < PASSES; ++pass) {
     const int ty = threadIdx.x / TX + pass * ROWS_PER_PASS;
     const int gx = x0 + tx, gy = y0 + ty;
     if (gx < I.nx && gy < I.ny) {
@@ -599,9 +614,8 @@ __global__ void __launch_bounds__(NTH) k_stage_tile(const InstDev* __restrict__ 
         o[k] = b;
       }
       if (STAGE == 2) {
-        const T* Bi = base + 4 * I.cell_off;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) o[k] = T(0.5) * Bi[k * cells + c] + T(0.5) * o[k];
+        for (int k = 0; k < 4; ++k) o[k] = T(0.5) * bpre[pass][k] + T(0.5) * o[k];
       }
       T* Di = dst + 4 * I.cell_off;
 #pragma unroll
