@@ -670,6 +670,18 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
   const T* Ki = K + 4 * I.cell_off;
   const int x0 = tl.y, y0 = tl.z, nx = I.nx, ny = I.ny;
   const int lim = LIM >= 0 ? LIM : I.limiter;
+  constexpr int PASSES = TY / ROWS_PER_PASS;
+  // E of this thread's cells (added at the end) is loaded first, so that the
+  // face work hides its latency
+  T epre[PASSES][4];
+#pragma unroll
+  for (int pass = 0; pass < PASSES; ++pass) {
+    const int gx = x0 + threadIdx.x % TX, gy = y0 + threadIdx.x / TX + pass * ROWS_PER_PASS;
+    const bool in = E && gx < nx && gy < ny;
+    const long long c = in ? 4 * I.cell_off + (long long)gy * nx + gx : 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) epre[pass][q] = in ? E[c + q * cells] : T(0);
+  }
 
   {  // cotangent tile: all loads first
     constexpr int N = ADJ_KX * ADJ_KY, PER = (N + NTH - 1) / NTH;
@@ -699,7 +711,6 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
   __syncthreads();
 
   const int tx = threadIdx.x % TX;
-  constexpr int PASSES = TY / ROWS_PER_PASS;
   T bW[PASSES][4];
 #pragma unroll
   for (int pass = 0; pass < PASSES; ++pass)
@@ -830,9 +841,8 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
       o[2] = kc[2] + bU[2] + sc.dtg * kc[3];
       o[3] = kc[3] + bU[3];
       if (E) {
-        const T* Ei = E + 4 * I.cell_off;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) o[q] = o[q] + escale * Ei[q * cells + c];
+        for (int q = 0; q < 4; ++q) o[q] = o[q] + escale * epre[pass][q];
       }
       T* Oi = out + 4 * I.cell_off;
 #pragma unroll
