@@ -309,6 +309,14 @@ rt_status rt_spectrum_2d(rt_ctx* ctx, const double* v, int flags, int inst, doub
 rt_status rt_reconstruct(rt_ctx* ctx, const double* v, int flags, int kind, double param, const double* eps,
                          double* out, int* kept_out);
 
+/* Measured FMA throughput of the current device (measurement support; the
+ * paper has no counterpart): independent fused multiply-add chains in every
+ * thread of a grid that fills every SM, FP32 and FP64, best of three timed
+ * launches after a warm-up; tflops_* = 2 FLOPs per FMA / time. Runs on the
+ * legacy default stream and synchronises the device. Errors: RT_EINVAL (null
+ * output), RT_ECUDA. */
+rt_status rt_fma_peak(double* tflops_f32, double* tflops_f64);
+
 /* Allocation-free objective of one final state. The paper has no
  * counterpart: this exists for callers that must not let a library allocate
  * device memory (a host framework that owns all device memory through its

@@ -37,7 +37,7 @@ EXPORTS = ("rt_init", "rt_destroy", "rt_last_error", "rt_num_instances", "rt_fie
            "rt_field_size", "rt_field_total", "rt_forward", "rt_gradient", "rt_constraint",
            "rt_project", "rt_get_state", "rt_get_dt", "rt_set_kernel_timing", "rt_kernel_times", "rt_stage_kernel",
            "cnop_solve", "rt_objective_noalloc", "rt_forward_series", "rt_spectrum_x", "rt_spectrum_2d",
-           "rt_reconstruct")
+           "rt_reconstruct", "rt_fma_peak")
 
 
 class RtError(RuntimeError):
@@ -144,6 +144,8 @@ def library():
         L.rt_spectrum_2d.restype = ip
         L.rt_reconstruct.argtypes = [vp, vp, ip, ip, ctypes.c_double, dp, vp, ctypes.POINTER(ip)]
         L.rt_reconstruct.restype = ip
+        L.rt_fma_peak.argtypes = [dp, dp]
+        L.rt_fma_peak.restype = ip
         L.cnop_solve.argtypes = [vp, ctypes.POINTER(CnopParams), vp, ip, dp, ctypes.POINTER(CnopResult)]
         L.cnop_solve.restype = ip
         _lib = L
@@ -403,6 +405,15 @@ class Context:
         out = {k: getattr(res, k) for k in ("iterations", "forward_evals", "gradient_evals", "ms")}
         return v, J, out | {"status": st, "C": C, "chi": chi, "grad_norm": gnorm, "stop": stop,
                             "J_history": hist[:res.iterations + 1]}
+
+
+def fma_peak():
+    """(FP32, FP64) FMA throughput of the current device in TFLOP/s (rt_fma_peak)."""
+    f32, f64 = ctypes.c_double(), ctypes.c_double()
+    st = library().rt_fma_peak(ctypes.byref(f32), ctypes.byref(f64))
+    if st != RT_OK:
+        raise RtError(st, "rt_fma_peak failed")
+    return f32.value, f64.value
 
 
 def field_layout(problems):

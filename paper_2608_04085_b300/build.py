@@ -24,6 +24,7 @@ UNITS = [
     ("rt_runtime.cu", []),
     ("rt_noalloc.cu", []),
     ("rt_spectra.cu", ["-fmad=false"]),
+    ("rt_peaks.cu", []),
 ]
 
 

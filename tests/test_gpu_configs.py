@@ -62,3 +62,12 @@ def test_large_grid_revolve_equals_sqrt():
     assert out[rt.RT_CKPT_REVOLVE][2]["segments"] < 0  # revolve reports recomputed steps
     assert out[rt.RT_CKPT_SQRT][0] == out[rt.RT_CKPT_REVOLVE][0]
     assert np.array_equal(out[rt.RT_CKPT_SQRT][1], out[rt.RT_CKPT_REVOLVE][1])
+
+
+def test_fma_peak_is_plausible():
+    """The FMA microbenchmark: FP32 between 20 and 150 TFLOP/s (148 SMs x
+    128 lanes x 2 FLOPs at 1-2.1 GHz is 38-80), FP64 well below FP32."""
+    import paper_2608_04085_b300 as rt
+    f32, f64 = rt.fma_peak()
+    assert 20.0 < f32 < 150.0, f32
+    assert 0.05 < f64 < f32, (f32, f64)
