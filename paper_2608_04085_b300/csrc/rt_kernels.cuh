@@ -520,9 +520,11 @@ constexpr int ST_SMEM_ELEMS = 4 * ST_EX * ST_EY + 4 * ST_NFX + 4 * ST_NFY;
 
 // Tile variant of the stage kernel: one CTA per 32 x 16 tile, primitive
 // states with 2 ghost layers in shared memory, one thread per face, then one
-// thread per cell for the update. Modes as for the sweep variant.
+// thread per cell for the update. Modes as for the sweep variant. FP32
+// launches are held to 6 CTAs per SM (40 registers), which the stage-2
+// variant with the step control would otherwise exceed.
 template <class T, int STAGE, int MODE, int LIM>
-__global__ void __launch_bounds__(NTH) k_stage_tile(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,
+__global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 6 : 1) k_stage_tile(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,
                                                const T* __restrict__ src, const T* __restrict__ base,
                                                T* __restrict__ dst, RunDev run, int n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
