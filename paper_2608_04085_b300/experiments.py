@@ -75,8 +75,43 @@ if __name__ == "__main__":
     import argparse
     import json
     ap = argparse.ArgumentParser(description="the paper's CNOP runs on synthetic random starts")
-    ap.add_argument("--run", default="T2_N128", choices=sorted(PAPER_RUNS))
+    ap.add_argument("--run", default="T2_N128", choices=sorted(PAPER_RUNS) + ["horizons"])
     ap.add_argument("--iters", type=int, default=None)
     ap.add_argument("--seeds", type=int, default=4)
     a = ap.parse_args()
-    print(json.dumps(paper_run(a.run, seeds=tuple(range(a.seeds)), iters=a.iters)), flush=True)
+    if a.run == "horizons":
+        print(json.dumps(horizon_sweep(iters=50 if a.iters is None else a.iters)), flush=True)
+    else:
+        print(json.dumps(paper_run(a.run, seeds=tuple(range(a.seeds)), iters=a.iters)), flush=True)
+
+
+def horizon_sweep(Ts=(1.0, 2.0, 4.0), iters=50, seed=0, eps=1e-4, method=None, precision=RT_FP32_STATE):
+    """CNOPs of the 256x768 RT box for several horizons T from one seeded
+    i.i.d. (v_x, v_y) start scaled to C = eps, all T in one batch (the
+    instances advance in lockstep; each stops at its own horizon), with the
+    spectral projected gradient by default; then, per T, J(T) of the CNOP,
+    of the random start and of the five-mode seed. Returns a dict."""
+    import time
+    import rt_inputs
+    from . import RT_CNOP_SPG
+    method = RT_CNOP_SPG if method is None else method
+    ws = [rt_inputs.single_256().replace(T=float(T)) for T in Ts]
+    n = 2 * ws[0].nx * ws[0].ny
+    xi = np.concatenate([rt_inputs.gaussian_field(seed, 2, ws[0].ny, ws[0].nx).ravel()] * len(ws))
+    t0 = time.perf_counter()
+    with Context(ws, precision=precision) as ctx:
+        v0 = ctx.project(xi, eps, to_budget=True)
+        v, J, res = ctx.cnop(xi, eps, iters, method=method)
+    solve_s = time.perf_counter() - t0
+    out = {"grid": [ws[0].nx, ws[0].ny], "iterations": res["iterations"], "eps": eps, "method": int(method),
+           "solve_seconds": solve_s, "horizons": []}
+    for k, w in enumerate(ws):
+        vk, v0k = v[k * n:(k + 1) * n], v0[k * n:(k + 1) * n]
+        with Context([w], precision=precision) as one:
+            five, _ = one.reconstruct(vk, RT_RECON_X_MODES, 5, eps)
+        with Context([w] * 3, precision=precision) as three:
+            Jc, _, st = three.forward(np.concatenate([vk, v0k, five]))
+        out["horizons"].append({"T": float(w.T), "steps": int(st["steps"]), "J_cnop": float(Jc[0]),
+                                "J_random": float(Jc[1]), "J_5modes": float(Jc[2]),
+                                "J_start": float(res["J_history"][0, k]), "stop": int(res["stop"][k])})
+    return out
