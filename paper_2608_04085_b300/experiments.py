@@ -100,7 +100,7 @@ def horizon_sweep(Ts=(1.0, 2.0, 4.0), iters=50, seed=0, eps=1e-4, method=None, p
     xi = np.concatenate([rt_inputs.gaussian_field(seed, 2, ws[0].ny, ws[0].nx).ravel()] * len(ws))
     t0 = time.perf_counter()
     with Context(ws, precision=precision) as ctx:
-        v0 = ctx.project(xi, eps, to_budget=True)
+        v0, _, _ = ctx.cnop(xi, eps, 0, method=method)          # the random starts
         v, J, res = ctx.cnop(xi, eps, iters, method=method)
     solve_s = time.perf_counter() - t0
     out = {"grid": [ws[0].nx, ws[0].ny], "iterations": res["iterations"], "eps": eps, "method": int(method),
