@@ -71,20 +71,6 @@ def paper_run(label, seeds=(0, 1, 2, 3), iters=None, eps=1e-6, h_loc=0.1, precis
     return out
 
 
-if __name__ == "__main__":
-    import argparse
-    import json
-    ap = argparse.ArgumentParser(description="the paper's CNOP runs on synthetic random starts")
-    ap.add_argument("--run", default="T2_N128", choices=sorted(PAPER_RUNS) + ["horizons"])
-    ap.add_argument("--iters", type=int, default=None)
-    ap.add_argument("--seeds", type=int, default=4)
-    a = ap.parse_args()
-    if a.run == "horizons":
-        print(json.dumps(horizon_sweep(iters=50 if a.iters is None else a.iters)), flush=True)
-    else:
-        print(json.dumps(paper_run(a.run, seeds=tuple(range(a.seeds)), iters=a.iters)), flush=True)
-
-
 def horizon_sweep(Ts=(1.0, 2.0, 4.0), iters=50, seed=0, eps=1e-4, method=None, precision=RT_FP32_STATE):
     """CNOPs of the 256x768 RT box for several horizons T from one seeded
     i.i.d. (v_x, v_y) start scaled to C = eps, all T in one batch (the
@@ -96,8 +82,8 @@ def horizon_sweep(Ts=(1.0, 2.0, 4.0), iters=50, seed=0, eps=1e-4, method=None, p
     from . import RT_CNOP_SPG
     method = RT_CNOP_SPG if method is None else method
     ws = [rt_inputs.single_256().replace(T=float(T)) for T in Ts]
-    n = 2 * ws[0].nx * ws[0].ny
-    xi = np.concatenate([rt_inputs.gaussian_field(seed, 2, ws[0].ny, ws[0].nx).ravel()] * len(ws))
+    n = ws[0].ncomp * ws[0].nx * ws[0].ny
+    xi = np.concatenate([rt_inputs.gaussian_field(seed, ws[0].ncomp, ws[0].ny, ws[0].nx).ravel()] * len(ws))
     t0 = time.perf_counter()
     with Context(ws, precision=precision) as ctx:
         v0, _, _ = ctx.cnop(xi, eps, 0, method=method)          # the random starts
@@ -115,3 +101,18 @@ def horizon_sweep(Ts=(1.0, 2.0, 4.0), iters=50, seed=0, eps=1e-4, method=None, p
                                 "J_random": float(Jc[1]), "J_5modes": float(Jc[2]),
                                 "J_start": float(res["J_history"][0, k]), "stop": int(res["stop"][k])})
     return out
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="the paper's CNOP runs on synthetic random starts")
+    ap.add_argument("--run", default="T2_N128", choices=sorted(PAPER_RUNS) + ["horizons"])
+    ap.add_argument("--iters", type=int, default=None)
+    ap.add_argument("--seeds", type=int, default=4)
+    a = ap.parse_args()
+    if a.run == "horizons":
+        print(json.dumps(horizon_sweep(iters=50 if a.iters is None else a.iters)), flush=True)
+    else:
+        print(json.dumps(paper_run(a.run, seeds=tuple(range(a.seeds)), iters=a.iters)), flush=True)
+
