@@ -103,3 +103,20 @@ def test_paper_run_driver_short():
         assert s["J_cnop"] > s["J_start"]
         assert np.isfinite(s["KE_amplification_vs_random"]) and s["KE_amplification_vs_random"] > 1.0
         assert len(s["dominant_modes"]) == 5 and all(1 <= n <= 64 for n in s["dominant_modes"])
+
+
+def test_horizon_sweep_driver_short():
+    """The horizon-sweep driver on short horizons and a cut-down budget: each
+    horizon's CNOP ends above its random start, later horizons take more steps,
+    the random start's J is the search's first J, and the five-mode seed
+    has a finite positive J."""
+    from paper_2608_04085_b300.experiments import horizon_sweep
+    out = horizon_sweep(Ts=(0.05, 0.1), iters=2)
+    assert out["iterations"] == 2 and out["grid"] == [256, 768]
+    hs = out["horizons"]
+    assert [h["T"] for h in hs] == [0.05, 0.1]
+    assert hs[0]["steps"] < hs[1]["steps"]
+    for h in hs:
+        assert h["J_cnop"] > h["J_start"] > 0
+        assert h["J_random"] == h["J_start"]
+        assert np.isfinite(h["J_5modes"]) and h["J_5modes"] > 0
