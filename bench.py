@@ -49,7 +49,7 @@ ADJ_BYTES_PER_CELL = {"stage2_adjoint": 12 * 4, "stage1_adjoint": 16 * 4, "mean"
 # DRAM traffic of k_adjoint<float, minmod> per cell per launch (read + write),
 # from the ncu capture summarised in profiles/k_adjoint_fp32_rtbox256x768x16_dram.md
 # (16 instances of the same grid; traffic grows in proportion to the cells).
-ADJ_TRAFFIC_BYTES_PER_CELL = 49.43
+ADJ_TRAFFIC_BYTES_PER_CELL = 49.48
 STEP_BYTES_PER_CELL_UPDATE = 68 * 4  # forward 20s + segment recompute 20s (U1 kept) + adjoint 12s + 16s (sqrt checkpointing)
 # Warp instructions k_adjoint<float, minmod> executes per cell per launch
 # (ncu sm__inst_executed.sum / cells on 16 instances of the same grid, mean of
@@ -57,7 +57,7 @@ STEP_BYTES_PER_CELL_UPDATE = 68 * 4  # forward 20s + segment recompute 20s (U1 k
 # The kernel is bound by instruction issue, not by HBM: the issue roofline
 # divides its executed instructions per second by the issue peak of
 # 148 SMs x 4 schedulers x 1 warp instruction per clock at the sampled SM clock.
-ADJ_WARP_INSTR_PER_CELL = 38.96
+ADJ_WARP_INSTR_PER_CELL = 40.88
 ISSUE_PER_SM_PER_CLK = 4
 
 

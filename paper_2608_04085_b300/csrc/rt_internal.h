@@ -46,6 +46,11 @@ struct InstDev {
   float gamma_f, gm1_f, g_f, dx_f, dy_f;  // the same constants rounded once for FP32 kernels
   const double* rho0;        // [ny] base density at cell centres
   const double* p0;          // [ny] base pressure at cell centres
+  // [ny] rho0 and p0 rounded to FP32. An FP32 state stores the deviation of
+  // each cell from its row's base (rho0, 0, 0, p0/(gamma-1)); the kernels add
+  // these back wherever they need the full state.
+  const float* rho0_f;
+  const float* p0_f;
   const double* ek0;         // [nx*ny] baseline e_k for the anomaly objective (or null)
 };
 

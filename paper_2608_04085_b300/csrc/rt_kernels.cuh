@@ -99,13 +99,71 @@ __device__ __forceinline__ StepC<T> step_const(const RunDev& run, int inst, int 
   return reinterpret_cast<const StepC<T>*>(run.dtc)[(long long)inst * run.max_steps + n];
 }
 
+// Stored state -> primitives (rho, u_x, u_y, p) of a cell of row `row`. An
+// FP64 state stores U itself. An FP32 state stores the deviation of U from
+// the row's hydrostatic base (rho0, 0, 0, p0/(gamma-1)): the stored values
+// and every update then round relative to the deviation, not to the O(1)
+// background, and the primitives add the base back: rho = rho0 + d_rho,
+// p = p0 + (gamma-1)(d_E - |m|^2/(2 rho)). In exact arithmetic both give
+// the same scheme.
+// The row's base (rho0, p0) as the FP32 conversion uses it (unused for FP64).
+struct RowBase {
+  float rho, p;
+};
+
+template <class T>
+__device__ __forceinline__ RowBase row_base(const InstDev& I, int row) {
+  if constexpr (sizeof(T) == 4) return {__ldg(I.rho0_f + row), __ldg(I.p0_f + row)};
+  else return {0.f, 0.f};
+}
+
+template <class T>
+__device__ __forceinline__ void state_to_prim_b(T s0, T s1, T s2, T s3, RowBase b, T gm1, T W[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const T r = s0 + b.rho;
+    W[0] = r;
+    W[1] = s1 / r;
+    W[2] = s2 / r;
+    W[3] = b.p + gm1 * (s3 - T(0.5) * (s1 * W[1] + s2 * W[2]));
+  } else {
+    cons_to_prim(s0, s1, s2, s3, gm1, W);
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void state_to_prim(T s0, T s1, T s2, T s3, const InstDev& I, int row, T gm1, T W[4]) {
+  state_to_prim_b(s0, s1, s2, s3, row_base<T>(I, row), gm1, W);
+}
+
+// Full density from the stored density and the row's base.
+template <class T>
+__device__ __forceinline__ T state_rho(T s0, RowBase b) {
+  if constexpr (sizeof(T) == 4) return s0 + b.rho;
+  else return s0;
+}
+
+// Full density and pressure in FP64 from a stored state (diagnostics and the
+// step-control derivative).
+template <class T>
+__device__ __forceinline__ void state_rho_p_f64(T s0, T s1, T s2, T s3, const InstDev& I, int row, double& rho,
+                                                double& p) {
+  const double m1 = s1, m2 = s2;
+  if constexpr (sizeof(T) == 4) {
+    rho = (double)s0 + (double)I.rho0_f[row];
+    p = (double)I.p0_f[row] + I.gm1 * ((double)s3 - 0.5 * (m1 * (m1 / rho) + m2 * (m2 / rho)));
+  } else {
+    rho = s0;
+    p = I.gm1 * (s3 - 0.5 * (m1 * (m1 / rho) + m2 * (m2 / rho)));
+  }
+}
+
 // Cell crossing time min(dx/(|u_x|+c), dy/(|u_y|+c)) of a conserved state in
 // the state's precision; `bad` flags a non-positive density or pressure, or
 // a NaN.
 template <class T>
-__device__ __forceinline__ T crossing_time(T r, T mx, T my, T E, const Phys<T>& P, bool& bad) {
+__device__ __forceinline__ T crossing_time(T s0, T s1, T s2, T s3, RowBase rb, const Phys<T>& P, bool& bad) {
   T W[4];
-  cons_to_prim(r, mx, my, E, P.gm1, W);
+  state_to_prim_b(s0, s1, s2, s3, rb, P.gm1, W);
   const T c = sqrt(P.gamma * W[3] / W[0]);
   const T wx = P.dx / (fabs(W[1]) + c);
   const T wy = P.dy / (fabs(W[2]) + c);
@@ -209,46 +267,23 @@ __global__ void __launch_bounds__(NTH) k_inject(const InstDev* __restrict__ inst
     const double vy = I.ncomp == 2 ? vi[cells + c] : vi[c];
     const double r0 = I.rho0[gy], p0 = I.p0[gy];
     T* Ui = U + 4 * I.cell_off;
-    const T u0 = (T)r0, u1 = (T)(r0 * vx), u2 = (T)(r0 * vy);
-    const T u3 = (T)(p0 / I.gm1 + 0.5 * r0 * (vx * vx + vy * vy));
+    // an FP32 state stores the deviation from the row's base (state_to_prim)
+    const double rb = sizeof(T) == 4 ? (double)I.rho0_f[gy] : 0.0;
+    const double pb = sizeof(T) == 4 ? (double)I.p0_f[gy] : 0.0;
+    const T u0 = (T)(r0 - rb), u1 = (T)(r0 * vx), u2 = (T)(r0 * vy);
+    const T u3 = (T)((p0 - pb) / I.gm1 + 0.5 * r0 * (vx * vx + vy * vy));
     Ui[c] = u0;
     Ui[cells + c] = u1;
     Ui[2 * cells + c] = u2;
     Ui[3 * cells + c] = u3;
     bool b = false;
-    const T cw = crossing_time<T>(u0, u1, u2, u3, P, b);
+    const T cw = crossing_time<T>(u0, u1, u2, u3, row_base<T>(I, gy), P, b);
     if (b) { bad = true; badc = c; } else if (cw < w) w = cw;
   }
   if (commit_crossing<T>(w, badc, bad, I, run, inst, red)) {
     run.t[inst] = 0.0;
     run.nstep[inst] = 0;
     if (record) finish_step<T>(I, run, inst, 0, 0.0);  // a replay keeps the recorded step 0
-  }
-}
-
-// Primitive state of cell (gx, gy) with the boundary conditions applied:
-// periodic x; y ghost rows mirror the interior (u_y negated) and, for the
-// hydrostatic boundary, extrapolate p_g = p_c + g_y rho_c (y_g - y_c).
-template <class T>
-__device__ __forceinline__ void load_prim(const T* __restrict__ Ui, const InstDev& I, long long cells, int gx,
-                                          int gy, const Phys<T>& P, T W[4]) {
-  gx = wrap_x(gx, I.nx);
-  int sy = gy, side = 0, k = 0;
-  if (gy < 0) { sy = -1 - gy; side = -1; k = -1 - gy; }
-  else if (gy >= I.ny) { sy = 2 * I.ny - 1 - gy; side = 1; k = gy - I.ny; }
-  if (sy < 0 || sy >= I.ny) {  // beyond the ghost layers any face uses: never read
-    W[0] = T(1); W[1] = T(0); W[2] = T(0); W[3] = T(1);
-    return;
-  }
-  const long long c = (long long)sy * I.nx + gx;
-  cons_to_prim(Ui[c], Ui[cells + c], Ui[2 * cells + c], Ui[3 * cells + c], P.gm1, W);
-  if (side != 0) {
-    W[2] = -W[2];
-    if (I.bc_y == 1) {
-      const T dyk = (T)((double)(2 * k + 1) * I.dy);
-      if (side < 0) W[3] = W[3] - P.g * W[0] * dyk;
-      else W[3] = W[3] + P.g * W[0] * dyk;
-    }
   }
 }
 
@@ -294,14 +329,27 @@ __device__ __forceinline__ void load_raw(const T* __restrict__ Ui, int nx, int n
   u[3] = Ui[3 * cells + c];
 }
 
-// Primitive state of row r from load_raw's values, with the y boundary
-// applied exactly as load_prim does.
+// Interior row whose base state row r uses: r itself, the row a ghost row
+// mirrors, or (rows beyond the ghost layers, which hold load_raw's
+// placeholder) the nearest interior row.
+__device__ __forceinline__ int base_row(int r, int ny) {
+  int sy = r;
+  if (r < 0) sy = -1 - r;
+  else if (r >= ny) sy = 2 * ny - 1 - r;
+  return sy < 0 ? 0 : (sy >= ny ? ny - 1 : sy);
+}
+
+// Primitive state of row r from load_raw's values and the base of
+// base_row(r), with the y boundary conditions applied: ghost rows mirror the
+// interior (u_y negated) and, for the hydrostatic boundary, extrapolate
+// p_g = p_c + g_y rho_c (y_g - y_c).
 template <class T>
-__device__ __forceinline__ void raw_to_prim(const T u[4], const InstDev& I, int r, const Phys<T>& P, T W[4]) {
-  cons_to_prim(u[0], u[1], u[2], u[3], P.gm1, W);
+__device__ __forceinline__ void raw_to_prim(const T u[4], const InstDev& I, int r, RowBase rb, const Phys<T>& P,
+                                            T W[4]) {
   int side = 0, k = 0;
   if (r < 0) { side = -1; k = -1 - r; }
   else if (r >= I.ny) { side = 1; k = r - I.ny; }
+  state_to_prim_b(u[0], u[1], u[2], u[3], rb, P.gm1, W);
   if (side != 0) {
     W[2] = -W[2];
     if (I.bc_y == 1) {
@@ -324,9 +372,15 @@ struct __align__(16) Q4 {
 
 template <class T, int EX, int EY, bool AOS = false>
 __device__ __forceinline__ void load_prim_tile(const T* __restrict__ Ui, const InstDev& I, long long cells, int gx0,
-                                               int gy0, const Phys<T>& P, T* __restrict__ sW) {
+                                               int gy0, const Phys<T>& P, T* __restrict__ sW,
+                                               RowBase* __restrict__ sRB) {
   constexpr int N = EX * EY;
   constexpr int PER = (N + NTH - 1) / NTH;
+  static_assert(EY <= NTH, "one thread per tile row fills the base table");
+  // FP32: the base of every tile row, loaded together with the state, stored
+  // once the state loads are issued and read back after the barrier
+  RowBase rbv{0.f, 0.f};
+  if (sizeof(T) == 4 && threadIdx.x < EY) rbv = row_base<T>(I, base_row(gy0 + threadIdx.x, I.ny));
   T u[PER][4];
   int rr[PER];
 #pragma unroll
@@ -339,13 +393,17 @@ __device__ __forceinline__ void load_prim_tile(const T* __restrict__ Ui, const I
       load_raw(Ui, I.nx, I.ny, cells, wrap_x(gx0 + ex, I.nx), rr[k], u[k]);
     }
   }
+  if (sizeof(T) == 4) {
+    if (threadIdx.x < EY) sRB[threadIdx.x] = rbv;
+    __syncthreads();
+  }
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
     const int e = threadIdx.x + k * NTH;
     if (e < N) {
       const int ey = e / EX, ex = e - ey * EX;
       T W[4];
-      raw_to_prim(u[k], I, rr[k], P, W);
+      raw_to_prim(u[k], I, rr[k], sizeof(T) == 4 ? sRB[ey] : RowBase{0.f, 0.f}, P, W);
       if (AOS) {
         Q4<T> c;
 #pragma unroll
@@ -396,10 +454,10 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS, 6) k_stage_sweep(const InstD
   T W0[4], W1[4], s_cur[4], Gb[4];
   {
     T Wa[4], Wb[4], WL[4], WR[4];
-    raw_to_prim(Ua, I, y0 - 2, P, Wa);
-    raw_to_prim(Ub, I, y0 - 1, P, Wb);
-    raw_to_prim(U0, I, y0, P, W0);
-    raw_to_prim(U1, I, y0 + 1, P, W1);
+    raw_to_prim(Ua, I, y0 - 2, row_base<T>(I, base_row(y0 - 2, ny)), P, Wa);
+    raw_to_prim(Ub, I, y0 - 1, row_base<T>(I, base_row(y0 - 1, ny)), P, Wb);
+    raw_to_prim(U0, I, y0, row_base<T>(I, base_row(y0, ny)), P, W0);
+    raw_to_prim(U1, I, y0 + 1, row_base<T>(I, base_row(y0 + 1, ny)), P, W1);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const T s_lo = limited_slope(Wa[q], Wb[q], W0[q], lim);
@@ -427,6 +485,7 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS, 6) k_stage_sweep(const InstD
         for (int k = 0; k < 4; ++k) B0[k] = T(0);
       }
     }
+    const RowBase rbj = row_base<T>(I, j);
     // x face on the left of this lane's cell in row j
     T Fl[4];
     {
@@ -445,7 +504,7 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS, 6) k_stage_sweep(const InstD
     for (int q = 0; q < 4; ++q) Fr[q] = shfl_down1(Fl[q]);
     // y face between rows j and j+1
     T W2[4], s_next[4], Gt[4];
-    raw_to_prim(U2, I, j + 2, P, W2);
+    raw_to_prim(U2, I, j + 2, row_base<T>(I, base_row(j + 2, ny)), P, W2);
     {
       T WL[4], WR[4];
 #pragma unroll
@@ -462,7 +521,7 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS, 6) k_stage_sweep(const InstD
       for (int k = 0; k < 4; ++k) {
         T b = U0[k] + sc.dtdx * (Fl[k] - Fr[k]);
         b = b + sc.dtdy * (Gb[k] - Gt[k]);
-        if (k == 2) b = b + sc.dt * (U0[0] * P.g);
+        if (k == 2) b = b + sc.dt * (state_rho(U0[0], rbj) * P.g);
         if (k == 3) b = b + sc.dt * (U0[2] * P.g);
         o[k] = STAGE == 2 ? T(0.5) * B0[k] + T(0.5) * b : b;
       }
@@ -470,7 +529,7 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS, 6) k_stage_sweep(const InstD
       for (int k = 0; k < 4; ++k) Di[k * cells + c] = o[k];
       if (STAGE == 2 && MODE == 0) {
         bool b = false;
-        const T cw = crossing_time<T>(o[0], o[1], o[2], o[3], P, b);
+        const T cw = crossing_time<T>(o[0], o[1], o[2], o[3], rbj, P, b);
         if (b) { bad = true; badc = c; } else if (cw < wmin) wmin = cw;
       }
     }
@@ -532,6 +591,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 6 : 1) k_stage_tile(cons
   Q4<T>* sF = sW + ST_EX * ST_EY;                  // [TY][TX+1]
   Q4<T>* sG = sF + ST_NFX;                         // [TY+1][TX]
   __shared__ T red[NTH / 32];
+  __shared__ RowBase sRB[ST_EY];
   const int4 tl = tiles[blockIdx.x];
   const int inst = tl.x;
   const InstDev& I = insts[inst];
@@ -543,7 +603,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 6 : 1) k_stage_tile(cons
   const T* Si = src + 4 * I.cell_off;
   const int x0 = tl.y, y0 = tl.z;
   const int lim = LIM >= 0 ? LIM : I.limiter;
-  load_prim_tile<T, ST_EX, ST_EY, true>(Si, I, cells, x0 - 2, y0 - 2, P, reinterpret_cast<T*>(sW));
+  load_prim_tile<T, ST_EX, ST_EY, true>(Si, I, cells, x0 - 2, y0 - 2, P, reinterpret_cast<T*>(sW), sRB);
   // stage 2 also needs U^n of this thread's cells in the update; their loads
   // are issued here so that the face work hides their latency
   constexpr int PASSES = TY / ROWS_PER_PASS;
@@ -604,6 +664,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 6 : 1) k_stage_tile(cons
     if (gx < I.nx && gy < I.ny) {
       const long long c = (long long)gy * I.nx + gx;
       const T u[4] = {Si[c], Si[cells + c], Si[2 * cells + c], Si[3 * cells + c]};
+      const RowBase rb = sizeof(T) == 4 ? sRB[ty + 2] : RowBase{0.f, 0.f};
       T o[4];
       const Q4<T> fl = sF[ty * (TX + 1) + tx], fr = sF[ty * (TX + 1) + tx + 1];
       const Q4<T> gd = sG[ty * TX + tx], gu = sG[(ty + 1) * TX + tx];
@@ -611,7 +672,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 6 : 1) k_stage_tile(cons
       for (int k = 0; k < 4; ++k) {
         T b = u[k] + sc.dtdx * (fl.v[k] - fr.v[k]);
         b = b + sc.dtdy * (gd.v[k] - gu.v[k]);
-        if (k == 2) b = b + sc.dt * (u[0] * P.g);
+        if (k == 2) b = b + sc.dt * (state_rho(u[0], rb) * P.g);
         if (k == 3) b = b + sc.dt * (u[2] * P.g);
         o[k] = b;
       }
@@ -624,7 +685,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 6 : 1) k_stage_tile(cons
       for (int k = 0; k < 4; ++k) Di[k * cells + c] = o[k];
       if (STAGE == 2 && MODE == 0) {
         bool b = false;
-        const T cw = crossing_time<T>(o[0], o[1], o[2], o[3], P, b);
+        const T cw = crossing_time<T>(o[0], o[1], o[2], o[3], rb, P, b);
         if (b) { bad = true; badc = c; } else if (cw < w) w = cw;
       }
     }
@@ -661,6 +722,7 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
   Q4<T>* sW = reinterpret_cast<Q4<T>*>(smem_raw);  // [AY][AX]
   Q4<T>* sK = sW + ADJ_AX * ADJ_AY;                // [KY][KX]
   Q4<T>* sB = sK + ADJ_KX * ADJ_KY;                // [4][ADJ_FACES]
+  __shared__ RowBase sRB[ADJ_AY];
   const int4 tl = tiles[blockIdx.x];
   const int inst = tl.x;
   const InstDev& I = insts[inst];
@@ -698,7 +760,7 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
 #pragma unroll
       for (int q = 0; q < 4; ++q) kv[k][q] = in ? Ki[q * cells + c] : T(0);
     }
-    load_prim_tile<T, ADJ_AX, ADJ_AY, true>(Ui, I, cells, x0 - 3, y0 - 3, P, reinterpret_cast<T*>(sW));
+    load_prim_tile<T, ADJ_AX, ADJ_AY, true>(Ui, I, cells, x0 - 3, y0 - 3, P, reinterpret_cast<T*>(sW), sRB);
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       const int e = threadIdx.x + k * NTH;
@@ -861,9 +923,10 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
 
 // Crossing times (x, y) of one conserved state, as crossing_time() computes them.
 template <class T>
-__device__ __forceinline__ void crossing_pair(T r, T mx, T my, T E, const Phys<T>& P, T& wx, T& wy) {
+__device__ __forceinline__ void crossing_pair(T s0, T s1, T s2, T s3, const InstDev& I, int row, const Phys<T>& P,
+                                              T& wx, T& wy) {
   T W[4];
-  cons_to_prim(r, mx, my, E, P.gm1, W);
+  state_to_prim(s0, s1, s2, s3, I, row, P.gm1, W);
   const T c = sqrt(P.gamma * W[3] / W[0]);
   wx = P.dx / (fabs(W[1]) + c);
   wy = P.dy / (fabs(W[2]) + c);
@@ -902,7 +965,7 @@ __global__ void __launch_bounds__(NTH) k_dt_partials(const InstDev* __restrict__
       }
       if (wmin > 0.0) {
         T wx, wy;
-        crossing_pair<T>(u[0], u[1], u[2], u[3], P, wx, wy);
+        crossing_pair<T>(u[0], u[1], u[2], u[3], I, gy, P, wx, wy);
         cnt += ((double)wx == wmin ? 1.0 : 0.0) + ((double)wy == wmin ? 1.0 : 0.0);
       }
     }
@@ -933,13 +996,14 @@ __global__ void __launch_bounds__(NTH) k_dt_apply(const InstDev* __restrict__ in
     const long long c = off + (long long)gy * I.nx + gx;
     const T r = U[c], mx = U[c + cells], my = U[c + 2 * cells], E = U[c + 3 * cells];
     T wx, wy;
-    crossing_pair<T>(r, mx, my, E, P, wx, wy);
+    crossing_pair<T>(r, mx, my, E, I, gy, P, wx, wy);
     const bool hx = (double)wx == wmin, hy = (double)wy == wmin;
     if (!hx && !hy) continue;
     // w = d / (|u_d| + c): dw = -d / (|u_d| + c)^2 (sign(u_d) du_d + dc), with
     // dc = gamma / (2 c rho) (dp - (p / rho) drho), p = (gamma-1)(E - |m|^2 / (2 rho))
-    const double rho = r, u = (double)mx / rho, v = (double)my / rho, gm1 = I.gm1;
-    const double p = gm1 * ((double)E - 0.5 * ((double)mx * u + (double)my * v));
+    double rho, p;
+    state_rho_p_f64(r, mx, my, E, I, gy, rho, p);
+    const double u = (double)mx / rho, v = (double)my / rho, gm1 = I.gm1;
     const double cs = sqrt(I.gamma * p / rho), q = I.gamma / (2.0 * cs * rho);
     double g[4] = {0.0, 0.0, 0.0, 0.0};
     for (int d = 0; d < 2; ++d) {
@@ -978,7 +1042,8 @@ __global__ void __launch_bounds__(NTH) k_objective(const InstDev* __restrict__ i
     const int gx = tl.y + e % TX, gy = tl.z + e / TX;
     if (gx >= I.nx || gy >= I.ny) continue;
     const long long c = (long long)gy * I.nx + gx;
-    const double r = (double)Si[c], mx = (double)Si[cells + c], my = (double)Si[2 * cells + c];
+    const double r = (double)Si[c] + (sizeof(T) == 4 ? (double)I.rho0_f[gy] : 0.0);
+    const double mx = (double)Si[cells + c], my = (double)Si[2 * cells + c];
     const double ek = 0.5 * (mx * mx + my * my) / r;
     const double a = ek - (I.ek0 ? I.ek0[c] : 0.0);
     ke += ek;
@@ -1016,7 +1081,8 @@ __global__ void __launch_bounds__(NTH) k_row_sums(const InstDev* __restrict__ in
   const T* U = slot_tab[nstep[r.x] & 1] + 4 * I.cell_off + (long long)r.y * I.nx;
   double sr = 0.0, sk = 0.0;
   for (int x = threadIdx.x; x < I.nx; x += NTH) {
-    const double rho = U[x], mx = U[cells + x], my = U[2 * cells + x];
+    const double rho = (double)U[x] + (sizeof(T) == 4 ? (double)I.rho0_f[r.y] : 0.0);
+    const double mx = U[cells + x], my = U[2 * cells + x];
     sr += rho;
     sk += 0.5 * (mx * mx + my * my) / rho;
   }

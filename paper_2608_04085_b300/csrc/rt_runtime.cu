@@ -71,6 +71,10 @@ struct rt_ctx {
   size_t esz = 8;          // bytes per state element
   size_t slot_bytes = 0;   // one state of every instance
   double* d_base = nullptr;  // rho0 / p0 of all instances
+  float* d_base_f = nullptr; // the same rounded to FP32: the base the FP32 state deviates from
+  std::vector<float> h_base_f;
+  long long base_rows = 0;   // rows of all instances (p0_f starts at d_base_f + base_rows)
+  std::vector<long long> row_off;
   double* d_ek0 = nullptr;   // baseline e_k (anomaly objective) or null
   double* d_ek = nullptr;    // e_k scratch
   void* sA = nullptr;        // forward ping-pong
@@ -1595,10 +1599,18 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
   } while (0)
   INIT_CU(cudaMalloc(&c->d_base, base.size() * sizeof(double)));
   INIT_CU(cudaMemcpy(c->d_base, base.data(), base.size() * sizeof(double), cudaMemcpyHostToDevice));
+  c->h_base_f.assign(base.begin(), base.end());
+  c->base_rows = rows;
+  INIT_CU(cudaMalloc(&c->d_base_f, base.size() * sizeof(float)));
+  INIT_CU(cudaMemcpy(c->d_base_f, c->h_base_f.data(), base.size() * sizeof(float), cudaMemcpyHostToDevice));
   roff = 0;
+  c->row_off.resize(N);
   for (int i = 0; i < N; ++i) {
+    c->row_off[i] = roff;
     c->h_inst[i].rho0 = c->d_base + roff;
     c->h_inst[i].p0 = c->d_base + rows + roff;
+    c->h_inst[i].rho0_f = c->d_base_f + roff;
+    c->h_inst[i].p0_f = c->d_base_f + rows + roff;
     roff += c->prob[i].ny;
   }
   INIT_CU(cudaMalloc(&c->d_inst, N * sizeof(InstDev)));
@@ -1665,7 +1677,7 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
 
 void rt_destroy(rt_ctx* c) {
   if (!c) return;
-  void* ptrs[] = {c->d_inst, c->d_tiles, c->d_strips, c->d_base, c->d_ek0, c->d_ek, c->sA, c->sB, c->sU1, c->lA, c->lB,
+  void* ptrs[] = {c->d_inst, c->d_tiles, c->d_strips, c->d_base, c->d_base_f, c->d_ek0, c->d_ek, c->sA, c->sB, c->sU1, c->lA, c->lB,
                   c->l1, c->d_tab, c->run.dtrec, c->run.wrec, c->d_blast, c->d_coef, c->run.dtc, c->run.counter, c->run.t, c->run.nstep, c->run.wmin, c->run.status,
                   c->run.bad_cell, c->d_partials, c->d_sums, c->d_scal, c->d_v, c->d_g, c->d_w1, c->d_w2,
                   c->d_w3, c->d_w4, c->d_pairs, c->d_rows, c->d_rowsum, c->d_sample};
@@ -1920,6 +1932,18 @@ rt_status rt_get_state(rt_ctx* c, int inst, double* out) {
     CU(cudaMemcpyAsync(f.data(), src, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     for (size_t k = 0; k < n; ++k) out[k] = f[k];
+    // the FP32 state holds the deviation from the row's base state: add
+    // rho0 to the density and p0/(gamma-1) to the energy
+    const size_t cells = (size_t)P.nx * P.ny;
+    const float* rb = c->h_base_f.data() + c->row_off[inst];
+    const float* pb = rb + c->base_rows;
+    const double gm1 = P.gamma - 1.0;
+    for (int y = 0; y < P.ny; ++y)
+      for (int x = 0; x < P.nx; ++x) {
+        const size_t k = (size_t)y * P.nx + x;
+        out[k] += (double)rb[y];
+        out[3 * cells + k] += (double)pb[y] / gm1;
+      }
   }
   return RT_OK;
 }

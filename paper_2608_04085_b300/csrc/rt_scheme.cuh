@@ -103,6 +103,19 @@ __device__ __forceinline__ void hllc(T rL, T uL, T vL, T pL, T rR, T uR, T vR, T
   F[2] = f0 * v;
   F[3] = u * (E + p);
   if (star) {
+    if constexpr (sizeof(T) == 4) {
+      // FP32: S (U* - U) written with q = rho*/rho - 1 = (S* - u) / (S - S*),
+      // U* - U = q (rho, rho S, rho v, E + p + m S*): the same values as the
+      // textbook form below (which FP64 keeps, in the oracle's order), without
+      // forming rho* - rho and E* - E as small differences of O(1) numbers
+      const T q = (Ss - u) / (S - Ss);
+      const T rq = r * q;
+      F[0] = F[0] + S * rq;
+      F[1] = F[1] + S * (rq * S);
+      F[2] = F[2] + S * (rq * v);
+      F[3] = F[3] + S * (q * ((E + p) + m * Ss));
+      return;
+    }
     const T fac = m / (S - Ss);
     const T us3 = fac * (E / r + (Ss - u) * (Ss + p / m));
     F[0] = F[0] + S * (fac - r);

@@ -5,7 +5,7 @@ steps), where the CPU oracle is too slow to run the whole horizon.
   grid; the FP64 GPU state and dt sequence must match bitwise.
 - Properties at full size: the FP32-state path in the benchmark's launch
   configuration (32 instances, sqrt(N) checkpointing) gives J within 1e-4 of
-  the FP64 GPU path; the FP64 gradient matches central differences of the
+  the FP64 GPU path for noise, localised and single-mode seeds; the FP64 gradient matches central differences of the
   FP64 forward (dt frozen) along seeded directions; the FP32 gradient has
   cosine >= 0.999 with the FP64 gradient.
 """
@@ -36,14 +36,11 @@ def test_full_grid_first_steps_bitwise_against_oracle():
 
 def test_full_horizon_fp32_batch_J_against_fp64():
     """FP32 state in the benchmark's launch configuration (32 instances) vs
-    the FP64 path at T = 2 (about 4870 steps).
-
-    A growing perturbation (a single Rayleigh-Taylor mode, the kind of seed
-    the CNOP converges to) keeps J within 1e-4. The benchmark's i.i.d.
-    grid-scale noise decays by about 160x in kinetic energy over the horizon,
-    and FP32 rounding of the O(1) background state is then about 3e-3
-    relative to what remains; that measured error is kept as a regression
-    bound (5e-3), not as the tolerance."""
+    the FP64 path at T = 2 (about 4870 steps): J within 1e-4 for the
+    benchmark's i.i.d. grid-scale noise (which loses about 160x of its kinetic
+    energy over the horizon, so J is a small remainder), for a localised
+    random start and for a growing single Rayleigh-Taylor mode (the kind of
+    seed the CNOP converges to)."""
     import math
     import oracle
     import paper_2608_04085_b300 as rt
@@ -54,16 +51,17 @@ def test_full_horizon_fp32_batch_J_against_fp64():
     k = 2 * math.pi * 8 / (w.x1 - w.x0)
     mode = np.cos(k * x)[None, :] * np.exp(-k * np.abs(y))[:, None]
     xi[3] = np.stack([0 * mode, mode])
+    xi[4] = oracle.random_start(w, xi[4], 0.1 * (w.y1 - w.y0), 1e-4)
     with rt.Context([w] * batch, precision=rt.RT_FP32_STATE, ckpt=rt.RT_CKPT_SQRT) as c32:
         v = c32.project(xi.reshape(-1), 1e-4, to_budget=True)
         J32, _, st = c32.forward(v)
     assert st["steps"] > 4000
     n = w.ncomp * w.nx * w.ny
-    with rt.Context([w, w], precision=rt.RT_FP64) as c64:
-        J64, _, _ = c64.forward(np.concatenate([v[3 * n:4 * n], v[5 * n:6 * n]]))
-    rel = np.abs(J32[[3, 5]] - J64) / np.abs(J64)
-    assert rel[0] <= 1e-4, rel
-    assert rel[1] <= 5e-3, rel
+    pick = [0, 3, 4, 5, 31]
+    with rt.Context([w] * len(pick), precision=rt.RT_FP64) as c64:
+        J64, _, _ = c64.forward(np.concatenate([v[i * n:(i + 1) * n] for i in pick]))
+    rel = np.abs(J32[pick] - J64) / np.abs(J64)
+    assert np.all(rel <= 1e-4), rel
 
 
 def test_full_horizon_gradients_fd_and_fp32_cosine():
