@@ -98,7 +98,10 @@ typedef struct {
 } rt_problem;
 
 typedef struct {
-  int precision;            /* RT_FP64, or RT_FP32_STATE: FP32 state with FP64 reductions */
+  int precision;            /* RT_FP64, or RT_FP32_STATE: FP32 state with FP64 reductions.
+                               The FP32 state holds each cell's deviation from the
+                               hydrostatic base state of its row, so that its rounding is
+                               relative to the perturbation, not to the O(1) background */
   int ckpt;                 /* RT_CKPT_AUTO | RT_CKPT_STORE_ALL | RT_CKPT_SQRT | RT_CKPT_REVOLVE;
                                AUTO takes the first that fits the cap in that order */
   double ckpt_hbm_cap_bytes;/* cap on checkpoint + segment memory; 0 = 60% of free memory.
@@ -191,7 +194,8 @@ rt_status rt_constraint(rt_ctx* ctx, const double* v, int flags, double* C_out);
 rt_status rt_project(rt_ctx* ctx, double* v, int flags, const double* eps, int to_budget);
 
 /* Final conserved state (rho, m_x, m_y, E) of instance i after the last
- * forward run, as FP64 [4][ny][nx] into a host array. */
+ * forward run, as FP64 [4][ny][nx] into a host array (for an FP32 state, the
+ * stored deviation plus the FP32-rounded base state, summed in FP64). */
 rt_status rt_get_state(rt_ctx* ctx, int inst, double* out);
 
 /* dt sequence of instance i recorded by the last run; *n_out = its length.
