@@ -103,16 +103,51 @@ def horizon_sweep(Ts=(1.0, 2.0, 4.0), iters=50, seed=0, eps=1e-4, method=None, p
     return out
 
 
+def precision_comparison(nx=1024, ny=3072, T=6.0, iters=20, seed=0, eps=1e-4, method=None, ckpt_cap_gb=40.0):
+    """CNOP of one RT box in FP32 state and in FP64 from the same seeded
+    i.i.d. (v_x, v_y) start (C = eps), revolve checkpointing under a memory
+    cap, the spectral projected gradient by default: the relative error of
+    the FP32 J(T) of the FP64 CNOP, the FP32 CNOP's J against the FP64 one,
+    and the cosine of the two CNOPs. Defaults: the 1024x3072, T = 6 box."""
+    import time
+    import rt_inputs
+    from . import RT_CKPT_REVOLVE, RT_CNOP_SPG
+    method = RT_CNOP_SPG if method is None else method
+    w = rt_inputs.rt_box(nx, ny, T=float(T))
+    xi = rt_inputs.gaussian_field(seed, w.ncomp, w.ny, w.nx).ravel()
+    out = {"grid": [nx, ny], "T": float(T), "iterations": iters, "eps": eps, "runs": {}}
+    v = {}
+    for name, prec in (("fp32", RT_FP32_STATE), ("fp64", RT_FP64)):
+        t0 = time.perf_counter()
+        with Context([w], precision=prec, ckpt=RT_CKPT_REVOLVE, ckpt_cap_bytes=ckpt_cap_gb * 1e9) as ctx:
+            v[name], J, res = ctx.cnop(xi, eps, iters, method=method)
+            _, _, st = ctx.forward(v[name])
+        out["runs"][name] = {"J": float(J[0]), "J_start": float(res["J_history"][0, 0]), "steps": int(st["steps"]),
+                             "iterations": int(res["iterations"]), "seconds": time.perf_counter() - t0}
+    with Context([w], precision=RT_FP32_STATE) as c32:
+        J32_of_v64 = float(c32.forward(v["fp64"])[0][0])
+    a, b = v["fp32"], v["fp64"]
+    J64 = out["runs"]["fp64"]["J"]
+    out["rel_err_J_fp32_at_fp64_cnop"] = abs(J32_of_v64 - J64) / abs(J64)
+    out["rel_diff_J_cnop"] = abs(out["runs"]["fp32"]["J"] - J64) / abs(J64)
+    out["cnop_cosine"] = float(np.dot(a, b) / (np.linalg.norm(a) * np.linalg.norm(b)))
+    return out
+
+
 if __name__ == "__main__":
     import argparse
     import json
     ap = argparse.ArgumentParser(description="the paper's CNOP runs on synthetic random starts")
-    ap.add_argument("--run", default="T2_N128", choices=sorted(PAPER_RUNS) + ["horizons"])
+    ap.add_argument("--run", default="T2_N128", choices=sorted(PAPER_RUNS) + ["horizons", "precision"])
+    ap.add_argument("--T", type=float, default=None)
     ap.add_argument("--iters", type=int, default=None)
     ap.add_argument("--seeds", type=int, default=4)
     a = ap.parse_args()
     if a.run == "horizons":
         print(json.dumps(horizon_sweep(iters=50 if a.iters is None else a.iters)), flush=True)
+    elif a.run == "precision":
+        print(json.dumps(precision_comparison(T=6.0 if a.T is None else a.T,
+                                              iters=20 if a.iters is None else a.iters)), flush=True)
     else:
         print(json.dumps(paper_run(a.run, seeds=tuple(range(a.seeds)), iters=a.iters)), flush=True)
 

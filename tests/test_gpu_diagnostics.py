@@ -120,3 +120,16 @@ def test_horizon_sweep_driver_short():
         assert h["J_cnop"] > h["J_start"] > 0
         assert h["J_random"] == h["J_start"]
         assert np.isfinite(h["J_5modes"]) and h["J_5modes"] > 0
+
+
+def test_precision_comparison_driver_short():
+    """The FP32-vs-FP64 CNOP driver (revolve checkpointing) on a small box:
+    both CNOPs rise above their common start, J of the FP64 CNOP evaluated
+    in FP32 is within 1e-4, and the two CNOPs point the same way."""
+    from paper_2608_04085_b300.experiments import precision_comparison
+    out = precision_comparison(nx=64, ny=192, T=0.2, iters=3, ckpt_cap_gb=0.005)
+    r = out["runs"]
+    assert r["fp32"]["J"] > r["fp32"]["J_start"] and r["fp64"]["J"] > r["fp64"]["J_start"]
+    assert abs(r["fp32"]["steps"] - r["fp64"]["steps"]) <= 1
+    assert out["rel_err_J_fp32_at_fp64_cnop"] <= 1e-4
+    assert out["cnop_cosine"] >= 0.999
