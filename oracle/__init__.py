@@ -93,6 +93,7 @@ def lib():
         L.o_tangent_dt.restype = ctypes.c_int
         L.o_gradient_dt.argtypes = [pp, dp, ctypes.c_int, dp, dp, dp]
         L.o_gradient_dt.restype = ctypes.c_int
+        L.o_forward_signature.argtypes = [pp, dp, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_ulonglong)]
         _lib = L
     return _lib
 
@@ -171,6 +172,17 @@ def forward(w, v, dt_replay=None, ek0=None, max_steps=400000):
                         _ptr(None if ek0 is None else _f64(ek0)), _ptr(U), _ptr(ek), _ptr(J))
     dt = rep.copy() if rep is not None else dts[:n].copy()
     return {"U": U, "ek": ek, "J_ke": J[0], "J_pap": J[1], "dt": dt, "nsteps": n}
+
+
+def branch_signature(w, v, dt_replay):
+    """(hash, count) of every kink decision (limiter pick, Davis speed
+    min/max, HLLC branch) of the forward run from v with the frozen step
+    sequence dt_replay. Equal signatures at v + h d and v - h d mean the
+    central difference along d straddles no kink."""
+    dt = _f64(dt_replay)
+    sig = (ctypes.c_ulonglong * 2)()
+    lib().o_forward_signature(ctypes.byref(_params(w)), _ptr(_f64(v)), _ptr(dt), len(dt), sig)
+    return int(sig[0]), int(sig[1])
 
 
 def objective_value(w, out):

@@ -16,6 +16,9 @@
 //   * tangent (forward-mode dual numbers) and reverse-mode gradient with the
 //     time step frozen; the reverse uses local flux Jacobians obtained by
 //     forward-mode dual numbers, transposed face by face             [Sec. 3.4]
+//   * branch signature of a forward run (a test aid): which side of every
+//     kink (limiter pick, Davis speed min/max, HLLC branch) each evaluation
+//     took, so that finite differences straddling a kink can be told apart
 // Built with -O2 -ffp-contract=off so that every expression rounds exactly as
 // written; the evaluation order of each expression is part of the scheme
 // definition (the CUDA FP64 path evaluates the same expressions).
@@ -41,6 +44,19 @@ enum { O_BC_REFLECT = 0, O_BC_HYDROSTATIC = 1 };
 enum { O_LIM_MINMOD = 0, O_LIM_MC = 1, O_LIM_NONE = 2 };
 enum { O_OBJ_KE = 0, O_OBJ_PAPER = 1 };
 static const int H = 2;  // ghost layers needed by PLM
+
+// Branch signature (o_forward_signature only): every kink decision of the
+// scheme, as a small code, folded in evaluation order into a 64-bit FNV-1a
+// hash. Off everywhere else; the oracle runs single-threaded.
+static bool g_sig_on = false;
+static unsigned long long g_sig = 0;
+static long long g_sig_n = 0;
+static inline void sig_add(int code) {
+  if (!g_sig_on) return;
+  g_sig ^= (unsigned long long)(unsigned)code;
+  g_sig *= 1099511628211ull;
+  ++g_sig_n;
+}
 
 // ---------------------------------------------------------------- dual numbers
 template <int N> struct Dual {
@@ -156,13 +172,23 @@ template <class R> inline R limited_slope(const R& qm, const R& q0, const R& qp,
   R dm = q0 - qm, dp = qp - q0;
   if (lim == O_LIM_NONE) return 0.5 * (dm + dp);
   if (lim == O_LIM_MINMOD) {
-    if (val(dm) > 0.0 && val(dp) > 0.0) return val(dm) <= val(dp) ? dm : dp;
-    if (val(dm) < 0.0 && val(dp) < 0.0) return val(dm) >= val(dp) ? dm : dp;
+    if (val(dm) > 0.0 && val(dp) > 0.0) { sig_add(val(dm) <= val(dp) ? 1 : 2); return val(dm) <= val(dp) ? dm : dp; }
+    if (val(dm) < 0.0 && val(dp) < 0.0) { sig_add(val(dm) >= val(dp) ? 3 : 4); return val(dm) >= val(dp) ? dm : dp; }
+    sig_add(5);
     return R(0.0);
   }
   R a = 2.0 * dm, c = 0.5 * (dm + dp), b = 2.0 * dp;
-  if (val(dm) > 0.0 && val(dp) > 0.0) { R s = val(a) <= val(c) ? a : c; return val(s) <= val(b) ? s : b; }
-  if (val(dm) < 0.0 && val(dp) < 0.0) { R s = val(a) >= val(c) ? a : c; return val(s) >= val(b) ? s : b; }
+  if (val(dm) > 0.0 && val(dp) > 0.0) {
+    R s = val(a) <= val(c) ? a : c;
+    sig_add(6 + (val(a) <= val(c) ? 0 : 1) + (val(s) <= val(b) ? 0 : 2));
+    return val(s) <= val(b) ? s : b;
+  }
+  if (val(dm) < 0.0 && val(dp) < 0.0) {
+    R s = val(a) >= val(c) ? a : c;
+    sig_add(10 + (val(a) >= val(c) ? 0 : 1) + (val(s) >= val(b) ? 0 : 2));
+    return val(s) >= val(b) ? s : b;
+  }
+  sig_add(14);
   return R(0.0);
 }
 
@@ -198,14 +224,16 @@ template <class R> inline void hllc(const R L[4], const R Rr[4], double gamma, d
   R SL = val(aL) <= val(aR) ? aL : aR;
   R bL = uL + cL, bR = uR + cR;
   R SR = val(bL) >= val(bR) ? bL : bR;
+  sig_add(20 + (val(aL) <= val(aR) ? 0 : 1) + (val(bL) >= val(bR) ? 0 : 2));
   R EL = pL / gm1 + 0.5 * rL * (uL * uL + vL * vL);
   R ER = pR / gm1 + 0.5 * rR * (uR * uR + vR * vR);
   R dL = SL - uL, dR = SR - uR;
   R mL = rL * dL, mR = rR * dR;
   R Ss = ((pR - pL) + uL * mL - uR * mR) / (mL - mR);
-  if (val(SL) >= 0.0) { phys_flux(rL, uL, vL, pL, EL, F); return; }
-  if (val(Ss) >= 0.0) { star_flux(rL, uL, vL, pL, EL, SL, Ss, mL, F); return; }
-  if (val(SR) >= 0.0) { star_flux(rR, uR, vR, pR, ER, SR, Ss, mR, F); return; }
+  if (val(SL) >= 0.0) { sig_add(30); phys_flux(rL, uL, vL, pL, EL, F); return; }
+  if (val(Ss) >= 0.0) { sig_add(31); star_flux(rL, uL, vL, pL, EL, SL, Ss, mL, F); return; }
+  if (val(SR) >= 0.0) { sig_add(32); star_flux(rR, uR, vR, pR, ER, SR, Ss, mR, F); return; }
+  sig_add(33);
   phys_flux(rR, uR, vR, pR, ER, F);
 }
 
@@ -459,6 +487,25 @@ extern "C" int o_forward(const OParams* P, const double* v, const double* dt_rep
         ek_out[(size_t)j * G.nx + i] = ek_cell(U[G.at(0, j, i)], U[G.at(1, j, i)], U[G.at(2, j, i)]);
   objectives(*P, U, ek0, J[0], J[1]);
   return n;
+}
+
+// Branch signature of the forward run from v with the frozen step sequence
+// dt_replay: sig[0] = the hash of every kink decision in evaluation order,
+// sig[1] = the number of decisions. Two runs with equal signatures took the
+// same branch at every kink, so J is smooth between them.
+extern "C" void o_forward_signature(const OParams* P, const double* v, const double* dt_replay, int n_replay,
+                                    unsigned long long* sig) {
+  const Grid G(*P);
+  std::vector<double> rho0(G.ny), p0(G.ny), U;
+  o_base_state(P, rho0.data(), p0.data());
+  inject(*P, rho0.data(), p0.data(), v, U);
+  g_sig = 1469598103934665603ull;
+  g_sig_n = 0;
+  g_sig_on = true;
+  for (int n = 0; n < n_replay; ++n) rk2_step(*P, U, dt_replay[n]);
+  g_sig_on = false;
+  sig[0] = g_sig;
+  sig[1] = (unsigned long long)g_sig_n;
 }
 
 // Directional derivative of J along dv (frozen dt sequence): forward mode.
