@@ -8,6 +8,11 @@
 // the next step's constants, so the kernels do no FP64 arithmetic per cell
 // and the host never reads dt inside the time loop.
 //
+// An FP64 state slot holds U; an FP32 slot holds U - U_b(y), the deviation
+// from the hydrostatic base U_b = (rho0, 0, 0, p0/(gamma-1)) of the cell's
+// row (state_to_prim adds the base back), so FP32 rounding is relative to the
+// perturbation rather than to the O(1) background. Both run the same scheme.
+//
 //   k_inject     Sec. 3.1: U0 = (rho0, rho0 v, p0/(gamma-1) + rho0|v|^2/2), first CFL minimum
 //   k_stage_*<1> U1 = U + dt L(U)                       (SSP-RK2 stage 1)
 //   k_stage_*<2> U' = U/2 + (U1 + dt L(U1))/2           (stage 2) + CFL minimum of U'
