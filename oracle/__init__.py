@@ -60,13 +60,15 @@ class OParams(ctypes.Structure):
                 ("bc_y", ctypes.c_int), ("limiter", ctypes.c_int),
                 ("cfl", ctypes.c_double), ("T", ctypes.c_double),
                 ("nsteps", ctypes.c_int), ("ncomp", ctypes.c_int),
-                ("objective", ctypes.c_int)]
+                ("objective", ctypes.c_int), ("flux", ctypes.c_int),
+                ("flux_theta", ctypes.c_double)]
 
 
 def _params(w) -> OParams:
     return OParams(w.nx, w.ny, w.x0, w.x1, w.y0, w.y1, w.gamma, w.g_y,
                    w.rho_heavy, w.rho_light, w.y_int, w.h_s, w.p_ref, w.y_ref,
-                   w.bc_y, w.limiter, w.cfl, w.T, w.nsteps, w.ncomp, w.objective)
+                   w.bc_y, w.limiter, w.cfl, w.T, w.nsteps, w.ncomp, w.objective,
+                   getattr(w, "flux", 0), getattr(w, "flux_theta", 2.0))
 
 
 def lib():

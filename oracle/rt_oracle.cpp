@@ -10,7 +10,8 @@
 //   * base state: tanh density profile and hydrostatic pressure   [Sec. 2.2, Eq. rho0]
 //   * inject: U0 = (rho0, rho0 v, p0/(gamma-1) + rho0 |v|^2 / 2)   [Sec. 3.1; Eq. total_energy]
 //   * one SSP-RK2 step of a finite-volume Godunov scheme: PLM on
-//     primitive variables, HLLC fluxes, gravity source            [Sec. 2.1 Eqs. mass/momentum/energy; Sec. 2.3]
+//     primitive variables, HLLC fluxes (or HLL, or the HLLC/HLL hybrid
+//     switched by the face pressure ratio), gravity source       [Sec. 2.1 Eqs. mass/momentum/energy; Sec. 2.3]
 //   * CFL time step and horizon clipping (scheme fixed by the workload, Sec. 2.3 leaves it open)
 //   * objectives: total kinetic energy, and the squared e_k anomaly  [Sec. 3.1, Eqs. ke, objective]
 //   * tangent (forward-mode dual numbers) and reverse-mode gradient with the
@@ -37,12 +38,15 @@ struct OParams {
   int bc_y, limiter;
   double cfl, T;
   int nsteps, ncomp, objective;
+  int flux;           // O_FLUX_HLLC | O_FLUX_HLL | O_FLUX_HYBRID
+  double flux_theta;  // hybrid: HLL where one face pressure exceeds flux_theta times the other
 };
 }
 
 enum { O_BC_REFLECT = 0, O_BC_HYDROSTATIC = 1 };
 enum { O_LIM_MINMOD = 0, O_LIM_MC = 1, O_LIM_NONE = 2 };
 enum { O_OBJ_KE = 0, O_OBJ_PAPER = 1 };
+enum { O_FLUX_HLLC = 0, O_FLUX_HLL = 1, O_FLUX_HYBRID = 2 };
 static const int H = 2;  // ghost layers needed by PLM
 
 // Branch signature (o_forward_signature only): every kink decision of the
@@ -237,6 +241,46 @@ template <class R> inline void hllc(const R L[4], const R Rr[4], double gamma, d
   phys_flux(rR, uR, vR, pR, ER, F);
 }
 
+// HLL Riemann flux (Harten, Lax & van Leer) with the same Davis wave speeds,
+// rotated frame: F_L where S_L >= 0, F_R where S_R < 0, otherwise the
+// single-state average (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L).
+template <class R> inline void hll(const R L[4], const R Rr[4], double gamma, double gm1, R F[4]) {
+  const R &rL = L[0], &uL = L[1], &vL = L[2], &pL = L[3];
+  const R &rR = Rr[0], &uR = Rr[1], &vR = Rr[2], &pR = Rr[3];
+  R cL = sqrt(gamma * pL / rL);
+  R cR = sqrt(gamma * pR / rR);
+  R aL = uL - cL, aR = uR - cR;
+  R SL = val(aL) <= val(aR) ? aL : aR;
+  R bL = uL + cL, bR = uR + cR;
+  R SR = val(bL) >= val(bR) ? bL : bR;
+  sig_add(20 + (val(aL) <= val(aR) ? 0 : 1) + (val(bL) >= val(bR) ? 0 : 2));
+  R EL = pL / gm1 + 0.5 * rL * (uL * uL + vL * vL);
+  R ER = pR / gm1 + 0.5 * rR * (uR * uR + vR * vR);
+  R FL[4], FR[4];
+  phys_flux(rL, uL, vL, pL, EL, FL);
+  phys_flux(rR, uR, vR, pR, ER, FR);
+  if (val(SL) >= 0.0) { sig_add(34); for (int k = 0; k < 4; ++k) F[k] = FL[k]; return; }
+  if (!(val(SR) >= 0.0)) { sig_add(36); for (int k = 0; k < 4; ++k) F[k] = FR[k]; return; }
+  sig_add(35);
+  const R UL[4] = {rL, rL * uL, rL * vL, EL};
+  const R UR[4] = {rR, rR * uR, rR * vR, ER};
+  const R D = SR - SL, SLR = SL * SR;
+  for (int k = 0; k < 4; ++k) F[k] = ((SR * FL[k] - SL * FR[k]) + SLR * (UR[k] - UL[k])) / D;
+}
+
+// Riemann flux of a face: HLLC, HLL, or the hybrid, which takes HLL where the
+// two face pressures differ by more than the factor flux_theta (a strong
+// jump, where HLLC's contact resolution is not wanted) and HLLC elsewhere.
+template <class R> inline void riemann_flux(const R L[4], const R Rr[4], const OParams& P, R F[4]) {
+  bool use_hll = P.flux == O_FLUX_HLL;
+  if (P.flux == O_FLUX_HYBRID) {
+    use_hll = val(L[3]) > P.flux_theta * val(Rr[3]) || val(Rr[3]) > P.flux_theta * val(L[3]);
+    sig_add(40 + (use_hll ? 1 : 0));
+  }
+  if (use_hll) hll(L, Rr, P.gamma, P.gamma - 1.0, F);
+  else hllc(L, Rr, P.gamma, P.gamma - 1.0, F);
+}
+
 // Flux through the face between cells a and b along direction dir (0 = x,
 // 1 = y), from the primitive states of cells a-1, a, b, b+1.
 template <class R> inline void face_flux(const R* Wm, const R* Wa, const R* Wb, const R* Wp, int dir,
@@ -252,7 +296,7 @@ template <class R> inline void face_flux(const R* Wm, const R* Wa, const R* Wb, 
   R L[4] = {WL[0], WL[n], WL[t], WL[3]};
   R Rr[4] = {WR[0], WR[n], WR[t], WR[3]};
   R f[4];
-  hllc(L, Rr, P.gamma, P.gamma - 1.0, f);
+  riemann_flux(L, Rr, P, f);
   F[0] = f[0]; F[n] = f[1]; F[t] = f[2]; F[3] = f[3];
 }
 

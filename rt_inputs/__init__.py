@@ -20,6 +20,7 @@ LIM_MINMOD, LIM_MC, LIM_NONE = 0, 1, 2
 PERT_VY, PERT_VXVY = 1, 2          # number of perturbed velocity components
 OBJ_KE, OBJ_EK_ANOMALY_L2 = 0, 1
 FP64, FP32_STATE = 0, 1
+FLUX_HLLC, FLUX_HLL, FLUX_HYBRID = 0, 1, 2
 
 
 @dataclasses.dataclass
@@ -46,6 +47,8 @@ class Workload:
     nsteps: int = 0                 # > 0: fixed step count, T ignored
     ncomp: int = PERT_VXVY
     objective: int = OBJ_KE
+    flux: int = FLUX_HLLC
+    flux_theta: float = 2.0         # hybrid: HLL where the face pressure ratio exceeds this
 
     def replace(self, **kw) -> "Workload":
         return dataclasses.replace(self, **kw)

@@ -12,6 +12,9 @@ CASES = {
     "box_mc_ke_vy": I.rt_box(12, 36, nsteps=30, limiter=I.LIM_MC, ncomp=I.PERT_VY),
     "paper_hydro_pap": I.paper_unit_square(16, 0.0).replace(nsteps=30, ny=20),
     "box_none_horizon": I.rt_box(10, 30, nsteps=0, T=0.15, limiter=I.LIM_NONE),
+    "box_hll_ke": I.rt_box(12, 36, nsteps=30, flux=I.FLUX_HLL),
+    # theta close to 1: both branches of the switch occur
+    "box_hybrid_ke": I.rt_box(12, 36, nsteps=30, flux=I.FLUX_HYBRID, flux_theta=1.0001),
 }
 
 

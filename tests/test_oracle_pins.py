@@ -134,11 +134,72 @@ def test_sod_along_x_periodic_pair(oracle_lib):
     assert np.max(np.abs(r[0] - r[0, ::-1])) < 1e-12
 
 
+def _riemann_y(oracle_lib, ny, left, right, **kw):
+    """1D Riemann problem along y (g = 0, reflecting walls, two identical
+    columns) to t = 0.2; left/right = (rho, v, p)."""
+    g = 1.4
+    w = I.Workload(nx=2, ny=ny, x0=0.0, x1=2.0 / ny, y0=0.0, y1=1.0, g_y=0.0, T=0.2, nsteps=0, cfl=0.4, **kw)
+    _, y = oracle_lib.cell_centres(w)
+    lo = y < 0.5
+    col = lambda a, b: np.where(lo, a, b)[:, None] * np.ones((1, 2))
+    rho, v, p = (col(left[k], right[k]) for k in range(3))
+    U0 = _cons(rho, np.zeros_like(rho), v, p, g)
+    U, _ = oracle_lib.run_state(w, U0)
+    return w, y, U0, U
+
+
+@pytest.mark.parametrize("flux", [I.FLUX_HLL, I.FLUX_HYBRID])
+def test_sod_with_hll_and_hybrid_converges_to_exact(oracle_lib, flux):
+    """HLL and the HLLC/HLL hybrid (Sec. 2.3's "hybrid HLLC", read as HLL at
+    strong pressure jumps): the L1 density error of Sod against the exact
+    Riemann solution falls under refinement, and HLL's is at least HLLC's
+    (it smears the contact that HLLC resolves)."""
+    errs, errs_hllc = [], []
+    for ny in (100, 200, 400):
+        w, y, _, U = _riemann_y(oracle_lib, ny, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1), flux=flux)
+        r = _prim(U, 1.4)[0]
+        ex = riemann_exact.sample((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4, (y - 0.5) / 0.2)
+        errs.append(np.mean(np.abs(r[:, 0] - ex[0])))
+        _, _, _, Uc = _riemann_y(oracle_lib, ny, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1))
+        errs_hllc.append(np.mean(np.abs(_prim(Uc, 1.4)[0][:, 0] - ex[0])))
+    assert errs[1] < 0.8 * errs[0] and errs[2] < 0.8 * errs[1], errs
+    assert errs[2] < 1e-2, errs
+    if flux == I.FLUX_HLL:
+        assert all(a > b for a, b in zip(errs, errs_hllc)), (errs, errs_hllc)
+
+
+def test_stationary_contact_exact_with_hllc_smeared_with_hll(oracle_lib):
+    """A stationary contact (density jump, uniform pressure, no flow): HLLC
+    keeps it to rounding, HLL diffuses it (Toro, Sec. 10.4); the hybrid sees
+    no pressure jump and behaves as HLLC."""
+    out = {}
+    for flux in (I.FLUX_HLLC, I.FLUX_HLL, I.FLUX_HYBRID):
+        _, _, U0, U = _riemann_y(oracle_lib, 100, (1.0, 0.0, 1.0), (0.5, 0.0, 1.0), flux=flux)
+        out[flux] = np.max(np.abs(U[0] - U0[0]))
+    assert out[I.FLUX_HLLC] <= 1e-12, out
+    assert out[I.FLUX_HYBRID] <= 1e-12, out
+    assert out[I.FLUX_HLL] >= 1e-2, out
+
+
+def test_hybrid_limits(oracle_lib):
+    """With an unreachable threshold the hybrid is HLLC bit for bit; on Sod
+    with threshold 2 it switches to HLL only where the face pressures jump,
+    so it differs from both."""
+    base = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+    U_c = _riemann_y(oracle_lib, 100, *base)[3]
+    U_l = _riemann_y(oracle_lib, 100, *base, flux=I.FLUX_HLL)[3]
+    U_h = _riemann_y(oracle_lib, 100, *base, flux=I.FLUX_HYBRID, flux_theta=1e30)[3]
+    assert np.array_equal(U_h, U_c)
+    U_2 = _riemann_y(oracle_lib, 100, *base, flux=I.FLUX_HYBRID, flux_theta=2.0)[3]
+    assert not np.array_equal(U_2, U_c) and not np.array_equal(U_2, U_l)
+
+
 # --------------------------------------------------------------- conservation
-def test_conservation_without_gravity(oracle_lib):
+@pytest.mark.parametrize("flux", [I.FLUX_HLLC, I.FLUX_HLL, I.FLUX_HYBRID])
+def test_conservation_without_gravity(oracle_lib, flux):
     """g = 0, periodic x, reflecting y: mass, x-momentum and energy are
     conserved to rounding; y-momentum changes only through the wall pressure."""
-    w = I.rt_box(16, 48, g_y=0.0, nsteps=300)
+    w = I.rt_box(16, 48, g_y=0.0, nsteps=300, flux=flux, flux_theta=1.01)
     v = 0.05 * I.gaussian_field(3, 2, w.ny, w.nx)
     U0 = oracle_lib.inject(w, v)
     out = oracle_lib.forward(w, v)
