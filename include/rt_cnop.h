@@ -63,6 +63,7 @@ typedef enum {
 
 enum { RT_BC_REFLECT = 0, RT_BC_HYDROSTATIC = 1 };
 enum { RT_LIM_MINMOD = 0, RT_LIM_MC = 1, RT_LIM_NONE = 2 };
+enum { RT_FLUX_HLLC = 0, RT_FLUX_HLL = 1, RT_FLUX_HYBRID = 2 };
 enum { RT_OBJ_KE = 0, RT_OBJ_EK_ANOMALY_L2 = 1 };
 enum { RT_FP64 = 0, RT_FP32_STATE = 1 };
 enum { RT_CKPT_AUTO = 0, RT_CKPT_STORE_ALL = 1, RT_CKPT_SQRT = 2, RT_CKPT_REVOLVE = 3 };
@@ -95,6 +96,12 @@ typedef struct {
   int nsteps;
   int perturb_ncomp; /* 1: u_y only (Sec. 3.1); 2: (u_x, u_y) */
   int objective;     /* RT_OBJ_KE | RT_OBJ_EK_ANOMALY_L2 */
+  int flux;          /* Riemann flux (Sec. 2.3, "hybrid HLLC"): RT_FLUX_HLLC (HLLC with
+                        Davis speeds), RT_FLUX_HLL (HLL, same speeds) or RT_FLUX_HYBRID:
+                        HLL at faces whose reconstructed pressures differ by more than
+                        the factor flux_theta (p_L > flux_theta p_R or p_R > flux_theta
+                        p_L), HLLC elsewhere */
+  double flux_theta; /* RT_FLUX_HYBRID threshold, >= 1; ignored otherwise */
 } rt_problem;
 
 typedef struct {

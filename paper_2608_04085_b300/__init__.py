@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "librt_cnop.so")
 RT_OK, RT_EINVAL, RT_ENOMEM, RT_ECUDA, RT_ENONFINITE, RT_ETIMEOUT, RT_ENOTCONVERGED, RT_ESTATE, RT_EIO = range(9)
 RT_BC_REFLECT, RT_BC_HYDROSTATIC = 0, 1
 RT_LIM_MINMOD, RT_LIM_MC, RT_LIM_NONE = 0, 1, 2
+RT_FLUX_HLLC, RT_FLUX_HLL, RT_FLUX_HYBRID = 0, 1, 2
 RT_OBJ_KE, RT_OBJ_EK_ANOMALY_L2 = 0, 1
 RT_FP64, RT_FP32_STATE = 0, 1
 RT_CKPT_AUTO, RT_CKPT_STORE_ALL, RT_CKPT_SQRT, RT_CKPT_REVOLVE = 0, 1, 2, 3
@@ -57,7 +58,11 @@ class RtProblem(ctypes.Structure):
                 ("bc_y", ctypes.c_int), ("limiter", ctypes.c_int),
                 ("cfl", ctypes.c_double), ("T", ctypes.c_double),
                 ("nsteps", ctypes.c_int), ("perturb_ncomp", ctypes.c_int),
-                ("objective", ctypes.c_int)]
+                ("objective", ctypes.c_int), ("flux", ctypes.c_int),
+                ("flux_theta", ctypes.c_double)]
+
+# rt_problem fields a problem description may leave out, with their values
+_PROBLEM_DEFAULTS = {"flux": RT_FLUX_HLLC, "flux_theta": 2.0}
 
 
 class RtOptions(ctypes.Structure):
@@ -168,11 +173,12 @@ def _field(w, name, alt=None, default=None):
 
 def make_problem(w) -> RtProblem:
     """rt_problem from any object or dict with the field names of rt_problem
-    (``ncomp`` is accepted for ``perturb_ncomp``)."""
+    (``ncomp`` is accepted for ``perturb_ncomp``; ``flux`` and ``flux_theta``
+    default to HLLC and 2)."""
     p = RtProblem()
     for name, _ in RtProblem._fields_:
         alt = "ncomp" if name == "perturb_ncomp" else None
-        val = _field(w, name, alt)
+        val = _field(w, name, alt, _PROBLEM_DEFAULTS.get(name))
         if val is None:
             raise ValueError(f"problem is missing field {name!r}")
         setattr(p, name, val)

@@ -44,6 +44,9 @@ struct InstDev {
   double gamma, gm1, g_y;
   double cfl, T;
   float gamma_f, gm1_f, g_f, dx_f, dy_f;  // the same constants rounded once for FP32 kernels
+  int flux;                  // RT_FLUX_HLLC | RT_FLUX_HLL | RT_FLUX_HYBRID
+  double flux_theta;         // hybrid threshold on the face pressure ratio (0 unless hybrid)
+  float flux_theta_f;
   const double* rho0;        // [ny] base density at cell centres
   const double* p0;          // [ny] base pressure at cell centres
   // [ny] rho0 and p0 rounded to FP32. An FP32 state stores the deviation of

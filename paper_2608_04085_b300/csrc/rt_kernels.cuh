@@ -99,6 +99,20 @@ template <> __device__ __forceinline__ Phys<double> phys<double>(const InstDev& 
   return {I.gamma, I.gm1, I.g_y, I.dx, I.dy};
 }
 
+// Riemann-flux choice of instance I in a kernel built for limiter LIM: the
+// limiter-specialised kernels (LIM >= 0) run HLLC only (the runtime sends
+// batches with another flux to the generic LIM = -1 kernels).
+template <class T, int LIM>
+__device__ __forceinline__ FluxSel<T> flux_sel(const InstDev& I) {
+  if constexpr (LIM >= 0) {
+    return {FLUX_HLLC, T(0)};
+  } else if constexpr (sizeof(T) == 4) {
+    return {I.flux, I.flux_theta_f};
+  } else {
+    return {I.flux, I.flux_theta};
+  }
+}
+
 template <class T>
 __device__ __forceinline__ StepC<T> step_const(const RunDev& run, int inst, int n) {
   return reinterpret_cast<const StepC<T>*>(run.dtc)[(long long)inst * run.max_steps + n];
@@ -438,6 +452,7 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS, 6) k_stage_sweep(const InstD
 
   const Phys<T> P = phys<T>(I);
   const int nx = I.nx, ny = I.ny, lim = LIM >= 0 ? LIM : I.limiter;
+  const FluxSel<T> fs = flux_sel<T, LIM>(I);
   const long long cells = (long long)nx * ny;
   const T* Si = src + 4 * I.cell_off;
   const T* Bi = base + 4 * I.cell_off;
@@ -470,7 +485,7 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS, 6) k_stage_sweep(const InstD
       WL[q] = Wb[q] + T(0.5) * s_lo;
       WR[q] = W0[q] - T(0.5) * s_cur[q];
     }
-    face_flux_states<T, 1>(WL, WR, P.gamma, P.gm1, Gb);
+    face_flux_states<T, 1>(WL, WR, P.gamma, P.gm1, fs, Gb);
   }
 
   T wmin = T(1e30);
@@ -502,7 +517,7 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS, 6) k_stage_sweep(const InstD
         WL[q] = shfl_up1(W0[q] + T(0.5) * sx);
         WR[q] = W0[q] - T(0.5) * sx;
       }
-      face_flux_states<T, 0>(WL, WR, P.gamma, P.gm1, Fl);
+      face_flux_states<T, 0>(WL, WR, P.gamma, P.gm1, fs, Fl);
     }
     T Fr[4];
 #pragma unroll
@@ -518,7 +533,7 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS, 6) k_stage_sweep(const InstD
         WL[q] = W0[q] + T(0.5) * s_cur[q];
         WR[q] = W1[q] - T(0.5) * s_next[q];
       }
-      face_flux_states<T, 1>(WL, WR, P.gamma, P.gm1, Gt);
+      face_flux_states<T, 1>(WL, WR, P.gamma, P.gm1, fs, Gt);
     }
     if (writer) {
       T o[4];
@@ -608,6 +623,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 6 : 1) k_stage_tile(cons
   const T* Si = src + 4 * I.cell_off;
   const int x0 = tl.y, y0 = tl.z;
   const int lim = LIM >= 0 ? LIM : I.limiter;
+  const FluxSel<T> fs = flux_sel<T, LIM>(I);
   load_prim_tile<T, ST_EX, ST_EY, true>(Si, I, cells, x0 - 2, y0 - 2, P, reinterpret_cast<T*>(sW), sRB);
   // stage 2 also needs U^n of this thread's cells in the update; their loads
   // are issued here so that the face work hides their latency
@@ -635,7 +651,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 6 : 1) k_stage_tile(cons
 #pragma unroll
         for (int q = 0; q < 4; ++q) w[p][q] = c.v[q];
       }
-      face_flux<T, 0>(w, lim, P.gamma, P.gm1, F);
+      face_flux<T, 0>(w, lim, P.gamma, P.gm1, fs, F);
       Q4<T> fq;
 #pragma unroll
       for (int q = 0; q < 4; ++q) fq.v[q] = F[q];
@@ -649,7 +665,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 6 : 1) k_stage_tile(cons
 #pragma unroll
         for (int q = 0; q < 4; ++q) w[p][q] = c.v[q];
       }
-      face_flux<T, 1>(w, lim, P.gamma, P.gm1, F);
+      face_flux<T, 1>(w, lim, P.gamma, P.gm1, fs, F);
       Q4<T> gq;
 #pragma unroll
       for (int q = 0; q < 4; ++q) gq.v[q] = F[q];
@@ -739,6 +755,7 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
   const T* Ki = K + 4 * I.cell_off;
   const int x0 = tl.y, y0 = tl.z, nx = I.nx, ny = I.ny;
   const int lim = LIM >= 0 ? LIM : I.limiter;
+  const FluxSel<T> fs = flux_sel<T, LIM>(I);
   constexpr int PASSES = TY / ROWS_PER_PASS;
   // E of this thread's cells (added at the end) is loaded first, so that the
   // face work hides its latency
@@ -801,7 +818,7 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
 #pragma unroll
       for (int q = 0; q < 4; ++q) mu[q] = sc.dtdx * (kr.v[q] - kl.v[q]);
     }
-    face_vjp<T, 0>(w, mu, lim, P.gamma, P.gm1, o);
+    face_vjp<T, 0>(w, mu, lim, P.gamma, P.gm1, fs, o);
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
       Q4<T> c;
@@ -839,7 +856,7 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
       const Q4<T> ku = sK[(fy + 1) * ADJ_KX + fx + 2], kd = sK[fy * ADJ_KX + fx + 2];
 #pragma unroll
       for (int q = 0; q < 4; ++q) mu[q] = sc.dtdy * (ku.v[q] - kd.v[q]);
-      face_vjp<T, 1>(w, mu, lim, P.gamma, P.gm1, o);
+      face_vjp<T, 1>(w, mu, lim, P.gamma, P.gm1, fs, o);
     } else {
 #pragma unroll
       for (int p = 0; p < 4; ++p)

@@ -24,7 +24,7 @@
 #include "rt_spectra.h"
 
 // The Python binding mirrors these layouts with ctypes.
-static_assert(sizeof(rt_problem) == 144, "rt_problem layout");
+static_assert(sizeof(rt_problem) == 152, "rt_problem layout");
 static_assert(sizeof(rt_options) == 24, "rt_options layout");
 static_assert(sizeof(cnop_params) == 96, "cnop_params layout");
 static_assert(sizeof(cnop_result) == 64, "cnop_result layout");
@@ -191,6 +191,9 @@ rt_status validate(rt_ctx* c, const rt_problem& P, int i) {
   if (P.bc_y != RT_BC_REFLECT && P.bc_y != RT_BC_HYDROSTATIC) return fail(c, RT_EINVAL, "instance %d: bc_y", i);
   if (P.limiter < 0 || P.limiter > 2) return fail(c, RT_EINVAL, "instance %d: limiter", i);
   if (P.perturb_ncomp != 1 && P.perturb_ncomp != 2) return fail(c, RT_EINVAL, "instance %d: perturb_ncomp", i);
+  if (P.flux < RT_FLUX_HLLC || P.flux > RT_FLUX_HYBRID) return fail(c, RT_EINVAL, "instance %d: flux", i);
+  if (P.flux == RT_FLUX_HYBRID && !(P.flux_theta >= 1.0))
+    return fail(c, RT_EINVAL, "instance %d: flux_theta must be >= 1", i);
   if (P.objective != RT_OBJ_KE && P.objective != RT_OBJ_EK_ANOMALY_L2)
     return fail(c, RT_EINVAL, "instance %d: objective", i);
   std::vector<double> r, p;
@@ -1570,6 +1573,9 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
     I.g_f = (float)I.g_y;
     I.dx_f = (float)I.dx;
     I.dy_f = (float)I.dy;
+    I.flux = P.flux;
+    I.flux_theta = P.flux == RT_FLUX_HYBRID ? P.flux_theta : 0.0;
+    I.flux_theta_f = (float)I.flux_theta;
     I.tile_begin = (int)c->h_tiles.size();
     for (int y0 = 0; y0 < P.ny; y0 += rt::TILE_Y)
       for (int x0 = 0; x0 < P.nx; x0 += rt::TILE_X) c->h_tiles.push_back(make_int4(i, x0, y0, 0));
@@ -1587,6 +1593,8 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
   for (int i = 1; i < n_instances; ++i)
     if (c->prob[i].limiter != c->lim) c->lim = -1;
   if (c->lim != RT_LIM_MINMOD) c->lim = -1;  // only minmod has specialised kernels
+  for (int i = 0; i < n_instances; ++i)      // ... and only with the HLLC flux
+    if (c->prob[i].flux != RT_FLUX_HLLC) c->lim = -1;
   const int N = n_instances;
 #define INIT_CU(call)                                                                            \
   do {                                                                                           \

@@ -23,6 +23,25 @@
 namespace rt {
 
 enum { LIM_MINMOD = 0, LIM_MC = 1, LIM_NONE = 2 };
+enum { FLUX_HLLC = 0, FLUX_HLL = 1, FLUX_HYBRID = 2 };
+
+// Riemann-flux choice of an instance (Sec. 2.3, "hybrid HLLC"): HLLC, HLL,
+// or the hybrid, which takes HLL where the reconstructed face pressures
+// differ by more than the factor theta and HLLC elsewhere. Kernels
+// specialised for one limiter pass the constant {FLUX_HLLC, 0}, which
+// removes the choice at compile time.
+template <class T>
+struct FluxSel {
+  int kind;
+  T theta;
+};
+
+template <class T>
+__device__ __forceinline__ bool use_hll(const FluxSel<T>& fs, T pL, T pR) {
+  if (fs.kind == FLUX_HLL) return true;
+  if (fs.kind == FLUX_HYBRID) return pL > fs.theta * pR || pR > fs.theta * pL;
+  return false;
+}
 
 // Conserved (rho, m_x, m_y, E) -> primitive (rho, u_x, u_y, p).
 template <class T>
@@ -230,13 +249,132 @@ __device__ __forceinline__ void hllc_vjp(T rL, T uL, T vL, T pL, T rR, T uR, T v
   bRs[0] = brR; bRs[1] = buR; bRs[2] = bvR; bRs[3] = bpR;
 }
 
+// HLL flux (Harten, Lax & van Leer) with the Davis speeds of hllc(), in
+// the frame (normal, tangential): F_L where S_L >= 0, F_R where S_R < 0,
+// otherwise (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L).
+template <class T>
+__device__ __forceinline__ void hll(T rL, T uL, T vL, T pL, T rR, T uR, T vR, T pR, T gamma, T gm1, T F[4]) {
+  const T cL = sqrt(gamma * pL / rL);
+  const T cR = sqrt(gamma * pR / rR);
+  const T aL = uL - cL, aR = uR - cR;
+  const T SL = aL <= aR ? aL : aR;
+  const T eL = uL + cL, eR = uR + cR;
+  const T SR = eL >= eR ? eL : eR;
+  const T EL = pL / gm1 + T(0.5) * rL * (uL * uL + vL * vL);
+  const T ER = pR / gm1 + T(0.5) * rR * (uR * uR + vR * vR);
+  const T f0L = rL * uL, f0R = rR * uR;
+  const T FL[4] = {f0L, f0L * uL + pL, f0L * vL, uL * (EL + pL)};
+  const T FR[4] = {f0R, f0R * uR + pR, f0R * vR, uR * (ER + pR)};
+  if (SL >= T(0)) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) F[k] = FL[k];
+    return;
+  }
+  if (!(SR >= T(0))) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) F[k] = FR[k];
+    return;
+  }
+  const T UL[4] = {rL, rL * uL, rL * vL, EL};
+  const T UR[4] = {rR, rR * uR, rR * vR, ER};
+  const T D = SR - SL, SLR = SL * SR;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) F[k] = ((SR * FL[k] - SL * FR[k]) + SLR * (UR[k] - UL[k])) / D;
+}
+
+// Reverse of one side's physical flux F = (r u, r u^2 + p, r u v, u (E + p))
+// and conserved state U = (r, r u, r v, E), E = p/(gamma-1) + r (u^2+v^2)/2:
+// cotangents of (r, u, v, p) from those of F and U.
+template <class T>
+__device__ __forceinline__ void flux_state_vjp(T r, T u, T v, T p, T E, T gm1, const T bF[4], const T bU[4],
+                                               T b[4]) {
+  const T f0 = r * u;
+  const T b_f0 = bF[0] + bF[1] * u + bF[2] * v;
+  T b_u = bF[1] * f0 + bF[3] * (E + p) + b_f0 * r + bU[1] * r;
+  T b_p = bF[1] + bF[3] * u;
+  T b_v = bF[2] * f0 + bU[2] * r;
+  const T b_E = bF[3] * u + bU[3];
+  T b_r = b_f0 * u + bU[0] + bU[1] * u + bU[2] * v;
+  b_p += b_E / gm1;
+  b_r += b_E * T(0.5) * (u * u + v * v);
+  b_u += b_E * r * u;
+  b_v += b_E * r * v;
+  b[0] = b_r;
+  b[1] = b_u;
+  b[2] = b_v;
+  b[3] = b_p;
+}
+
+// Reverse of hll(): cotangents of the left and right rotated primitive
+// states for the flux cotangent bF (for the branch taken). With
+// D = S_R - S_L and dU = U_R - U_L: dF/dS_L = (F - F_R + S_R dU) / D,
+// dF/dS_R = (F_L - F + S_L dU) / D.
+template <class T>
+__device__ __forceinline__ void hll_vjp(T rL, T uL, T vL, T pL, T rR, T uR, T vR, T pR, T gamma, T gm1,
+                                        const T bF[4], T bLs[4], T bRs[4]) {
+  const T cL = sqrt(gamma * pL / rL);
+  const T cR = sqrt(gamma * pR / rR);
+  const T aL = uL - cL, aR = uR - cR;
+  const bool slL = aL <= aR;
+  const T SL = slL ? aL : aR;
+  const T eL = uL + cL, eR = uR + cR;
+  const bool srL = eL >= eR;
+  const T SR = srL ? eL : eR;
+  const T EL = pL / gm1 + T(0.5) * rL * (uL * uL + vL * vL);
+  const T ER = pR / gm1 + T(0.5) * rR * (uR * uR + vR * vR);
+  const T f0L = rL * uL, f0R = rR * uR;
+  const T FL[4] = {f0L, f0L * uL + pL, f0L * vL, uL * (EL + pL)};
+  const T FR[4] = {f0R, f0R * uR + pR, f0R * vR, uR * (ER + pR)};
+  T bFL[4], bFR[4], bUL[4], bUR[4];
+  T bSL = T(0), bSR = T(0);
+  const bool left = SL >= T(0), right = !left && !(SR >= T(0));
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    bFL[k] = left ? bF[k] : T(0);
+    bFR[k] = right ? bF[k] : T(0);
+    bUL[k] = T(0);
+    bUR[k] = T(0);
+  }
+  if (!left && !right) {
+    const T UL[4] = {rL, rL * uL, rL * vL, EL};
+    const T UR[4] = {rR, rR * uR, rR * vR, ER};
+    const T D = SR - SL, SLR = SL * SR;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const T dU = UR[k] - UL[k];
+      const T Fk = ((SR * FL[k] - SL * FR[k]) + SLR * dU) / D;
+      bFL[k] = bF[k] * SR / D;
+      bFR[k] = -bF[k] * SL / D;
+      bUR[k] = bF[k] * SLR / D;
+      bUL[k] = -bUR[k];
+      bSL += bF[k] * ((Fk - FR[k]) + SR * dU) / D;
+      bSR += bF[k] * ((FL[k] - Fk) + SL * dU) / D;
+    }
+  }
+  flux_state_vjp(rL, uL, vL, pL, EL, gm1, bFL, bUL, bLs);
+  flux_state_vjp(rR, uR, vR, pR, ER, gm1, bFR, bUR, bRs);
+  // Davis speeds S_L = min(u_L - c_L, u_R - c_R), S_R = max(u_L + c_L, u_R + c_R)
+  const T tL = slL ? bSL : T(0), tR = bSL - tL;
+  const T sL = srL ? bSR : T(0), sR = bSR - sL;
+  bLs[1] += tL + sL;
+  bRs[1] += tR + sR;
+  const T bcL = sL - tL, bcR = sR - tR;
+  // c = sqrt(gamma p / rho)
+  bLs[3] += bcL * T(0.5) * cL / pL;
+  bLs[0] -= bcL * T(0.5) * cL / rL;
+  bRs[3] += bcR * T(0.5) * cR / pR;
+  bRs[0] -= bcR * T(0.5) * cR / rR;
+}
+
 // Flux through a face along DIR (0: x, 1: y) from the reconstructed face
 // states WL = W_a + s_a/2 and WR = W_b - s_b/2 (primitive, unrotated).
 template <class T, int DIR>
-__device__ __forceinline__ void face_flux_states(const T WL[4], const T WR[4], T gamma, T gm1, T F[4]) {
+__device__ __forceinline__ void face_flux_states(const T WL[4], const T WR[4], T gamma, T gm1, FluxSel<T> fs,
+                                                 T F[4]) {
   constexpr int n = 1 + DIR, t = 2 - DIR;
   T f[4];
-  hllc(WL[0], WL[n], WL[t], WL[3], WR[0], WR[n], WR[t], WR[3], gamma, gm1, f);
+  if (use_hll(fs, WL[3], WR[3])) hll(WL[0], WL[n], WL[t], WL[3], WR[0], WR[n], WR[t], WR[3], gamma, gm1, f);
+  else hllc(WL[0], WL[n], WL[t], WL[3], WR[0], WR[n], WR[t], WR[3], gamma, gm1, f);
   F[0] = f[0];
   F[n] = f[1];
   F[t] = f[2];
@@ -246,7 +384,7 @@ __device__ __forceinline__ void face_flux_states(const T WL[4], const T WR[4], T
 // Flux through the face between cells a and b along DIR (0: x, 1: y), from
 // the primitive states w[0..3] of cells a-1, a, b, b+1 (index [cell][var]).
 template <class T, int DIR>
-__device__ __forceinline__ void face_flux(const T w[4][4], int lim, T gamma, T gm1, T F[4]) {
+__device__ __forceinline__ void face_flux(const T w[4][4], int lim, T gamma, T gm1, FluxSel<T> fs, T F[4]) {
   T WL[4], WR[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -255,18 +393,19 @@ __device__ __forceinline__ void face_flux(const T w[4][4], int lim, T gamma, T g
     WL[q] = w[1][q] + T(0.5) * sa;
     WR[q] = w[2][q] - T(0.5) * sb;
   }
-  face_flux_states<T, DIR>(WL, WR, gamma, gm1, F);
+  face_flux_states<T, DIR>(WL, WR, gamma, gm1, fs, F);
 }
 
 // Reverse of the HLLC part of a face: the cotangents of the reconstructed
 // face states WL, WR (primitive, unrotated) for the flux cotangent mu.
 template <class T, int DIR>
 __device__ __forceinline__ void face_states_vjp(const T WL[4], const T WR[4], const T mu[4], T gamma, T gm1,
-                                                T bWL[4], T bWR[4]) {
+                                                FluxSel<T> fs, T bWL[4], T bWR[4]) {
   constexpr int n = 1 + DIR, t = 2 - DIR;
   const T bf[4] = {mu[0], mu[n], mu[t], mu[3]};
   T bl[4], br[4];
-  hllc_vjp(WL[0], WL[n], WL[t], WL[3], WR[0], WR[n], WR[t], WR[3], gamma, gm1, bf, bl, br);
+  if (use_hll(fs, WL[3], WR[3])) hll_vjp(WL[0], WL[n], WL[t], WL[3], WR[0], WR[n], WR[t], WR[3], gamma, gm1, bf, bl, br);
+  else hllc_vjp(WL[0], WL[n], WL[t], WL[3], WR[0], WR[n], WR[t], WR[3], gamma, gm1, bf, bl, br);
   bWL[0] = bl[0]; bWL[n] = bl[1]; bWL[t] = bl[2]; bWL[3] = bl[3];
   bWR[0] = br[0]; bWR[n] = br[1]; bWR[t] = br[2]; bWR[3] = br[3];
 }
@@ -274,7 +413,7 @@ __device__ __forceinline__ void face_states_vjp(const T WL[4], const T WR[4], co
 // Transposed face flux: out[cell][var] = (dF/dW_cell,var)^T mu for the four
 // cells a-1, a, b, b+1.
 template <class T, int DIR>
-__device__ __forceinline__ void face_vjp(const T w[4][4], const T mu[4], int lim, T gamma, T gm1,
+__device__ __forceinline__ void face_vjp(const T w[4][4], const T mu[4], int lim, T gamma, T gm1, FluxSel<T> fs,
                                          T out[4][4]) {
   T WL[4], WR[4], bWL[4], bWR[4];
   if constexpr (sizeof(T) == 4) {
@@ -296,7 +435,7 @@ __device__ __forceinline__ void face_vjp(const T w[4][4], const T mu[4], int lim
         WL[q] = w[1][q] + T(0.5) * (sa ? (ka ? dma : dpa) : T(0));
         WR[q] = w[2][q] - T(0.5) * (sb ? (kb ? dmb : dpb) : T(0));
       }
-      face_states_vjp<T, DIR>(WL, WR, mu, gamma, gm1, bWL, bWR);
+      face_states_vjp<T, DIR>(WL, WR, mu, gamma, gm1, fs, bWL, bWR);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const T bsa = T(0.5) * bWL[q];   // W_L = W_a + s_a / 2
@@ -321,7 +460,7 @@ __device__ __forceinline__ void face_vjp(const T w[4][4], const T mu[4], int lim
     WL[q] = w[1][q] + T(0.5) * sa;
     WR[q] = w[2][q] - T(0.5) * sb;
   }
-  face_states_vjp<T, DIR>(WL, WR, mu, gamma, gm1, bWL, bWR);
+  face_states_vjp<T, DIR>(WL, WR, mu, gamma, gm1, fs, bWL, bWR);
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const T bsa = T(0.5) * bWL[q];   // W_L = W_a + s_a / 2

@@ -31,8 +31,9 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_sizes_match_header_layout():
     import paper_2608_04085_b300 as rt
-    # rt_problem: 2 ints, 12 doubles, 2 ints, 2 doubles, 3 ints (+ padding)
-    assert ctypes.sizeof(rt.RtProblem) == 8 + 12 * 8 + 8 + 16 + 16
+    # rt_problem: 2 ints, 12 doubles, 2 ints, 2 doubles, 4 ints, 1 double
+    assert ctypes.sizeof(rt.RtProblem) == 8 + 12 * 8 + 8 + 16 + 16 + 8
+    assert rt.RtProblem.flux.offset == 140 and rt.RtProblem.flux_theta.offset == 144
     assert ctypes.sizeof(rt.RtOptions) == 24
     # cnop_params: 3 ints (+ pad), 4 doubles, a pointer, 2 ints, a double, 2 pointers, 2 ints
     # cnop_result: 3 ints (+ pad), a double, 5 pointers

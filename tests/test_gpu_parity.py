@@ -33,6 +33,10 @@ FWD_CASES = {
     "paper20_horizon": (I.paper_unit_square(20, 0.05).replace(ny=27), 2),
     # minimal sizes: nx = 4, ny = 2 (a single ragged tile, mirror ghosts of 2 rows)
     "tiny4x2_none": (I.rt_box(4, 2, nsteps=7, limiter=I.LIM_NONE), 3),
+    # HLL flux; the HLLC/HLL hybrid with a threshold that both branches meet
+    "box32x40_hll": (I.rt_box(32, 40, nsteps=40, flux=I.FLUX_HLL), 4),
+    "ragged37x45_mc_hybrid": (I.rt_box(37, 45, nsteps=40, limiter=I.LIM_MC, flux=I.FLUX_HYBRID,
+                                       flux_theta=1.0001), 5),
 }
 
 
@@ -83,6 +87,8 @@ GRAD_CASES = {
                                         bc_y=I.BC_HYDROSTATIC),
     "paper16_pap_horizon": I.paper_unit_square(16, 0.04).replace(ny=20),
     "tiny4x2": I.rt_box(4, 2, nsteps=6, limiter=I.LIM_NONE),
+    "box24x36_hll": I.rt_box(24, 36, nsteps=30, flux=I.FLUX_HLL),
+    "box24x36_hybrid": I.rt_box(24, 36, nsteps=30, flux=I.FLUX_HYBRID, flux_theta=1.0001),
 }
 
 
@@ -236,3 +242,30 @@ def test_invalid_problem_rejected():
     with pytest.raises(rt.RtError) as e:
         rt.Context([I.rt_box(3, 8)])
     assert e.value.status == rt.RT_EINVAL
+
+
+def test_mixed_flux_batch_matches_single_runs_and_bad_flux_is_rejected():
+    """An HLLC, an HLL and a hybrid instance in one batch (which runs the
+    generic kernels) give each instance the bits of its own oracle run, in
+    FP64; the FP32 state keeps J within 1e-4 of FP64 with HLLC and within
+    1e-3 with HLL and the hybrid (whose HLL average keeps the textbook
+    U_R - U_L form). An unknown flux or a hybrid threshold below 1 is
+    rejected."""
+    import oracle
+    rt = _rt()
+    ws = [I.rt_box(24, 36, nsteps=30), I.rt_box(24, 36, nsteps=30, flux=I.FLUX_HLL),
+          I.rt_box(24, 36, nsteps=30, flux=I.FLUX_HYBRID, flux_theta=1.0001)]
+    vs = [_v(w, 20 + k) for k, w in enumerate(ws)]
+    flat = np.concatenate([v.ravel() for v in vs])
+    with rt.Context(ws, precision=rt.RT_FP64) as ctx:
+        J64, _, _ = ctx.forward(flat)
+        for k, w in enumerate(ws):
+            ref = oracle.forward(w, vs[k])
+            assert np.array_equal(ctx.state(k), ref["U"]), k
+    with rt.Context(ws, precision=rt.RT_FP32_STATE) as ctx:
+        J32, _, _ = ctx.forward(flat)
+    rel = np.abs(J32 - J64) / np.abs(J64)
+    assert rel[0] <= 1e-4 and np.all(rel <= 1e-3), rel
+    for bad in (dict(flux=3), dict(flux=I.FLUX_HYBRID, flux_theta=0.5)):
+        with pytest.raises(rt.RtError):
+            rt.Context([I.rt_box(8, 8, nsteps=2, **bad)], precision=rt.RT_FP64)
