@@ -13,7 +13,9 @@ in ``rt_oracle.cpp``
 act on whole fields (constraint, projection, random start, spectral projected
 gradient and projected L-BFGS with a non-monotone line search, 1D Fourier
 spectrum, five-mode reconstruction) are plain NumPy here. Each function names the paper passage it
-follows.
+follows. ``branch_signature`` is a test aid: it records which side of every
+kink of the scheme a run took, so that finite differences across a kink can be
+told apart.
 
 Parity status: every function below is pinned by a ``-m "not gpu"`` test
 (``tests/test_oracle_*.py``) against closed forms, textbook solutions,

@@ -241,8 +241,8 @@ template <class R> inline void hllc(const R L[4], const R Rr[4], double gamma, d
   phys_flux(rR, uR, vR, pR, ER, F);
 }
 
-// HLL Riemann flux (Harten, Lax & van Leer) with the same Davis wave speeds,
-// rotated frame: F_L where S_L >= 0, F_R where S_R < 0, otherwise the
+// HLL Riemann flux (Harten, Lax & van Leer; Toro Sec. 10.3) with the same
+// Davis wave speeds, rotated frame: F_L where S_L >= 0, F_R where S_R < 0, otherwise the
 // single-state average (S_R F_L - S_L F_R + S_L S_R (U_R - U_L)) / (S_R - S_L).
 template <class R> inline void hll(const R L[4], const R Rr[4], double gamma, double gm1, R F[4]) {
   const R &rL = L[0], &uL = L[1], &vL = L[2], &pL = L[3];
@@ -268,9 +268,10 @@ template <class R> inline void hll(const R L[4], const R Rr[4], double gamma, do
   for (int k = 0; k < 4; ++k) F[k] = ((SR * FL[k] - SL * FR[k]) + SLR * (UR[k] - UL[k])) / D;
 }
 
-// Riemann flux of a face: HLLC, HLL, or the hybrid, which takes HLL where the
-// two face pressures differ by more than the factor flux_theta (a strong
-// jump, where HLLC's contact resolution is not wanted) and HLLC elsewhere.
+// Riemann flux of a face [Sec. 2.3, "hybrid HLLC", which the paper does not
+// define; read as]: HLLC, HLL, or the hybrid, which takes HLL where the two
+// face pressures differ by more than the factor flux_theta (a strong jump,
+// where HLLC's contact resolution is not wanted) and HLLC elsewhere.
 template <class R> inline void riemann_flux(const R L[4], const R Rr[4], const OParams& P, R F[4]) {
   bool use_hll = P.flux == O_FLUX_HLL;
   if (P.flux == O_FLUX_HYBRID) {
