@@ -57,3 +57,20 @@ def test_header_enums_match_binding_constants():
     assert len(consts) >= 25
     for name, value in consts.items():
         assert getattr(rt, name) == value, name
+
+
+def test_make_problem_fills_the_flux_fields():
+    """A problem description without the flux fields gets HLLC (threshold 2);
+    given ones pass through; a missing required field is an error."""
+    import paper_2608_04085_b300 as rt
+    import rt_inputs as I
+    w = I.rt_box(8, 16, nsteps=3)
+    d = {k: v for k, v in w.__dict__.items() if k not in ("flux", "flux_theta")}
+    p = rt.make_problem(d)
+    assert p.flux == rt.RT_FLUX_HLLC and p.flux_theta == 2.0
+    assert p.perturb_ncomp == w.ncomp and p.nx == 8 and p.ny == 16
+    q = rt.make_problem(w.replace(flux=I.FLUX_HYBRID, flux_theta=1.5))
+    assert q.flux == rt.RT_FLUX_HYBRID and q.flux_theta == 1.5
+    del d["gamma"]
+    with pytest.raises(ValueError, match="gamma"):
+        rt.make_problem(d)
