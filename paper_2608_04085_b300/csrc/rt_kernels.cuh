@@ -118,13 +118,6 @@ __device__ __forceinline__ StepC<T> step_const(const RunDev& run, int inst, int 
   return reinterpret_cast<const StepC<T>*>(run.dtc)[(long long)inst * run.max_steps + n];
 }
 
-// Stored state -> primitives (rho, u_x, u_y, p) of a cell of row `row`. An
-// FP64 state stores U itself. An FP32 state stores the deviation of U from
-// the row's hydrostatic base (rho0, 0, 0, p0/(gamma-1)): the stored values
-// and every update then round relative to the deviation, not to the O(1)
-// background, and the primitives add the base back: rho = rho0 + d_rho,
-// p = p0 + (gamma-1)(d_E - |m|^2/(2 rho)). In exact arithmetic both give
-// the same scheme.
 // The row's base (rho0, p0) as the FP32 conversion uses it (unused for FP64).
 struct RowBase {
   float rho, p;
@@ -136,6 +129,13 @@ __device__ __forceinline__ RowBase row_base(const InstDev& I, int row) {
   else return {0.f, 0.f};
 }
 
+// Stored state -> primitives (rho, u_x, u_y, p) of a cell whose row has the
+// base b. An FP64 state stores U itself. An FP32 state stores the deviation
+// of U from the row's hydrostatic base (rho0, 0, 0, p0/(gamma-1)): the stored
+// values and every update then round relative to the deviation, not to the
+// O(1) background, and the primitives add the base back: rho = rho0 + d_rho,
+// p = p0 + (gamma-1)(d_E - |m|^2/(2 rho)). In exact arithmetic both give the
+// same scheme.
 template <class T>
 __device__ __forceinline__ void state_to_prim_b(T s0, T s1, T s2, T s3, RowBase b, T gm1, T W[4]) {
   if constexpr (sizeof(T) == 4) {
