@@ -74,3 +74,36 @@ def test_make_problem_fills_the_flux_fields():
     del d["gamma"]
     with pytest.raises(ValueError, match="gamma"):
         rt.make_problem(d)
+
+
+def test_null_arguments_return_einval_without_a_gpu():
+    """The ABI's error contract on the host: every entry point answers a null
+    context or a missing argument with a status (never a crash), before any
+    device call, so it holds on a machine without a GPU."""
+    import paper_2608_04085_b300 as rt
+    L = rt.library()
+    h = ctypes.c_void_p()
+    assert L.rt_init(None, 0, None, None, ctypes.byref(h)) == rt.RT_EINVAL and not h.value
+    assert L.rt_init(None, 1, None, None, None) == rt.RT_EINVAL
+    assert L.rt_forward(None, None, 0, None, None, None) == rt.RT_EINVAL
+    assert L.rt_gradient(None, None, 0, None, None, None) == rt.RT_EINVAL
+    assert L.rt_constraint(None, None, 0, None) == rt.RT_EINVAL
+    assert L.rt_project(None, None, 0, None, 0) == rt.RT_EINVAL
+    assert L.rt_get_state(None, 0, None) == rt.RT_EINVAL
+    assert L.rt_get_dt(None, 0, None, 0, None) == rt.RT_EINVAL
+    assert L.rt_forward_series(None, None, 0, 1, 1, None, None, None, None) == rt.RT_EINVAL
+    assert L.rt_spectrum_x(None, None, 0, 0, None, None) == rt.RT_EINVAL
+    assert L.rt_spectrum_2d(None, None, 0, 0, None) == rt.RT_EINVAL
+    assert L.rt_reconstruct(None, None, 0, 0, 1.0, None, None, None) == rt.RT_EINVAL
+    assert L.cnop_solve(None, None, None, 0, None, None) == rt.RT_EINVAL
+    assert L.rt_set_kernel_timing(None, 1) == rt.RT_EINVAL
+    assert L.rt_kernel_times(None, None, None, None) == rt.RT_EINVAL
+    assert L.rt_fma_peak(None, None) == rt.RT_EINVAL
+    assert L.rt_last_error(None) == b"null context"
+    assert L.rt_num_instances(None) == 0 and L.rt_field_total(None) == 0
+    assert L.rt_field_offset(None, 0) == 0 and L.rt_field_size(None, 0) == 0
+    L.rt_destroy(None)
+    f = ctypes.CDLL(rt.LIB_PATH).rt_objective_noalloc  # a private handle: no shared prototype changes
+    f.argtypes = [ctypes.c_void_p] * 5
+    f.restype = ctypes.c_int
+    assert f(None, None, None, None, None) == rt.RT_EINVAL
