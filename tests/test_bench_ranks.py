@@ -48,3 +48,19 @@ def test_ranks_get_disjoint_seeded_batches():
     assert a.shape == b.shape == (bench.BATCH * 2 * bench.NY * bench.NX,)
     assert not np.array_equal(a[:1000], b[:1000])
     assert np.array_equal(a, bench.bench_inputs(0))
+
+
+def test_clock_summary_of_nvidia_smi_rows():
+    """The clocks object of the JSON line: median SM clock, highest max clock,
+    every throttle reason that was Active in any sample; unreadable clock
+    fields are skipped."""
+    import bench
+    row = lambda sm, mx, *act: ["0", sm, mx, "900.0", "0x0"] + list(act)
+    na, a = "Not Active", "Active"
+    rows = [row("2032", "2032", na, na, na, na), row("1980", "2032", na, na, na, a),
+            row("[N/A]", "2032", na, na, na, na), row("2010", "2032", na, na, na, na)]
+    out = bench.summarise_clocks(rows)
+    assert out == {"sm_mhz": 2010.0, "sm_max_mhz": 2032.0, "reasons": ["sw_power_cap"], "samples": 4}
+    hot = bench.summarise_clocks([row("1500", "2032", a, na, a, na)])
+    assert hot["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    assert bench.summarise_clocks([])["reasons"] == ["no samples"]
