@@ -6,9 +6,10 @@
  *     Euler equations with a uniform gravity source, ideal-gas EOS;
  *   * Sec. 2.1-2.2, Eq. rho0: periodic x; tanh density interface in
  *     hydrostatic balance; y boundary reflecting or hydrostatic;
- *   * Sec. 2.3: finite-volume Godunov scheme with HLLC fluxes and a gravity
- *     source (this library: PLM on primitive variables, HLLC with Davis wave
- *     speeds, SSP-RK2, CFL time step);
+ *   * Sec. 2.3: finite-volume Godunov scheme with "hybrid HLLC" fluxes and a
+ *     gravity source (this library: PLM on primitive variables, HLLC with
+ *     Davis wave speeds by default, or HLL, or an HLLC/HLL hybrid switched by
+ *     the face pressure ratio (rt_problem.flux); SSP-RK2, CFL time step);
  *   * Sec. 3.1, Eqs. ke, objective, constraint: the forward map F_t from a
  *     velocity perturbation v0, the objective J (final kinetic energy, or the
  *     squared kinetic-energy-density anomaly) and the budget C(v0) <= eps;
