@@ -10,12 +10,20 @@ minimum over ranks of each slab's crossing-time minimum, and sums over cells
 (objective, constraint) are sums over ranks of each slab's own rows. At the
 physical walls (y = y0 and y = y1 of the domain) the slab holds no halo and
 the boundary condition applies as in the whole-domain step.
+
+The reverse sweep works on whole steps: the transposed step maps the
+cotangent of row k back to rows k-4 .. k+4 (two stages of two rows each), and
+the forward map behind row k reads the state four rows further out. A rank
+therefore applies the reverse of one step to its own rows exactly when it
+holds the step's input state and the incoming cotangent with STEP_REVERSE_HALO
+rows on each side; after the step it refreshes the cotangent halos.
 """
 from __future__ import annotations
 
 from dataclasses import dataclass
 
-HALO = 2  # rows on each side that one PLM + flux + update stage reads
+HALO = 2               # rows on each side that one PLM + flux + update stage reads
+STEP_REVERSE_HALO = 8  # rows on each side that the reverse of one RK2 step reads
 
 
 @dataclass(frozen=True)
@@ -28,6 +36,7 @@ class Slab:
     e1: int          # one past the last held row
     down: int | None  # rank owning the rows below, or None at the bottom wall
     up: int | None    # rank owning the rows above, or None at the top wall
+    halo: int = HALO  # halo rows held on each side with a neighbour
 
     @property
     def own(self) -> slice:
@@ -36,11 +45,11 @@ class Slab:
 
     def send_down(self) -> slice:
         """Held-row slice sent to the rank below (its upper halo)."""
-        return slice(self.y0 - self.e0, self.y0 - self.e0 + HALO)
+        return slice(self.y0 - self.e0, self.y0 - self.e0 + self.halo)
 
     def send_up(self) -> slice:
         """Held-row slice sent to the rank above (its lower halo)."""
-        return slice(self.y1 - self.e0 - HALO, self.y1 - self.e0)
+        return slice(self.y1 - self.e0 - self.halo, self.y1 - self.e0)
 
     def recv_down(self) -> slice:
         """Held-row slice filled by the rank below."""
@@ -51,14 +60,14 @@ class Slab:
         return slice(self.y1 - self.e0, self.e1 - self.e0)
 
 
-def slab_rows(ny: int, world: int) -> list[tuple[int, int]]:
+def slab_rows(ny: int, world: int, halo: int = HALO) -> list[tuple[int, int]]:
     """Owned rows [y0, y1) of each rank: ny split as evenly as possible, the
-    first ny % world ranks one row taller; every slab at least HALO rows, so
+    first ny % world ranks one row taller; every slab at least `halo` rows, so
     that a halo comes from a single neighbour."""
     if world < 1:
         raise ValueError("world must be >= 1")
-    if ny < HALO * world:
-        raise ValueError(f"{ny} rows cannot give {world} slabs of at least {HALO} rows")
+    if ny < halo * world:
+        raise ValueError(f"{ny} rows cannot give {world} slabs of at least {halo} rows")
     base, extra = divmod(ny, world)
     out, y = [], 0
     for r in range(world):
@@ -68,13 +77,15 @@ def slab_rows(ny: int, world: int) -> list[tuple[int, int]]:
     return out
 
 
-def slab(ny: int, world: int, rank: int) -> Slab:
-    """The slab of `rank`: owned rows, held rows and neighbours."""
+def slab(ny: int, world: int, rank: int, halo: int = HALO) -> Slab:
+    """The slab of `rank`: owned rows, held rows (with `halo` rows on each
+    side that has a neighbour) and neighbours. The owned rows do not depend on
+    the halo width, as long as every slab has at least `halo` rows."""
     if not 0 <= rank < world:
         raise ValueError("rank out of range")
-    y0, y1 = slab_rows(ny, world)[rank]
+    y0, y1 = slab_rows(ny, world, halo)[rank]
     down = rank - 1 if rank > 0 else None
     up = rank + 1 if rank < world - 1 else None
-    e0 = y0 - HALO if down is not None else y0
-    e1 = y1 + HALO if up is not None else y1
-    return Slab(rank, world, y0, y1, e0, e1, down, up)
+    e0 = y0 - halo if down is not None else y0
+    e1 = y1 + halo if up is not None else y1
+    return Slab(rank, world, y0, y1, e0, e1, down, up, halo)
