@@ -156,6 +156,21 @@ def workload_problems():
     return [I.single_256().replace(T=T_HORIZON) for _ in range(BATCH)]
 
 
+def host_cpu():
+    """The host the CPU baseline ran on: logical CPUs and the CPU model name
+    (None where /proc/cpuinfo does not say)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"host_cpus": os.cpu_count(), "cpu_model": model}
+
+
 def cpu_oracle_sample(n_steps=6):
     """FP64 CPU oracle on a bounded sample of the workload: one 256x768
     instance, n_steps CFL steps forward plus the reverse sweep. Returns
@@ -189,7 +204,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD + " (oracle: bounded sample per step)", "grid": [NX, NY], "T": T_HORIZON},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+                         **host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -309,7 +325,7 @@ def run_ours(args):
         if not args.no_cpu:
             rate, secs, desc = cpu_oracle_sample(6)
             line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
-                                    "seconds": secs}
+                                    "seconds": secs, **host_cpu()}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

@@ -64,3 +64,10 @@ def test_clock_summary_of_nvidia_smi_rows():
     hot = bench.summarise_clocks([row("1500", "2032", a, na, a, na)])
     assert hot["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
     assert bench.summarise_clocks([])["reasons"] == ["no samples"]
+
+
+def test_host_cpu_description():
+    import bench
+    h = bench.host_cpu()
+    assert h["host_cpus"] == __import__("os").cpu_count() and h["host_cpus"] >= 1
+    assert h["cpu_model"] is None or isinstance(h["cpu_model"], str)
