@@ -1,9 +1,18 @@
-"""The paper's forward comparison runs (Sec. 3.5, Tab. comp_runs; Sec. 4.3
-and App. B), composed from the library's entry points: for one configuration,
-the CNOP seed, the random seed it started from, the five-mode seed and the
-90%-power seed advance in one batch, each with its KE(t) and h_mix(t) series
-and its objective at the horizon. Marshalling only: every number comes from
-librt_cnop.so."""
+"""Experiment drivers composed from the library's entry points (marshalling
+only: every number comes from librt_cnop.so).
+
+- comparison_runs: the paper's forward comparison runs (Sec. 3.5, Tab.
+  comp_runs; Sec. 4.3 and App. B): for one configuration, the CNOP seed, the
+  random seed it started from, the five-mode seed and the 90%-power seed
+  advance in one batch, each with its KE(t) and h_mix(t) series and its
+  objective at the horizon.
+- paper_run: one of the paper's three CNOP runs (Tab. runs) from localised
+  random starts, followed by comparison_runs for each seed.
+- horizon_sweep: CNOPs of one box for several horizons T in one batch, with
+  J of the CNOP, the random start and the five-mode seed per T.
+- precision_comparison: the CNOP of one box in FP32 state and in FP64 from
+  the same start under revolve checkpointing; J errors and the CNOP cosine.
+"""
 from __future__ import annotations
 
 import numpy as np
