@@ -229,7 +229,8 @@ rt_status rt_kernel_times(rt_ctx* ctx, double* mean_ms, long long* samples, long
 
 typedef struct {
   int max_iter;          /* total iterations (a resumed run continues up to it) */
-  int gll_memory;        /* non-monotone memory M (max of the last M values); 0 = 10 */
+  int gll_memory;        /* non-monotone memory M (the reference is the smallest of the
+                            last M accepted J values); 0 = 10 */
   int max_backtracks;    /* per iteration; 0 = 30 */
   double armijo_c;       /* sufficient-increase constant, e.g. 1e-4 */
   double alpha_min, alpha_max; /* SPG step safeguards; 0 = 1e-30, 1e30 */
@@ -278,9 +279,9 @@ typedef struct {
  *    <s, y> <= 0 skipped, H0 = <s, y>/<y, y> of the newest stored pair
  *    (||v||/||gh|| when none); if <gh, p> <= 0 the pairs are dropped and
  *    p = (||v||/||gh||) gh; trial points P(v + lam p), lam = 1, 1/2, ...,
- *    accepted once J >= max(last gll_memory J) + armijo_c <gh, P(v + lam p) - v>.
+ *    accepted once J >= min(last gll_memory J) + armijo_c <gh, P(v + lam p) - v>.
  *  RT_CNOP_SPG: d = P(v + alpha g) - v, trial points v + lam d accepted once
- *    J >= max(last gll_memory J) + armijo_c lam <g, d>, and the
+ *    J >= min(last gll_memory J) + armijo_c lam <g, d>, and the
  *    Barzilai-Borwein step alpha = <s,s>/<s,y> clipped to
  *    [alpha_min, alpha_max] (alpha_max when <s,y> <= 0).
  * On return v_inout holds the CNOP of every instance and J_out[i] (nullable)

@@ -22,8 +22,9 @@ Parity status: every function below is pinned by a ``-m "not gpu"`` test
 invariants or brute force, except ``spg`` and ``lbfgs`` at finite amplitude,
 whose results have no closed form (parity unpinned there); they are pinned in
 the small-amplitude limit, where they must reproduce the leading eigenvector of
-the tangent-linear problem, and ``projected_lbfgs`` / ``lbfgs_direction`` are
-pinned on analytic objectives and against the dense BFGS update.
+the tangent-linear problem, and their cores ``projected_spg`` and
+``projected_lbfgs`` / ``lbfgs_direction`` are pinned on analytic objectives
+(and the latter against the dense BFGS update).
 """
 from __future__ import annotations
 
@@ -295,34 +296,38 @@ def random_start(w, xi, h_loc, eps):
     return scale_to_budget(w, v, eps)
 
 
-def spg(w, v_start, eps, iters, memory=10, armijo=1e-4, alpha_min=1e-30, alpha_max=1e30,
-        max_backtracks=30, ek0=None, log=None):
-    """Spectral projected gradient ascent on J over {C <= eps} with the radial
-    projection of Eq. projection and a non-monotone (max over the last
-    ``memory`` values) Armijo backtracking line search (Sec. 3.4).
+def projected_spg(value, value_and_grad, proj, v_start, iters, memory=10, armijo=1e-4, alpha_min=1e-30,
+                  alpha_max=1e30, max_backtracks=30, log=None):
+    """Spectral projected gradient ascent of value(v) over the set onto which
+    proj projects, with the non-monotone Armijo backtracking line search of
+    Grippo, Lampariello & Lucidi (Sec. 3.4): a trial is measured against the
+    worst, i.e. smallest, of the last ``memory`` accepted values, so that J
+    may dip temporarily.
 
-    Iteration k: d = P(v + alpha g) - v; accept v + lam d once
-    J(v + lam d) >= max_recent J + armijo * lam * <g, d>, halving lam otherwise;
-    then alpha = <s, s> / <s, y'> with s the step and y' = -(g_new - g_old)
-    (the gradient change of the minimised objective -J), clipped to
-    [alpha_min, alpha_max], and alpha_max when <s, y'> <= 0. The first alpha
-    is ||v0|| / ||g0||. Returns a dict with v, J, the history and counts."""
-    v = project(w, v_start, eps)
-    J, g, _ = value_and_gradient(w, v, ek0)
+    Iteration k: d = proj(v + alpha g) - v; accept v + lam d once
+    value(v + lam d) >= min_recent + armijo * lam * <g, d>, halving lam
+    otherwise; then alpha = <s, s> / <s, y'> with s the step and
+    y' = -(g_new - g_old) (the gradient change of the minimised objective
+    -value), clipped to [alpha_min, alpha_max], and alpha_max when
+    <s, y'> <= 0. The first alpha is ||v0|| / ||g0||. The stationarity chi of
+    App. A is recorded per iteration. Returns a dict with v, J, the history,
+    the per-iteration records and the evaluation counts."""
+    v = proj(v_start)
+    J, g = value_and_grad(v)
     evals, grads = 1, 1
     hist = [J]
     alpha = float(np.linalg.norm(v) / max(np.linalg.norm(g), 1e-300))
     alpha = min(max(alpha, alpha_min), alpha_max)
     records = []
     for k in range(iters):
-        d = project(w, v + alpha * g, eps) - v
+        d = proj(v + alpha * g) - v
         gd = float(np.sum(g * d))
-        Jref = max(hist[-memory:])
+        Jref = min(hist[-memory:])
         lam = 1.0
         accepted = False
         for _ in range(max_backtracks):
             vt = v + lam * d
-            Jt = objective_value(w, forward(w, vt, ek0=ek0))
+            Jt = value(vt)
             evals += 1
             if Jt >= Jref + armijo * lam * gd:
                 accepted = True
@@ -330,7 +335,7 @@ def spg(w, v_start, eps, iters, memory=10, armijo=1e-4, alpha_min=1e-30, alpha_m
             lam *= 0.5
         if not accepted:
             break
-        Jn, gn, _ = value_and_gradient(w, vt, ek0)
+        Jn, gn = value_and_grad(vt)
         grads += 1
         s = vt - v
         yv = -(gn - g)
@@ -338,12 +343,29 @@ def spg(w, v_start, eps, iters, memory=10, armijo=1e-4, alpha_min=1e-30, alpha_m
         alpha = alpha_max if sy <= 0.0 else min(max(float(np.sum(s * s)) / sy, alpha_min), alpha_max)
         v, J, g = vt, Jn, gn
         hist.append(J)
-        chi = float(np.max(np.abs(project(w, v + g, eps) - v)))
+        chi = float(np.max(np.abs(proj(v + g) - v)))
         records.append({"iter": k, "J": J, "lam": lam, "alpha": alpha, "chi": chi,
                         "grad_norm": float(np.linalg.norm(g))})
         if log is not None:
             log(records[-1])
     return {"v": v, "J": J, "history": hist, "records": records, "evals": evals, "grads": grads}
+
+
+def spg(w, v_start, eps, iters, memory=10, armijo=1e-4, alpha_min=1e-30, alpha_max=1e30,
+        max_backtracks=30, ek0=None, log=None):
+    """Spectral projected gradient ascent (projected_spg) of the workload's
+    objective over {C <= eps} with the radial projection of Eq. projection
+    (Sec. 3.4), starting from P(v_start)."""
+    def value(v):
+        return objective_value(w, forward(w, v, ek0=ek0))
+
+    def value_and_grad(v):
+        J, g, _ = value_and_gradient(w, v, ek0)
+        return J, g
+
+    return projected_spg(value, value_and_grad, lambda v: project(w, v, eps), v_start, iters, memory=memory,
+                         armijo=armijo, alpha_min=alpha_min, alpha_max=alpha_max,
+                         max_backtracks=max_backtracks, log=log)
 
 
 # ------------------------------------- projected L-BFGS, Sec. 3.4 (Eq. projection)
@@ -389,7 +411,7 @@ def projected_lbfgs(value, value_and_grad, proj, v_start, iters, m=10, memory=10
       - if <gh, p> <= 0 while pairs are stored, every pair is dropped and
         p = (||v|| / ||gh||) gh, then tangent (steepest-ascent restart);
       - trial points v(lam) = P(v + lam p), lam = 1, 1/2, 1/4, ...; the first
-        with J(v(lam)) >= max(last ``memory`` accepted J) + armijo <gh, v(lam) - v>
+        with J(v(lam)) >= min(last ``memory`` accepted J) + armijo <gh, v(lam) - v>
         is taken (Grippo-Lampariello-Lucidi non-monotone rule). None within
         ``max_backtracks`` trials ends the run;
       - the pair (s, y) = (v_new - v, -(gh_new - gh)) is stored with
@@ -440,7 +462,7 @@ def projected_lbfgs(value, value_and_grad, proj, v_start, iters, m=10, memory=10
             pairs = [(s, y, 0.0) for s, y, _ in pairs]
             p = tangent(v, steepest_gamma(v, g) * g)
             restart = True
-        Jref = max(hist[-memory:])
+        Jref = min(hist[-memory:])
         lam = 1.0
         accepted = False
         for _ in range(max_backtracks):

@@ -1335,9 +1335,12 @@ rt_status cnop_run(rt_ctx* c, const cnop_params* prm, double* v_inout, int flags
       for (int i = 0; i < N; ++i) term[i] = prm->armijo_c * gs[i];
       return RT_OK;
     };
+    // non-monotone reference (Grippo, Lampariello & Lucidi, for the maximised
+    // J): the worst, i.e. smallest, of the last M accepted values, so that J may
+    // dip temporarily
     for (int i = 0; i < N; ++i) {
       const size_t h0 = st.hist[i].size() > (size_t)M ? st.hist[i].size() - M : 0;
-      Jref[i] = *std::max_element(st.hist[i].begin() + h0, st.hist[i].end());
+      Jref[i] = *std::min_element(st.hist[i].begin() + h0, st.hist[i].end());
     }
     std::vector<char> acc(N, 0);
     for (int i = 0; i < N; ++i) acc[i] = !running(i);
