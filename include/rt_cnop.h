@@ -38,6 +38,24 @@
  *     Scalar outputs (J, C, statistics) are always host arrays.
  *   * The caller owns every array it passes; the library keeps no pointer to
  *     caller memory after a call returns.
+ *
+ * A typical sequence (host arrays, one FP32 batch, error checks elided):
+ *
+ *   rt_problem p[32];  ... fill each instance ...
+ *   rt_options o = {RT_FP32_STATE, RT_CKPT_AUTO, 0.0, 0, RT_STAGE_AUTO};
+ *   rt_ctx* ctx;
+ *   rt_init(p, 32, &o, NULL, &ctx);
+ *   size_t n = rt_field_total(ctx);              // doubles in v0 and grad
+ *   double J[32], *v0 = ..., *grad = ...;         // v0: seeded N(0,1) fields
+ *   double eps[32] = {1e-4, ...};
+ *   rt_project(ctx, v0, 0, eps, 1);               // scale onto C = eps
+ *   rt_gradient(ctx, v0, 0, J, grad, NULL);       // J and dJ/dv0
+ *   cnop_params cp = {0};                         // zero fields take their defaults,
+ *   cp.max_iter = 50;  cp.armijo_c = 1e-4;        // except armijo_c (0 = no sufficient increase)
+ *   cp.eps = eps;  cp.method = RT_CNOP_LBFGS;
+ *   cnop_result cr = {0};
+ *   cnop_solve(ctx, &cp, v0, 0, J, &cr);          // v0 becomes the CNOP
+ *   rt_destroy(ctx);
  */
 #ifndef RT_CNOP_H
 #define RT_CNOP_H
