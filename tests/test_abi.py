@@ -107,3 +107,43 @@ def test_null_arguments_return_einval_without_a_gpu():
     f.argtypes = [ctypes.c_void_p] * 5
     f.restype = ctypes.c_int
     assert f(None, None, None, None, None) == rt.RT_EINVAL
+
+
+C_USER = r"""
+#include <stdlib.h>
+#include "rt_cnop.h"
+int main(void) {
+  rt_problem p[2] = {{0}};
+  rt_options o = {RT_FP32_STATE, RT_CKPT_AUTO, 0.0, 0, RT_STAGE_AUTO};
+  rt_ctx* ctx;
+  if (rt_init(p, 2, &o, NULL, &ctx) != RT_OK) return 1;
+  size_t n = rt_field_total(ctx);
+  double J[2], eps[2] = {1e-4, 1e-4};
+  double *v0 = calloc(n, sizeof(double)), *g = calloc(n, sizeof(double));
+  rt_project(ctx, v0, 0, eps, 1);
+  rt_gradient(ctx, v0, 0, J, g, NULL);
+  cnop_params cp = {0};
+  cp.max_iter = 5; cp.armijo_c = 1e-4; cp.eps = eps; cp.method = RT_CNOP_LBFGS;
+  cnop_result cr = {0};
+  cnop_solve(ctx, &cp, v0, 0, J, &cr);
+  rt_destroy(ctx);
+  free(v0); free(g);
+  return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_a_c_program_links(tmp_path):
+    """include/rt_cnop.h compiles as strict C99 with warnings as errors, and a
+    C caller links against the library (nothing is run)."""
+    import shutil
+    import subprocess
+    from paper_2608_04085_b300 import build
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    lib = build.build()
+    src = tmp_path / "user.c"
+    src.write_text(C_USER)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-L", os.path.dirname(lib), "-lrt_cnop", "-o", str(tmp_path / "user")],
+                   check=True, capture_output=True)
