@@ -91,6 +91,10 @@ def test_branch_signature_counts_every_kink_and_sees_a_crossing(oracle_lib):
     assert zero[1] == 3 * 2 * faces * 10
     lin = o.branch_signature(w.replace(limiter=I.LIM_NONE), np.zeros((2, w.ny, w.nx)), dt)
     assert lin[1] == 3 * 2 * faces * 2
+    # HLL has the same two decisions per face (Davis speeds, branch); the hybrid adds its sensor
+    hll = o.branch_signature(w.replace(limiter=I.LIM_NONE, flux=I.FLUX_HLL), np.zeros((2, w.ny, w.nx)), dt)
+    hyb = o.branch_signature(w.replace(limiter=I.LIM_NONE, flux=I.FLUX_HYBRID), np.zeros((2, w.ny, w.nx)), dt)
+    assert hll[1] == lin[1] and hll[0] != lin[0] and hyb[1] == 3 * 2 * faces * 3
     xi = I.gaussian_field(1, 2, w.ny, w.nx)
     tiny = o.branch_signature(w, 1e-10 * xi, dt)
     assert tiny[1] == zero[1] and tiny[0] != zero[0]
