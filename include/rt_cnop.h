@@ -340,6 +340,19 @@ rt_status rt_spectrum_2d(rt_ctx* ctx, const double* v, int flags, int inst, doub
 rt_status rt_reconstruct(rt_ctx* ctx, const double* v, int flags, int kind, double param, const double* eps,
                          double* out, int* kept_out);
 
+/* Binomial checkpoint plan (Sec. 3.4 names checkpointing; the schedule is
+ * Griewank & Walther's revolve): the forward steps that rt_gradient with
+ * RT_CKPT_REVOLVE recomputes to reverse `steps` time steps with `slots` free
+ * checkpoint slots besides the initial state (slots = cap / slot size - 4),
+ * and Griewank & Walther's minimum t n - beta(slots + 2, t - 1) with
+ * beta(c, t) = C(c + t, c) and t the smallest integer with
+ * beta(slots + 1, t) >= n. The two are equal: the schedule is optimal. A
+ * host computation; it needs no device and no context.
+ *   recomputed  host long long, the schedule's count (NULL: not written);
+ *   optimum     host double, the closed-form minimum (NULL: not written).
+ * Errors: RT_EINVAL (steps < 0 or slots < 0). */
+rt_status rt_revolve_plan(int steps, int slots, long long* recomputed, double* optimum);
+
 /* Measured FMA throughput of the current device (measurement support; the
  * paper has no counterpart): independent fused multiply-add chains in every
  * thread of a grid that fills every SM, FP32 and FP64, best of three timed
@@ -359,13 +372,16 @@ rt_status rt_fma_peak(double* tflops_f32, double* tflops_f64);
  *          layout rt_get_state returns;
  *   ek0    device FP64 reference e_k [ny][nx], or NULL for zero;
  *   J      device FP64 [2]: J[0] = sum e_k dx dy (total kinetic energy),
- *          J[1] = sum (e_k - ek0)^2 dx dy (Eq. objective form).
+ *          J[1] = sum (e_k - ek0)^2 dx dy.
  * The work is queued on cuda_stream (NULL = legacy default stream) and the
  * call returns without waiting for it. Per-block partial sums live in a
  * fixed 256 KiB device array inside the library, so grids above 4,194,304
  * cells return RT_EINVAL (with a message on stderr). The first call on each
  * device looks up that array's device address (cudaGetSymbolAddress) with
- * the device current; make that first call before any stream capture. All
+ * the device current; make that first call before any stream capture. The
+ * address is kept per device number for the life of the process: it does not
+ * survive cudaDeviceReset (which unloads the library's device image), so
+ * calling this entry point after a reset of that device is not supported. All
  * calls share the array: calls whose kernels overlap on the GPU race on it.
  * Errors: RT_EINVAL (null pointer, empty domain, size), RT_ECUDA. */
 rt_status rt_objective_noalloc(const rt_problem* p, const double* state, const double* ek0, double* J,

@@ -46,7 +46,7 @@ def build(force: bool = False) -> str:
     stale = (not os.path.exists(_LIB_PATH)
              or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
     if force or stale:
-        cmd = ["g++", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c++17",
+        cmd = ["g++", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c++17", "-fopenmp",
                "-shared", "-fPIC", "-o", _LIB_PATH, _SRC]
         subprocess.check_call(cmd)
     return _LIB_PATH
@@ -99,6 +99,10 @@ def lib():
         L.o_gradient_dt.argtypes = [pp, dp, ctypes.c_int, dp, dp, dp]
         L.o_gradient_dt.restype = ctypes.c_int
         L.o_forward_signature.argtypes = [pp, dp, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_ulonglong)]
+        L.o_set_threads.argtypes = [ctypes.c_int]
+        L.o_set_threads.restype = None
+        L.o_get_threads.restype = ctypes.c_int
+        L.o_num_procs.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -112,6 +116,21 @@ def _ptr(a):
 
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def set_threads(n):
+    """Host threads of the oracle's row loops (OpenMP); results are bitwise
+    the same for any count. The default is 1."""
+    lib().o_set_threads(int(n))
+
+
+def get_threads():
+    return lib().o_get_threads()
+
+
+def num_procs():
+    """Processors available to this process (OpenMP's count)."""
+    return lib().o_num_procs()
 
 
 def grid_spacing(w):

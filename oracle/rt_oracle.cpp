@@ -28,6 +28,8 @@
 #include <cstring>
 #include <vector>
 
+#include <omp.h>
+
 extern "C" {
 struct OParams {
   int nx, ny;
@@ -61,6 +63,17 @@ static inline void sig_add(int code) {
   g_sig *= 1099511628211ull;
   ++g_sig_n;
 }
+
+// Host threads for the loops over rows (OpenMP). Every parallel loop writes
+// rows or faces of its own and every sum keeps its serial order, so results
+// are bitwise the same for any thread count. One thread by default (no
+// thread pool is started, so processes forked later stay safe); the branch
+// signature, a running hash, always runs on one thread.
+static int g_threads = 1;
+static inline int nthreads() { return g_sig_on ? 1 : g_threads; }
+extern "C" void o_set_threads(int n) { g_threads = n < 1 ? 1 : n; }
+extern "C" int o_get_threads() { return g_threads; }
+extern "C" int o_num_procs() { return omp_get_num_procs(); }
 
 // ---------------------------------------------------------------- dual numbers
 template <int N> struct Dual {
@@ -339,6 +352,7 @@ template <class R> static void fill_ghosts(Ext<R>& X, const OParams& P, double d
 
 template <class R> static void to_ext(const std::vector<R>& U, const Grid& G, const OParams& P, Ext<R>& X) {
   const double gm1 = P.gamma - 1.0;
+#pragma omp parallel for num_threads(nthreads()) schedule(static)
   for (int j = 0; j < G.ny; ++j)
     for (int i = 0; i < G.nx; ++i) {
       R u[4] = {U[G.at(0, j, i)], U[G.at(1, j, i)], U[G.at(2, j, i)], U[G.at(3, j, i)]};
@@ -357,14 +371,17 @@ template <class R, class Q = double> static void stage(const OParams& P, const s
   Ext<R> X(nx, ny);
   to_ext(U, G, P, X);
   std::vector<R> Fx((size_t)ny * nx * 4), Gy((size_t)(ny + 1) * nx * 4);
+#pragma omp parallel for num_threads(nthreads()) schedule(static)
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i)  // face i: left face of cell i
       face_flux(X.at(j, i - 2), X.at(j, i - 1), X.at(j, i), X.at(j, i + 1), 0, P, &Fx[((size_t)j * nx + i) * 4]);
+#pragma omp parallel for num_threads(nthreads()) schedule(static)
   for (int j = 0; j <= ny; ++j)
     for (int i = 0; i < nx; ++i)  // face j: bottom face of cell j
       face_flux(X.at(j - 2, i), X.at(j - 1, i), X.at(j, i), X.at(j + 1, i), 1, P, &Gy[((size_t)j * nx + i) * 4]);
   const Q dtdx = dt / G.dx, dtdy = dt / G.dy;
   out.resize(U.size());
+#pragma omp parallel for num_threads(nthreads()) schedule(static)
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       const R* fl = &Fx[((size_t)j * nx + i) * 4];
@@ -393,7 +410,8 @@ template <class R, class Q = double> static void rk2_step(const OParams& P, std:
 static double cfl_wmin(const OParams& P, const std::vector<double>& U) {
   const Grid G(P);
   const double gm1 = P.gamma - 1.0;
-  double wmin = INFINITY;
+  std::vector<double> row_min(G.ny, INFINITY);  // per-row minima, combined in row order
+#pragma omp parallel for num_threads(nthreads()) schedule(static)
   for (int j = 0; j < G.ny; ++j)
     for (int i = 0; i < G.nx; ++i) {
       double u[4] = {U[G.at(0, j, i)], U[G.at(1, j, i)], U[G.at(2, j, i)], U[G.at(3, j, i)]}, W[4];
@@ -402,8 +420,11 @@ static double cfl_wmin(const OParams& P, const std::vector<double>& U) {
       const double wx = G.dx / (std::fabs(W[1]) + c);
       const double wy = G.dy / (std::fabs(W[2]) + c);
       const double w = wx <= wy ? wx : wy;
-      if (w < wmin) wmin = w;
+      if (w < row_min[j]) row_min[j] = w;
     }
+  double wmin = INFINITY;
+  for (int j = 0; j < G.ny; ++j)
+    if (row_min[j] < wmin) wmin = row_min[j];
   return wmin;
 }
 
@@ -608,7 +629,8 @@ static void stage_vjp(const OParams& P, const std::vector<double>& U, double dt,
   Ext<double> B(nx, ny);  // cotangent of the extended primitive field
   for (auto& b : B.W) b = 0.0;
 
-  auto face_vjp = [&](double* w4[4], double* b4[4], int dir, const double mu[4]) {
+  // (dF/dW)^T mu of one face for its four cells, [cell][var]
+  auto face_vjp = [&](double* w4[4], int dir, const double mu[4], double s16[16]) {
     D16 Wd[4][4];
     for (int c = 0; c < 4; ++c)
       for (int q = 0; q < 4; ++q) { Wd[c][q] = D16(w4[c][q]); Wd[c][q].d[4 * c + q] = 1.0; }
@@ -618,28 +640,42 @@ static void stage_vjp(const OParams& P, const std::vector<double>& U, double dt,
       for (int q = 0; q < 4; ++q) {
         double s = 0.0;
         for (int k = 0; k < 4; ++k) s += mu[k] * F[k].d[4 * c + q];
-        b4[c][q] += s;
+        s16[4 * c + q] = s;
       }
   };
   auto kp = [&](int k, int j, int i) { return kap[G.at(k, j, i)]; };
 
+  // x faces: a face of row j touches only row j, so rows run in parallel
+#pragma omp parallel for num_threads(nthreads()) schedule(static)
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {  // x face i between cells i-1 and i
       const int im = (i - 1 + nx) % nx;
-      double mu[4];
+      double mu[4], s16[16];
       for (int k = 0; k < 4; ++k) mu[k] = dtdx * (kp(k, j, i) - kp(k, j, im));
       double* w4[4] = {X.at(j, i - 2), X.at(j, i - 1), X.at(j, i), X.at(j, i + 1)};
+      face_vjp(w4, 0, mu, s16);
       double* b4[4] = {B.at(j, i - 2), B.at(j, i - 1), B.at(j, i), B.at(j, i + 1)};
-      face_vjp(w4, b4, 0, mu);
+      for (int c = 0; c < 4; ++c)
+        for (int q = 0; q < 4; ++q) b4[c][q] += s16[4 * c + q];
     }
+  // y faces: a face touches four rows, so the faces' contributions are
+  // formed in parallel and then added face by face in the serial order
+  std::vector<double> Sy((size_t)(ny + 1) * nx * 16);
+#pragma omp parallel for num_threads(nthreads()) schedule(static)
   for (int j = 0; j <= ny; ++j)
     for (int i = 0; i < nx; ++i) {  // y face j between cells j-1 and j
       double mu[4];
       for (int k = 0; k < 4; ++k)
         mu[k] = dtdy * ((j < ny ? kp(k, j, i) : 0.0) - (j >= 1 ? kp(k, j - 1, i) : 0.0));
       double* w4[4] = {X.at(j - 2, i), X.at(j - 1, i), X.at(j, i), X.at(j + 1, i)};
+      face_vjp(w4, 1, mu, &Sy[((size_t)j * nx + i) * 16]);
+    }
+  for (int j = 0; j <= ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const double* s16 = &Sy[((size_t)j * nx + i) * 16];
       double* b4[4] = {B.at(j - 2, i), B.at(j - 1, i), B.at(j, i), B.at(j + 1, i)};
-      face_vjp(w4, b4, 1, mu);
+      for (int c = 0; c < 4; ++c)
+        for (int q = 0; q < 4; ++q) b4[c][q] += s16[4 * c + q];
     }
   // fold ghost cotangents onto their source cells (transpose of fill_ghosts)
   for (int j = 0; j < ny; ++j)
@@ -661,6 +697,7 @@ static void stage_vjp(const OParams& P, const std::vector<double>& U, double dt,
       }
     }
   // primitive -> conserved transpose, identity part of b, gravity source
+#pragma omp parallel for num_threads(nthreads()) schedule(static)
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       D4 u[4], W[4];

@@ -38,7 +38,7 @@ EXPORTS = ("rt_init", "rt_destroy", "rt_last_error", "rt_num_instances", "rt_fie
            "rt_field_size", "rt_field_total", "rt_forward", "rt_gradient", "rt_constraint",
            "rt_project", "rt_get_state", "rt_get_dt", "rt_set_kernel_timing", "rt_kernel_times", "rt_stage_kernel",
            "cnop_solve", "rt_objective_noalloc", "rt_forward_series", "rt_spectrum_x", "rt_spectrum_2d",
-           "rt_reconstruct", "rt_fma_peak")
+           "rt_reconstruct", "rt_fma_peak", "rt_revolve_plan")
 
 
 class RtError(RuntimeError):
@@ -151,6 +151,8 @@ def library():
         L.rt_reconstruct.restype = ip
         L.rt_fma_peak.argtypes = [dp, dp]
         L.rt_fma_peak.restype = ip
+        L.rt_revolve_plan.argtypes = [ip, ip, ctypes.POINTER(ctypes.c_longlong), dp]
+        L.rt_revolve_plan.restype = ip
         L.cnop_solve.argtypes = [vp, ctypes.POINTER(CnopParams), vp, ip, dp, ctypes.POINTER(CnopResult)]
         L.cnop_solve.restype = ip
         _lib = L
@@ -411,6 +413,18 @@ class Context:
         out = {k: getattr(res, k) for k in ("iterations", "forward_evals", "gradient_evals", "ms")}
         return v, J, out | {"status": st, "C": C, "chi": chi, "grad_norm": gnorm, "stop": stop,
                             "J_history": hist[:res.iterations + 1]}
+
+
+def revolve_plan(steps, slots):
+    """(recomputed steps of the binomial schedule, Griewank-Walther minimum)
+    for `steps` time steps and `slots` free checkpoint slots (rt_revolve_plan;
+    host arithmetic, no device needed)."""
+    n = ctypes.c_longlong(0)
+    o = ctypes.c_double(0.0)
+    st = library().rt_revolve_plan(int(steps), int(slots), ctypes.byref(n), ctypes.byref(o))
+    if st != RT_OK:
+        raise RtError(st, "rt_revolve_plan: steps and slots must be >= 0")
+    return n.value, o.value
 
 
 def fma_peak():

@@ -36,6 +36,8 @@ static __device__ __align__(256) double g_partials[2 * kMaxBlocks];
 
 // Device address of g_partials, looked up once per device. In host code the
 // symbol's name is only a host-side stand-in, so kernels get this address.
+// The cache lives as long as the process; a cudaDeviceReset unloads the
+// device image it points into, so calls after a reset are not supported.
 double* g_addr[kMaxDevices] = {nullptr};
 std::mutex g_mu;
 

@@ -21,6 +21,7 @@
 #include "../../include/rt_cnop.h"
 #include "rt_internal.h"
 #include "rt_launch.h"
+#include "rt_revolve.h"
 #include "rt_spectra.h"
 
 // The Python binding mirrors these layouts with ctypes.
@@ -603,17 +604,11 @@ rt_status series_impl(rt_ctx* c, const double* d_v, int flags, int every, std::v
   return take(n_done);
 }
 
-// beta(s, t) = C(s + t, s): steps reversible with s checkpoints and t
-// forward repetitions (binomial checkpointing, Griewank & Walther).
-double binom_beta(int s, int t) {
-  double b = 1.0;
-  for (int i = 1; i <= s; ++i) b = b * (t + i) / i;
-  return b;
-}
-
 // Binomial-checkpointing reverse sweep over steps [l, r) given U^l in `Ul`,
-// with `free_slots` checkpoint slots left in `slots`. Every step's adjoint
-// needs U^n and its stage-1 state, recomputed from the nearest checkpoint.
+// with the checkpoint slots in `free` unused; the split points and the count
+// of recomputed steps are those of rt_revolve.h (Griewank & Walther's
+// optimum). Every step's adjoint needs U^n and its stage-1 state, recomputed
+// from the nearest checkpoint.
 template <class T>
 struct Revolve {
   rt_ctx* c;
@@ -659,11 +654,7 @@ struct Revolve {
       }
       return RT_OK;
     }
-    int t = 1;
-    while (binom_beta(s, t) < n) ++t;
-    int left = (int)std::min<double>(binom_beta(s, t - 1), (double)(n - 1));
-    if (left < 1) left = 1;
-    const int m = l + left;
+    const int m = l + rt::revolve_split(n, s);
     void* Um = free.back();
     free.pop_back();
     CHK(advance(l, m, Ul, Um));
@@ -2019,6 +2010,13 @@ rt_status cnop_solve(rt_ctx* c, const cnop_params* prm, double* v_inout, int fla
   const float ms = tm.stop();
   if (res) res->ms = ms;
   return s;
+}
+
+rt_status rt_revolve_plan(int steps, int slots, long long* recomputed, double* optimum) {
+  if (steps < 0 || slots < 0) return RT_EINVAL;
+  if (recomputed) *recomputed = rt::revolve_recomputed(steps, slots);
+  if (optimum) *optimum = rt::revolve_optimum(steps, slots);
+  return RT_OK;
 }
 
 }  // extern "C"

@@ -275,9 +275,21 @@ __device__ __forceinline__ void hll(T rL, T uL, T vL, T pL, T rR, T uR, T vR, T 
     for (int k = 0; k < 4; ++k) F[k] = FR[k];
     return;
   }
+  const T D = SR - SL, SLR = SL * SR;
+  if constexpr (sizeof(T) == 4) {
+    // FP32: U_R - U_L from differences of the primitives. p_R - p_L and
+    // rho_R - rho_L of nearby face states are exact, so the diffusive term
+    // rounds relative to the jump; E_R - E_L formed from the two O(1)
+    // energies would round relative to the background energy p/(gamma-1).
+    // The same values as the textbook form below in exact arithmetic.
+    const T dU[4] = {rR - rL, rR * uR - rL * uL, rR * vR - rL * vL,
+                     (pR - pL) / gm1 + T(0.5) * (rR * (uR * uR + vR * vR) - rL * (uL * uL + vL * vL))};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) F[k] = ((SR * FL[k] - SL * FR[k]) + SLR * dU[k]) / D;
+    return;
+  }
   const T UL[4] = {rL, rL * uL, rL * vL, EL};
   const T UR[4] = {rR, rR * uR, rR * vR, ER};
-  const T D = SR - SL, SLR = SL * SR;
 #pragma unroll
   for (int k = 0; k < 4; ++k) F[k] = ((SR * FL[k] - SL * FR[k]) + SLR * (UR[k] - UL[k])) / D;
 }

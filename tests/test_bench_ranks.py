@@ -43,11 +43,27 @@ def test_timing_reduction_two_ranks():
 
 def test_ranks_get_disjoint_seeded_batches():
     import bench
-    a = bench.bench_inputs(0)
-    b = bench.bench_inputs(1)
-    assert a.shape == b.shape == (bench.BATCH * 2 * bench.NY * bench.NX,)
+    a = bench.config_inputs(bench.make_config("default", 0))
+    b = bench.config_inputs(bench.make_config("default", 1))
+    assert a.shape == b.shape == (32 * 2 * bench.NY * bench.NX,)
     assert not np.array_equal(a[:1000], b[:1000])
-    assert np.array_equal(a, bench.bench_inputs(0))
+    assert np.array_equal(a, bench.config_inputs(bench.make_config("default", 0)))
+
+
+def test_uneven_and_high_resolution_configurations():
+    """The uneven batch: 32 x 128x384, 24 x 256x768, 8 x 512x1536 in that
+    order, T = 2, budgets cycling 1e-5, 1e-4, 1e-3 by instance, seed = index;
+    the high-resolution case: one 1024x3072 instance, T = 6, revolve capped
+    at 40 GB."""
+    import bench
+    c = bench.make_config("uneven64", 0)
+    assert [(w.nx, w.ny) for w in c.problems] == [(128, 384)] * 32 + [(256, 768)] * 24 + [(512, 1536)] * 8
+    assert {w.T for w in c.problems} == {2.0}
+    assert c.deltas[:4] == [1e-5, 1e-4, 1e-3, 1e-5] and c.seeds == list(range(64))
+    assert bench.make_config("uneven64", 1).seeds == list(range(64, 128))
+    h = bench.make_config("hires", 0)
+    assert [(w.nx, w.ny, w.T) for w in h.problems] == [(1024, 3072, 6.0)]
+    assert h.cap_bytes == 40e9
 
 
 def test_clock_summary_of_nvidia_smi_rows():

@@ -206,3 +206,32 @@ def test_cnop_rejects_bad_arguments():
         # the context stays usable, with every instance switched back on
         J, _, _ = ctx.forward(np.zeros(2 * w.nx * w.ny))
         assert np.isfinite(J[0])
+
+
+def test_paper_unit_square_fp32_against_fp64():
+    """The paper's configuration (Sec. 2 and its parameter table: unit square,
+    gamma 5/3, g = 1, hydrostatic walls, u_y only, squared e_k anomaly,
+    eps = 1e-6, localised start with h_loc = 0.1) at 128 x 128 and t* = 2.
+    FP32 state against FP64 from the same start: J within 1e-4, and the
+    projected L-BFGS CNOP after 8 iterations within cosine 0.999 with J
+    within 1e-4."""
+    import paper_2608_04085_b300 as rt
+    w = I.paper_unit_square(128, 2.0)
+    eps, h_loc, iters = 1e-6, 0.1, 8
+    xi = I.gaussian_field(0, w.ncomp, w.ny, w.nx).ravel()
+    out = {}
+    for prec in (rt.RT_FP64, rt.RT_FP32_STATE):
+        with rt.Context([w], precision=prec) as ctx:
+            v0, J0, _ = ctx.cnop(xi, eps, 0, method=rt.RT_CNOP_LBFGS, h_loc=h_loc)
+            Jf, _, _ = ctx.forward(v0)
+            v, J, res = ctx.cnop(xi, eps, iters, method=rt.RT_CNOP_LBFGS, h_loc=h_loc)
+            assert res["status"] == rt.RT_OK
+            out[prec] = (v0, Jf[0], v, J[0])
+    v0_64, Jf64, v64, J64 = out[rt.RT_FP64]
+    v0_32, Jf32, v32, J32 = out[rt.RT_FP32_STATE]
+    assert np.array_equal(v0_64, v0_32)  # the start is FP64 in both
+    assert abs(Jf32 - Jf64) <= 1e-4 * abs(Jf64), (Jf32, Jf64)
+    cos = abs(v32 @ v64) / (np.linalg.norm(v32) * np.linalg.norm(v64))
+    assert cos >= 0.999, cos
+    assert abs(J32 - J64) <= 1e-4 * abs(J64), (J32, J64)
+    assert J64 > Jf64  # the search raised J

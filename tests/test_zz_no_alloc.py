@@ -71,3 +71,34 @@ def test_noalloc_rejects_grid_above_scratch_limit():
     st = f(ctypes.byref(prob), ctypes.c_void_p(d.data_ptr()), None, ctypes.c_void_p(d.data_ptr()),
            ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == rt.RT_EINVAL
+
+
+@pytest.mark.parametrize("nx,ny", [(256, 768), (2048, 2048)], ids=["768_blocks", "at_the_limit"])
+def test_noalloc_many_blocks_and_the_size_limit(nx, ny):
+    """Grids of more than 256 blocks exercise the strided loop of the final
+    reduction; 2048 x 2048 is exactly the 4,194,304-cell limit (16,384
+    blocks, every partial slot in use) and must be accepted. Both against
+    rt_forward's J_KE of the same one-step run, on two calls in a row."""
+    import torch
+    import paper_2608_04085_b300 as rt
+    f = _noalloc_fn()
+    w = I.rt_box(nx, ny, nsteps=1)
+    with rt.Context([w], precision=rt.RT_FP64) as ctx:
+        v = ctx.project(I.gaussian_field(9, 2, ny, nx).ravel(), 1e-4, to_budget=True)
+        _, Jke, _ = ctx.forward(v)
+        U = ctx.state(0)
+    d_U = torch.from_numpy(np.ascontiguousarray(U)).to("cuda")
+    ek = 0.5 * (U[1] * U[1] + U[2] * U[2]) / U[0]
+    dA = ((w.x1 - w.x0) / nx) * ((w.y1 - w.y0) / ny)
+    stream = torch.cuda.current_stream().cuda_stream
+    prob = rt.make_problem(w)
+    for call in range(2):
+        d_J = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+        st = f(ctypes.byref(prob), ctypes.c_void_p(d_U.data_ptr()), None, ctypes.c_void_p(d_J.data_ptr()),
+               ctypes.c_void_p(stream))
+        assert st == rt.RT_OK, (call, st)
+        torch.cuda.synchronize()
+        out = d_J.cpu().numpy()
+        assert out[0] == pytest.approx(Jke[0], rel=1e-12), call
+        # with no reference field J[1] is the sum of e_k^2 dA
+        assert out[1] == pytest.approx(np.sum(ek * ek) * dA, rel=1e-12), call
