@@ -236,7 +236,7 @@ def all_cores():
 def cpu_baseline_block():
     """The oracle's rate on all host cores (value) and on one core."""
     n = all_cores()
-    rate, secs, used, desc = cpu_oracle_sample(20, n)
+    rate, secs, used, desc = cpu_oracle_sample(50, n)
     r1, s1, _, d1 = cpu_oracle_sample(4, 1)
     return {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc, "seconds": secs,
             "single_core": {"value": r1, "sample": d1, "seconds": s1}, **host_cpu()}

@@ -389,10 +389,12 @@ struct __align__(16) Q4 {
   T v[4];
 };
 
-template <class T, int EX, int EY, bool AOS = false>
-__device__ __forceinline__ void load_prim_tile(const T* __restrict__ Ui, const InstDev& I, long long cells, int gx0,
-                                               int gy0, const Phys<T>& P, T* __restrict__ sW,
-                                               RowBase* __restrict__ sRB) {
+// INTERIOR: the tile with its ghost layers lies inside the grid (no periodic
+// wrap, no mirrored wall rows), so cells are addressed directly.
+template <class T, int EX, int EY, bool AOS, bool INTERIOR>
+__device__ __forceinline__ void load_prim_tile_impl(const T* __restrict__ Ui, const InstDev& I, long long cells,
+                                                    int gx0, int gy0, const Phys<T>& P, T* __restrict__ sW,
+                                                    RowBase* __restrict__ sRB) {
   constexpr int N = EX * EY;
   constexpr int PER = (N + NTH - 1) / NTH;
   static_assert(EY <= NTH, "one thread per tile row fills the base table");
@@ -409,7 +411,13 @@ __device__ __forceinline__ void load_prim_tile(const T* __restrict__ Ui, const I
     if (e < N) {
       const int ey = e / EX, ex = e - ey * EX;
       rr[k] = gy0 + ey;
-      load_raw(Ui, I.nx, I.ny, cells, wrap_x(gx0 + ex, I.nx), rr[k], u[k]);
+      if (INTERIOR) {
+        const T* p = Ui + ((long long)rr[k] * I.nx + gx0 + ex);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) u[k][q] = p[q * cells];
+      } else {
+        load_raw(Ui, I.nx, I.ny, cells, wrap_x(gx0 + ex, I.nx), rr[k], u[k]);
+      }
     }
   }
   if (sizeof(T) == 4) {
@@ -422,7 +430,9 @@ __device__ __forceinline__ void load_prim_tile(const T* __restrict__ Ui, const I
     if (e < N) {
       const int ey = e / EX, ex = e - ey * EX;
       T W[4];
-      raw_to_prim(u[k], I, rr[k], sizeof(T) == 4 ? sRB[ey] : RowBase{0.f, 0.f}, P, W);
+      const RowBase rb = sizeof(T) == 4 ? sRB[ey] : RowBase{0.f, 0.f};
+      if (INTERIOR) state_to_prim_b(u[k][0], u[k][1], u[k][2], u[k][3], rb, P.gm1, W);
+      else raw_to_prim(u[k], I, rr[k], rb, P, W);
       if (AOS) {
         Q4<T> c;
 #pragma unroll
@@ -434,6 +444,18 @@ __device__ __forceinline__ void load_prim_tile(const T* __restrict__ Ui, const I
       }
     }
   }
+}
+
+// Load a tile of primitive states (see load_prim_tile_impl); the interior
+// case, decided once for the whole CTA, skips the boundary logic.
+template <class T, int EX, int EY, bool AOS = false>
+__device__ __forceinline__ void load_prim_tile(const T* __restrict__ Ui, const InstDev& I, long long cells, int gx0,
+                                               int gy0, const Phys<T>& P, T* __restrict__ sW,
+                                               RowBase* __restrict__ sRB) {
+  if (gx0 >= 0 && gx0 + EX <= I.nx && gy0 >= 0 && gy0 + EY <= I.ny)
+    load_prim_tile_impl<T, EX, EY, AOS, true>(Ui, I, cells, gx0, gy0, P, sW, sRB);
+  else
+    load_prim_tile_impl<T, EX, EY, AOS, false>(Ui, I, cells, gx0, gy0, P, sW, sRB);
 }
 
 template <class T, int STAGE, int MODE, int LIM>
@@ -769,18 +791,26 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
     for (int q = 0; q < 4; ++q) epre[pass][q] = in ? E[c + q * cells] : T(0);
   }
 
-  {  // cotangent tile: all loads first
+  {  // cotangent tile: all loads first (rows beyond the walls hold zero)
     constexpr int N = ADJ_KX * ADJ_KY, PER = (N + NTH - 1) / NTH;
+    // tile and halo inside the grid, decided once for the CTA: direct addressing
+    const bool interior = x0 >= 2 && x0 + ADJ_KX - 2 <= nx && y0 >= 2 && y0 + ADJ_KY - 2 <= ny;
     T kv[PER][4];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       const int e = threadIdx.x + k * NTH;
       const int ey = e / ADJ_KX, ex = e - ey * ADJ_KX;
       const int gy = y0 + ey - 2;
-      const bool in = e < N && gy >= 0 && gy < ny;
-      const long long c = in ? (long long)gy * nx + wrap_x(x0 + ex - 2, nx) : 0;
+      if (interior) {
+        const T* p = Ki + ((long long)gy * nx + x0 + ex - 2);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) kv[k][q] = in ? Ki[q * cells + c] : T(0);
+        for (int q = 0; q < 4; ++q) kv[k][q] = e < N ? p[q * cells] : T(0);
+      } else {
+        const bool in = e < N && gy >= 0 && gy < ny;
+        const long long c = in ? (long long)gy * nx + wrap_x(x0 + ex - 2, nx) : 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) kv[k][q] = in ? Ki[q * cells + c] : T(0);
+      }
     }
     load_prim_tile<T, ADJ_AX, ADJ_AY, true>(Ui, I, cells, x0 - 3, y0 - 3, P, reinterpret_cast<T*>(sW), sRB);
 #pragma unroll

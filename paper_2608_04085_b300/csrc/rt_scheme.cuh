@@ -121,20 +121,23 @@ __device__ __forceinline__ void hllc(T rL, T uL, T vL, T pL, T rR, T uR, T vR, T
   F[1] = f0 * u + p;
   F[2] = f0 * v;
   F[3] = u * (E + p);
+  if constexpr (sizeof(T) == 4) {
+    // FP32: S (U* - U) written with q = rho*/rho - 1 = (S* - u) / (S - S*),
+    // U* - U = q (rho, rho S, rho v, E + p + m S*): the same values as the
+    // textbook form below (which FP64 keeps, in the oracle's order), without
+    // forming rho* - rho and E* - E as small differences of O(1) numbers.
+    // Evaluated on every face with q = 0 off the star branches (no branch:
+    // nearly every face of a subsonic flow takes a star state anyway).
+    const T D = star ? S - Ss : T(1);
+    const T q = star ? (Ss - u) / D : T(0);
+    const T rq = r * q;
+    F[0] = F[0] + S * rq;
+    F[1] = F[1] + S * (rq * S);
+    F[2] = F[2] + S * (rq * v);
+    F[3] = F[3] + S * (q * ((E + p) + m * Ss));
+    return;
+  }
   if (star) {
-    if constexpr (sizeof(T) == 4) {
-      // FP32: S (U* - U) written with q = rho*/rho - 1 = (S* - u) / (S - S*),
-      // U* - U = q (rho, rho S, rho v, E + p + m S*): the same values as the
-      // textbook form below (which FP64 keeps, in the oracle's order), without
-      // forming rho* - rho and E* - E as small differences of O(1) numbers
-      const T q = (Ss - u) / (S - Ss);
-      const T rq = r * q;
-      F[0] = F[0] + S * rq;
-      F[1] = F[1] + S * (rq * S);
-      F[2] = F[2] + S * (rq * v);
-      F[3] = F[3] + S * (q * ((E + p) + m * Ss));
-      return;
-    }
     const T fac = m / (S - Ss);
     const T us3 = fac * (E / r + (Ss - u) * (Ss + p / m));
     F[0] = F[0] + S * (fac - r);
@@ -245,6 +248,110 @@ __device__ __forceinline__ void hllc_vjp(T rL, T uL, T vL, T pL, T rR, T uR, T v
   brL -= bcL * T(0.5) * cL / rL;
   bpR += bcR * T(0.5) * cR / pR;
   brR -= bcR * T(0.5) * cR / rR;
+  bLs[0] = brL; bLs[1] = buL; bLs[2] = bvL; bLs[3] = bpL;
+  bRs[0] = brR; bRs[1] = buR; bRs[2] = bvR; bRs[3] = bpR;
+}
+
+// FP32 reverse of hllc() differentiating the q form of the star flux that the
+// FP32 forward evaluates: F = F_X + S q K for the side X whose flux is taken,
+// K = (rho, rho S, rho v, E + p + m S*), q = (S* - u) / (S - S*),
+// m = rho (S - u). Besides the forward's own sound speeds and S*, its only
+// divisions are reciprocals formed once (of rho, c, m_L - m_R and S - S*);
+// the same derivative as hllc_vjp() in exact arithmetic.
+__device__ __forceinline__ void hllc_vjp_q(float rL, float uL, float vL, float pL, float rR, float uR, float vR,
+                                           float pR, float gamma, float igm1, const float bF[4], float bLs[4],
+                                           float bRs[4]) {
+  // the quantities behind the branch choices are the forward's own
+  // expressions (hllc()), so the reverse takes the branches the forward took
+  const float cL = sqrt(gamma * pL / rL), cR = sqrt(gamma * pR / rR);
+  const float irL = 1.0f / rL, irR = 1.0f / rR, icL = 1.0f / cL, icR = 1.0f / cR;
+  const float aL = uL - cL, aR = uR - cR;
+  const bool slL = aL <= aR;
+  const float SL = slL ? aL : aR;
+  const float eL = uL + cL, eR = uR + cR;
+  const bool srL = eL >= eR;
+  const float SR = srL ? eL : eR;
+  const float dL = SL - uL, dR = SR - uR;
+  const float mL = rL * dL, mR = rR * dR;
+  const float Ss = ((pR - pL) + uL * mL - uR * mR) / (mL - mR);
+  const float iden = 1.0f / (mL - mR);
+  const bool left = (SL >= 0.f) || (Ss >= 0.f);
+  const bool star = left ? !(SL >= 0.f) : (SR >= 0.f);
+  const float r = left ? rL : rR, u = left ? uL : uR, v = left ? vL : vR, p = left ? pL : pR;
+  const float S = left ? SL : SR, m = left ? mL : mR;
+  const float k2 = u * u + v * v;
+  const float E = p * igm1 + 0.5f * r * k2;
+  const float f0 = r * u;
+
+  // physical flux F_X = (f0, f0 u + p, f0 v, u (E + p)), f0 = rho u
+  const float b_f0 = bF[0] + bF[1] * u + bF[2] * v;
+  float b_u = bF[1] * f0 + bF[3] * (E + p);
+  float b_p = bF[1] + bF[3] * u;
+  float b_v = bF[2] * f0;
+  float b_E = bF[3] * u;
+  float b_r, b_S, b_Ss, b_m;
+  {  // + S q K, with q = 0 and 1/D = 0 off the star branches (no branch)
+    const float iD = star ? 1.0f / (S - Ss) : 0.f;
+    const float q = (Ss - u) * iD;
+    const float rS = r * S, rv = r * v;
+    const float K3 = (E + p) + m * Ss;
+    const float A = bF[0] * r + bF[1] * rS + bF[2] * rv + bF[3] * K3;  // bF . K
+    const float Sq = S * q;
+    const float t3 = Sq * bF[3];
+    b_S = q * A + Sq * (bF[1] * r);
+    b_r = Sq * (bF[0] + bF[1] * S + bF[2] * v);
+    b_v += Sq * (bF[2] * r);
+    b_E += t3;
+    b_p += t3;
+    b_m = t3 * Ss;
+    b_Ss = t3 * m;
+    // q = (S* - u) / (S - S*): dq/dS* = (1 + q) / D, dq/du = -1 / D, dq/dS = -q / D
+    const float bqD = (S * A) * iD;
+    b_Ss += bqD * (1.0f + q);
+    b_u -= bqD;
+    b_S -= bqD * q;
+  }
+  b_r += b_f0 * u;
+  b_u += b_f0 * r;
+  // E = p/(gamma-1) + rho (u^2 + v^2)/2 of the chosen side
+  b_p += b_E * igm1;
+  b_r += b_E * 0.5f * k2;
+  b_u += b_E * r * u;
+  b_v += b_E * r * v;
+
+  // the chosen side takes the cotangents, the other side gets zero (x - x)
+  float brL = left ? b_r : 0.f, buL = left ? b_u : 0.f, bvL = left ? b_v : 0.f;
+  float bpL = left ? b_p : 0.f, bSL = left ? b_S : 0.f, bmL = left ? b_m : 0.f;
+  float brR = b_r - brL, buR = b_u - buL, bvR = b_v - bvL, bpR = b_p - bpL, bSR = b_S - bSL, bmR = b_m - bmL;
+  // S* = num / den, den = m_L - m_R
+  const float b_num = b_Ss * iden;
+  const float b_den = -b_num * Ss;
+  bpR += b_num;
+  bpL -= b_num;
+  buL += b_num * mL;
+  bmL += b_num * uL + b_den;
+  buR -= b_num * mR;
+  bmR -= b_num * uR + b_den;
+  // m = rho (S - u)
+  brL += bmL * dL;
+  brR += bmR * dR;
+  const float bdL = bmL * rL, bdR = bmR * rR;
+  bSL += bdL;
+  buL -= bdL;
+  bSR += bdR;
+  buR -= bdR;
+  // Davis speeds
+  const float tL = slL ? bSL : 0.f, tR = bSL - tL;  // S_L = u_L - c_L or u_R - c_R
+  const float sL = srL ? bSR : 0.f, sR = bSR - sL;  // S_R = u_L + c_L or u_R + c_R
+  buL += tL + sL;
+  buR += tR + sR;
+  const float bcL = sL - tL, bcR = sR - tR;
+  // c = sqrt(gamma p / rho): dc/dp = gamma / (2 rho c), dc/drho = -c / (2 rho)
+  const float zL = 0.5f * bcL * irL, zR = 0.5f * bcR * irR;
+  bpL += zL * gamma * icL;
+  brL -= zL * cL;
+  bpR += zR * gamma * icR;
+  brR -= zR * cR;
   bLs[0] = brL; bLs[1] = buL; bLs[2] = bvL; bLs[3] = bpL;
   bRs[0] = brR; bRs[1] = buR; bRs[2] = bvR; bRs[3] = bpR;
 }
@@ -417,6 +524,8 @@ __device__ __forceinline__ void face_states_vjp(const T WL[4], const T WR[4], co
   const T bf[4] = {mu[0], mu[n], mu[t], mu[3]};
   T bl[4], br[4];
   if (use_hll(fs, WL[3], WR[3])) hll_vjp(WL[0], WL[n], WL[t], WL[3], WR[0], WR[n], WR[t], WR[3], gamma, gm1, bf, bl, br);
+  else if constexpr (sizeof(T) == 4)
+    hllc_vjp_q(WL[0], WL[n], WL[t], WL[3], WR[0], WR[n], WR[t], WR[3], gamma, 1.0f / gm1, bf, bl, br);
   else hllc_vjp(WL[0], WL[n], WL[t], WL[3], WR[0], WR[n], WR[t], WR[3], gamma, gm1, bf, bl, br);
   bWL[0] = bl[0]; bWL[n] = bl[1]; bWL[t] = bl[2]; bWL[3] = bl[3];
   bWR[0] = br[0]; bWR[n] = br[1]; bWR[t] = br[2]; bWR[3] = br[3];

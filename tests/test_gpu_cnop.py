@@ -212,9 +212,11 @@ def test_paper_unit_square_fp32_against_fp64():
     """The paper's configuration (Sec. 2 and its parameter table: unit square,
     gamma 5/3, g = 1, hydrostatic walls, u_y only, squared e_k anomaly,
     eps = 1e-6, localised start with h_loc = 0.1) at 128 x 128 and t* = 2.
-    FP32 state against FP64 from the same start: J within 1e-4, and the
-    projected L-BFGS CNOP after 8 iterations within cosine 0.999 with J
-    within 1e-4."""
+    FP32 state against FP64 from the same start: J within 1e-4 at the start;
+    the projected L-BFGS CNOPs after 8 iterations within cosine 0.999; and
+    at the FP32 CNOP the FP32 J within 1e-4 of the FP64 J of that same
+    point. (The two searches follow slightly different paths, so their final
+    J differ by more than the evaluation error.)"""
     import paper_2608_04085_b300 as rt
     w = I.paper_unit_square(128, 2.0)
     eps, h_loc, iters = 1e-6, 0.1, 8
@@ -233,5 +235,11 @@ def test_paper_unit_square_fp32_against_fp64():
     assert abs(Jf32 - Jf64) <= 1e-4 * abs(Jf64), (Jf32, Jf64)
     cos = abs(v32 @ v64) / (np.linalg.norm(v32) * np.linalg.norm(v64))
     assert cos >= 0.999, cos
-    assert abs(J32 - J64) <= 1e-4 * abs(J64), (J32, J64)
-    assert J64 > Jf64  # the search raised J
+    with rt.Context([w], precision=rt.RT_FP64) as ctx:
+        J32_in64 = ctx.forward(v32)[0][0]
+    assert abs(J32 - J32_in64) <= 1e-4 * abs(J32_in64), (J32, J32_in64)
+    # the two 8-iteration searches end at different points of the same ridge
+    # (cosine above); their J differ by a few 1e-3 (7e-4 and 2.6e-3 measured
+    # on builds that differ only in FP32 rounding), so only a loose bound here
+    assert abs(J32 - J64) <= 1e-2 * abs(J64), (J32, J64)
+    assert J64 > Jf64 and J32 > Jf32  # the search raised J
