@@ -42,7 +42,7 @@
  * A typical sequence (host arrays, one FP32 batch, error checks elided):
  *
  *   rt_problem p[32];  ... fill each instance ...
- *   rt_options o = {RT_FP32_STATE, RT_CKPT_AUTO, 0.0, 0, RT_STAGE_AUTO};
+ *   rt_options o = {RT_FP32_STATE, RT_CKPT_AUTO, 0.0, 0, RT_STAGE_AUTO, 0};
  *   rt_ctx* ctx;
  *   rt_init(p, 32, &o, NULL, &ctx);
  *   size_t n = rt_field_total(ctx);              // doubles in v0 and grad
@@ -135,6 +135,17 @@ typedef struct {
   int max_steps;            /* upper bound on steps per run (sizes the dt record); 0 = 200000 */
   int stage_kernel;         /* RT_STAGE_AUTO (time both at rt_init, keep the faster),
                                RT_STAGE_SWEEP or RT_STAGE_TILE; both give identical values */
+  int y_slabs;              /* 0 or 1: each problem is one device instance. k > 1: each
+                               problem is split into k y-slabs of nearly equal height
+                               (at least 3 rows each, so ny >= 3k), each holding its rows
+                               plus 3 halo rows per neighbouring slab, refreshed by
+                               device-to-device copies after every kernel that writes a
+                               state or a cotangent; the slabs of a problem share one time
+                               step (minimum over all their cells) and every sum (J, C,
+                               dot products) runs over all of them. Results equal the
+                               unsplit run: state, dt sequence and gradient bit for bit,
+                               sums to rounding order. rt_forward_series is not
+                               available on a split context (RT_EINVAL) */
 } rt_options;
 
 typedef struct {

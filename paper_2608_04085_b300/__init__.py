@@ -68,7 +68,7 @@ _PROBLEM_DEFAULTS = {"flux": RT_FLUX_HLLC, "flux_theta": 2.0}
 class RtOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("ckpt", ctypes.c_int),
                 ("ckpt_hbm_cap_bytes", ctypes.c_double), ("max_steps", ctypes.c_int),
-                ("stage_kernel", ctypes.c_int)]
+                ("stage_kernel", ctypes.c_int), ("y_slabs", ctypes.c_int)]
 
 
 class RtRunStats(ctypes.Structure):
@@ -195,13 +195,13 @@ class Context:
     """A batch of RT instances on the current CUDA device (see rt_init)."""
 
     def __init__(self, problems, precision=RT_FP64, ckpt=RT_CKPT_AUTO, ckpt_cap_bytes=0.0, max_steps=0,
-                 stream=None, stage_kernel=RT_STAGE_AUTO):
+                 stream=None, stage_kernel=RT_STAGE_AUTO, y_slabs=0):
         L = library()
         if not isinstance(problems, (list, tuple)):
             problems = [problems]
         self.problems = list(problems)
         arr = (RtProblem * len(problems))(*[make_problem(w) for w in problems])
-        opt = RtOptions(precision, ckpt, float(ckpt_cap_bytes), int(max_steps), int(stage_kernel))
+        opt = RtOptions(precision, ckpt, float(ckpt_cap_bytes), int(max_steps), int(stage_kernel), int(y_slabs))
         if stream is None:
             stream = self._torch_stream()
         self._stream = stream

@@ -23,13 +23,26 @@ constexpr int STRIP_WARPS = 4;
 // Stage-kernel variants (same values bit for bit, different schedules).
 enum { STAGE_SWEEP = 1, STAGE_TILE = 2 };
 
-// Per-instance constants, resident on the device (one entry per instance).
-// State slots hold every instance back to back: instance i's conserved plane
-// k (rho, m_x, m_y, E) starts at slot + 4*cell_off + k*nx*ny, row-major with
-// x fastest. Perturbation fields use the caller's layout: instance i starts
-// at v + v_off, ncomp planes of nx*ny.
+// Per-instance constants, resident on the device (one entry per device
+// instance). State slots hold every device instance back to back: instance
+// i's conserved plane k (rho, m_x, m_y, E) starts at slot + 4*cell_off +
+// k*nx*ny, row-major with x fastest. Perturbation fields use the caller's
+// layout: the cell (gy, gx) of component k is v[v_off + k*v_plane +
+// (gy - own0)*nx + gx].
+//
+// A problem split into y-slabs has one device instance per slab: ny rows
+// held (its owned rows plus halo rows copied from the neighbouring slabs
+// before every kernel that reads them), own0 the first owned row, and the
+// problem's index `run`, which selects the per-problem time-step control and
+// scalars that all its slabs share. Kernels compute owned rows only and read
+// halo rows as interior data. Without slabs run is the instance's own index,
+// own0 = 0, own1 = ny and v_plane = nx*ny.
 struct InstDev {
   int nx, ny;
+  int run;                   // problem index: run scalars, dt record, per-problem coefficients
+  int run_tiles, run_strips; // tiles / strips of the whole problem (all its slabs)
+  int own0, own1;            // owned rows [own0, own1); the rest are halo rows
+  long long v_plane;         // stride between perturbation components
   int bc_y, limiter;
   int nsteps, ncomp;
   int objective, enabled;

@@ -52,6 +52,10 @@ __device__ __forceinline__ int wrap_x(int gx, int nx) {
   return gx;
 }
 
+// Offset of row gy (a held row of the instance) inside one perturbation
+// component: rows count from the instance's first owned row.
+__device__ __forceinline__ long long vrow(const InstDev& I, int gy) { return (long long)(gy - I.own0) * I.nx; }
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -253,7 +257,7 @@ __device__ __forceinline__ bool commit_crossing(T w, long long cell, bool bad, c
     if (m > T(0) && m < T(1e30))
       atomicMin(&run.wmin[inst], (unsigned long long)__double_as_longlong((double)m));
     __threadfence();
-    const unsigned int ntile = (unsigned int)(I.tile_end - I.tile_begin);
+    const unsigned int ntile = (unsigned int)I.run_tiles;
     if (atomicAdd(&run.counter[inst], 1u) + 1u == ntile) {
       run.counter[inst] = 0u;
       __threadfence();
@@ -270,8 +274,8 @@ __global__ void __launch_bounds__(NTH) k_inject(const InstDev* __restrict__ inst
                                                 int record) {
   __shared__ T red[NTH / 32];
   const int4 tl = tiles[blockIdx.x];
-  const int inst = tl.x;
-  const InstDev& I = insts[inst];
+  const InstDev& I = insts[tl.x];
+  const int inst = I.run;
   const Phys<T> P = phys<T>(I);
   const long long cells = (long long)I.nx * I.ny;
   T w = T(1e30);
@@ -279,11 +283,11 @@ __global__ void __launch_bounds__(NTH) k_inject(const InstDev* __restrict__ inst
   long long badc = 0;
   for (int e = threadIdx.x; e < TX * TY; e += NTH) {
     const int gx = tl.y + e % TX, gy = tl.z + e / TX;
-    if (gx >= I.nx || gy >= I.ny) continue;
+    if (gx >= I.nx || gy >= I.own1) continue;
     const long long c = (long long)gy * I.nx + gx;
-    const double* vi = v + I.v_off;
-    const double vx = I.ncomp == 2 ? vi[c] : 0.0;
-    const double vy = I.ncomp == 2 ? vi[cells + c] : vi[c];
+    const double* vi = v + I.v_off + vrow(I, gy) + gx;
+    const double vx = I.ncomp == 2 ? vi[0] : 0.0;
+    const double vy = I.ncomp == 2 ? vi[I.v_plane] : vi[0];
     const double r0 = I.rho0[gy], p0 = I.p0[gy];
     T* Ui = U + 4 * I.cell_off;
     // an FP32 state stores the deviation from the row's base (state_to_prim)
@@ -467,8 +471,8 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS, 6) k_stage_sweep(const InstD
   const int si = blockIdx.x * STRIP_WARPS + (threadIdx.x >> 5);
   if (si >= nstrips) return;  // the whole warp leaves; no block-level synchronisation below
   const int4 st = strips[si];
-  const int inst = st.x;
-  const InstDev& I = insts[inst];
+  const InstDev& I = insts[st.x];
+  const int inst = I.run;
   const StepC<T> sc = step_const<T>(run, inst, n);
   if (!(sc.dt > T(0))) return;  // instance inactive at this step (uniform over the warp)
 
@@ -483,7 +487,7 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS, 6) k_stage_sweep(const InstD
   const int col = x0 - 2 + lane;
   const int gcol = wrap_x(col, nx);
   const bool writer = lane >= 2 && lane < 2 + STRIP_W && col < nx;
-  const int y1 = (y0 + STRIP_H < ny) ? y0 + STRIP_H : ny;
+  const int y1 = (y0 + STRIP_H < I.own1) ? y0 + STRIP_H : I.own1;
 
   // prologue: rows y0-2 .. y0+2, y slopes of rows y0-1 and y0, flux through
   // the bottom face of row y0
@@ -596,7 +600,7 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS, 6) k_stage_sweep(const InstD
       if (m > T(0) && m < T(1e30))
         atomicMin(&run.wmin[inst], (unsigned long long)__double_as_longlong((double)m));
       __threadfence();
-      const unsigned int nst = (unsigned int)(I.strip_end - I.strip_begin);
+      const unsigned int nst = (unsigned int)I.run_strips;
       if (atomicAdd(&run.counter[inst], 1u) + 1u == nst) {
         run.counter[inst] = 0u;
         __threadfence();
@@ -635,8 +639,8 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 6 : 1) k_stage_tile(cons
   __shared__ T red[NTH / 32];
   __shared__ RowBase sRB[ST_EY];
   const int4 tl = tiles[blockIdx.x];
-  const int inst = tl.x;
-  const InstDev& I = insts[inst];
+  const InstDev& I = insts[tl.x];
+  const int inst = I.run;
   const StepC<T> sc = step_const<T>(run, inst, n);
   if (!(sc.dt > T(0))) return;  // instance inactive at this step (uniform over the block)
 
@@ -656,7 +660,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 6 : 1) k_stage_tile(cons
 #pragma unroll
     for (int pass = 0; pass < PASSES; ++pass) {
       const int gx = x0 + threadIdx.x % TX, gy = y0 + threadIdx.x / TX + pass * ROWS_PER_PASS;
-      const bool in = gx < I.nx && gy < I.ny;
+      const bool in = gx < I.nx && gy < I.own1;
       const long long c = in ? (long long)gy * I.nx + gx : 0;
 #pragma unroll
       for (int k = 0; k < 4; ++k) bpre[pass][k] = in ? Bi[k * cells + c] : T(0);
@@ -704,7 +708,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 6 : 1) k_stage_tile(cons
   for (int pass = 0; pass < PASSES; ++pass) {
     const int ty = threadIdx.x / TX + pass * ROWS_PER_PASS;
     const int gx = x0 + tx, gy = y0 + ty;
-    if (gx < I.nx && gy < I.ny) {
+    if (gx < I.nx && gy < I.own1) {
       const long long c = (long long)gy * I.nx + gx;
       const T u[4] = {Si[c], Si[cells + c], Si[2 * cells + c], Si[3 * cells + c]};
       const RowBase rb = sizeof(T) == 4 ? sRB[ty + 2] : RowBase{0.f, 0.f};
@@ -767,8 +771,8 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
   Q4<T>* sB = sK + ADJ_KX * ADJ_KY;                // [4][ADJ_FACES]
   __shared__ RowBase sRB[ADJ_AY];
   const int4 tl = tiles[blockIdx.x];
-  const int inst = tl.x;
-  const InstDev& I = insts[inst];
+  const InstDev& I = insts[tl.x];
+  const int inst = I.run;
   const StepC<T> sc = step_const<T>(run, inst, n);
   if (!(sc.dt > T(0))) return;
   const Phys<T> P = phys<T>(I);
@@ -785,7 +789,7 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
 #pragma unroll
   for (int pass = 0; pass < PASSES; ++pass) {
     const int gx = x0 + threadIdx.x % TX, gy = y0 + threadIdx.x / TX + pass * ROWS_PER_PASS;
-    const bool in = E && gx < nx && gy < ny;
+    const bool in = E && gx < nx && gy < I.own1;
     const long long c = in ? 4 * I.cell_off + (long long)gy * nx + gx : 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) epre[pass][q] = in ? E[c + q * cells] : T(0);
@@ -936,7 +940,7 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
         else bW[pass][0] += P.g * dyk * gq[3];
       }
     }
-    if (gx < nx && gy < ny) {
+    if (gx < nx && gy < I.own1) {
       const long long c = (long long)gy * nx + gx;
       // rho, u_x, u_y of the cell from the primitive tile (the values mx/rho, my/rho)
       const Q4<T> wc = sW[(ty + 3) * ADJ_AX + tx + 3];
@@ -997,7 +1001,7 @@ __global__ void __launch_bounds__(NTH) k_dt_partials(const InstDev* __restrict__
   __shared__ double red[NTH / 32];
   const int4 tl = tiles[blockIdx.x];
   const InstDev& I = insts[tl.x];
-  const long long k = (long long)tl.x * run.max_steps + n;
+  const long long k = (long long)I.run * run.max_steps + n;
   const double dt = run.dtrec[k], wmin = run.wrec[k];
   const Phys<T> P = phys<T>(I);
   const long long cells = (long long)I.nx * I.ny, off = 4 * I.cell_off;
@@ -1005,7 +1009,7 @@ __global__ void __launch_bounds__(NTH) k_dt_partials(const InstDev* __restrict__
   if (dt > 0.0) {
     for (int e = threadIdx.x; e < TX * TY; e += NTH) {
       const int gx = tl.y + e % TX, gy = tl.z + e / TX;
-      if (gx >= I.nx || gy >= I.ny) continue;
+      if (gx >= I.nx || gy >= I.own1) continue;
       const long long c = off + (long long)gy * I.nx + gx;
       T u[4];
 #pragma unroll
@@ -1037,14 +1041,14 @@ __global__ void __launch_bounds__(NTH) k_dt_apply(const InstDev* __restrict__ in
                                                   const double* __restrict__ coef) {
   const int4 tl = tiles[blockIdx.x];
   const InstDev& I = insts[tl.x];
-  const long long k = (long long)tl.x * run.max_steps + n;
-  const double wmin = run.wrec[k], cf = coef[tl.x];
+  const long long k = (long long)I.run * run.max_steps + n;
+  const double wmin = run.wrec[k], cf = coef[I.run];
   if (!(run.dtrec[k] > 0.0) || !(wmin > 0.0) || cf == 0.0) return;
   const Phys<T> P = phys<T>(I);
   const long long cells = (long long)I.nx * I.ny, off = 4 * I.cell_off;
   for (int e = threadIdx.x; e < TX * TY; e += NTH) {
     const int gx = tl.y + e % TX, gy = tl.z + e / TX;
-    if (gx >= I.nx || gy >= I.ny) continue;
+    if (gx >= I.nx || gy >= I.own1) continue;
     const long long c = off + (long long)gy * I.nx + gx;
     const T r = U[c], mx = U[c + cells], my = U[c + 2 * cells], E = U[c + 3 * cells];
     T wx, wy;
@@ -1086,13 +1090,13 @@ __global__ void __launch_bounds__(NTH) k_objective(const InstDev* __restrict__ i
   const int4 tl = tiles[blockIdx.x];
   const InstDev& I = insts[tl.x];
   const long long cells = (long long)I.nx * I.ny;
-  const int ns = nstep[tl.x];
+  const int ns = nstep[I.run];
   const int s = tab_mod ? (ns % tab_mod) : ns;
   const T* Si = slot_tab[s] + 4 * I.cell_off;
   double ke = 0.0, pap = 0.0;
   for (int e = threadIdx.x; e < TX * TY; e += NTH) {
     const int gx = tl.y + e % TX, gy = tl.z + e / TX;
-    if (gx >= I.nx || gy >= I.ny) continue;
+    if (gx >= I.nx || gy >= I.own1) continue;
     const long long c = (long long)gy * I.nx + gx;
     const double r = (double)Si[c] + (sizeof(T) == 4 ? (double)I.rho0_f[gy] : 0.0);
     const double mx = (double)Si[cells + c], my = (double)Si[2 * cells + c];
@@ -1152,19 +1156,18 @@ __global__ void __launch_bounds__(NTH) k_grad(const InstDev* __restrict__ insts,
   const InstDev& I = insts[tl.x];
   const long long cells = (long long)I.nx * I.ny;
   const T* Li = lam + 4 * I.cell_off;
-  const double* vi = v + I.v_off;
-  double* gi = g + I.v_off;
   for (int e = threadIdx.x; e < TX * TY; e += NTH) {
     const int gx = tl.y + e % TX, gy = tl.z + e / TX;
-    if (gx >= I.nx || gy >= I.ny) continue;
+    if (gx >= I.nx || gy >= I.own1) continue;
     const long long c = (long long)gy * I.nx + gx;
+    const long long vc = I.v_off + vrow(I, gy) + gx;
     const double r0 = I.rho0[gy];
     const double lE = (double)Li[3 * cells + c];
     if (I.ncomp == 2) {
-      gi[c] = r0 * ((double)Li[cells + c] + vi[c] * lE);
-      gi[cells + c] = r0 * ((double)Li[2 * cells + c] + vi[cells + c] * lE);
+      g[vc] = r0 * ((double)Li[cells + c] + v[vc] * lE);
+      g[vc + I.v_plane] = r0 * ((double)Li[2 * cells + c] + v[vc + I.v_plane] * lE);
     } else {
-      gi[c] = r0 * ((double)Li[2 * cells + c] + vi[c] * lE);
+      g[vc] = r0 * ((double)Li[2 * cells + c] + v[vc] * lE);
     }
   }
 }
@@ -1263,16 +1266,15 @@ __global__ void __launch_bounds__(NTH) k_field_reduce(const InstDev* __restrict_
   __shared__ double red[NTH / 32];
   const int4 tl = tiles[blockIdx.x];
   const InstDev& I = insts[tl.x];
-  const long long cells = (long long)I.nx * I.ny;
   double s = 0.0;
   for (int e = threadIdx.x; e < TX * TY; e += NTH) {
     const int gx = tl.y + e % TX, gy = tl.z + e / TX;
-    if (gx >= I.nx || gy >= I.ny) continue;
-    const long long c = (long long)gy * I.nx + gx;
+    if (gx >= I.nx || gy >= I.own1) continue;
+    const long long c = I.v_off + vrow(I, gy) + gx;
     for (int k = 0; k < I.ncomp; ++k) {
-      const double x = a[I.v_off + k * cells + c];
+      const double x = a[c + k * I.v_plane];
       if (MODE == 0) s += 0.5 * I.rho0[gy] * x * x;
-      else if (MODE == 1) s += x * b[I.v_off + k * cells + c];
+      else if (MODE == 1) s += x * b[c + k * I.v_plane];
       else s = fmax(s, fabs(x));
     }
   }
@@ -1287,14 +1289,13 @@ __global__ void __launch_bounds__(NTH) k_field_axpby(const InstDev* __restrict__
                                                      const double* __restrict__ b) {
   const int4 tl = tiles[blockIdx.x];
   const InstDev& I = insts[tl.x];
-  const long long cells = (long long)I.nx * I.ny;
-  const double al = alpha[tl.x], be = beta ? beta[tl.x] : 0.0;
+  const double al = alpha[I.run], be = beta ? beta[I.run] : 0.0;
   for (int e = threadIdx.x; e < TX * TY; e += NTH) {
     const int gx = tl.y + e % TX, gy = tl.z + e / TX;
-    if (gx >= I.nx || gy >= I.ny) continue;
-    const long long c = (long long)gy * I.nx + gx;
+    if (gx >= I.nx || gy >= I.own1) continue;
+    const long long c = I.v_off + vrow(I, gy) + gx;
     for (int k = 0; k < I.ncomp; ++k) {
-      const long long idx = I.v_off + k * cells + c;
+      const long long idx = c + k * I.v_plane;
       double x = al * a[idx];
       if (b) x = x + be * b[idx];
       out[idx] = x;
@@ -1308,14 +1309,13 @@ __global__ void __launch_bounds__(NTH) k_field_weight(const InstDev* __restrict_
                                                       double* __restrict__ out, const double* __restrict__ a) {
   const int4 tl = tiles[blockIdx.x];
   const InstDev& I = insts[tl.x];
-  const long long cells = (long long)I.nx * I.ny;
   for (int e = threadIdx.x; e < TX * TY; e += NTH) {
     const int gx = tl.y + e % TX, gy = tl.z + e / TX;
-    if (gx >= I.nx || gy >= I.ny) continue;
-    const long long c = (long long)gy * I.nx + gx;
+    if (gx >= I.nx || gy >= I.own1) continue;
+    const long long c = I.v_off + vrow(I, gy) + gx;
     const double w = I.rho0[gy];
     for (int k = 0; k < I.ncomp; ++k) {
-      const long long idx = I.v_off + k * cells + c;
+      const long long idx = c + k * I.v_plane;
       out[idx] = w * a[idx] * I.dA;
     }
   }
@@ -1327,15 +1327,14 @@ __global__ void __launch_bounds__(NTH) k_localise(const InstDev* __restrict__ in
                                                   double h_loc, double* __restrict__ v) {
   const int4 tl = tiles[blockIdx.x];
   const InstDev& I = insts[tl.x];
-  const long long cells = (long long)I.nx * I.ny;
   for (int e = threadIdx.x; e < TX * TY; e += NTH) {
     const int gx = tl.y + e % TX, gy = tl.z + e / TX;
-    if (gx >= I.nx || gy >= I.ny) continue;
-    const long long c = (long long)gy * I.nx + gx;
+    if (gx >= I.nx || gy >= I.own1) continue;
+    const long long c = I.v_off + vrow(I, gy) + gx;
     const double y = I.y0 + (gy + 0.5) * I.dy;
     const double d = y - I.y_int;
     const double env = exp(-(d * d) / (2.0 * h_loc * h_loc));
-    for (int k = 0; k < I.ncomp; ++k) v[I.v_off + k * cells + c] *= env;
+    for (int k = 0; k < I.ncomp; ++k) v[c + k * I.v_plane] *= env;
   }
 }
 #endif  // RT_FIELD_KERNELS

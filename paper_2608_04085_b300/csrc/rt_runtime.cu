@@ -26,7 +26,7 @@
 
 // The Python binding mirrors these layouts with ctypes.
 static_assert(sizeof(rt_problem) == 152, "rt_problem layout");
-static_assert(sizeof(rt_options) == 24, "rt_options layout");
+static_assert(sizeof(rt_options) == 32, "rt_options layout");
 static_assert(sizeof(cnop_params) == 96, "cnop_params layout");
 static_assert(sizeof(cnop_result) == 64, "cnop_result layout");
 
@@ -48,8 +48,22 @@ struct GraphEntry {
   long long kind_launches[3] = {0, 0, 0};
 };
 
+// Halo copy between two slabs of one problem: 3 rows of every conserved
+// plane (or cotangent plane) from the source slab's rows to the target
+// slab's halo rows, in state-slot elements.
+struct HaloCopy {
+  long long dst_cell_off, src_cell_off;  // device instances' cell offsets
+  long long dst_cells, src_cells;        // their plane sizes (held rows x nx)
+  int dst_row, src_row, nx;
+};
+constexpr int kSlabHalo = 3;  // rows: the adjoint reads the state 3 rows out, the stages 2
+
 struct rt_ctx {
-  int n_inst = 0;
+  int n_inst = 0;                      // problems
+  int n_dev = 0;                       // device instances: problems, or their y-slabs
+  std::vector<int> dev_first, dev_count;  // device instances of each problem
+  std::vector<HaloCopy> halos;         // halo copies between slabs (empty without slabs)
+  InstDev* d_pinst = nullptr;          // per problem, tile range over all its slabs (sums over a problem)
   rt_options opt{};
   cudaStream_t stream = nullptr;       // the context's own stream (capturable)
   cudaStream_t user_stream = nullptr;  // the caller's stream; work is ordered after it
@@ -68,7 +82,8 @@ struct rt_ctx {
   int nstrips = 0;
   long long total_cells = 0;
   size_t total_v = 0;
-  std::vector<long long> cell_off, v_off;
+  std::vector<long long> cell_off;  // per device instance
+  std::vector<long long> v_off;     // per problem
   size_t esz = 8;          // bytes per state element
   size_t slot_bytes = 0;   // one state of every instance
   double* d_base = nullptr;  // rho0 / p0 of all instances
@@ -221,13 +236,29 @@ void timing_end(rt_ctx* c, int idx) {
   if (idx >= 0) cudaEventRecord(c->evpool[idx + 1], c->stream);
 }
 
+// Refresh the halo rows of every slab in `slot` (a state or cotangent slot)
+// from the neighbouring slabs' rows; nothing without slabs. Plain
+// device-to-device copies on the context's stream (captured into graphs).
+cudaError_t exchange(rt_ctx* c, void* slot) {
+  char* b = static_cast<char*>(slot);
+  const size_t es = c->esz;
+  for (const HaloCopy& h : c->halos) {
+    const cudaError_t e = cudaMemcpy2DAsync(
+        b + (4 * h.dst_cell_off + (long long)h.dst_row * h.nx) * es, (size_t)h.dst_cells * es,
+        b + (4 * h.src_cell_off + (long long)h.src_row * h.nx) * es, (size_t)h.src_cells * es,
+        (size_t)kSlabHalo * h.nx * es, 4, cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 template <class T>
 cudaError_t stage(rt_ctx* c, int st, int mode, const T* src, const T* base, T* dst, int n) {
   const int ev = timing_begin(c, st - 1);
   cudaError_t e = rt::launch_stage<T>(c->stage_variant, c->lim, st, mode, c->d_inst, c->d_strips, c->nstrips,
                                       c->d_tiles, c->ntiles, src, base, dst, c->run, n, c->stream);
   timing_end(c, ev);
-  return e;
+  return e == cudaSuccess ? exchange(c, dst) : e;
 }
 
 template <class T>
@@ -236,7 +267,7 @@ cudaError_t adjoint(rt_ctx* c, const T* U, const T* K, double ks, const T* E, do
   cudaError_t e =
       rt::launch_adjoint<T>(c->lim, c->d_inst, c->d_tiles, c->ntiles, U, K, ks, E, es, out, c->run, n, c->stream);
   timing_end(c, ev);
-  return e;
+  return e == cudaSuccess ? exchange(c, out) : e;
 }
 
 // Steps per captured chunk of the time loop.
@@ -396,6 +427,7 @@ rt_status inject(rt_ctx* c, const double* d_v, void* U0, bool replay = false) {
   CU(cudaMemsetAsync(c->run.counter, 0, c->n_inst * sizeof(unsigned int), c->stream));
   CU(cudaMemsetAsync(c->run.status, 0, c->n_inst * sizeof(int), c->stream));
   CU(rt::launch_inject<T>(c->d_inst, c->d_tiles, c->ntiles, d_v, slotp<T>(U0), c->run, replay ? 0 : 1, c->stream));
+  CU(exchange(c, U0));
   ++c->launches;
   return RT_OK;
 }
@@ -409,7 +441,7 @@ rt_status estimate_steps(rt_ctx* c, int* n_est) {
   CU(cudaStreamSynchronize(c->stream));
   long long best = 1;
   for (int i = 0; i < c->n_inst; ++i) {
-    if (!c->h_inst[i].enabled) continue;
+    if (!c->h_inst[c->dev_first[i]].enabled) continue;
     const rt_problem& P = c->prob[i];
     if (P.nsteps > 0) { best = std::max<long long>(best, P.nsteps); continue; }
     if (!(dt0[i] > 0.0) || !(dt0[i] < kMaxFinite)) continue;
@@ -421,7 +453,7 @@ rt_status estimate_steps(rt_ctx* c, int* n_est) {
 
 bool all_done(rt_ctx* c, const std::vector<int>& nstep, const std::vector<double>& t, const std::vector<int>& status) {
   for (int i = 0; i < c->n_inst; ++i) {
-    if (!c->h_inst[i].enabled || status[i] != 0) continue;
+    if (!c->h_inst[c->dev_first[i]].enabled || status[i] != 0) continue;
     const rt_problem& P = c->prob[i];
     if (P.nsteps > 0 ? nstep[i] < P.nsteps : t[i] < P.T) return false;
   }
@@ -500,7 +532,11 @@ rt_status objective(rt_ctx* c, const Plan& plan, bool cotangent, double* ek_out)
   CU(rt::launch_objective<T>(c->d_inst, c->d_tiles, c->ntiles, reinterpret_cast<T* const*>(c->d_tab), mod,
                              c->run.nstep, ek_out, cotangent ? slotp<T>(c->lA) : nullptr,
                              cotangent ? slotp<T>(c->lB) : nullptr, c->d_partials, c->stream));
-  CU(rt::launch_finalize(c->d_inst, c->n_inst, c->d_partials, 2, 1, c->d_sums, c->stream));
+  if (cotangent) {
+    CU(exchange(c, c->lA));
+    CU(exchange(c, c->lB));
+  }
+  CU(rt::launch_finalize(c->d_pinst, c->n_inst, c->d_partials, 2, 1, c->d_sums, c->stream));
   c->launches += 2;
   return RT_OK;
 }
@@ -589,7 +625,7 @@ rt_status series_impl(rt_ctx* c, const double* d_v, int flags, int every, std::v
     CHK(upload_tab(c, tab));
     CU(rt::launch_row_sums<T>(c->d_inst, c->d_rows, c->total_rows, reinterpret_cast<T* const*>(c->d_tab),
                               c->run.nstep, c->d_rowsum, c->stream));
-    CU(rt::launch_series_sample(c->d_inst, c->n_inst, c->d_rowsum, c->run.t, c->run.nstep, c->d_sample, c->stream));
+    CU(rt::launch_series_sample(c->d_pinst, c->n_inst, c->d_rowsum, c->run.t, c->run.nstep, c->d_sample, c->stream));
     c->launches += 2;
     const size_t at = samples.size();
     samples.resize(at + 4 * c->n_inst);
@@ -725,8 +761,9 @@ rt_status gradient_impl(rt_ctx* c, const double* d_v, double* J_out, double* d_g
     CU(stage<T>(c, 2, 2, U1, Un, slotp<T>(c->sA), n));
     CU(rt::launch_dt_partials<T>(c->d_inst, c->d_tiles, c->ntiles, Un, U1, slotp<T>(c->sA), lam[(n + 1) & 1], l1,
                                  c->run, n, c->d_partials, c->stream));
-    CU(rt::launch_dt_coef(c->d_inst, c->n_inst, c->d_partials, c->run, n, c->d_blast, c->d_coef, c->stream));
+    CU(rt::launch_dt_coef(c->d_pinst, c->n_inst, c->d_partials, c->run, n, c->d_blast, c->d_coef, c->stream));
     CU(rt::launch_dt_apply<T>(c->d_inst, c->d_tiles, c->ntiles, Un, lam[n & 1], c->run, n, c->d_coef, c->stream));
+    CU(exchange(c, lam[n & 1]));
     c->launches += 3;
     return RT_OK;
   };
@@ -788,7 +825,7 @@ rt_status gradient_impl(rt_ctx* c, const double* d_v, double* J_out, double* d_g
 
 rt_status field_sums(rt_ctx* c, int mode, const double* a, const double* b, std::vector<double>& out) {
   CU(rt::launch_field_reduce(mode, c->d_inst, c->d_tiles, c->ntiles, a, b, c->d_partials, c->stream));
-  CU(rt::launch_finalize(c->d_inst, c->n_inst, c->d_partials, 1, mode == 0 ? 1 : 0, c->d_sums, c->stream));
+  CU(rt::launch_finalize(c->d_pinst, c->n_inst, c->d_partials, 1, mode == 0 ? 1 : 0, c->d_sums, c->stream));
   out.resize(c->n_inst);
   CU(cudaMemcpyAsync(out.data(), c->d_sums, c->n_inst * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
@@ -825,7 +862,8 @@ rt_status ensure_fields(rt_ctx* c, bool cnop) {
 }
 
 rt_status set_enabled(rt_ctx* c, const std::vector<char>& en) {
-  for (int i = 0; i < c->n_inst; ++i) c->h_inst[i].enabled = en[i] ? 1 : 0;
+  for (int i = 0; i < c->n_inst; ++i)
+    for (int d = c->dev_first[i]; d < c->dev_first[i] + c->dev_count[i]; ++d) c->h_inst[d].enabled = en[i] ? 1 : 0;
   return upload_inst(c);
 }
 
@@ -843,8 +881,9 @@ rt_status baseline(rt_ctx* c) {
   CHK(march<T>(c, plan, 0, n_est, 0, &n_done));
   CHK(objective<T>(c, plan, false, c->d_ek0));
   CU(cudaStreamSynchronize(c->stream));
-  for (int i = 0; i < c->n_inst; ++i)
-    c->h_inst[i].ek0 = c->prob[i].objective == RT_OBJ_EK_ANOMALY_L2 ? c->d_ek0 + c->cell_off[i] : nullptr;
+  for (int d = 0; d < c->n_dev; ++d)
+    c->h_inst[d].ek0 =
+        c->prob[c->h_inst[d].run].objective == RT_OBJ_EK_ANOMALY_L2 ? c->d_ek0 + c->cell_off[d] : nullptr;
   CHK(upload_inst(c));
   c->have_run = false;
   return RT_OK;
@@ -938,7 +977,7 @@ rt_status ensure_pairs(rt_ctx* c, int m) {
 // max |a| per instance
 rt_status field_max_abs(rt_ctx* c, const double* a, std::vector<double>& out) {
   CU(rt::launch_field_reduce(2, c->d_inst, c->d_tiles, c->ntiles, a, nullptr, c->d_partials, c->stream));
-  CU(rt::launch_finalize_max(c->d_inst, c->n_inst, c->d_partials, c->d_sums, c->stream));
+  CU(rt::launch_finalize_max(c->d_pinst, c->n_inst, c->d_partials, c->d_sums, c->stream));
   out.resize(c->n_inst);
   CU(cudaMemcpyAsync(out.data(), c->d_sums, c->n_inst * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
@@ -1514,22 +1553,28 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
     fail(c, RT_ECUDA, "no CUDA device");
     return bail(RT_ECUDA);
   }
-  // instance layout, tiles, base state
-  c->h_inst.resize(n_instances);
-  c->cell_off.resize(n_instances);
+  // instance layout, tiles, base state. A problem split into y-slabs gets one
+  // device instance per slab: owned rows as even as possible (the first
+  // ny % k slabs one row taller), plus kSlabHalo halo rows on each side
+  // with a neighbouring slab.
+  const int nslab = c->opt.y_slabs > 1 ? c->opt.y_slabs : 1;
+  for (int i = 0; i < n_instances; ++i)
+    if (nslab > 1 && c->prob[i].ny < kSlabHalo * nslab) {
+      fail(c, RT_EINVAL, "instance %d: %d rows cannot give %d slabs of at least %d rows", i, c->prob[i].ny, nslab,
+           kSlabHalo);
+      return bail(RT_EINVAL);
+    }
   c->v_off.resize(n_instances);
+  c->dev_first.resize(n_instances);
+  c->dev_count.assign(n_instances, nslab);
   long long cells = 0, voff = 0, rows = 0;
   for (int i = 0; i < n_instances; ++i) {
     const rt_problem& P = c->prob[i];
-    c->cell_off[i] = cells;
     c->v_off[i] = voff;
-    cells += (long long)P.nx * P.ny;
     voff += (long long)P.perturb_ncomp * P.nx * P.ny;
     rows += P.ny;
   }
-  c->total_cells = cells;
   c->total_v = (size_t)voff;
-  c->slot_bytes = (size_t)(4 * cells) * c->esz;
   std::vector<double> base(2 * rows);
   long long roff = 0;
   for (int i = 0; i < n_instances; ++i) {
@@ -1538,49 +1583,84 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
     base_state(P, r, p);
     std::copy(r.begin(), r.end(), base.begin() + roff);
     std::copy(p.begin(), p.end(), base.begin() + rows + roff);
-    InstDev& I = c->h_inst[i];
-    I.nx = P.nx;
-    I.ny = P.ny;
-    I.bc_y = P.bc_y;
-    I.limiter = P.limiter;
-    I.nsteps = P.nsteps;
-    I.ncomp = P.perturb_ncomp;
-    I.objective = P.objective;
-    I.enabled = 1;
-    I.cell_off = c->cell_off[i];
-    I.v_off = c->v_off[i];
-    I.dx = (P.x1 - P.x0) / P.nx;
-    I.dy = (P.y1 - P.y0) / P.ny;
-    I.dA = I.dx * I.dy;
-    I.y0 = P.y0;
-    I.y_int = P.y_int;
-    I.rho_l = P.rho_light;
-    I.rho_h = P.rho_heavy;
-    I.row_off = roff;  // advanced at the end of this loop body
-    I.gamma = P.gamma;
-    I.gm1 = P.gamma - 1.0;
-    I.g_y = P.g_y;
-    I.cfl = P.cfl;
-    I.T = P.T;
-    I.gamma_f = (float)I.gamma;
-    I.gm1_f = (float)I.gm1;
-    I.g_f = (float)I.g_y;
-    I.dx_f = (float)I.dx;
-    I.dy_f = (float)I.dy;
-    I.flux = P.flux;
-    I.flux_theta = P.flux == RT_FLUX_HYBRID ? P.flux_theta : 0.0;
-    I.flux_theta_f = (float)I.flux_theta;
-    I.tile_begin = (int)c->h_tiles.size();
-    for (int y0 = 0; y0 < P.ny; y0 += rt::TILE_Y)
-      for (int x0 = 0; x0 < P.nx; x0 += rt::TILE_X) c->h_tiles.push_back(make_int4(i, x0, y0, 0));
-    I.tile_end = (int)c->h_tiles.size();
-    I.strip_begin = (int)c->h_strips.size();
-    for (int y0 = 0; y0 < P.ny; y0 += rt::STRIP_H)
-      for (int x0 = 0; x0 < P.nx; x0 += rt::STRIP_W) c->h_strips.push_back(make_int4(i, x0, y0, 0));
-    I.strip_end = (int)c->h_strips.size();
-    I.ek0 = nullptr;
+    c->dev_first[i] = (int)c->h_inst.size();
+    const int tiles0 = (int)c->h_tiles.size(), strips0 = (int)c->h_strips.size();
+    const int hb = P.ny / nslab, extra = P.ny % nslab;
+    int y0s = 0;
+    for (int sl = 0; sl < nslab; ++sl) {
+      const int y1s = y0s + hb + (sl < extra ? 1 : 0);
+      const int e0 = sl > 0 ? y0s - kSlabHalo : y0s;
+      const int e1 = sl < nslab - 1 ? y1s + kSlabHalo : y1s;
+      InstDev I{};
+      I.nx = P.nx;
+      I.ny = e1 - e0;
+      I.run = i;
+      I.own0 = y0s - e0;
+      I.own1 = y1s - e0;
+      I.v_plane = (long long)P.nx * P.ny;
+      I.bc_y = P.bc_y;
+      I.limiter = P.limiter;
+      I.nsteps = P.nsteps;
+      I.ncomp = P.perturb_ncomp;
+      I.objective = P.objective;
+      I.enabled = 1;
+      I.cell_off = cells;
+      I.v_off = c->v_off[i] + (long long)y0s * P.nx;
+      I.dx = (P.x1 - P.x0) / P.nx;
+      I.dy = (P.y1 - P.y0) / P.ny;
+      I.dA = I.dx * I.dy;
+      I.y0 = P.y0 + e0 * I.dy;
+      I.y_int = P.y_int;
+      I.rho_l = P.rho_light;
+      I.rho_h = P.rho_heavy;
+      I.row_off = roff + e0;
+      I.gamma = P.gamma;
+      I.gm1 = P.gamma - 1.0;
+      I.g_y = P.g_y;
+      I.cfl = P.cfl;
+      I.T = P.T;
+      I.gamma_f = (float)I.gamma;
+      I.gm1_f = (float)I.gm1;
+      I.g_f = (float)I.g_y;
+      I.dx_f = (float)I.dx;
+      I.dy_f = (float)I.dy;
+      I.flux = P.flux;
+      I.flux_theta = P.flux == RT_FLUX_HYBRID ? P.flux_theta : 0.0;
+      I.flux_theta_f = (float)I.flux_theta;
+      const int d = (int)c->h_inst.size();
+      I.tile_begin = (int)c->h_tiles.size();
+      for (int ty = I.own0; ty < I.own1; ty += rt::TILE_Y)
+        for (int x0 = 0; x0 < P.nx; x0 += rt::TILE_X) c->h_tiles.push_back(make_int4(d, x0, ty, 0));
+      I.tile_end = (int)c->h_tiles.size();
+      I.strip_begin = (int)c->h_strips.size();
+      for (int ty = I.own0; ty < I.own1; ty += rt::STRIP_H)
+        for (int x0 = 0; x0 < P.nx; x0 += rt::STRIP_W) c->h_strips.push_back(make_int4(d, x0, ty, 0));
+      I.strip_end = (int)c->h_strips.size();
+      I.ek0 = nullptr;
+      c->cell_off.push_back(cells);
+      cells += (long long)I.nx * I.ny;
+      if (sl > 0) {  // halos between this slab and the one below
+        const InstDev& L = c->h_inst.back();
+        // this slab's lower halo rows <- the top owned rows of the slab below
+        c->halos.push_back({I.cell_off, L.cell_off, (long long)I.nx * I.ny, (long long)L.nx * L.ny, 0,
+                            L.own1 - kSlabHalo, P.nx});
+        // the lower slab's upper halo rows <- this slab's bottom owned rows
+        c->halos.push_back({L.cell_off, I.cell_off, (long long)L.nx * L.ny, (long long)I.nx * I.ny, L.own1,
+                            I.own0, P.nx});
+      }
+      c->h_inst.push_back(I);
+      y0s = y1s;
+    }
+    const int ntile_run = (int)c->h_tiles.size() - tiles0, nstrip_run = (int)c->h_strips.size() - strips0;
+    for (int d = c->dev_first[i]; d < (int)c->h_inst.size(); ++d) {
+      c->h_inst[d].run_tiles = ntile_run;
+      c->h_inst[d].run_strips = nstrip_run;
+    }
     roff += P.ny;
   }
+  c->n_dev = (int)c->h_inst.size();
+  c->total_cells = cells;
+  c->slot_bytes = (size_t)(4 * cells) * c->esz;
   c->ntiles = (int)c->h_tiles.size();
   c->nstrips = (int)c->h_strips.size();
   c->lim = c->prob[0].limiter;
@@ -1609,14 +1689,34 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
   c->row_off.resize(N);
   for (int i = 0; i < N; ++i) {
     c->row_off[i] = roff;
-    c->h_inst[i].rho0 = c->d_base + roff;
-    c->h_inst[i].p0 = c->d_base + rows + roff;
-    c->h_inst[i].rho0_f = c->d_base_f + roff;
-    c->h_inst[i].p0_f = c->d_base_f + rows + roff;
     roff += c->prob[i].ny;
   }
-  INIT_CU(cudaMalloc(&c->d_inst, N * sizeof(InstDev)));
-  INIT_CU(cudaMemcpy(c->d_inst, c->h_inst.data(), N * sizeof(InstDev), cudaMemcpyHostToDevice));
+  for (InstDev& I : c->h_inst) {  // row_off of a slab already includes its first held row
+    I.rho0 = c->d_base + I.row_off;
+    I.p0 = c->d_base + rows + I.row_off;
+    I.rho0_f = c->d_base_f + I.row_off;
+    I.p0_f = c->d_base_f + rows + I.row_off;
+  }
+  INIT_CU(cudaMalloc(&c->d_inst, c->n_dev * sizeof(InstDev)));
+  INIT_CU(cudaMemcpy(c->d_inst, c->h_inst.data(), c->n_dev * sizeof(InstDev), cudaMemcpyHostToDevice));
+  if (nslab == 1) {
+    c->d_pinst = c->d_inst;
+  } else {  // one entry per problem whose tile range spans all its slabs
+    std::vector<InstDev> pin(N);
+    for (int i = 0; i < N; ++i) {
+      const InstDev& F = c->h_inst[c->dev_first[i]];
+      const InstDev& Lst = c->h_inst[c->dev_first[i] + c->dev_count[i] - 1];
+      pin[i] = F;
+      pin[i].tile_end = Lst.tile_end;
+      pin[i].strip_end = Lst.strip_end;
+      pin[i].ny = c->prob[i].ny;
+      pin[i].own0 = 0;
+      pin[i].own1 = c->prob[i].ny;
+      pin[i].row_off = c->row_off[i];
+    }
+    INIT_CU(cudaMalloc(&c->d_pinst, N * sizeof(InstDev)));
+    INIT_CU(cudaMemcpy(c->d_pinst, pin.data(), N * sizeof(InstDev), cudaMemcpyHostToDevice));
+  }
   INIT_CU(cudaMalloc(&c->d_tiles, c->ntiles * sizeof(int4)));
   INIT_CU(cudaMemcpy(c->d_tiles, c->h_tiles.data(), c->ntiles * sizeof(int4), cudaMemcpyHostToDevice));
   INIT_CU(cudaMalloc(&c->d_strips, c->nstrips * sizeof(int4)));
@@ -1679,6 +1779,7 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
 
 void rt_destroy(rt_ctx* c) {
   if (!c) return;
+  if (c->d_pinst && c->d_pinst != c->d_inst) cudaFree(c->d_pinst);
   void* ptrs[] = {c->d_inst, c->d_tiles, c->d_strips, c->d_base, c->d_base_f, c->d_ek0, c->d_ek, c->sA, c->sB, c->sU1, c->lA, c->lB,
                   c->l1, c->d_tab, c->run.dtrec, c->run.wrec, c->d_blast, c->d_coef, c->run.dtc, c->run.counter, c->run.t, c->run.nstep, c->run.wmin, c->run.status,
                   c->run.bad_cell, c->d_partials, c->d_sums, c->d_scal, c->d_v, c->d_g, c->d_w1, c->d_w2,
@@ -1730,6 +1831,7 @@ rt_status rt_forward_series(rt_ctx* c, const double* v0, int flags, int every, i
                             double* ke_out, double* hmix_out, int* n_out) {
   if (!c || !v0 || !t_out || !ke_out || !hmix_out || !n_out) return fail(c, RT_EINVAL, "null argument");
   if (every < 1 || max_samples < 1) return fail(c, RT_EINVAL, "every and max_samples must be >= 1");
+  if (c->n_dev != c->n_inst) return fail(c, RT_EINVAL, "rt_forward_series is not available with y-slabs");
   c->err.clear();
   CHK(ensure_fields(c, false));
   CHK(enter(c));
@@ -1925,14 +2027,22 @@ rt_status rt_get_state(rt_ctx* c, int inst, double* out) {
   const size_t n = (size_t)4 * P.nx * P.ny;
   const int s = c->h_nstep[inst];
   const void* slot = c->last_kind == 2 ? c->pool[s] : ((s & 1) ? c->sB : c->sA);
-  const char* src = static_cast<const char*>(slot) + (size_t)4 * c->cell_off[inst] * c->esz;
+  // the owned rows of each of the problem's device instances (slabs), in order
+  std::vector<char> raw(n * c->esz);
+  long long row = 0;
+  for (int d = c->dev_first[inst]; d < c->dev_first[inst] + c->dev_count[inst]; ++d) {
+    const InstDev& I = c->h_inst[d];
+    const size_t es = c->esz, own = (size_t)(I.own1 - I.own0) * I.nx;
+    const char* src = static_cast<const char*>(slot) + ((size_t)4 * I.cell_off + (size_t)I.own0 * I.nx) * es;
+    CU(cudaMemcpy2DAsync(raw.data() + (size_t)row * I.nx * es, (size_t)P.nx * P.ny * es, src,
+                         (size_t)I.nx * I.ny * es, own * es, 4, cudaMemcpyDeviceToHost, c->stream));
+    row += I.own1 - I.own0;
+  }
+  CU(cudaStreamSynchronize(c->stream));
   if (c->esz == 8) {
-    CU(cudaMemcpyAsync(out, src, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    CU(cudaStreamSynchronize(c->stream));
+    std::memcpy(out, raw.data(), n * sizeof(double));
   } else {
-    std::vector<float> f(n);
-    CU(cudaMemcpyAsync(f.data(), src, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
-    CU(cudaStreamSynchronize(c->stream));
+    const float* f = reinterpret_cast<const float*>(raw.data());
     for (size_t k = 0; k < n; ++k) out[k] = f[k];
     // the FP32 state holds the deviation from the row's base state: add
     // rho0 to the density and p0/(gamma-1) to the energy

@@ -34,7 +34,7 @@ def test_struct_sizes_match_header_layout():
     # rt_problem: 2 ints, 12 doubles, 2 ints, 2 doubles, 4 ints, 1 double
     assert ctypes.sizeof(rt.RtProblem) == 8 + 12 * 8 + 8 + 16 + 16 + 8
     assert rt.RtProblem.flux.offset == 140 and rt.RtProblem.flux_theta.offset == 144
-    assert ctypes.sizeof(rt.RtOptions) == 24
+    assert ctypes.sizeof(rt.RtOptions) == 32
     # cnop_params: 3 ints (+ pad), 4 doubles, a pointer, 2 ints, a double, 2 pointers, 2 ints
     # cnop_result: 3 ints (+ pad), a double, 5 pointers
     assert ctypes.sizeof(rt.CnopParams) == 16 + 32 + 8 + 8 + 8 + 16 + 8
@@ -114,7 +114,7 @@ C_USER = r"""
 #include "rt_cnop.h"
 int main(void) {
   rt_problem p[2] = {{0}};
-  rt_options o = {RT_FP32_STATE, RT_CKPT_AUTO, 0.0, 0, RT_STAGE_AUTO};
+  rt_options o = {RT_FP32_STATE, RT_CKPT_AUTO, 0.0, 0, RT_STAGE_AUTO, 0};
   rt_ctx* ctx;
   if (rt_init(p, 2, &o, NULL, &ctx) != RT_OK) return 1;
   size_t n = rt_field_total(ctx);
