@@ -137,6 +137,7 @@ struct rt_ctx {
   std::vector<std::pair<int, int>> evused;  // (kind, index of the start event; end = index + 1)
   double kind_ms[3] = {0, 0, 0};
   long long kind_samples[3] = {0, 0, 0};
+  int kind_pairs[3] = {0, 0, 0};  // event pairs in use per kind (each kind gets a third of the pool)
   // stage-kernel variant in use and the autotuner's timings (ms per step)
   int stage_variant = rt::STAGE_SWEEP;
   int lim = -1;  // limiter shared by every instance (compile-time specialised kernels), or -1
@@ -227,7 +228,8 @@ int timing_begin(rt_ctx* c, int kind) {
   const long long k = c->kind_launches[kind]++;
   if (c->time_every <= 0 || k % c->time_every != 0) return -1;
   const int idx = (int)(2 * c->evused.size());
-  if (idx + 1 >= (int)c->evpool.size()) return -1;
+  if (idx + 1 >= (int)c->evpool.size() || c->kind_pairs[kind] >= (int)(c->evpool.size() / 6)) return -1;
+  ++c->kind_pairs[kind];
   cudaEventRecord(c->evpool[idx], c->stream);
   c->evused.push_back({kind, idx});
   return idx;
@@ -321,6 +323,7 @@ void reset_accounting(rt_ctx* c) {
   c->launches = 0;
   for (int k = 0; k < 3; ++k) { c->kind_launches[k] = 0; c->kind_ms[k] = 0.0; c->kind_samples[k] = 0; }
   c->evused.clear();
+  for (int k = 0; k < 3; ++k) c->kind_pairs[k] = 0;
 }
 
 // Called after the stream has drained: fold the sampled event pairs.
@@ -333,6 +336,7 @@ void collect_timing(rt_ctx* c) {
     }
   }
   c->evused.clear();
+  for (int k = 0; k < 3; ++k) c->kind_pairs[k] = 0;
 }
 
 rt_status upload_inst(rt_ctx* c) {

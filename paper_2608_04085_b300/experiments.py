@@ -112,12 +112,17 @@ def horizon_sweep(Ts=(1.0, 2.0, 4.0), iters=50, seed=0, eps=1e-4, method=None, p
     return out
 
 
-def precision_comparison(nx=1024, ny=3072, T=6.0, iters=20, seed=0, eps=1e-4, method=None, ckpt_cap_gb=40.0):
+def precision_comparison(nx=1024, ny=3072, T=6.0, iters=20, seed=0, eps=1e-4, method=None, ckpt_cap_gb=40.0,
+                         fp64_cnop=True):
     """CNOP of one RT box in FP32 state and in FP64 from the same seeded
     i.i.d. (v_x, v_y) start (C = eps), revolve checkpointing under a memory
     cap, the spectral projected gradient by default: the relative error of
     the FP32 J(T) of the FP64 CNOP, the FP32 CNOP's J against the FP64 one,
-    and the cosine of the two CNOPs. Defaults: the 1024x3072, T = 6 box."""
+    and the cosine of the two CNOPs. Defaults: the 1024x3072, T = 6 box.
+
+    fp64_cnop=False runs the FP32 CNOP only and evaluates J of the FP32 CNOP
+    and of the start with one FP64 forward each: the FP32 path's error in
+    J(T) at those two points, without the FP64 search."""
     import time
     import rt_inputs
     from . import RT_CKPT_REVOLVE, RT_CNOP_SPG
@@ -126,6 +131,28 @@ def precision_comparison(nx=1024, ny=3072, T=6.0, iters=20, seed=0, eps=1e-4, me
     xi = rt_inputs.gaussian_field(seed, w.ncomp, w.ny, w.nx).ravel()
     out = {"grid": [nx, ny], "T": float(T), "iterations": iters, "eps": eps, "runs": {}}
     v = {}
+    if not fp64_cnop:
+        t0 = time.perf_counter()
+        with Context([w], precision=RT_FP32_STATE, ckpt=RT_CKPT_REVOLVE, ckpt_cap_bytes=ckpt_cap_gb * 1e9) as ctx:
+            v0, J0, _ = ctx.cnop(xi, eps, 0, method=method)
+            v32, J, res = ctx.cnop(xi, eps, iters, method=method)
+            _, _, g = ctx.gradient(v32)
+            J32_start = float(ctx.forward(v0)[0][0])
+        out["runs"]["fp32"] = {"J": float(J[0]), "J_start": float(res["J_history"][0, 0]), "steps": int(g["steps"]),
+                               "iterations": int(res["iterations"]), "gradient_evals": int(res["gradient_evals"]),
+                               "forward_evals": int(res["forward_evals"]), "seconds": time.perf_counter() - t0,
+                               "revolve_recomputed_steps_per_gradient": -int(g["segments"]),
+                               "gradient_ms": float(g["ms"])}
+        t0 = time.perf_counter()
+        with Context([w], precision=RT_FP64) as c64:
+            J64_cnop = float(c64.forward(v32)[0][0])
+            J64_start = float(c64.forward(v0)[0][0])
+        out["fp64_forward_seconds"] = time.perf_counter() - t0
+        out["J_fp64_at_fp32_cnop"] = J64_cnop
+        out["rel_err_J_fp32_at_fp32_cnop"] = abs(out["runs"]["fp32"]["J"] - J64_cnop) / abs(J64_cnop)
+        out["J_fp64_at_start"] = J64_start
+        out["rel_err_J_fp32_at_start"] = abs(J32_start - J64_start) / abs(J64_start)
+        return out
     for name, prec in (("fp32", RT_FP32_STATE), ("fp64", RT_FP64)):
         t0 = time.perf_counter()
         with Context([w], precision=prec, ckpt=RT_CKPT_REVOLVE, ckpt_cap_bytes=ckpt_cap_gb * 1e9) as ctx:
@@ -151,12 +178,15 @@ if __name__ == "__main__":
     ap.add_argument("--T", type=float, default=None)
     ap.add_argument("--iters", type=int, default=None)
     ap.add_argument("--seeds", type=int, default=4)
+    ap.add_argument("--no-fp64-cnop", action="store_true",
+                    help="precision run: FP32 CNOP only, J checked with FP64 forwards")
     a = ap.parse_args()
     if a.run == "horizons":
         print(json.dumps(horizon_sweep(iters=50 if a.iters is None else a.iters)), flush=True)
     elif a.run == "precision":
         print(json.dumps(precision_comparison(T=6.0 if a.T is None else a.T,
-                                              iters=20 if a.iters is None else a.iters)), flush=True)
+                                              iters=20 if a.iters is None else a.iters,
+                                              fp64_cnop=not a.no_fp64_cnop)), flush=True)
     else:
         print(json.dumps(paper_run(a.run, seeds=tuple(range(a.seeds)), iters=a.iters)), flush=True)
 

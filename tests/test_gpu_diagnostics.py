@@ -133,3 +133,15 @@ def test_precision_comparison_driver_short():
     assert abs(r["fp32"]["steps"] - r["fp64"]["steps"]) <= 1
     assert out["rel_err_J_fp32_at_fp64_cnop"] <= 1e-4
     assert out["cnop_cosine"] >= 0.999
+
+
+def test_precision_comparison_fp32_search_with_fp64_checks():
+    """The high-resolution mode of the driver (FP32 CNOP only, J re-evaluated
+    by FP64 forwards) on a small box: J rises, and the FP32 J at the CNOP and
+    at the start are within 1e-4 of the FP64 forwards."""
+    from paper_2608_04085_b300.experiments import precision_comparison
+    out = precision_comparison(nx=64, ny=192, T=0.2, iters=3, ckpt_cap_gb=0.005, fp64_cnop=False)
+    r = out["runs"]["fp32"]
+    assert r["J"] > r["J_start"] and r["revolve_recomputed_steps_per_gradient"] > 0
+    assert out["rel_err_J_fp32_at_fp32_cnop"] <= 1e-4
+    assert out["rel_err_J_fp32_at_start"] <= 1e-4
