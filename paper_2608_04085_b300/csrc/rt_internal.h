@@ -34,7 +34,8 @@ enum { STAGE_SWEEP = 1, STAGE_TILE = 2 };
 // held (its owned rows plus halo rows copied from the neighbouring slabs
 // before every kernel that reads them), own0 the first owned row, and the
 // problem's index `run`, which selects the per-problem time-step control and
-// scalars that all its slabs share. Kernels compute owned rows only and read
+// scalars that all its slabs share (the tile and strip descriptors carry it
+// too, with their row count). Kernels compute owned rows only and read
 // halo rows as interior data. Without slabs run is the instance's own index,
 // own0 = 0, own1 = ny and v_plane = nx*ny.
 struct InstDev {

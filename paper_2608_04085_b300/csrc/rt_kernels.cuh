@@ -56,6 +56,13 @@ __device__ __forceinline__ int wrap_x(int gx, int nx) {
 // component: rows count from the instance's first owned row.
 __device__ __forceinline__ long long vrow(const InstDev& I, int gy) { return (long long)(gy - I.own0) * I.nx; }
 
+// The 4th component of a tile or strip descriptor packs the problem index
+// (bits 0-23) and the descriptor's rows to compute (bits 24-31, at most the
+// tile height): the hot kernels bound their rows and select the problem's run
+// scalars from data they already hold.
+__device__ __forceinline__ int desc_run(int w) { return w & 0xffffff; }
+__device__ __forceinline__ int desc_rows(int w) { return (int)((unsigned)w >> 24); }
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -275,7 +282,7 @@ __global__ void __launch_bounds__(NTH) k_inject(const InstDev* __restrict__ inst
   __shared__ T red[NTH / 32];
   const int4 tl = tiles[blockIdx.x];
   const InstDev& I = insts[tl.x];
-  const int inst = I.run;
+  const int inst = desc_run(tl.w);
   const Phys<T> P = phys<T>(I);
   const long long cells = (long long)I.nx * I.ny;
   T w = T(1e30);
@@ -472,7 +479,7 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS, 6) k_stage_sweep(const InstD
   if (si >= nstrips) return;  // the whole warp leaves; no block-level synchronisation below
   const int4 st = strips[si];
   const InstDev& I = insts[st.x];
-  const int inst = I.run;
+  const int inst = desc_run(st.w);
   const StepC<T> sc = step_const<T>(run, inst, n);
   if (!(sc.dt > T(0))) return;  // instance inactive at this step (uniform over the warp)
 
@@ -487,7 +494,7 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS, 6) k_stage_sweep(const InstD
   const int col = x0 - 2 + lane;
   const int gcol = wrap_x(col, nx);
   const bool writer = lane >= 2 && lane < 2 + STRIP_W && col < nx;
-  const int y1 = (y0 + STRIP_H < I.own1) ? y0 + STRIP_H : I.own1;
+  const int y1 = y0 + desc_rows(st.w);
 
   // prologue: rows y0-2 .. y0+2, y slopes of rows y0-1 and y0, flux through
   // the bottom face of row y0
@@ -640,7 +647,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 6 : 1) k_stage_tile(cons
   __shared__ RowBase sRB[ST_EY];
   const int4 tl = tiles[blockIdx.x];
   const InstDev& I = insts[tl.x];
-  const int inst = I.run;
+  const int inst = desc_run(tl.w);
   const StepC<T> sc = step_const<T>(run, inst, n);
   if (!(sc.dt > T(0))) return;  // instance inactive at this step (uniform over the block)
 
@@ -659,8 +666,9 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 6 : 1) k_stage_tile(cons
     const T* Bi = base + 4 * I.cell_off;
 #pragma unroll
     for (int pass = 0; pass < PASSES; ++pass) {
-      const int gx = x0 + threadIdx.x % TX, gy = y0 + threadIdx.x / TX + pass * ROWS_PER_PASS;
-      const bool in = gx < I.nx && gy < I.own1;
+      const int ty = threadIdx.x / TX + pass * ROWS_PER_PASS;
+      const int gx = x0 + threadIdx.x % TX, gy = y0 + ty;
+      const bool in = gx < I.nx && ty < desc_rows(tl.w);
       const long long c = in ? (long long)gy * I.nx + gx : 0;
 #pragma unroll
       for (int k = 0; k < 4; ++k) bpre[pass][k] = in ? Bi[k * cells + c] : T(0);
@@ -708,7 +716,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 6 : 1) k_stage_tile(cons
   for (int pass = 0; pass < PASSES; ++pass) {
     const int ty = threadIdx.x / TX + pass * ROWS_PER_PASS;
     const int gx = x0 + tx, gy = y0 + ty;
-    if (gx < I.nx && gy < I.own1) {
+    if (gx < I.nx && ty < desc_rows(tl.w)) {
       const long long c = (long long)gy * I.nx + gx;
       const T u[4] = {Si[c], Si[cells + c], Si[2 * cells + c], Si[3 * cells + c]};
       const RowBase rb = sizeof(T) == 4 ? sRB[ty + 2] : RowBase{0.f, 0.f};
@@ -772,7 +780,7 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
   __shared__ RowBase sRB[ADJ_AY];
   const int4 tl = tiles[blockIdx.x];
   const InstDev& I = insts[tl.x];
-  const int inst = I.run;
+  const int inst = desc_run(tl.w);
   const StepC<T> sc = step_const<T>(run, inst, n);
   if (!(sc.dt > T(0))) return;
   const Phys<T> P = phys<T>(I);
@@ -789,7 +797,7 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
 #pragma unroll
   for (int pass = 0; pass < PASSES; ++pass) {
     const int gx = x0 + threadIdx.x % TX, gy = y0 + threadIdx.x / TX + pass * ROWS_PER_PASS;
-    const bool in = E && gx < nx && gy < I.own1;
+    const bool in = E && gx < nx && gy < ny;
     const long long c = in ? 4 * I.cell_off + (long long)gy * nx + gx : 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) epre[pass][q] = in ? E[c + q * cells] : T(0);
@@ -940,7 +948,9 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
         else bW[pass][0] += P.g * dyk * gq[3];
       }
     }
-    if (gx < nx && gy < I.own1) {
+    // every held row; a slab's halo rows among them are overwritten by the
+    // halo exchange that follows the launch (the adjoint has no reduction)
+    if (gx < nx && gy < ny) {
       const long long c = (long long)gy * nx + gx;
       // rho, u_x, u_y of the cell from the primitive tile (the values mx/rho, my/rho)
       const Q4<T> wc = sW[(ty + 3) * ADJ_AX + tx + 3];

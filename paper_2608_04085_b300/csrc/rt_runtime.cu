@@ -1562,6 +1562,10 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
   // ny % k slabs one row taller), plus kSlabHalo halo rows on each side
   // with a neighbouring slab.
   const int nslab = c->opt.y_slabs > 1 ? c->opt.y_slabs : 1;
+  if (n_instances >= (1 << 24)) {  // tile descriptors carry the problem index in 24 bits
+    fail(c, RT_EINVAL, "at most %d instances", (1 << 24) - 1);
+    return bail(RT_EINVAL);
+  }
   for (int i = 0; i < n_instances; ++i)
     if (nslab > 1 && c->prob[i].ny < kSlabHalo * nslab) {
       fail(c, RT_EINVAL, "instance %d: %d rows cannot give %d slabs of at least %d rows", i, c->prob[i].ny, nslab,
@@ -1634,11 +1638,13 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
       const int d = (int)c->h_inst.size();
       I.tile_begin = (int)c->h_tiles.size();
       for (int ty = I.own0; ty < I.own1; ty += rt::TILE_Y)
-        for (int x0 = 0; x0 < P.nx; x0 += rt::TILE_X) c->h_tiles.push_back(make_int4(d, x0, ty, 0));
+        for (int x0 = 0; x0 < P.nx; x0 += rt::TILE_X)
+          c->h_tiles.push_back(make_int4(d, x0, ty, i | (std::min(rt::TILE_Y, I.own1 - ty) << 24)));
       I.tile_end = (int)c->h_tiles.size();
       I.strip_begin = (int)c->h_strips.size();
       for (int ty = I.own0; ty < I.own1; ty += rt::STRIP_H)
-        for (int x0 = 0; x0 < P.nx; x0 += rt::STRIP_W) c->h_strips.push_back(make_int4(d, x0, ty, 0));
+        for (int x0 = 0; x0 < P.nx; x0 += rt::STRIP_W)
+          c->h_strips.push_back(make_int4(d, x0, ty, i | (std::min(rt::STRIP_H, I.own1 - ty) << 24)));
       I.strip_end = (int)c->h_strips.size();
       I.ek0 = nullptr;
       c->cell_off.push_back(cells);
