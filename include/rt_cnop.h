@@ -86,7 +86,7 @@ enum { RT_FLUX_HLLC = 0, RT_FLUX_HLL = 1, RT_FLUX_HYBRID = 2 };
 enum { RT_OBJ_KE = 0, RT_OBJ_EK_ANOMALY_L2 = 1 };
 enum { RT_FP64 = 0, RT_FP32_STATE = 1 };
 enum { RT_CKPT_AUTO = 0, RT_CKPT_STORE_ALL = 1, RT_CKPT_SQRT = 2, RT_CKPT_REVOLVE = 3 };
-enum { RT_STAGE_AUTO = 0, RT_STAGE_SWEEP = 1, RT_STAGE_TILE = 2 };
+enum { RT_STAGE_AUTO = 0, RT_STAGE_SWEEP = 1, RT_STAGE_TILE = 2, RT_STAGE_TILE8 = 3, RT_STAGE_TILE32 = 4 };
 enum { RT_CNOP_SPG = 0, RT_CNOP_LBFGS = 1 };
 
 /* flags for rt_forward / rt_gradient / rt_constraint / rt_project / cnop_solve:
@@ -248,12 +248,20 @@ rt_status rt_get_dt(rt_ctx* ctx, int inst, double* out, int max_n, int* n_out);
  * NULL). */
 rt_status rt_set_kernel_timing(rt_ctx* ctx, int every);
 
-/* Stage-kernel variant in use (RT_STAGE_SWEEP or RT_STAGE_TILE; no
- * counterpart in the paper). With RT_STAGE_AUTO, rt_init timed four CFL
- * steps of the unperturbed batch with each variant and kept the faster;
- * tuned_ms (nullable, [2]) receives those mean times per step (sweep, tile),
- * or zeros when the variant was fixed by the options. */
+/* Stage-kernel variant in use (no counterpart in the paper): RT_STAGE_SWEEP
+ * (one warp per 28 x 16 strip) or the shared-memory tile kernel with tiles
+ * of 32 columns by 16 (RT_STAGE_TILE), 8 (RT_STAGE_TILE8) or 32
+ * (RT_STAGE_TILE32) rows; all give the same values bit for bit in FP64.
+ * With RT_STAGE_AUTO, rt_init timed four CFL steps of the unperturbed batch
+ * with each of the four and kept the fastest; tuned_ms (nullable, [2])
+ * receives the mean times per step of the sweep and of the 16-row tile
+ * kernel, or zeros when the variant was fixed by the options. */
 int rt_stage_kernel(const rt_ctx* ctx, double* tuned_ms);
+
+/* All four autotuner timings, ms per step (no counterpart in the paper):
+ * ms[0] sweep, ms[1] tiles of 8 rows, ms[2] of 16 rows, ms[3] of 32 rows;
+ * zeros when the variant was fixed by the options. Errors: RT_EINVAL. */
+rt_status rt_stage_tuning(const rt_ctx* ctx, double* ms);
 rt_status rt_kernel_times(rt_ctx* ctx, double* mean_ms, long long* samples, long long* launches);
 
 typedef struct {

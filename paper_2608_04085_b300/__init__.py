@@ -25,7 +25,7 @@ RT_FLUX_HLLC, RT_FLUX_HLL, RT_FLUX_HYBRID = 0, 1, 2
 RT_OBJ_KE, RT_OBJ_EK_ANOMALY_L2 = 0, 1
 RT_FP64, RT_FP32_STATE = 0, 1
 RT_CKPT_AUTO, RT_CKPT_STORE_ALL, RT_CKPT_SQRT, RT_CKPT_REVOLVE = 0, 1, 2, 3
-RT_STAGE_AUTO, RT_STAGE_SWEEP, RT_STAGE_TILE = 0, 1, 2
+RT_STAGE_AUTO, RT_STAGE_SWEEP, RT_STAGE_TILE, RT_STAGE_TILE8, RT_STAGE_TILE32 = 0, 1, 2, 3, 4
 RT_DEVICE_PTRS, RT_REPLAY_DT, RT_GRAD_DT = 1, 2, 4
 RT_CNOP_SPG, RT_CNOP_LBFGS = 0, 1
 RT_RECON_X_MODES, RT_RECON_2D_POWER = 0, 1
@@ -38,7 +38,7 @@ EXPORTS = ("rt_init", "rt_destroy", "rt_last_error", "rt_num_instances", "rt_fie
            "rt_field_size", "rt_field_total", "rt_forward", "rt_gradient", "rt_constraint",
            "rt_project", "rt_get_state", "rt_get_dt", "rt_set_kernel_timing", "rt_kernel_times", "rt_stage_kernel",
            "cnop_solve", "rt_objective_noalloc", "rt_forward_series", "rt_spectrum_x", "rt_spectrum_2d",
-           "rt_reconstruct", "rt_fma_peak", "rt_revolve_plan")
+           "rt_reconstruct", "rt_fma_peak", "rt_revolve_plan", "rt_stage_tuning")
 
 
 class RtError(RuntimeError):
@@ -136,6 +136,8 @@ def library():
         L.rt_get_dt.restype = ip
         L.rt_stage_kernel.argtypes = [vp, dp]
         L.rt_stage_kernel.restype = ip
+        L.rt_stage_tuning.argtypes = [vp, dp]
+        L.rt_stage_tuning.restype = ip
         L.rt_set_kernel_timing.argtypes = [vp, ip]
         L.rt_set_kernel_timing.restype = ip
         llp = ctypes.POINTER(ctypes.c_longlong)
@@ -319,10 +321,12 @@ class Context:
         return out[:n.value]
 
     def stage_kernel(self):
-        """(variant in use, {"sweep": ms/step, "tile": ms/step} from the autotuner)."""
-        t = np.zeros(2)
-        v = library().rt_stage_kernel(self._h, _dptr(t))
-        return v, {"sweep": t[0], "tile": t[1]}
+        """(variant in use, {"sweep", "tile8", "tile", "tile32": ms/step} from the
+        autotuner; "tile" is the 16-row tile kernel)."""
+        t = np.zeros(4)
+        v = library().rt_stage_kernel(self._h, None)
+        self._check(library().rt_stage_tuning(self._h, _dptr(t)))
+        return v, {"sweep": t[0], "tile8": t[1], "tile": t[2], "tile32": t[3]}
 
     def set_kernel_timing(self, every):
         """Sample CUDA-event timings of every `every`-th time-step kernel launch."""

@@ -20,8 +20,12 @@ constexpr int STRIP_W = 28;
 constexpr int STRIP_H = 16;
 constexpr int STRIP_WARPS = 4;
 
-// Stage-kernel variants (same values bit for bit, different schedules).
-enum { STAGE_SWEEP = 1, STAGE_TILE = 2 };
+// Stage-kernel variants (same values bit for bit, different schedules): the
+// warp sweep, and the shared-memory tile kernel with tiles of 16, 8 or 32
+// rows (32 columns). Every variant has its own work list of tiles.
+enum { STAGE_SWEEP = 1, STAGE_TILE = 2, STAGE_TILE8 = 3, STAGE_TILE32 = 4 };
+constexpr int tile_rows_of(int variant) { return variant == STAGE_TILE8 ? 8 : (variant == STAGE_TILE32 ? 32 : 16); }
+constexpr int tile_list_of(int variant) { return variant == STAGE_TILE8 ? 0 : (variant == STAGE_TILE32 ? 2 : 1); }
 
 // Per-instance constants, resident on the device (one entry per device
 // instance). State slots hold every device instance back to back: instance
@@ -42,6 +46,7 @@ struct InstDev {
   int nx, ny;
   int run;                   // problem index: run scalars, dt record, per-problem coefficients
   int run_tiles, run_strips; // tiles / strips of the whole problem (all its slabs)
+  int run_tiles_h[3];        // the problem's tiles in the tile-stage lists of 8, 16 and 32 rows
   int own0, own1;            // owned rows [own0, own1); the rest are halo rows
   long long v_plane;         // stride between perturbation components
   int bc_y, limiter;

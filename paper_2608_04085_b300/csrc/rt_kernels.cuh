@@ -248,7 +248,7 @@ __device__ void finish_step(const InstDev& I, const RunDev& run, int inst, int n
 // and report whether this CTA is the instance's last one of the launch.
 // All threads must call; the result is valid in thread 0.
 template <class T>
-__device__ __forceinline__ bool commit_crossing(T w, long long cell, bool bad, const InstDev& I, const RunDev& run,
+__device__ __forceinline__ bool commit_crossing(T w, long long cell, bool bad, int ntile_run, const RunDev& run,
                                                 int inst, T* red) {
   if (bad) {
     if (atomicCAS(&run.status[inst], 0, 1) == 0) run.bad_cell[inst] = cell;
@@ -264,8 +264,7 @@ __device__ __forceinline__ bool commit_crossing(T w, long long cell, bool bad, c
     if (m > T(0) && m < T(1e30))
       atomicMin(&run.wmin[inst], (unsigned long long)__double_as_longlong((double)m));
     __threadfence();
-    const unsigned int ntile = (unsigned int)I.run_tiles;
-    if (atomicAdd(&run.counter[inst], 1u) + 1u == ntile) {
+    if (atomicAdd(&run.counter[inst], 1u) + 1u == (unsigned int)ntile_run) {
       run.counter[inst] = 0u;
       __threadfence();
       last = true;
@@ -310,7 +309,7 @@ __global__ void __launch_bounds__(NTH) k_inject(const InstDev* __restrict__ inst
     const T cw = crossing_time<T>(u0, u1, u2, u3, row_base<T>(I, gy), P, b);
     if (b) { bad = true; badc = c; } else if (cw < w) w = cw;
   }
-  if (commit_crossing<T>(w, badc, bad, I, run, inst, red)) {
+  if (commit_crossing<T>(w, badc, bad, I.run_tiles, run, inst, red)) {
     run.t[inst] = 0.0;
     run.nstep[inst] = 0;
     if (record) finish_step<T>(I, run, inst, 0, 0.0);  // a replay keeps the recorded step 0
@@ -626,25 +625,32 @@ __global__ void __launch_bounds__(32 * STRIP_WARPS, 6) k_stage_sweep(const InstD
 // --------------------------------------------------------- stage (tile variant)
 // Shared memory, cell-major (the 4 values of a cell or face together, Q4):
 // primitive tile with 2 ghost layers, x-face and y-face fluxes.
-constexpr int ST_EX = TX + 4, ST_EY = TY + 4;
-constexpr int ST_NFX = (TX + 1) * TY, ST_NFY = TX * (TY + 1);
-constexpr int ST_SMEM_ELEMS = 4 * ST_EX * ST_EY + 4 * ST_NFX + 4 * ST_NFY;
+// Geometry of a tile of H rows (32 columns).
+template <int H>
+struct StTile {
+  static constexpr int EX = TX + 4, EY = H + 4;
+  static constexpr int NFX = (TX + 1) * H, NFY = TX * (H + 1);
+  static constexpr int SMEM_ELEMS = 4 * EX * EY + 4 * NFX + 4 * NFY;
+  static constexpr int PASSES = (H + ROWS_PER_PASS - 1) / ROWS_PER_PASS;
+  static constexpr int LIST = H == 8 ? 0 : (H == 16 ? 1 : 2);  // index into InstDev::run_tiles_h
+};
 
 // Tile variant of the stage kernel: one CTA per 32 x 16 tile, primitive
 // states with 2 ghost layers in shared memory, one thread per face, then one
 // thread per cell for the update. Modes as for the sweep variant. FP32
 // launches are held to 6 CTAs per SM (40 registers), which the stage-2
 // variant with the step control would otherwise exceed.
-template <class T, int STAGE, int MODE, int LIM>
-__global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 6 : 1) k_stage_tile(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,
+template <class T, int STAGE, int MODE, int LIM, int H>
+__global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? (H <= 16 ? 6 : 4) : 1) k_stage_tile(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,
                                                const T* __restrict__ src, const T* __restrict__ base,
                                                T* __restrict__ dst, RunDev run, int n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  using G = StTile<H>;
   Q4<T>* sW = reinterpret_cast<Q4<T>*>(smem_raw);  // [EY][EX]
-  Q4<T>* sF = sW + ST_EX * ST_EY;                  // [TY][TX+1]
-  Q4<T>* sG = sF + ST_NFX;                         // [TY+1][TX]
+  Q4<T>* sF = sW + G::EX * G::EY;                  // [H][TX+1]
+  Q4<T>* sG = sF + G::NFX;                         // [H+1][TX]
   __shared__ T red[NTH / 32];
-  __shared__ RowBase sRB[ST_EY];
+  __shared__ RowBase sRB[G::EY];
   const int4 tl = tiles[blockIdx.x];
   const InstDev& I = insts[tl.x];
   const int inst = desc_run(tl.w);
@@ -657,10 +663,10 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 6 : 1) k_stage_tile(cons
   const int x0 = tl.y, y0 = tl.z;
   const int lim = LIM >= 0 ? LIM : I.limiter;
   const FluxSel<T> fs = flux_sel<T, LIM>(I);
-  load_prim_tile<T, ST_EX, ST_EY, true>(Si, I, cells, x0 - 2, y0 - 2, P, reinterpret_cast<T*>(sW), sRB);
+  load_prim_tile<T, G::EX, G::EY, true>(Si, I, cells, x0 - 2, y0 - 2, P, reinterpret_cast<T*>(sW), sRB);
   // stage 2 also needs U^n of this thread's cells in the update; their loads
   // are issued here so that the face work hides their latency
-  constexpr int PASSES = TY / ROWS_PER_PASS;
+  constexpr int PASSES = G::PASSES;
   T bpre[PASSES][4];
   if (STAGE == 2) {
     const T* Bi = base + 4 * I.cell_off;
@@ -675,13 +681,13 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 6 : 1) k_stage_tile(cons
     }
   }
   __syncthreads();
-  for (int f = threadIdx.x; f < ST_NFX + ST_NFY; f += NTH) {
+  for (int f = threadIdx.x; f < G::NFX + G::NFY; f += NTH) {
     T w[4][4], F[4];
-    if (f < ST_NFX) {  // x face fx of row fy: between tile cells fx-1 and fx
+    if (f < G::NFX) {  // x face fx of row fy: between tile cells fx-1 and fx
       const int fy = f / (TX + 1), fx = f - fy * (TX + 1);
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
-        const Q4<T> c = sW[(fy + 2) * ST_EX + fx + p];
+        const Q4<T> c = sW[(fy + 2) * G::EX + fx + p];
 #pragma unroll
         for (int q = 0; q < 4; ++q) w[p][q] = c.v[q];
       }
@@ -691,11 +697,11 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 6 : 1) k_stage_tile(cons
       for (int q = 0; q < 4; ++q) fq.v[q] = F[q];
       sF[f] = fq;
     } else {  // y face fy of column fx: between tile rows fy-1 and fy
-      const int g = f - ST_NFX;
+      const int g = f - G::NFX;
       const int fy = g / TX, fx = g - fy * TX;
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
-        const Q4<T> c = sW[(fy + p) * ST_EX + fx + 2];
+        const Q4<T> c = sW[(fy + p) * G::EX + fx + 2];
 #pragma unroll
         for (int q = 0; q < 4; ++q) w[p][q] = c.v[q];
       }
@@ -746,7 +752,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 6 : 1) k_stage_tile(cons
     }
   }
   if (STAGE == 2 && MODE == 0) {
-    if (commit_crossing<T>(w, badc, bad, I, run, inst, red)) {
+    if (commit_crossing<T>(w, badc, bad, I.run_tiles_h[G::LIST], run, inst, red)) {
       const double dt = run.dtrec[(long long)inst * run.max_steps + n];
       const double t = run.t[inst];
       const double tn = I.nsteps > 0 ? t + dt : (dt >= I.T - t ? I.T : t + dt);

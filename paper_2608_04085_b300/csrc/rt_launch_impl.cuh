@@ -14,6 +14,22 @@ cudaError_t launch_inject(const InstDev* insts, const int4* tiles, int ntiles, c
   return cudaGetLastError();
 }
 
+// tile variant with tiles of H rows; `tiles` is that height's work list
+template <class T, int LIM, int H>
+void launch_stage_tile(int stage, int mode, const InstDev* insts, const int4* tiles, int ntiles, const T* src,
+                       const T* base, T* dst, const RunDev& run, int n, cudaStream_t s) {
+  const size_t sm = StTile<H>::SMEM_ELEMS * sizeof(T);
+  if (stage == 1) {
+    k_stage_tile<T, 1, 2, LIM, H><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
+  } else if (mode == 0) {
+    k_stage_tile<T, 2, 0, LIM, H><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
+  } else if (mode == 1) {
+    k_stage_tile<T, 2, 1, LIM, H><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
+  } else {
+    k_stage_tile<T, 2, 2, LIM, H><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
+  }
+}
+
 template <class T, int LIM>
 cudaError_t launch_stage_lim(int variant, int stage, int mode, const InstDev* insts, const int4* strips, int nstrips,
                              const int4* tiles, int ntiles, const T* src, const T* base, T* dst, const RunDev& run,
@@ -29,17 +45,12 @@ cudaError_t launch_stage_lim(int variant, int stage, int mode, const InstDev* in
     } else {
       k_stage_sweep<T, 2, 2, LIM><<<grid, block, 0, s>>>(insts, strips, nstrips, src, base, dst, run, n);
     }
+  } else if (variant == STAGE_TILE8) {
+    launch_stage_tile<T, LIM, 8>(stage, mode, insts, tiles, ntiles, src, base, dst, run, n, s);
+  } else if (variant == STAGE_TILE32) {
+    launch_stage_tile<T, LIM, 32>(stage, mode, insts, tiles, ntiles, src, base, dst, run, n, s);
   } else {
-    const size_t sm = ST_SMEM_ELEMS * sizeof(T);
-    if (stage == 1) {
-      k_stage_tile<T, 1, 2, LIM><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
-    } else if (mode == 0) {
-      k_stage_tile<T, 2, 0, LIM><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
-    } else if (mode == 1) {
-      k_stage_tile<T, 2, 1, LIM><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
-    } else {
-      k_stage_tile<T, 2, 2, LIM><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
-    }
+    launch_stage_tile<T, LIM, 16>(stage, mode, insts, tiles, ntiles, src, base, dst, run, n, s);
   }
   return cudaGetLastError();
 }
@@ -104,14 +115,23 @@ cudaError_t launch_grad(const InstDev* insts, const int4* tiles, int ntiles, con
   return cudaGetLastError();
 }
 
+template <class T, int LIM, int H>
+cudaError_t configure_tile() {
+  const int st = (int)(StTile<H>::SMEM_ELEMS * sizeof(T));
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(k_stage_tile<T, 1, 2, LIM, H>, a, st);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage_tile<T, 2, 0, LIM, H>, a, st);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage_tile<T, 2, 1, LIM, H>, a, st);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage_tile<T, 2, 2, LIM, H>, a, st);
+  return e;
+}
+
 template <class T, int LIM>
 cudaError_t configure_lim() {
-  const int st = (int)(ST_SMEM_ELEMS * sizeof(T));
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(k_stage_tile<T, 1, 2, LIM>, a, st);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage_tile<T, 2, 0, LIM>, a, st);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage_tile<T, 2, 1, LIM>, a, st);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_stage_tile<T, 2, 2, LIM>, a, st);
+  cudaError_t e = configure_tile<T, LIM, 8>();
+  if (e == cudaSuccess) e = configure_tile<T, LIM, 16>();
+  if (e == cudaSuccess) e = configure_tile<T, LIM, 32>();
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adjoint<T, LIM>, a, (int)(ADJ_SMEM_ELEMS * sizeof(T)));
   return e;
 }

@@ -74,9 +74,12 @@ struct rt_ctx {
   std::vector<rt_problem> prob;
   std::vector<InstDev> h_inst;
   InstDev* d_inst = nullptr;
-  std::vector<int4> h_tiles;
+  std::vector<int4> h_tiles;   // tiles of 16 rows: every tile kernel's work list
   int4* d_tiles = nullptr;
   int ntiles = 0;
+  std::vector<int4> h_tiles_h[3];  // tile-stage work lists of 8, 16 (= h_tiles) and 32 rows
+  int4* d_tiles_h[3] = {nullptr, nullptr, nullptr};
+  int ntiles_h[3] = {0, 0, 0};
   std::vector<int4> h_strips;  // sweep-kernel strips over all instances
   int4* d_strips = nullptr;
   int nstrips = 0;
@@ -141,7 +144,7 @@ struct rt_ctx {
   // stage-kernel variant in use and the autotuner's timings (ms per step)
   int stage_variant = rt::STAGE_SWEEP;
   int lim = -1;  // limiter shared by every instance (compile-time specialised kernels), or -1
-  double tune_ms[3] = {0, 0, 0};
+  double tune_ms[5] = {0, 0, 0, 0, 0};  // by variant: sweep, tile 16, tile 8, tile 32
 };
 
 namespace {
@@ -257,8 +260,9 @@ cudaError_t exchange(rt_ctx* c, void* slot) {
 template <class T>
 cudaError_t stage(rt_ctx* c, int st, int mode, const T* src, const T* base, T* dst, int n) {
   const int ev = timing_begin(c, st - 1);
+  const int L = rt::tile_list_of(c->stage_variant);
   cudaError_t e = rt::launch_stage<T>(c->stage_variant, c->lim, st, mode, c->d_inst, c->d_strips, c->nstrips,
-                                      c->d_tiles, c->ntiles, src, base, dst, c->run, n, c->stream);
+                                      c->d_tiles_h[L], c->ntiles_h[L], src, base, dst, c->run, n, c->stream);
   timing_end(c, ev);
   return e == cudaSuccess ? exchange(c, dst) : e;
 }
@@ -898,7 +902,7 @@ rt_status baseline(rt_ctx* c) {
 template <class T>
 rt_status autotune_stage(rt_ctx* c) {
   CU(cudaMemsetAsync(c->d_v, 0, c->total_v * sizeof(double), c->stream));
-  const int variants[2] = {rt::STAGE_SWEEP, rt::STAGE_TILE};
+  const int variants[4] = {rt::STAGE_SWEEP, rt::STAGE_TILE8, rt::STAGE_TILE, rt::STAGE_TILE32};
   const int warm = 2, timed = 4;
   double best = 1e300;
   int best_v = rt::STAGE_SWEEP;
@@ -909,10 +913,12 @@ rt_status autotune_stage(rt_ctx* c) {
       if (n == warm) CU(cudaEventRecord(c->ev0, c->stream));
       void* src = (n & 1) ? c->sB : c->sA;
       void* dst = (n & 1) ? c->sA : c->sB;
-      CU(rt::launch_stage<T>(v, c->lim, 1, 0, c->d_inst, c->d_strips, c->nstrips, c->d_tiles, c->ntiles,
-                             slotp<T>(src), nullptr, slotp<T>(c->sU1), c->run, n, c->stream));
-      CU(rt::launch_stage<T>(v, c->lim, 2, 0, c->d_inst, c->d_strips, c->nstrips, c->d_tiles, c->ntiles,
-                             slotp<T>(c->sU1), slotp<T>(src), slotp<T>(dst), c->run, n, c->stream));
+      const int L = rt::tile_list_of(v);
+      CU(rt::launch_stage<T>(v, c->lim, 1, 0, c->d_inst, c->d_strips, c->nstrips, c->d_tiles_h[L],
+                             c->ntiles_h[L], slotp<T>(src), nullptr, slotp<T>(c->sU1), c->run, n, c->stream));
+      CU(rt::launch_stage<T>(v, c->lim, 2, 0, c->d_inst, c->d_strips, c->nstrips, c->d_tiles_h[L],
+                             c->ntiles_h[L], slotp<T>(c->sU1), slotp<T>(src), slotp<T>(dst), c->run, n,
+                             c->stream));
     }
     CU(cudaEventRecord(c->ev1, c->stream));
     CU(cudaEventSynchronize(c->ev1));
@@ -1593,6 +1599,7 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
     std::copy(p.begin(), p.end(), base.begin() + rows + roff);
     c->dev_first[i] = (int)c->h_inst.size();
     const int tiles0 = (int)c->h_tiles.size(), strips0 = (int)c->h_strips.size();
+    const int t8 = (int)c->h_tiles_h[0].size(), t32 = (int)c->h_tiles_h[2].size();
     const int hb = P.ny / nslab, extra = P.ny % nslab;
     int y0s = 0;
     for (int sl = 0; sl < nslab; ++sl) {
@@ -1641,6 +1648,12 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
         for (int x0 = 0; x0 < P.nx; x0 += rt::TILE_X)
           c->h_tiles.push_back(make_int4(d, x0, ty, i | (std::min(rt::TILE_Y, I.own1 - ty) << 24)));
       I.tile_end = (int)c->h_tiles.size();
+      for (int L : {0, 2}) {  // the tile-stage lists of 8 and 32 rows
+        const int h = L == 0 ? 8 : 32;
+        for (int ty = I.own0; ty < I.own1; ty += h)
+          for (int x0 = 0; x0 < P.nx; x0 += rt::TILE_X)
+            c->h_tiles_h[L].push_back(make_int4(d, x0, ty, i | (std::min(h, I.own1 - ty) << 24)));
+      }
       I.strip_begin = (int)c->h_strips.size();
       for (int ty = I.own0; ty < I.own1; ty += rt::STRIP_H)
         for (int x0 = 0; x0 < P.nx; x0 += rt::STRIP_W)
@@ -1665,6 +1678,9 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
     for (int d = c->dev_first[i]; d < (int)c->h_inst.size(); ++d) {
       c->h_inst[d].run_tiles = ntile_run;
       c->h_inst[d].run_strips = nstrip_run;
+      c->h_inst[d].run_tiles_h[0] = (int)c->h_tiles_h[0].size() - t8;
+      c->h_inst[d].run_tiles_h[1] = ntile_run;
+      c->h_inst[d].run_tiles_h[2] = (int)c->h_tiles_h[2].size() - t32;
     }
     roff += P.ny;
   }
@@ -1729,6 +1745,15 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
   }
   INIT_CU(cudaMalloc(&c->d_tiles, c->ntiles * sizeof(int4)));
   INIT_CU(cudaMemcpy(c->d_tiles, c->h_tiles.data(), c->ntiles * sizeof(int4), cudaMemcpyHostToDevice));
+  c->h_tiles_h[1] = c->h_tiles;
+  c->d_tiles_h[1] = c->d_tiles;
+  c->ntiles_h[1] = c->ntiles;
+  for (int L : {0, 2}) {
+    c->ntiles_h[L] = (int)c->h_tiles_h[L].size();
+    INIT_CU(cudaMalloc(&c->d_tiles_h[L], c->ntiles_h[L] * sizeof(int4)));
+    INIT_CU(cudaMemcpy(c->d_tiles_h[L], c->h_tiles_h[L].data(), c->ntiles_h[L] * sizeof(int4),
+                       cudaMemcpyHostToDevice));
+  }
   INIT_CU(cudaMalloc(&c->d_strips, c->nstrips * sizeof(int4)));
   INIT_CU(cudaMemcpy(c->d_strips, c->h_strips.data(), c->nstrips * sizeof(int4), cudaMemcpyHostToDevice));
   void** bufs[6] = {&c->sA, &c->sB, &c->sU1, &c->lA, &c->lB, &c->l1};
@@ -1772,7 +1797,8 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
     if (s == RT_OK) s = c->esz == 8 ? baseline<double>(c) : baseline<float>(c);
     if (s != RT_OK) return bail(s);
   }
-  if (c->opt.stage_kernel == RT_STAGE_SWEEP || c->opt.stage_kernel == RT_STAGE_TILE) {
+  if (c->opt.stage_kernel == RT_STAGE_SWEEP || c->opt.stage_kernel == RT_STAGE_TILE ||
+      c->opt.stage_kernel == RT_STAGE_TILE8 || c->opt.stage_kernel == RT_STAGE_TILE32) {
     c->stage_variant = c->opt.stage_kernel;
   } else if (c->opt.stage_kernel == RT_STAGE_AUTO) {
     rt_status s = ensure_fields(c, false);
@@ -1790,6 +1816,8 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
 void rt_destroy(rt_ctx* c) {
   if (!c) return;
   if (c->d_pinst && c->d_pinst != c->d_inst) cudaFree(c->d_pinst);
+  if (c->d_tiles_h[0]) cudaFree(c->d_tiles_h[0]);
+  if (c->d_tiles_h[2]) cudaFree(c->d_tiles_h[2]);
   void* ptrs[] = {c->d_inst, c->d_tiles, c->d_strips, c->d_base, c->d_base_f, c->d_ek0, c->d_ek, c->sA, c->sB, c->sU1, c->lA, c->lB,
                   c->l1, c->d_tab, c->run.dtrec, c->run.wrec, c->d_blast, c->d_coef, c->run.dtc, c->run.counter, c->run.t, c->run.nstep, c->run.wmin, c->run.status,
                   c->run.bad_cell, c->d_partials, c->d_sums, c->d_scal, c->d_v, c->d_g, c->d_w1, c->d_w2,
@@ -2101,6 +2129,15 @@ int rt_stage_kernel(const rt_ctx* c, double* tuned_ms) {
     tuned_ms[1] = c->tune_ms[rt::STAGE_TILE];
   }
   return c->stage_variant;
+}
+
+rt_status rt_stage_tuning(const rt_ctx* c, double* ms) {
+  if (!c || !ms) return RT_EINVAL;
+  ms[0] = c->tune_ms[rt::STAGE_SWEEP];
+  ms[1] = c->tune_ms[rt::STAGE_TILE8];
+  ms[2] = c->tune_ms[rt::STAGE_TILE];
+  ms[3] = c->tune_ms[rt::STAGE_TILE32];
+  return RT_OK;
 }
 
 rt_status rt_kernel_times(rt_ctx* c, double* mean_ms, long long* samples, long long* launches) {

@@ -40,8 +40,16 @@ FWD_CASES = {
 }
 
 
+VARIANTS = ["sweep", "tile", "tile8", "tile32"]
+
+
+def _variant(rt, name):
+    return {"sweep": rt.RT_STAGE_SWEEP, "tile": rt.RT_STAGE_TILE, "tile8": rt.RT_STAGE_TILE8,
+            "tile32": rt.RT_STAGE_TILE32}[name]
+
+
 @pytest.mark.parametrize("name", sorted(FWD_CASES))
-@pytest.mark.parametrize("variant", ["sweep", "tile"])
+@pytest.mark.parametrize("variant", VARIANTS)
 def test_fp64_forward_bitwise(name, variant):
     import oracle
     w, seed = FWD_CASES[name]
@@ -49,7 +57,7 @@ def test_fp64_forward_bitwise(name, variant):
     ek0 = oracle.baseline_ek(w) if w.objective == I.OBJ_EK_ANOMALY_L2 else None
     ref = oracle.forward(w, v, ek0=ek0)
     rt = _rt()
-    sk = rt.RT_STAGE_SWEEP if variant == "sweep" else rt.RT_STAGE_TILE
+    sk = _variant(rt, variant)
     with rt.Context([w], precision=rt.RT_FP64, stage_kernel=sk) as ctx:
         assert ctx.stage_kernel()[0] == sk
         J, Jke, st = ctx.forward(v.ravel())
@@ -62,7 +70,7 @@ def test_fp64_forward_bitwise(name, variant):
     assert J[0] == pytest.approx(oracle.objective_value(w, ref), rel=1e-12)
 
 
-@pytest.mark.parametrize("variant", ["sweep", "tile"])
+@pytest.mark.parametrize("variant", VARIANTS)
 def test_fp64_batch_of_uneven_grids_matches_single_runs(variant):
     """One batched launch over uneven instances gives each instance the same
     bits as running it alone."""
@@ -71,7 +79,7 @@ def test_fp64_batch_of_uneven_grids_matches_single_runs(variant):
           I.rt_box(8, 96, nsteps=0, T=0.03, ncomp=I.PERT_VY)]
     vs = [_v(w, 10 + k) for k, w in enumerate(ws)]
     rt = _rt()
-    sk = rt.RT_STAGE_SWEEP if variant == "sweep" else rt.RT_STAGE_TILE
+    sk = _variant(rt, variant)
     with rt.Context(ws, precision=rt.RT_FP64, stage_kernel=sk) as ctx:
         J, Jke, st = ctx.forward(np.concatenate([v.ravel() for v in vs]))
         for k, w in enumerate(ws):
@@ -220,23 +228,32 @@ def test_nonfinite_state_is_reported():
 
 
 def test_autotuner_picks_a_variant_and_matches_forced_ones():
+    """The autotuner times the warp sweep and the tile kernel with 8-, 16- and
+    32-row tiles and keeps the fastest; every variant gives the same FP32
+    state to FP32 rounding (FP64 is bitwise in all, see above)."""
     w = I.rt_box(96, 160, nsteps=20)
     v = _v(w, 4).ravel()
     rt = _rt()
     out = {}
-    for sk in (rt.RT_STAGE_AUTO, rt.RT_STAGE_SWEEP, rt.RT_STAGE_TILE):
+    keys = {rt.RT_STAGE_SWEEP: "sweep", rt.RT_STAGE_TILE8: "tile8", rt.RT_STAGE_TILE: "tile",
+            rt.RT_STAGE_TILE32: "tile32"}
+    for sk in (rt.RT_STAGE_AUTO, *keys):
         with rt.Context([w], precision=rt.RT_FP32_STATE, stage_kernel=sk) as ctx:
             var, tuned = ctx.stage_kernel()
             out[sk] = (ctx.forward(v)[0][0], ctx.state(0))
             if sk == rt.RT_STAGE_AUTO:
-                assert var in (rt.RT_STAGE_SWEEP, rt.RT_STAGE_TILE)
-                assert tuned["sweep"] > 0 and tuned["tile"] > 0
-                assert tuned["sweep" if var == rt.RT_STAGE_SWEEP else "tile"] == min(tuned.values())
-    # FP32 with FMA contraction: the two schedules may fuse products differently,
-    # so they agree to FP32 rounding (the FP64 path is bitwise in both)
-    a, b = out[rt.RT_STAGE_SWEEP], out[rt.RT_STAGE_TILE]
-    assert abs(a[0] - b[0]) <= 1e-5 * abs(a[0])
-    assert np.max(np.abs(a[1] - b[1])) <= 1e-5 * np.max(np.abs(a[1]))
+                assert var in keys
+                assert all(t > 0 for t in tuned.values())
+                assert tuned[keys[var]] == min(tuned.values())
+            else:
+                assert var == sk and all(t == 0 for t in tuned.values())
+    # FP32 with FMA contraction: the schedules may fuse products differently,
+    # so they agree to FP32 rounding (the FP64 path is bitwise in all)
+    a = out[rt.RT_STAGE_TILE]
+    for sk in keys:
+        b = out[sk]
+        assert abs(a[0] - b[0]) <= 1e-5 * abs(a[0]), sk
+        assert np.max(np.abs(a[1] - b[1])) <= 1e-5 * np.max(np.abs(a[1])), sk
 
 
 def test_invalid_problem_rejected():

@@ -40,12 +40,13 @@ def _v(w, seed, eps):
 
 @pytest.mark.parametrize("slabs", [2, 3])
 @pytest.mark.parametrize("name", sorted(CASES))
-@pytest.mark.parametrize("variant", ["tile", "sweep"])
+@pytest.mark.parametrize("variant", ["tile", "sweep", "tile8", "tile32"])
 def test_fp64_forward_split_equals_unsplit(name, slabs, variant):
     rt = _rt()
     w, eps = CASES[name]
     v = _v(w, 3, eps)
-    sk = rt.RT_STAGE_TILE if variant == "tile" else rt.RT_STAGE_SWEEP
+    sk = {"tile": rt.RT_STAGE_TILE, "sweep": rt.RT_STAGE_SWEEP, "tile8": rt.RT_STAGE_TILE8,
+          "tile32": rt.RT_STAGE_TILE32}[variant]
     out = {}
     for k in (0, slabs):
         with rt.Context([w], precision=rt.RT_FP64, stage_kernel=sk, y_slabs=k) as ctx:
