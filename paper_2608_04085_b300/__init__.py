@@ -232,11 +232,12 @@ class Context:
             raise RtError(st, library().rt_last_error(self._h).decode())
 
     def _arg(self, a):
-        """(pointer, flags, keepalive) for a host ndarray or a CUDA tensor."""
-        if hasattr(a, "data_ptr") and getattr(a, "is_cuda", False):
+        """(pointer, flags, keepalive) for a host ndarray, a host (for example
+        pinned) torch tensor, or a CUDA tensor; tensors are passed by pointer."""
+        if hasattr(a, "data_ptr"):
             import torch
             assert a.dtype == torch.float64 and a.is_contiguous() and a.numel() == self.total
-            return ctypes.c_void_p(a.data_ptr()), RT_DEVICE_PTRS, a
+            return ctypes.c_void_p(a.data_ptr()), (RT_DEVICE_PTRS if a.is_cuda else 0), a
         a = np.ascontiguousarray(a, dtype=np.float64)
         assert a.size == self.total, (a.size, self.total)
         return a.ctypes.data_as(ctypes.c_void_p), 0, a

@@ -147,3 +147,22 @@ def test_header_is_plain_c_and_a_c_program_links(tmp_path):
     subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
                     str(src), "-L", os.path.dirname(lib), "-lrt_cnop", "-o", str(tmp_path / "user")],
                    check=True, capture_output=True)
+
+
+def test_binding_passes_tensors_by_pointer():
+    """Host torch tensors (pinned or not) reach the C ABI as host pointers to
+    their own storage, CUDA tensors would carry RT_DEVICE_PTRS, and NumPy
+    arrays pass as host pointers: no copy in the binding."""
+    import numpy as np
+    import torch
+    import paper_2608_04085_b300 as rt
+    ctx = rt.Context.__new__(rt.Context)  # no device needed for the marshalling
+    ctx.total = 8
+    t = torch.arange(8, dtype=torch.float64)
+    p, flags, keep = ctx._arg(t)
+    assert flags == 0 and p.value == t.data_ptr() and keep is t
+    a = np.arange(8, dtype=np.float64)
+    p, flags, keep = ctx._arg(a)
+    assert flags == 0 and p.value == a.ctypes.data
+    with pytest.raises(AssertionError):
+        ctx._arg(torch.zeros(8, dtype=torch.float32))
