@@ -2,7 +2,9 @@
 steps), where the CPU oracle is too slow to run the whole horizon.
 
 - Sampled against the oracle: the oracle runs the first steps of the full
-  grid; the FP64 GPU state and dt sequence must match bitwise.
+  grid; the FP64 GPU state and dt sequence must match bitwise. The same holds
+  on the two larger grids (512x1536, 1024x3072), where the gradient over the
+  first steps is compared too, FP64 and FP32, in their checkpoint modes.
 - Properties at full size: the FP32-state path in the benchmark's launch
   configuration (32 instances, sqrt(N) checkpointing) gives J within 1e-4 of
   the FP64 GPU path for noise, localised and single-mode seeds; the FP64 gradient matches central differences of the
@@ -83,4 +85,44 @@ def test_full_horizon_gradients_fd_and_fp32_cosine():
     with rt.Context([w], precision=rt.RT_FP32_STATE, ckpt=rt.RT_CKPT_SQRT) as c32:
         _, g32, _ = c32.gradient(v)
     cos = (g32 @ g) / (np.linalg.norm(g32) * np.linalg.norm(g))
+    assert cos >= 0.999, cos
+
+
+@pytest.mark.parametrize("nx,ny,ckpt", [(512, 1536, "sqrt"), (1024, 3072, "revolve")])
+def test_largest_grids_first_steps_against_oracle(nx, ny, ckpt):
+    """The largest grids of the uneven 64-instance batch (512x1536, sqrt(N)
+    checkpointing) and of the high-resolution problem (1024x3072, revolve
+    capped at 40 GB), sampled against the oracle over the first two CFL
+    steps, run on all host cores: the FP64 state and dt sequence bitwise,
+    also with the grid split into 2 y-slabs; the FP64 gradient within 1e-11
+    relative L2; the FP32 path in the same checkpoint mode with J within 1e-4
+    and gradient cosine >= 0.999."""
+    import oracle
+    import paper_2608_04085_b300 as rt
+    w = I.rt_box(nx, ny, T=2.0).replace(nsteps=2)
+    v = _v(w, 11)
+    threads = oracle.get_threads()
+    oracle.set_threads(oracle.num_procs())
+    try:
+        ref = oracle.forward(w, v)
+        Jr, gr = oracle.gradient(w, v, ref["dt"])
+    finally:
+        oracle.set_threads(threads)
+    mode, cap = (rt.RT_CKPT_SQRT, 0.0) if ckpt == "sqrt" else (rt.RT_CKPT_REVOLVE, 40e9)
+    for slabs in (0, 2):
+        with rt.Context([w], precision=rt.RT_FP64, y_slabs=slabs) as ctx:
+            ctx.forward(v.ravel())
+            assert np.array_equal(ctx.dt(0), ref["dt"])
+            assert np.array_equal(ctx.state(0), ref["U"])
+    with rt.Context([w], precision=rt.RT_FP64, ckpt=mode, ckpt_cap_bytes=cap) as ctx:
+        J, g, _ = ctx.gradient(v.ravel())
+    g = g.reshape(gr.shape)
+    assert J[0] == pytest.approx(Jr, rel=1e-12)
+    err = np.linalg.norm(g - gr) / np.linalg.norm(gr)
+    assert err <= 1e-11, err
+    with rt.Context([w], precision=rt.RT_FP32_STATE, ckpt=mode, ckpt_cap_bytes=cap) as ctx:
+        J32, g32, _ = ctx.gradient(v.ravel())
+    assert abs(J32[0] - Jr) / Jr <= 1e-4
+    g32 = g32.reshape(gr.shape)
+    cos = np.sum(g32 * gr) / (np.linalg.norm(g32) * np.linalg.norm(gr))
     assert cos >= 0.999, cos
