@@ -42,7 +42,7 @@
  * A typical sequence (host arrays, one FP32 batch, error checks elided):
  *
  *   rt_problem p[32];  ... fill each instance ...
- *   rt_options o = {RT_FP32_STATE, RT_CKPT_AUTO, 0.0, 0, RT_STAGE_AUTO, 0};
+ *   rt_options o = {RT_FP32_STATE, RT_CKPT_AUTO, 0.0, 0, RT_STAGE_AUTO, 0, RT_LOADS_TMA};
  *   rt_ctx* ctx;
  *   rt_init(p, 32, &o, NULL, &ctx);
  *   size_t n = rt_field_total(ctx);              // doubles in v0 and grad
@@ -87,6 +87,8 @@ enum { RT_OBJ_KE = 0, RT_OBJ_EK_ANOMALY_L2 = 1 };
 enum { RT_FP64 = 0, RT_FP32_STATE = 1 };
 enum { RT_CKPT_AUTO = 0, RT_CKPT_STORE_ALL = 1, RT_CKPT_SQRT = 2, RT_CKPT_REVOLVE = 3 };
 enum { RT_STAGE_AUTO = 0, RT_STAGE_SWEEP = 1, RT_STAGE_TILE = 2, RT_STAGE_TILE8 = 3, RT_STAGE_TILE32 = 4 };
+/* rt_options.tile_loads */
+enum { RT_LOADS_TMA = 0, RT_LOADS_PLAIN = 1 };
 enum { RT_CNOP_SPG = 0, RT_CNOP_LBFGS = 1 };
 
 /* flags for rt_forward / rt_gradient / rt_constraint / rt_project / cnop_solve:
@@ -146,6 +148,13 @@ typedef struct {
                                unsplit run: state, dt sequence and gradient bit for bit,
                                sums to rounding order. rt_forward_series is not
                                available on a split context (RT_EINVAL) */
+  int tile_loads;           /* RT_LOADS_TMA (default): the tile kernels fetch every tile
+                               whose box lies inside the grid with one TMA tensor copy per
+                               state slot (instances in runs of one shape, at most 4 runs,
+                               with rows of a 16-byte multiple); other tiles use plain loads.
+                               RT_LOADS_PLAIN: plain loads everywhere. Same values either
+                               way. A TMA wait that gives up (bounded) fails the call with
+                               RT_ETIMEOUT */
 } rt_options;
 
 typedef struct {

@@ -26,6 +26,7 @@ RT_OBJ_KE, RT_OBJ_EK_ANOMALY_L2 = 0, 1
 RT_FP64, RT_FP32_STATE = 0, 1
 RT_CKPT_AUTO, RT_CKPT_STORE_ALL, RT_CKPT_SQRT, RT_CKPT_REVOLVE = 0, 1, 2, 3
 RT_STAGE_AUTO, RT_STAGE_SWEEP, RT_STAGE_TILE, RT_STAGE_TILE8, RT_STAGE_TILE32 = 0, 1, 2, 3, 4
+RT_LOADS_TMA, RT_LOADS_PLAIN = 0, 1
 RT_DEVICE_PTRS, RT_REPLAY_DT, RT_GRAD_DT = 1, 2, 4
 RT_CNOP_SPG, RT_CNOP_LBFGS = 0, 1
 RT_RECON_X_MODES, RT_RECON_2D_POWER = 0, 1
@@ -68,7 +69,7 @@ _PROBLEM_DEFAULTS = {"flux": RT_FLUX_HLLC, "flux_theta": 2.0}
 class RtOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("ckpt", ctypes.c_int),
                 ("ckpt_hbm_cap_bytes", ctypes.c_double), ("max_steps", ctypes.c_int),
-                ("stage_kernel", ctypes.c_int), ("y_slabs", ctypes.c_int)]
+                ("stage_kernel", ctypes.c_int), ("y_slabs", ctypes.c_int), ("tile_loads", ctypes.c_int)]
 
 
 class RtRunStats(ctypes.Structure):
@@ -197,13 +198,14 @@ class Context:
     """A batch of RT instances on the current CUDA device (see rt_init)."""
 
     def __init__(self, problems, precision=RT_FP64, ckpt=RT_CKPT_AUTO, ckpt_cap_bytes=0.0, max_steps=0,
-                 stream=None, stage_kernel=RT_STAGE_AUTO, y_slabs=0):
+                 stream=None, stage_kernel=RT_STAGE_AUTO, y_slabs=0, tile_loads=RT_LOADS_TMA):
         L = library()
         if not isinstance(problems, (list, tuple)):
             problems = [problems]
         self.problems = list(problems)
         arr = (RtProblem * len(problems))(*[make_problem(w) for w in problems])
-        opt = RtOptions(precision, ckpt, float(ckpt_cap_bytes), int(max_steps), int(stage_kernel), int(y_slabs))
+        opt = RtOptions(precision, ckpt, float(ckpt_cap_bytes), int(max_steps), int(stage_kernel), int(y_slabs),
+                        int(tile_loads))
         if stream is None:
             stream = self._torch_stream()
         self._stream = stream

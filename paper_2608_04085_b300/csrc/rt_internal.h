@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace rt {
@@ -27,6 +28,20 @@ enum { STAGE_SWEEP = 1, STAGE_TILE = 2, STAGE_TILE8 = 3, STAGE_TILE32 = 4 };
 constexpr int tile_rows_of(int variant) { return variant == STAGE_TILE8 ? 8 : (variant == STAGE_TILE32 ? 32 : 16); }
 constexpr int tile_list_of(int variant) { return variant == STAGE_TILE8 ? 0 : (variant == STAGE_TILE32 ? 2 : 1); }
 
+// Tensor-memory-accelerator (TMA) tile loads. A TMA group is a run of
+// consecutive device instances of one grid shape; over a state slot it is the
+// 4-D tensor (x, y, component, instance) with x fastest, described by one
+// tensor map per slot and group. A launch passes the maps of the slots it
+// reads; instances outside every group (and tiles whose box would leave the
+// grid) use plain loads. The box spans TMA_BOX_X columns from x0 - 4 (16-byte
+// aligned, since x0 is a multiple of 32), the tile's rows with their ghost
+// rows, and the 4 components of one instance.
+constexpr int TMA_GROUPS = 4;
+constexpr int TMA_BOX_X = TILE_X + 8;
+struct TileMaps {
+  CUtensorMap m[TMA_GROUPS];
+};
+
 // Per-instance constants, resident on the device (one entry per device
 // instance). State slots hold every device instance back to back: instance
 // i's conserved plane k (rho, m_x, m_y, E) starts at slot + 4*cell_off +
@@ -48,6 +63,7 @@ struct InstDev {
   int run_tiles, run_strips; // tiles / strips of the whole problem (all its slabs)
   int run_tiles_h[3];        // the problem's tiles in the tile-stage lists of 8, 16 and 32 rows
   int own0, own1;            // owned rows [own0, own1); the rest are halo rows
+  int tma_g, tma_z;          // TMA group (-1: plain loads only) and index within it
   long long v_plane;         // stride between perturbation components
   int bc_y, limiter;
   int nsteps, ncomp;
@@ -88,7 +104,7 @@ struct RunDev {
   int* nstep;                // steps taken
   unsigned long long* wmin;  // running min of the cell crossing time (bits of a positive double)
   unsigned int* counter;     // CTAs of the instance finished in the current launch
-  int* status;               // 0 ok; 1 non-finite / non-positive state seen
+  int* status;               // 0 ok; 1 non-finite / non-positive state seen; 2 a TMA tile load timed out
   long long* bad_cell;       // first bad cell (j*nx+i)
   int max_steps;
   int n_inst;

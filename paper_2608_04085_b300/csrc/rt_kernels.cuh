@@ -468,6 +468,102 @@ __device__ __forceinline__ void load_prim_tile(const T* __restrict__ Ui, const I
     load_prim_tile_impl<T, EX, EY, AOS, false>(Ui, I, cells, gx0, gy0, P, sW, sRB);
 }
 
+// ------------------------------------------------------------- TMA tile loads
+// One thread initialises an mbarrier, announces the bytes to expect and
+// issues one cp.async.bulk.tensor copy per box; every thread then waits on
+// the barrier's phase 0 (once per CTA) before reading the staged boxes.
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// First 128-byte boundary at or after p (the staging areas have the slack).
+template <class T>
+__device__ __forceinline__ T* align128(void* p) {
+  const uint32_t a = smem_addr(p);
+  return reinterpret_cast<T*>(static_cast<unsigned char*>(p) + ((128u - (a & 127u)) & 127u));
+}
+
+__device__ __forceinline__ void mbar_init_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Box (x, y, component 0, instance z) of the map's tensor into dst.
+__device__ __forceinline__ void tma_box(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(0), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Poll phase `parity` of the barrier at most `limit` times (each poll may
+// suspend the thread for a hardware-defined interval); false if it never
+// completed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit) {
+  for (int i = 0; i < limit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+constexpr int TMA_WAIT_POLLS = 1 << 18;
+
+// Wait for this CTA's TMA boxes. A wait that gives up records status 2 for
+// the problem (the host reports RT_ETIMEOUT) and waits once more, again
+// bounded, for the copies still in flight; the CTA then finishes on whatever
+// the staging area holds, so the launch always ends.
+__device__ __forceinline__ void tma_wait(uint64_t* bar, const RunDev& run, int inst) {
+  if (!mbar_wait(bar, 0, TMA_WAIT_POLLS)) {
+    atomicCAS(&run.status[inst], 0, 2);
+    mbar_wait(bar, 0, TMA_WAIT_POLLS);
+  }
+}
+
+// A tile takes its box from TMA: the instance belongs to a TMA group and the
+// box (TMA_BOX_X columns from x0 - 4, rows y0 - gy .. y0 + rows + gy - 1)
+// lies inside the held rows and columns. Tiles at the periodic seam or a
+// wall keep the plain loads, whose per-cell wrap and mirror logic TMA cannot
+// express (a box with that logic done afterwards measured slower).
+__device__ __forceinline__ bool tma_tile(const InstDev& I, int x0, int y0, int rows, int gy) {
+  return I.tma_g >= 0 && x0 >= 4 && x0 - 4 + TMA_BOX_X <= I.nx && y0 >= gy && y0 + rows + gy <= I.ny;
+}
+
+// Staged box [4][BY][TMA_BOX_X] -> tile of primitive states (cell-major Q4)
+// of EX x EY cells starting at column `ox` of the box and at its first row;
+// the box lies inside the grid (tma_tile). sRB holds the base of every box
+// row (FP32).
+template <class T, int EX, int EY, int BY>
+__device__ __forceinline__ void prim_from_box(const T* __restrict__ box, int ox, const Phys<T>& P,
+                                              const RowBase* __restrict__ sRB, Q4<T>* __restrict__ sW) {
+  constexpr int N = EX * EY, PER = (N + NTH - 1) / NTH, PL = BY * TMA_BOX_X;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int e = threadIdx.x + k * NTH;
+    if (e < N) {
+      const int ey = e / EX, ex = e - ey * EX;
+      const T* b = box + ey * TMA_BOX_X + ex + ox;
+      const RowBase rb = sizeof(T) == 4 ? sRB[ey] : RowBase{0.f, 0.f};
+      T W[4];
+      state_to_prim_b(b[0], b[PL], b[2 * PL], b[3 * PL], rb, P.gm1, W);
+      Q4<T> c;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) c.v[q] = W[q];
+      sW[e] = c;
+    }
+  }
+}
+
 template <class T, int STAGE, int MODE, int LIM>
 __global__ void __launch_bounds__(32 * STRIP_WARPS, 6) k_stage_sweep(const InstDev* __restrict__ insts,
                                                             const int4* __restrict__ strips, int nstrips,
@@ -643,7 +739,8 @@ struct StTile {
 template <class T, int STAGE, int MODE, int LIM, int H>
 __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? (H <= 16 ? 6 : 4) : 1) k_stage_tile(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,
                                                const T* __restrict__ src, const T* __restrict__ base,
-                                               T* __restrict__ dst, RunDev run, int n) {
+                                               T* __restrict__ dst, RunDev run, int n,
+                                               const __grid_constant__ TileMaps tm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using G = StTile<H>;
   Q4<T>* sW = reinterpret_cast<Q4<T>*>(smem_raw);  // [EY][EX]
@@ -651,6 +748,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? (H <= 16 ? 6 : 4) : 1) k
   Q4<T>* sG = sF + G::NFX;                         // [H+1][TX]
   __shared__ T red[NTH / 32];
   __shared__ RowBase sRB[G::EY];
+  __shared__ __align__(8) uint64_t s_bar;
   const int4 tl = tiles[blockIdx.x];
   const InstDev& I = insts[tl.x];
   const int inst = desc_run(tl.w);
@@ -663,7 +761,21 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? (H <= 16 ? 6 : 4) : 1) k
   const int x0 = tl.y, y0 = tl.z;
   const int lim = LIM >= 0 ? LIM : I.limiter;
   const FluxSel<T> fs = flux_sel<T, LIM>(I);
-  load_prim_tile<T, G::EX, G::EY, true>(Si, I, cells, x0 - 2, y0 - 2, P, reinterpret_cast<T*>(sW), sRB);
+  // the primitive tile: from a TMA box staged in the (not yet used) face
+  // buffers, or by plain loads
+  constexpr int BOX = 4 * G::EY * TMA_BOX_X;
+  static_assert((G::NFX + G::NFY) * 4 >= BOX + 128 / sizeof(T), "staging area too small");
+  const bool tma = tma_tile(I, x0, y0, H, 2);
+  T* box = align128<T>(sF);
+  if (tma) {
+    if (threadIdx.x == 0) {
+      mbar_init_expect(&s_bar, BOX * sizeof(T));
+      tma_box(box, &tm.m[I.tma_g], x0 - 4, y0 - 2, I.tma_z, &s_bar);
+    }
+    if (sizeof(T) == 4 && threadIdx.x < G::EY) sRB[threadIdx.x] = row_base<T>(I, y0 - 2 + threadIdx.x);
+  } else {
+    load_prim_tile<T, G::EX, G::EY, true>(Si, I, cells, x0 - 2, y0 - 2, P, reinterpret_cast<T*>(sW), sRB);
+  }
   // stage 2 also needs U^n of this thread's cells in the update; their loads
   // are issued here so that the face work hides their latency
   constexpr int PASSES = G::PASSES;
@@ -679,6 +791,11 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? (H <= 16 ? 6 : 4) : 1) k
 #pragma unroll
       for (int k = 0; k < 4; ++k) bpre[pass][k] = in ? Bi[k * cells + c] : T(0);
     }
+  }
+  if (tma) {
+    __syncthreads();  // barrier initialised, row bases stored
+    tma_wait(&s_bar, run, inst);
+    prim_from_box<T, G::EX, G::EY, G::EY>(box, 2, P, sRB, sW);
   }
   __syncthreads();
   for (int f = threadIdx.x; f < G::NFX + G::NFY; f += NTH) {
@@ -778,12 +895,13 @@ template <class T, int LIM>
 __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 3 : 1)
 k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, const T* __restrict__ U,
           const T* __restrict__ K, T kscale, const T* __restrict__ E, T escale, T* __restrict__ out, RunDev run,
-          int n) {
+          int n, const __grid_constant__ TileMaps tmu, const __grid_constant__ TileMaps tmk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Q4<T>* sW = reinterpret_cast<Q4<T>*>(smem_raw);  // [AY][AX]
   Q4<T>* sK = sW + ADJ_AX * ADJ_AY;                // [KY][KX]
   Q4<T>* sB = sK + ADJ_KX * ADJ_KY;                // [4][ADJ_FACES]
   __shared__ RowBase sRB[ADJ_AY];
+  __shared__ __align__(8) uint64_t s_bar;
   const int4 tl = tiles[blockIdx.x];
   const InstDev& I = insts[tl.x];
   const int inst = desc_run(tl.w);
@@ -797,6 +915,18 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
   const int lim = LIM >= 0 ? LIM : I.limiter;
   const FluxSel<T> fs = flux_sel<T, LIM>(I);
   constexpr int PASSES = TY / ROWS_PER_PASS;
+  // state and cotangent boxes by TMA, staged in the (not yet used) face buffer
+  constexpr int UBOX = 4 * ADJ_AY * TMA_BOX_X, KBOX = 4 * ADJ_KY * TMA_BOX_X;
+  static_assert(16 * ADJ_FACES >= UBOX + KBOX + 128 / sizeof(T), "staging area too small");
+  static_assert(UBOX * sizeof(T) % 128 == 0, "the cotangent box must stay 128-byte aligned");
+  const bool tma = tma_tile(I, x0, y0, TY, 3);
+  T* ubox = align128<T>(sB);
+  T* kbox = ubox + UBOX;
+  if (tma && threadIdx.x == 0) {
+    mbar_init_expect(&s_bar, (UBOX + KBOX) * sizeof(T));
+    tma_box(ubox, &tmu.m[I.tma_g], x0 - 4, y0 - 3, I.tma_z, &s_bar);
+    tma_box(kbox, &tmk.m[I.tma_g], x0 - 4, y0 - 2, I.tma_z, &s_bar);
+  }
   // E of this thread's cells (added at the end) is loaded first, so that the
   // face work hides its latency
   T epre[PASSES][4];
@@ -809,7 +939,25 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
     for (int q = 0; q < 4; ++q) epre[pass][q] = in ? E[c + q * cells] : T(0);
   }
 
-  {  // cotangent tile: all loads first (rows beyond the walls hold zero)
+  if (tma) {
+    if (sizeof(T) == 4 && threadIdx.x < ADJ_AY) sRB[threadIdx.x] = row_base<T>(I, y0 - 3 + threadIdx.x);
+    __syncthreads();  // barrier initialised, row bases stored
+    tma_wait(&s_bar, run, inst);
+    prim_from_box<T, ADJ_AX, ADJ_AY, ADJ_AY>(ubox, 1, P, sRB, sW);
+    constexpr int N = ADJ_KX * ADJ_KY, PER = (N + NTH - 1) / NTH, PL = ADJ_KY * TMA_BOX_X;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int e = threadIdx.x + k * NTH;
+      if (e < N) {
+        const int ey = e / ADJ_KX, ex = e - ey * ADJ_KX;
+        const T* b = kbox + ey * TMA_BOX_X + ex + 2;
+        Q4<T> kc;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) kc.v[q] = kscale * b[q * PL];
+        sK[e] = kc;
+      }
+    }
+  } else {  // cotangent tile: all loads first (rows beyond the walls hold zero)
     constexpr int N = ADJ_KX * ADJ_KY, PER = (N + NTH - 1) / NTH;
     // tile and halo inside the grid, decided once for the CTA: direct addressing
     const bool interior = x0 >= 2 && x0 + ADJ_KX - 2 <= nx && y0 >= 2 && y0 + ADJ_KY - 2 <= ny;

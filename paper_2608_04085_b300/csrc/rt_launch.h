@@ -11,17 +11,19 @@ namespace rt {
 template <class T>
 cudaError_t launch_inject(const InstDev* insts, const int4* tiles, int ntiles, const double* v, T* U,
                           const RunDev& run, int record, cudaStream_t s);
-// variant: STAGE_SWEEP or STAGE_TILE; mode: 0 CFL control, 1 replay counting
-// steps, 2 replay (recompute)
+// variant: STAGE_SWEEP or a tile variant; mode: 0 CFL control, 1 replay
+// counting steps, 2 replay (recompute)
 // lim: the batch's common limiter (compile-time specialised kernels), or -1
+// tm: TMA maps of src (tile variants; boxes of tile height + 4 rows)
 template <class T>
 cudaError_t launch_stage(int variant, int lim, int stage, int mode, const InstDev* insts, const int4* strips,
                          int nstrips, const int4* tiles, int ntiles, const T* src, const T* base, T* dst,
-                         const RunDev& run, int n, cudaStream_t s);
+                         const RunDev& run, int n, const TileMaps& tm, cudaStream_t s);
+// tmu, tmk: TMA maps of U (boxes of TILE_Y + 6 rows) and K (TILE_Y + 4 rows)
 template <class T>
 cudaError_t launch_adjoint(int lim, const InstDev* insts, const int4* tiles, int ntiles, const T* U, const T* K,
                            double kscale, const T* E, double escale, T* out, const RunDev& run, int n,
-                           cudaStream_t s);
+                           const TileMaps& tmu, const TileMaps& tmk, cudaStream_t s);
 template <class T>
 cudaError_t launch_objective(const InstDev* insts, const int4* tiles, int ntiles, T* const* slot_tab, int tab_mod,
                              const int* nstep, double* ek_out, T* lamA, T* lamB, double* partials,

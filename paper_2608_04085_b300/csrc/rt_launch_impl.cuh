@@ -17,23 +17,23 @@ cudaError_t launch_inject(const InstDev* insts, const int4* tiles, int ntiles, c
 // tile variant with tiles of H rows; `tiles` is that height's work list
 template <class T, int LIM, int H>
 void launch_stage_tile(int stage, int mode, const InstDev* insts, const int4* tiles, int ntiles, const T* src,
-                       const T* base, T* dst, const RunDev& run, int n, cudaStream_t s) {
+                       const T* base, T* dst, const RunDev& run, int n, const TileMaps& tm, cudaStream_t s) {
   const size_t sm = StTile<H>::SMEM_ELEMS * sizeof(T);
   if (stage == 1) {
-    k_stage_tile<T, 1, 2, LIM, H><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
+    k_stage_tile<T, 1, 2, LIM, H><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n, tm);
   } else if (mode == 0) {
-    k_stage_tile<T, 2, 0, LIM, H><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
+    k_stage_tile<T, 2, 0, LIM, H><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n, tm);
   } else if (mode == 1) {
-    k_stage_tile<T, 2, 1, LIM, H><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
+    k_stage_tile<T, 2, 1, LIM, H><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n, tm);
   } else {
-    k_stage_tile<T, 2, 2, LIM, H><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n);
+    k_stage_tile<T, 2, 2, LIM, H><<<ntiles, NTH, sm, s>>>(insts, tiles, src, base, dst, run, n, tm);
   }
 }
 
 template <class T, int LIM>
 cudaError_t launch_stage_lim(int variant, int stage, int mode, const InstDev* insts, const int4* strips, int nstrips,
                              const int4* tiles, int ntiles, const T* src, const T* base, T* dst, const RunDev& run,
-                             int n, cudaStream_t s) {
+                             int n, const TileMaps& tm, cudaStream_t s) {
   if (variant == STAGE_SWEEP) {
     const int grid = (nstrips + STRIP_WARPS - 1) / STRIP_WARPS, block = 32 * STRIP_WARPS;
     if (stage == 1) {  // stage 1 reads the recorded step constants in every mode
@@ -46,11 +46,11 @@ cudaError_t launch_stage_lim(int variant, int stage, int mode, const InstDev* in
       k_stage_sweep<T, 2, 2, LIM><<<grid, block, 0, s>>>(insts, strips, nstrips, src, base, dst, run, n);
     }
   } else if (variant == STAGE_TILE8) {
-    launch_stage_tile<T, LIM, 8>(stage, mode, insts, tiles, ntiles, src, base, dst, run, n, s);
+    launch_stage_tile<T, LIM, 8>(stage, mode, insts, tiles, ntiles, src, base, dst, run, n, tm, s);
   } else if (variant == STAGE_TILE32) {
-    launch_stage_tile<T, LIM, 32>(stage, mode, insts, tiles, ntiles, src, base, dst, run, n, s);
+    launch_stage_tile<T, LIM, 32>(stage, mode, insts, tiles, ntiles, src, base, dst, run, n, tm, s);
   } else {
-    launch_stage_tile<T, LIM, 16>(stage, mode, insts, tiles, ntiles, src, base, dst, run, n, s);
+    launch_stage_tile<T, LIM, 16>(stage, mode, insts, tiles, ntiles, src, base, dst, run, n, tm, s);
   }
   return cudaGetLastError();
 }
@@ -58,23 +58,24 @@ cudaError_t launch_stage_lim(int variant, int stage, int mode, const InstDev* in
 template <class T>
 cudaError_t launch_stage(int variant, int lim, int stage, int mode, const InstDev* insts, const int4* strips,
                          int nstrips, const int4* tiles, int ntiles, const T* src, const T* base, T* dst,
-                         const RunDev& run, int n, cudaStream_t s) {
+                         const RunDev& run, int n, const TileMaps& tm, cudaStream_t s) {
   if (lim == LIM_MINMOD)
     return launch_stage_lim<T, LIM_MINMOD>(variant, stage, mode, insts, strips, nstrips, tiles, ntiles, src, base,
-                                           dst, run, n, s);
+                                           dst, run, n, tm, s);
   return launch_stage_lim<T, -1>(variant, stage, mode, insts, strips, nstrips, tiles, ntiles, src, base, dst, run,
-                                 n, s);
+                                 n, tm, s);
 }
 
 template <class T>
 cudaError_t launch_adjoint(int lim, const InstDev* insts, const int4* tiles, int ntiles, const T* U, const T* K,
                            double kscale, const T* E, double escale, T* out, const RunDev& run, int n,
-                           cudaStream_t s) {
+                           const TileMaps& tmu, const TileMaps& tmk, cudaStream_t s) {
   const size_t sm = ADJ_SMEM_ELEMS * sizeof(T);
   if (lim == LIM_MINMOD)
-    k_adjoint<T, LIM_MINMOD><<<ntiles, NTH, sm, s>>>(insts, tiles, U, K, (T)kscale, E, (T)escale, out, run, n);
+    k_adjoint<T, LIM_MINMOD>
+        <<<ntiles, NTH, sm, s>>>(insts, tiles, U, K, (T)kscale, E, (T)escale, out, run, n, tmu, tmk);
   else
-    k_adjoint<T, -1><<<ntiles, NTH, sm, s>>>(insts, tiles, U, K, (T)kscale, E, (T)escale, out, run, n);
+    k_adjoint<T, -1><<<ntiles, NTH, sm, s>>>(insts, tiles, U, K, (T)kscale, E, (T)escale, out, run, n, tmu, tmk);
   return cudaGetLastError();
 }
 
@@ -147,9 +148,11 @@ cudaError_t configure_kernels() {
   template cudaError_t launch_inject<T>(const InstDev*, const int4*, int, const double*, T*, const RunDev&, int,  \
                                         cudaStream_t);                                                           \
   template cudaError_t launch_stage<T>(int, int, int, int, const InstDev*, const int4*, int, const int4*, int,    \
-                                       const T*, const T*, T*, const RunDev&, int, cudaStream_t);                \
+                                       const T*, const T*, T*, const RunDev&, int, const TileMaps&,              \
+                                       cudaStream_t);                                                            \
   template cudaError_t launch_adjoint<T>(int, const InstDev*, const int4*, int, const T*, const T*, double,       \
-                                         const T*, double, T*, const RunDev&, int, cudaStream_t);                \
+                                         const T*, double, T*, const RunDev&, int, const TileMaps&,              \
+                                         const TileMaps&, cudaStream_t);                                         \
   template cudaError_t launch_objective<T>(const InstDev*, const int4*, int, T* const*, int, const int*, double*, \
                                            T*, T*, double*, cudaStream_t);                                       \
   template cudaError_t launch_grad<T>(const InstDev*, const int4*, int, const T*, const double*, double*,         \

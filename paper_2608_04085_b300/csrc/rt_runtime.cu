@@ -145,6 +145,12 @@ struct rt_ctx {
   int stage_variant = rt::STAGE_SWEEP;
   int lim = -1;  // limiter shared by every instance (compile-time specialised kernels), or -1
   double tune_ms[5] = {0, 0, 0, 0, 0};  // by variant: sweep, tile 16, tile 8, tile 32
+  // TMA groups: runs of consecutive device instances of one grid shape whose
+  // tiles the tile kernels fetch with tensor copies (InstDev::tma_g)
+  struct TmaGroup {
+    int first, count, nx, ny;
+  };
+  std::vector<TmaGroup> tma_groups;
 };
 
 namespace {
@@ -257,21 +263,116 @@ cudaError_t exchange(rt_ctx* c, void* slot) {
   return cudaSuccess;
 }
 
+// ------------------------------------------------------------ TMA tensor maps
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver (null if the driver lacks it).
+EncodeTiledFn encode_tiled() {
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// Map of group g over a state slot at `slot`: the 4-D tensor (x, y, component,
+// instance) with boxes of TMA_BOX_X x rows x 4 x 1. Host-side encoding only.
+bool encode_group(const rt_ctx* c, const rt_ctx::TmaGroup& g, const void* slot, int rows, CUtensorMap* m) {
+  const EncodeTiledFn enc = encode_tiled();
+  if (!enc) return false;
+  const cuuint64_t es = c->esz, plane = (cuuint64_t)g.nx * g.ny * es;
+  const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, 4, (cuuint64_t)g.count};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.nx * es, plane, 4 * plane};
+  const cuuint32_t box[4] = {(cuuint32_t)rt::TMA_BOX_X, (cuuint32_t)rows, 4, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  void* base = const_cast<char*>(static_cast<const char*>(slot)) + 4 * c->cell_off[g.first] * (long long)es;
+  return enc(m, es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides,
+             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Maps of every TMA group over `slot` with boxes of `rows` rows (all zero, and
+// never read, without groups).
+cudaError_t tile_maps(const rt_ctx* c, const void* slot, int rows, rt::TileMaps& m) {
+  std::memset(&m, 0, sizeof(m));
+  for (size_t g = 0; g < c->tma_groups.size(); ++g)
+    if (!encode_group(c, c->tma_groups[g], slot, rows, &m.m[g])) return cudaErrorInvalidValue;
+  return cudaSuccess;
+}
+
+// Box rows of the tile stage kernels (tile height + 2 ghost rows each side)
+// and of the adjoint's state (3) and cotangent (2) tiles.
+constexpr int kStageBoxRows[3] = {8 + 4, rt::TILE_Y + 4, 32 + 4};
+constexpr int kAdjBoxRowsU = rt::TILE_Y + 6, kAdjBoxRowsK = rt::TILE_Y + 4;
+
+// Split the device instances into TMA groups (maximal runs of one grid shape
+// whose rows are 16-byte multiples and that hold a box of every kind), keep
+// the TMA_GROUPS largest, and check that their maps encode.
+void assign_tma_groups(rt_ctx* c) {
+  c->tma_groups.clear();
+  for (InstDev& I : c->h_inst) {
+    I.tma_g = -1;
+    I.tma_z = 0;
+  }
+  if (c->opt.tile_loads == RT_LOADS_PLAIN || !encode_tiled()) return;
+  std::vector<rt_ctx::TmaGroup> runs;
+  for (int d = 0; d < c->n_dev;) {
+    int e = d + 1;
+    while (e < c->n_dev && c->h_inst[e].nx == c->h_inst[d].nx && c->h_inst[e].ny == c->h_inst[d].ny) ++e;
+    const InstDev& I = c->h_inst[d];
+    if ((I.nx * c->esz) % 16 == 0 && I.nx >= rt::TMA_BOX_X + rt::TILE_X && I.ny >= kStageBoxRows[2])
+      runs.push_back({d, e - d, I.nx, I.ny});
+    d = e;
+  }
+  std::stable_sort(runs.begin(), runs.end(), [](const rt_ctx::TmaGroup& a, const rt_ctx::TmaGroup& b) {
+    return (long long)a.count * a.nx * a.ny > (long long)b.count * b.nx * b.ny;
+  });
+  if ((int)runs.size() > rt::TMA_GROUPS) runs.resize(rt::TMA_GROUPS);
+  const void* probe = reinterpret_cast<const void*>(uintptr_t(1) << 20);  // any 256-byte aligned address
+  for (const rt_ctx::TmaGroup& g : runs) {
+    CUtensorMap m;
+    bool ok = true;
+    for (int rows : {kStageBoxRows[0], kStageBoxRows[1], kStageBoxRows[2], kAdjBoxRowsU, kAdjBoxRowsK})
+      ok = ok && encode_group(c, g, probe, rows, &m);
+    if (!ok) continue;
+    const int gi = (int)c->tma_groups.size();
+    c->tma_groups.push_back(g);
+    for (int k = 0; k < g.count; ++k) {
+      c->h_inst[g.first + k].tma_g = gi;
+      c->h_inst[g.first + k].tma_z = k;
+    }
+  }
+}
+
 template <class T>
 cudaError_t stage(rt_ctx* c, int st, int mode, const T* src, const T* base, T* dst, int n) {
-  const int ev = timing_begin(c, st - 1);
   const int L = rt::tile_list_of(c->stage_variant);
-  cudaError_t e = rt::launch_stage<T>(c->stage_variant, c->lim, st, mode, c->d_inst, c->d_strips, c->nstrips,
-                                      c->d_tiles_h[L], c->ntiles_h[L], src, base, dst, c->run, n, c->stream);
+  rt::TileMaps tm;
+  cudaError_t e = tile_maps(c, src, kStageBoxRows[L], tm);
+  if (e != cudaSuccess) return e;
+  const int ev = timing_begin(c, st - 1);
+  e = rt::launch_stage<T>(c->stage_variant, c->lim, st, mode, c->d_inst, c->d_strips, c->nstrips, c->d_tiles_h[L],
+                          c->ntiles_h[L], src, base, dst, c->run, n, tm, c->stream);
   timing_end(c, ev);
   return e == cudaSuccess ? exchange(c, dst) : e;
 }
 
 template <class T>
 cudaError_t adjoint(rt_ctx* c, const T* U, const T* K, double ks, const T* E, double es, T* out, int n) {
+  rt::TileMaps tmu, tmk;
+  cudaError_t e = tile_maps(c, U, kAdjBoxRowsU, tmu);
+  if (e == cudaSuccess) e = tile_maps(c, K, kAdjBoxRowsK, tmk);
+  if (e != cudaSuccess) return e;
   const int ev = timing_begin(c, 2);
-  cudaError_t e =
-      rt::launch_adjoint<T>(c->lim, c->d_inst, c->d_tiles, c->ntiles, U, K, ks, E, es, out, c->run, n, c->stream);
+  e = rt::launch_adjoint<T>(c->lim, c->d_inst, c->d_tiles, c->ntiles, U, K, ks, E, es, out, c->run, n, tmu, tmk,
+                            c->stream);
   timing_end(c, ev);
   return e == cudaSuccess ? exchange(c, out) : e;
 }
@@ -401,6 +502,11 @@ rt_status read_run(rt_ctx* c, std::vector<int>& nstep, std::vector<double>& t, s
 }
 
 rt_status nonfinite(rt_ctx* c, const std::vector<int>& status, rt_run_stats* st) {
+  for (int i = 0; i < c->n_inst; ++i)
+    if (status[i] == 2) {
+      if (st) st->bad_instance = i;
+      return fail(c, RT_ETIMEOUT, "instance %d: a TMA tile load did not complete within its wait limit", i);
+    }
   for (int i = 0; i < c->n_inst; ++i)
     if (status[i] != 0) {
       long long cell = -1;
@@ -828,6 +934,12 @@ rt_status gradient_impl(rt_ctx* c, const double* d_v, double* J_out, double* d_g
   CU(rt::launch_grad<T>(c->d_inst, c->d_tiles, c->ntiles, lam[0], d_v, d_g, c->stream));
   ++c->launches;
   if (segments_out) *segments_out = segments;
+  {  // a tile load of the reverse sweep that gave up its wait (status 2)
+    std::vector<int> nstep, status;
+    std::vector<double> t;
+    CHK(read_run(c, nstep, t, status));
+    CHK(nonfinite(c, status, nullptr));
+  }
   return RT_OK;
 }
 
@@ -913,12 +1025,8 @@ rt_status autotune_stage(rt_ctx* c) {
       if (n == warm) CU(cudaEventRecord(c->ev0, c->stream));
       void* src = (n & 1) ? c->sB : c->sA;
       void* dst = (n & 1) ? c->sA : c->sB;
-      const int L = rt::tile_list_of(v);
-      CU(rt::launch_stage<T>(v, c->lim, 1, 0, c->d_inst, c->d_strips, c->nstrips, c->d_tiles_h[L],
-                             c->ntiles_h[L], slotp<T>(src), nullptr, slotp<T>(c->sU1), c->run, n, c->stream));
-      CU(rt::launch_stage<T>(v, c->lim, 2, 0, c->d_inst, c->d_strips, c->nstrips, c->d_tiles_h[L],
-                             c->ntiles_h[L], slotp<T>(c->sU1), slotp<T>(src), slotp<T>(dst), c->run, n,
-                             c->stream));
+      CU(stage<T>(c, 1, 0, slotp<T>(src), nullptr, slotp<T>(c->sU1), n));
+      CU(stage<T>(c, 2, 0, slotp<T>(c->sU1), slotp<T>(src), slotp<T>(dst), n));
     }
     CU(cudaEventRecord(c->ev1, c->stream));
     CU(cudaEventSynchronize(c->ev1));
@@ -1552,6 +1660,10 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
     fail(c, RT_EINVAL, "precision");
     return bail(RT_EINVAL);
   }
+  if (c->opt.tile_loads != RT_LOADS_TMA && c->opt.tile_loads != RT_LOADS_PLAIN) {
+    fail(c, RT_EINVAL, "tile_loads must be RT_LOADS_TMA or RT_LOADS_PLAIN");
+    return bail(RT_EINVAL);
+  }
   c->esz = c->opt.precision == RT_FP64 ? sizeof(double) : sizeof(float);
   c->user_stream = static_cast<cudaStream_t>(cuda_stream);
   c->prob.assign(problems, problems + n_instances);
@@ -1723,6 +1835,7 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
     I.rho0_f = c->d_base_f + I.row_off;
     I.p0_f = c->d_base_f + rows + I.row_off;
   }
+  assign_tma_groups(c);
   INIT_CU(cudaMalloc(&c->d_inst, c->n_dev * sizeof(InstDev)));
   INIT_CU(cudaMemcpy(c->d_inst, c->h_inst.data(), c->n_dev * sizeof(InstDev), cudaMemcpyHostToDevice));
   if (nslab == 1) {

@@ -114,7 +114,7 @@ C_USER = r"""
 #include "rt_cnop.h"
 int main(void) {
   rt_problem p[2] = {{0}};
-  rt_options o = {RT_FP32_STATE, RT_CKPT_AUTO, 0.0, 0, RT_STAGE_AUTO, 0};
+  rt_options o = {RT_FP32_STATE, RT_CKPT_AUTO, 0.0, 0, RT_STAGE_AUTO, 0, RT_LOADS_TMA};
   rt_ctx* ctx;
   if (rt_init(p, 2, &o, NULL, &ctx) != RT_OK) return 1;
   size_t n = rt_field_total(ctx);
