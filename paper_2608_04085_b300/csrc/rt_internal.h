@@ -108,6 +108,8 @@ struct RunDev {
   long long* bad_cell;       // first bad cell (j*nx+i)
   int max_steps;
   int n_inst;
+  int tma_polls = 1 << 18;   // bound on the polls of a TMA wait (see tma_wait)
+  int tma_skip = 0;          // fault injection: barriers armed, no copy issued, so every TMA wait runs out
 };
 
 template <class T>

@@ -501,32 +501,33 @@ __device__ __forceinline__ void tma_box(void* dst, const CUtensorMap* map, int x
       : "memory");
 }
 
-// Poll phase `parity` of the barrier at most `limit` times (each poll may
-// suspend the thread for a hardware-defined interval); false if it never
-// completed.
+// Poll phase `parity` of the barrier at most `limit` times, each poll
+// suspending the thread for at most TMA_POLL_NS nanoseconds while the phase
+// is incomplete; false if it never completed.
+constexpr int TMA_POLL_NS = 1000;
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit) {
   for (int i = 0; i < limit; ++i) {
     uint32_t done;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, "
+        "p;\n\t}"
         : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "n"(TMA_POLL_NS)
         : "memory");
     if (done) return true;
   }
   return false;
 }
 
-constexpr int TMA_WAIT_POLLS = 1 << 18;
-
-// Wait for this CTA's TMA boxes. A wait that gives up records status 2 for
-// the problem (the host reports RT_ETIMEOUT) and waits once more, again
-// bounded, for the copies still in flight; the CTA then finishes on whatever
-// the staging area holds, so the launch always ends.
+// Wait for this CTA's TMA boxes, at most run.tma_polls polls (2^18, about a
+// quarter of a second). A wait that gives up records status 2 for the
+// problem (the host reports RT_ETIMEOUT) and waits once more, again bounded,
+// for copies still in flight; the CTA then finishes on whatever the staging
+// area holds, so the launch always ends.
 __device__ __forceinline__ void tma_wait(uint64_t* bar, const RunDev& run, int inst) {
-  if (!mbar_wait(bar, 0, TMA_WAIT_POLLS)) {
+  if (!mbar_wait(bar, 0, run.tma_polls)) {
     atomicCAS(&run.status[inst], 0, 2);
-    mbar_wait(bar, 0, TMA_WAIT_POLLS);
+    mbar_wait(bar, 0, run.tma_polls);
   }
 }
 
@@ -770,7 +771,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? (H <= 16 ? 6 : 4) : 1) k
   if (tma) {
     if (threadIdx.x == 0) {
       mbar_init_expect(&s_bar, BOX * sizeof(T));
-      tma_box(box, &tm.m[I.tma_g], x0 - 4, y0 - 2, I.tma_z, &s_bar);
+      if (!run.tma_skip) tma_box(box, &tm.m[I.tma_g], x0 - 4, y0 - 2, I.tma_z, &s_bar);
     }
     if (sizeof(T) == 4 && threadIdx.x < G::EY) sRB[threadIdx.x] = row_base<T>(I, y0 - 2 + threadIdx.x);
   } else {
@@ -924,8 +925,10 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
   T* kbox = ubox + UBOX;
   if (tma && threadIdx.x == 0) {
     mbar_init_expect(&s_bar, (UBOX + KBOX) * sizeof(T));
-    tma_box(ubox, &tmu.m[I.tma_g], x0 - 4, y0 - 3, I.tma_z, &s_bar);
-    tma_box(kbox, &tmk.m[I.tma_g], x0 - 4, y0 - 2, I.tma_z, &s_bar);
+    if (!run.tma_skip) {
+      tma_box(ubox, &tmu.m[I.tma_g], x0 - 4, y0 - 3, I.tma_z, &s_bar);
+      tma_box(kbox, &tmk.m[I.tma_g], x0 - 4, y0 - 2, I.tma_z, &s_bar);
+    }
   }
   // E of this thread's cells (added at the end) is loaded first, so that the
   // face work hides its latency

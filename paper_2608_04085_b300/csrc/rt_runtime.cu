@@ -1898,6 +1898,13 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
   {
     const char* g = getenv("RT_CNOP_GRAPHS");
     c->graphs = !(g && g[0] == '0');
+    // fault injection for the TMA wait's timeout path: arm the barriers, issue
+    // no copy, bound each wait by a few polls; every tile-kernel call then
+    // fails with RT_ETIMEOUT and nothing is left in flight
+    const char* f = getenv("RT_CNOP_TMA_WAIT_FAULT");
+    const bool fault = f && f[0] == '1';
+    c->run.tma_skip = fault ? 1 : 0;
+    c->run.tma_polls = fault ? 16 : (1 << 18);
   }
   INIT_CU(c->esz == 8 ? rt::configure_kernels<double>() : rt::configure_kernels<float>());
   size_t freeb = 0, totb = 0;

@@ -5,7 +5,8 @@ stage-kernel variant, both limiter paths (minmod-specialised and generic),
 uneven batches with more grid shapes than TMA groups (one instance falls
 back to plain loads), y-slabs, and grids whose width is not a multiple of the
 tile width. The FP64 TMA path also matches the oracle bit for bit. FP32
-runs agree to rounding."""
+runs agree to rounding. A TMA wait that runs out (fault injected from the
+host) ends in RT_ETIMEOUT with the device still usable."""
 import numpy as np
 import pytest
 
@@ -124,3 +125,23 @@ def test_bad_tile_loads_rejected():
     with pytest.raises(rt.RtError) as e:
         rt.Context([I.rt_box(16, 16, nsteps=2)], precision=rt.RT_FP64, tile_loads=7)
     assert e.value.status == rt.RT_EINVAL
+
+
+def test_tma_wait_that_runs_out_reports_etimeout(monkeypatch):
+    """Fault injection from the host: with RT_CNOP_TMA_WAIT_FAULT=1 the tile
+    kernels arm their barriers but issue no copy, so every TMA wait runs out
+    after its bounded polls (nothing is in flight when the CTAs finish). The
+    forward fails with RT_ETIMEOUT, and the device stays usable: a context
+    without the switch then runs normally."""
+    rt = _rt()
+    w = I.rt_box(128, 96, nsteps=5)
+    v = _v([w], 1)
+    monkeypatch.setenv("RT_CNOP_TMA_WAIT_FAULT", "1")
+    with rt.Context([w], precision=rt.RT_FP64, stage_kernel=rt.RT_STAGE_TILE) as ctx:
+        with pytest.raises(rt.RtError) as e:
+            ctx.forward(v)
+        assert e.value.status == rt.RT_ETIMEOUT
+    monkeypatch.delenv("RT_CNOP_TMA_WAIT_FAULT")
+    with rt.Context([w], precision=rt.RT_FP64, stage_kernel=rt.RT_STAGE_TILE) as ctx:
+        J, _, st = ctx.forward(v)
+        assert st["steps"] == 5 and np.isfinite(J[0])
