@@ -57,7 +57,7 @@ ADJ_BYTES_PER_CELL = {"stage2_adjoint": 12 * 4, "stage1_adjoint": 16 * 4, "mean"
 # DRAM traffic of k_adjoint<float, minmod> per cell per launch (read + write),
 # from one ncu capture of 16 instances of the benchmark grid (traffic grows in
 # proportion to the cells); None while the kernel differs from the profiled one.
-ADJ_TRAFFIC_BYTES_PER_CELL = 49.67
+ADJ_TRAFFIC_BYTES_PER_CELL = 49.62
 STEP_BYTES_PER_CELL_UPDATE = 68 * 4  # forward 20s + segment recompute 20s (U1 kept) + adjoint 12s + 16s (sqrt checkpointing)
 # Warp instructions k_adjoint<float, minmod> executes per cell per launch
 # (ncu sm__inst_executed.sum / cells, 16 instances of the benchmark grid, mean
@@ -65,7 +65,7 @@ STEP_BYTES_PER_CELL_UPDATE = 68 * 4  # forward 20s + segment recompute 20s (U1 k
 # issue roofline divides its executed instructions per second by the issue
 # peak of 148 SMs x 4 schedulers x 1 warp instruction per clock at the
 # sampled SM clock.
-ADJ_WARP_INSTR_PER_CELL = 34.92
+ADJ_WARP_INSTR_PER_CELL = 34.95
 ISSUE_PER_SM_PER_CLK = 4
 KERNEL_TIMING_EVERY = 8
 
