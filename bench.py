@@ -301,6 +301,13 @@ def run_ours(args):
     ctx = rt.Context(cfg.problems, precision=rt.RT_FP32_STATE, ckpt=cfg.ckpt, ckpt_cap_bytes=cfg.cap_bytes)
     # scale each instance onto C = delta (Eq. constraint) with the library's projection kernel
     v_host = ctx.project(xi, cfg.deltas, to_budget=True)
+    # the stage-kernel variant the autotuner kept, and its timings
+    variant, tuning = ctx.stage_kernel()
+    stage_name = {rt.RT_STAGE_SWEEP: "sweep", rt.RT_STAGE_TILE8: "tile8", rt.RT_STAGE_TILE: "tile",
+                  rt.RT_STAGE_TILE32: "tile32"}.get(variant, str(variant))
+    stage_tuning = {k: round(float(t), 4) for k, t in tuning.items()}
+    adj_rows, adj_t = ctx.adjoint_rows()
+    adj_tuning = {str(k): round(float(t), 4) for k, t in adj_t.items()}
     v_dev = torch.from_numpy(v_host).to(dev)
     g_dev = torch.empty_like(v_dev)
     torch.cuda.synchronize()
@@ -378,7 +385,10 @@ def run_ours(args):
                        "T": sorted({w.T for w in cfg.problems}), "rk2_steps_max": steps_run,
                        "checkpointing": {rt.RT_CKPT_SQRT: "sqrt(N)", rt.RT_CKPT_REVOLVE: "revolve"}[cfg.ckpt],
                        "checkpoint_cap_bytes": cfg.cap_bytes or None,
-                       "l2": "working set > L2 (no flush)"},
+                       "l2": "working set > L2 (no flush)",
+                       "stage_kernel": stage_name, "stage_tuning_ms_per_step": stage_tuning,
+                       "adjoint_tile_rows": adj_rows, "adjoint_tuning_ms_per_launch": adj_tuning,
+                       "tile_loads": "tma"},
             "grad_evals_per_s": grad_evals,
             "e2e": {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": int(ctx.total * 8),
                     "d2h_bytes_per_step": int(ctx.total * 8 + n_inst * 8), "calls": len(e2e_s),
@@ -423,16 +433,18 @@ def run_ours(args):
 
 def run_profile_case(args):
     """Small case for ncu captures: 16 instances of the benchmark grid with a
-    short horizon (T = 0.01, about 25 RK2 steps) and the benchmark's sqrt(N)
-    checkpointing, so one gradient launches the same kernel mix as a
-    benchmark step (about 130 launches instead of about 29,000); about 1 GB on
-    the device, each kernel's working set (4 x 50 MB) still larger than L2."""
+    short horizon (T = 0.01, about 25 RK2 steps), the benchmark's sqrt(N)
+    checkpointing and its stage kernel (32-row tiles), so one gradient
+    launches the same kernel mix as a benchmark step (about 130 launches
+    instead of about 29,000); about 1 GB on the device, each kernel's working
+    set (4 x 50 MB) still larger than L2."""
     import paper_2608_04085_b300 as rt
     nb = 16
     probs = [I.single_256().replace(T=0.01) for _ in range(nb)]
-    # the tile variant, which the autotuner picks for the benchmark: under a
-    # profiler the autotuner's timings are distorted and could pick the other
-    with rt.Context(probs, precision=rt.RT_FP32_STATE, ckpt=rt.RT_CKPT_SQRT, stage_kernel=rt.RT_STAGE_TILE) as ctx:
+    # the tile variant with 32-row tiles, which the autotuner keeps for the
+    # benchmark batch: under a profiler the autotuner's timings are distorted
+    # and could pick another
+    with rt.Context(probs, precision=rt.RT_FP32_STATE, ckpt=rt.RT_CKPT_SQRT, stage_kernel=rt.RT_STAGE_TILE32) as ctx:
         v = ctx.project(I.gaussian_batch(range(nb), 2, NY, NX).reshape(-1), DELTA, to_budget=True)
         for k in range(3):
             ctx.set_kernel_timing(1 if k == 2 else 0)

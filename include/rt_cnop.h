@@ -271,6 +271,15 @@ int rt_stage_kernel(const rt_ctx* ctx, double* tuned_ms);
  * ms[0] sweep, ms[1] tiles of 8 rows, ms[2] of 16 rows, ms[3] of 32 rows;
  * zeros when the variant was fixed by the options. Errors: RT_EINVAL. */
 rt_status rt_stage_tuning(const rt_ctx* ctx, double* ms);
+
+/* Adjoint tile height in use (no counterpart in the paper): 16 (tiles of
+ * 32 x 16 cells on 256 threads), or 24 (32 x 24 cells on 384 threads, FP32
+ * state only); both give the same values. For FP32, rt_init timed three
+ * adjoint launches of the unperturbed batch with each and kept the faster;
+ * ms (nullable, [2]) receives those times per launch (zeros for FP64, which
+ * always uses 16). The environment variable RT_CNOP_ADJ_ROWS=16|24 fixes the
+ * choice at rt_init. Returns 0 for a null context. */
+int rt_adjoint_rows(const rt_ctx* ctx, double* ms);
 rt_status rt_kernel_times(rt_ctx* ctx, double* mean_ms, long long* samples, long long* launches);
 
 typedef struct {

@@ -39,7 +39,7 @@ EXPORTS = ("rt_init", "rt_destroy", "rt_last_error", "rt_num_instances", "rt_fie
            "rt_field_size", "rt_field_total", "rt_forward", "rt_gradient", "rt_constraint",
            "rt_project", "rt_get_state", "rt_get_dt", "rt_set_kernel_timing", "rt_kernel_times", "rt_stage_kernel",
            "cnop_solve", "rt_objective_noalloc", "rt_forward_series", "rt_spectrum_x", "rt_spectrum_2d",
-           "rt_reconstruct", "rt_fma_peak", "rt_revolve_plan", "rt_stage_tuning")
+           "rt_reconstruct", "rt_fma_peak", "rt_revolve_plan", "rt_stage_tuning", "rt_adjoint_rows")
 
 
 class RtError(RuntimeError):
@@ -139,6 +139,8 @@ def library():
         L.rt_stage_kernel.restype = ip
         L.rt_stage_tuning.argtypes = [vp, dp]
         L.rt_stage_tuning.restype = ip
+        L.rt_adjoint_rows.argtypes = [vp, dp]
+        L.rt_adjoint_rows.restype = ip
         L.rt_set_kernel_timing.argtypes = [vp, ip]
         L.rt_set_kernel_timing.restype = ip
         llp = ctypes.POINTER(ctypes.c_longlong)
@@ -330,6 +332,13 @@ class Context:
         v = library().rt_stage_kernel(self._h, None)
         self._check(library().rt_stage_tuning(self._h, _dptr(t)))
         return v, {"sweep": t[0], "tile8": t[1], "tile": t[2], "tile32": t[3]}
+
+    def adjoint_rows(self):
+        """(adjoint tile height in use, {16: ms, 24: ms} per launch from the
+        autotuner; zeros when it did not run)."""
+        t = np.zeros(2)
+        rows = library().rt_adjoint_rows(self._h, _dptr(t))
+        return rows, {16: t[0], 24: t[1]}
 
     def set_kernel_timing(self, every):
         """Sample CUDA-event timings of every `every`-th time-step kernel launch."""

@@ -401,13 +401,13 @@ struct __align__(16) Q4 {
 
 // INTERIOR: the tile with its ghost layers lies inside the grid (no periodic
 // wrap, no mirrored wall rows), so cells are addressed directly.
-template <class T, int EX, int EY, bool AOS, bool INTERIOR>
+template <class T, int EX, int EY, bool AOS, bool INTERIOR, int NT = NTH>
 __device__ __forceinline__ void load_prim_tile_impl(const T* __restrict__ Ui, const InstDev& I, long long cells,
                                                     int gx0, int gy0, const Phys<T>& P, T* __restrict__ sW,
                                                     RowBase* __restrict__ sRB) {
   constexpr int N = EX * EY;
-  constexpr int PER = (N + NTH - 1) / NTH;
-  static_assert(EY <= NTH, "one thread per tile row fills the base table");
+  constexpr int PER = (N + NT - 1) / NT;
+  static_assert(EY <= NT, "one thread per tile row fills the base table");
   // FP32: the base of every tile row, loaded together with the state, stored
   // once the state loads are issued and read back after the barrier
   RowBase rbv{0.f, 0.f};
@@ -416,7 +416,7 @@ __device__ __forceinline__ void load_prim_tile_impl(const T* __restrict__ Ui, co
   int rr[PER];
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
-    const int e = threadIdx.x + k * NTH;
+    const int e = threadIdx.x + k * NT;
     rr[k] = 0;
     if (e < N) {
       const int ey = e / EX, ex = e - ey * EX;
@@ -436,7 +436,7 @@ __device__ __forceinline__ void load_prim_tile_impl(const T* __restrict__ Ui, co
   }
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
-    const int e = threadIdx.x + k * NTH;
+    const int e = threadIdx.x + k * NT;
     if (e < N) {
       const int ey = e / EX, ex = e - ey * EX;
       T W[4];
@@ -458,14 +458,14 @@ __device__ __forceinline__ void load_prim_tile_impl(const T* __restrict__ Ui, co
 
 // Load a tile of primitive states (see load_prim_tile_impl); the interior
 // case, decided once for the whole CTA, skips the boundary logic.
-template <class T, int EX, int EY, bool AOS = false>
+template <class T, int EX, int EY, bool AOS = false, int NT = NTH>
 __device__ __forceinline__ void load_prim_tile(const T* __restrict__ Ui, const InstDev& I, long long cells, int gx0,
                                                int gy0, const Phys<T>& P, T* __restrict__ sW,
                                                RowBase* __restrict__ sRB) {
   if (gx0 >= 0 && gx0 + EX <= I.nx && gy0 >= 0 && gy0 + EY <= I.ny)
-    load_prim_tile_impl<T, EX, EY, AOS, true>(Ui, I, cells, gx0, gy0, P, sW, sRB);
+    load_prim_tile_impl<T, EX, EY, AOS, true, NT>(Ui, I, cells, gx0, gy0, P, sW, sRB);
   else
-    load_prim_tile_impl<T, EX, EY, AOS, false>(Ui, I, cells, gx0, gy0, P, sW, sRB);
+    load_prim_tile_impl<T, EX, EY, AOS, false, NT>(Ui, I, cells, gx0, gy0, P, sW, sRB);
 }
 
 // ------------------------------------------------------------- TMA tile loads
@@ -544,13 +544,13 @@ __device__ __forceinline__ bool tma_tile(const InstDev& I, int x0, int y0, int r
 // of EX x EY cells starting at column `ox` of the box and at its first row;
 // the box lies inside the grid (tma_tile). sRB holds the base of every box
 // row (FP32).
-template <class T, int EX, int EY, int BY>
+template <class T, int EX, int EY, int BY, int NT = NTH>
 __device__ __forceinline__ void prim_from_box(const T* __restrict__ box, int ox, const Phys<T>& P,
                                               const RowBase* __restrict__ sRB, Q4<T>* __restrict__ sW) {
-  constexpr int N = EX * EY, PER = (N + NTH - 1) / NTH, PL = BY * TMA_BOX_X;
+  constexpr int N = EX * EY, PER = (N + NT - 1) / NT, PL = BY * TMA_BOX_X;
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
-    const int e = threadIdx.x + k * NTH;
+    const int e = threadIdx.x + k * NT;
     if (e < N) {
       const int ey = e / EX, ex = e - ey * EX;
       const T* b = box + ey * TMA_BOX_X + ex + ox;
@@ -887,21 +887,37 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? (H <= 16 ? 6 : 4) : 1) k
 // tile with 3 ghost layers, cotangent tile with 2, and one face buffer (the
 // 4 variables of each of the face's 4 cells) used first by the x faces and
 // then by the y faces.
-constexpr int ADJ_AX = TX + 6, ADJ_AY = TY + 6, ADJ_KX = TX + 4, ADJ_KY = TY + 4;
-constexpr int ADJ_NFX = (TX + 3) * TY, ADJ_NFY = TX * (TY + 3);
-constexpr int ADJ_FACES = ADJ_NFX > ADJ_NFY ? ADJ_NFX : ADJ_NFY;
-constexpr int ADJ_SMEM_ELEMS = 4 * ADJ_AX * ADJ_AY + 4 * ADJ_KX * ADJ_KY + 16 * ADJ_FACES;
+// Geometry of an adjoint tile of H rows (32 columns), two cells per thread:
+// 16 rows on 256 threads (3 FP32 CTAs per SM) or 24 rows on 384 threads (2
+// FP32 CTAs per SM: the same 24 warps, a third fewer halo faces per cell and
+// block barriers per cell). Every cell sums its contributions in the same
+// order in both, so both give the same values.
+template <int H>
+struct AdjTile {
+  static_assert(H == 16 || H == 24, "adjoint tiles of 16 or 24 rows");
+  static constexpr int ROWS = H;
+  static constexpr int NT = H == 24 ? 384 : 256;
+  static constexpr int MIN_CTAS = H == 24 ? 2 : 3;  // FP32 CTAs per SM (launch bounds)
+  static constexpr int RPP = NT / TX;                // tile rows covered by one pass of the block
+  static constexpr int PASSES = H / RPP;
+  static constexpr int AX = TX + 6, AY = H + 6, KX = TX + 4, KY = H + 4;
+  static constexpr int NFX = (TX + 3) * H, NFY = TX * (H + 3);
+  static constexpr int FACES = NFX > NFY ? NFX : NFY;
+  static constexpr int SMEM_ELEMS = 4 * AX * AY + 4 * KX * KY + 16 * FACES;
+  static_assert(H % RPP == 0, "tile rows must be a multiple of the rows per pass");
+};
 
-template <class T, int LIM>
-__global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 3 : 1)
+template <class T, int LIM, int AH>
+__global__ void __launch_bounds__(AdjTile<AH>::NT, sizeof(T) == 4 ? AdjTile<AH>::MIN_CTAS : 1)
 k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, const T* __restrict__ U,
           const T* __restrict__ K, T kscale, const T* __restrict__ E, T escale, T* __restrict__ out, RunDev run,
           int n, const __grid_constant__ TileMaps tmu, const __grid_constant__ TileMaps tmk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  using G = AdjTile<AH>;
   Q4<T>* sW = reinterpret_cast<Q4<T>*>(smem_raw);  // [AY][AX]
-  Q4<T>* sK = sW + ADJ_AX * ADJ_AY;                // [KY][KX]
-  Q4<T>* sB = sK + ADJ_KX * ADJ_KY;                // [4][ADJ_FACES]
-  __shared__ RowBase sRB[ADJ_AY];
+  Q4<T>* sK = sW + G::AX * G::AY;                   // [KY][KX]
+  Q4<T>* sB = sK + G::KX * G::KY;                   // [4][FACES]
+  __shared__ RowBase sRB[G::AY];
   __shared__ __align__(8) uint64_t s_bar;
   const int4 tl = tiles[blockIdx.x];
   const InstDev& I = insts[tl.x];
@@ -915,12 +931,12 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
   const int x0 = tl.y, y0 = tl.z, nx = I.nx, ny = I.ny;
   const int lim = LIM >= 0 ? LIM : I.limiter;
   const FluxSel<T> fs = flux_sel<T, LIM>(I);
-  constexpr int PASSES = TY / ROWS_PER_PASS;
+  constexpr int PASSES = G::PASSES;
   // state and cotangent boxes by TMA, staged in the (not yet used) face buffer
-  constexpr int UBOX = 4 * ADJ_AY * TMA_BOX_X, KBOX = 4 * ADJ_KY * TMA_BOX_X;
-  static_assert(16 * ADJ_FACES >= UBOX + KBOX + 128 / sizeof(T), "staging area too small");
+  constexpr int UBOX = 4 * G::AY * TMA_BOX_X, KBOX = 4 * G::KY * TMA_BOX_X;
+  static_assert(16 * G::FACES >= UBOX + KBOX + 128 / sizeof(T), "staging area too small");
   static_assert(UBOX * sizeof(T) % 128 == 0, "the cotangent box must stay 128-byte aligned");
-  const bool tma = tma_tile(I, x0, y0, TY, 3);
+  const bool tma = tma_tile(I, x0, y0, G::ROWS, 3);
   T* ubox = align128<T>(sB);
   T* kbox = ubox + UBOX;
   if (tma && threadIdx.x == 0) {
@@ -935,7 +951,7 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
   T epre[PASSES][4];
 #pragma unroll
   for (int pass = 0; pass < PASSES; ++pass) {
-    const int gx = x0 + threadIdx.x % TX, gy = y0 + threadIdx.x / TX + pass * ROWS_PER_PASS;
+    const int gx = x0 + threadIdx.x % TX, gy = y0 + threadIdx.x / TX + pass * G::RPP;
     const bool in = E && gx < nx && gy < ny;
     const long long c = in ? 4 * I.cell_off + (long long)gy * nx + gx : 0;
 #pragma unroll
@@ -943,16 +959,16 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
   }
 
   if (tma) {
-    if (sizeof(T) == 4 && threadIdx.x < ADJ_AY) sRB[threadIdx.x] = row_base<T>(I, y0 - 3 + threadIdx.x);
+    if (sizeof(T) == 4 && threadIdx.x < G::AY) sRB[threadIdx.x] = row_base<T>(I, y0 - 3 + threadIdx.x);
     __syncthreads();  // barrier initialised, row bases stored
     tma_wait(&s_bar, run, inst);
-    prim_from_box<T, ADJ_AX, ADJ_AY, ADJ_AY>(ubox, 1, P, sRB, sW);
-    constexpr int N = ADJ_KX * ADJ_KY, PER = (N + NTH - 1) / NTH, PL = ADJ_KY * TMA_BOX_X;
+    prim_from_box<T, G::AX, G::AY, G::AY, G::NT>(ubox, 1, P, sRB, sW);
+    constexpr int N = G::KX * G::KY, PER = (N + G::NT - 1) / G::NT, PL = G::KY * TMA_BOX_X;
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-      const int e = threadIdx.x + k * NTH;
+      const int e = threadIdx.x + k * G::NT;
       if (e < N) {
-        const int ey = e / ADJ_KX, ex = e - ey * ADJ_KX;
+        const int ey = e / G::KX, ex = e - ey * G::KX;
         const T* b = kbox + ey * TMA_BOX_X + ex + 2;
         Q4<T> kc;
 #pragma unroll
@@ -961,14 +977,14 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
       }
     }
   } else {  // cotangent tile: all loads first (rows beyond the walls hold zero)
-    constexpr int N = ADJ_KX * ADJ_KY, PER = (N + NTH - 1) / NTH;
+    constexpr int N = G::KX * G::KY, PER = (N + G::NT - 1) / G::NT;
     // tile and halo inside the grid, decided once for the CTA: direct addressing
-    const bool interior = x0 >= 2 && x0 + ADJ_KX - 2 <= nx && y0 >= 2 && y0 + ADJ_KY - 2 <= ny;
+    const bool interior = x0 >= 2 && x0 + G::KX - 2 <= nx && y0 >= 2 && y0 + G::KY - 2 <= ny;
     T kv[PER][4];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-      const int e = threadIdx.x + k * NTH;
-      const int ey = e / ADJ_KX, ex = e - ey * ADJ_KX;
+      const int e = threadIdx.x + k * G::NT;
+      const int ey = e / G::KX, ex = e - ey * G::KX;
       const int gy = y0 + ey - 2;
       if (interior) {
         const T* p = Ki + ((long long)gy * nx + x0 + ex - 2);
@@ -981,10 +997,10 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
         for (int q = 0; q < 4; ++q) kv[k][q] = in ? Ki[q * cells + c] : T(0);
       }
     }
-    load_prim_tile<T, ADJ_AX, ADJ_AY, true>(Ui, I, cells, x0 - 3, y0 - 3, P, reinterpret_cast<T*>(sW), sRB);
+    load_prim_tile<T, G::AX, G::AY, true, G::NT>(Ui, I, cells, x0 - 3, y0 - 3, P, reinterpret_cast<T*>(sW), sRB);
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-      const int e = threadIdx.x + k * NTH;
+      const int e = threadIdx.x + k * G::NT;
       if (e < N) {
         Q4<T> kc;
 #pragma unroll
@@ -1003,17 +1019,17 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
     for (int q = 0; q < 4; ++q) bW[pass][q] = T(0);
 
   // x faces: fx of row fy is the left face of tile cell fx-1 (cells fx-3 .. fx)
-  for (int f = threadIdx.x; f < ADJ_NFX; f += NTH) {
+  for (int f = threadIdx.x; f < G::NFX; f += G::NT) {
     const int fy = f / (TX + 3), fx = f - fy * (TX + 3);
     T w[4][4], mu[4], o[4][4];
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-      const Q4<T> c = sW[(fy + 3) * ADJ_AX + fx + p];
+      const Q4<T> c = sW[(fy + 3) * G::AX + fx + p];
 #pragma unroll
       for (int q = 0; q < 4; ++q) w[p][q] = c.v[q];
     }
     {
-      const Q4<T> kr = sK[(fy + 2) * ADJ_KX + fx + 1], kl = sK[(fy + 2) * ADJ_KX + fx];
+      const Q4<T> kr = sK[(fy + 2) * G::KX + fx + 1], kl = sK[(fy + 2) * G::KX + fx];
 #pragma unroll
       for (int q = 0; q < 4; ++q) mu[q] = sc.dtdx * (kr.v[q] - kl.v[q]);
     }
@@ -1023,16 +1039,16 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
       Q4<T> c;
 #pragma unroll
       for (int q = 0; q < 4; ++q) c.v[q] = o[p][q];
-      sB[p * ADJ_FACES + f] = c;
+      sB[p * G::FACES + f] = c;
     }
   }
   __syncthreads();
 #pragma unroll
   for (int pass = 0; pass < PASSES; ++pass) {
-    const int ty = threadIdx.x / TX + pass * ROWS_PER_PASS;
+    const int ty = threadIdx.x / TX + pass * G::RPP;
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-      const Q4<T> c = sB[p * ADJ_FACES + ty * (TX + 3) + tx + 3 - p];
+      const Q4<T> c = sB[p * G::FACES + ty * (TX + 3) + tx + 3 - p];
 #pragma unroll
       for (int q = 0; q < 4; ++q) bW[pass][q] += c.v[q];
     }
@@ -1040,7 +1056,7 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
   __syncthreads();
 
   // y faces: fy of column fx is the bottom face of tile row fy-1 (global face y0+fy-1)
-  for (int f = threadIdx.x; f < ADJ_NFY; f += NTH) {
+  for (int f = threadIdx.x; f < G::NFY; f += G::NT) {
     const int fy = f / TX, fx = f - fy * TX;
     const int gf = y0 + fy - 1;
     T o[4][4];
@@ -1048,11 +1064,11 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
       T w[4][4], mu[4];
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
-        const Q4<T> c = sW[(fy + p) * ADJ_AX + fx + 3];
+        const Q4<T> c = sW[(fy + p) * G::AX + fx + 3];
 #pragma unroll
         for (int q = 0; q < 4; ++q) w[p][q] = c.v[q];
       }
-      const Q4<T> ku = sK[(fy + 1) * ADJ_KX + fx + 2], kd = sK[fy * ADJ_KX + fx + 2];
+      const Q4<T> ku = sK[(fy + 1) * G::KX + fx + 2], kd = sK[fy * G::KX + fx + 2];
 #pragma unroll
       for (int q = 0; q < 4; ++q) mu[q] = sc.dtdy * (ku.v[q] - kd.v[q]);
       face_vjp<T, 1>(w, mu, lim, P.gamma, P.gm1, fs, o);
@@ -1067,18 +1083,18 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
       Q4<T> c;
 #pragma unroll
       for (int q = 0; q < 4; ++q) c.v[q] = o[p][q];
-      sB[p * ADJ_FACES + f] = c;
+      sB[p * G::FACES + f] = c;
     }
   }
   __syncthreads();
 
 #pragma unroll
   for (int pass = 0; pass < PASSES; ++pass) {
-    const int ty = threadIdx.x / TX + pass * ROWS_PER_PASS;
+    const int ty = threadIdx.x / TX + pass * G::RPP;
     const int gx = x0 + tx, gy = y0 + ty;
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-      const Q4<T> c = sB[p * ADJ_FACES + (ty + 3 - p) * TX + tx];
+      const Q4<T> c = sB[p * G::FACES + (ty + 3 - p) * TX + tx];
 #pragma unroll
       for (int q = 0; q < 4; ++q) bW[pass][q] += c.v[q];
     }
@@ -1088,10 +1104,10 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
       if (side == 0) { if (gy > 1) continue; k = gy; gly = -1 - k - y0; }
       else { if (gy < ny - 2 || gy >= ny) continue; k = ny - 1 - gy; gly = ny + k - y0; }
       T gq[4] = {T(0), T(0), T(0), T(0)};
-      const int f_lo = gly > 0 ? gly : 0, f_hi = (gly + 3) < (TY + 2) ? (gly + 3) : (TY + 2);
+      const int f_lo = gly > 0 ? gly : 0, f_hi = (gly + 3) < (G::ROWS + 2) ? (gly + 3) : (G::ROWS + 2);
       for (int fy = f_lo; fy <= f_hi; ++fy) {
         const int p = gly - fy + 3;
-        const Q4<T> c = sB[p * ADJ_FACES + fy * TX + tx];
+        const Q4<T> c = sB[p * G::FACES + fy * TX + tx];
 #pragma unroll
         for (int q = 0; q < 4; ++q) gq[q] += c.v[q];
       }
@@ -1110,7 +1126,7 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
     if (gx < nx && gy < ny) {
       const long long c = (long long)gy * nx + gx;
       // rho, u_x, u_y of the cell from the primitive tile (the values mx/rho, my/rho)
-      const Q4<T> wc = sW[(ty + 3) * ADJ_AX + tx + 3];
+      const Q4<T> wc = sW[(ty + 3) * G::AX + tx + 3];
       const T r = wc.v[0], u = wc.v[1], v = wc.v[2];
       const T* b = bW[pass];
       T bU[4];
@@ -1118,7 +1134,7 @@ k_adjoint(const InstDev* __restrict__ insts, const int4* __restrict__ tiles, con
       bU[1] = b[1] / r - P.gm1 * u * b[3];
       bU[2] = b[2] / r - P.gm1 * v * b[3];
       bU[3] = P.gm1 * b[3];
-      const Q4<T> kq = sK[(ty + 2) * ADJ_KX + tx + 2];
+      const Q4<T> kq = sK[(ty + 2) * G::KX + tx + 2];
       T kc[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) kc[q] = kq.v[q];

@@ -19,10 +19,11 @@ template <class T>
 cudaError_t launch_stage(int variant, int lim, int stage, int mode, const InstDev* insts, const int4* strips,
                          int nstrips, const int4* tiles, int ntiles, const T* src, const T* base, T* dst,
                          const RunDev& run, int n, const TileMaps& tm, cudaStream_t s);
-// tmu, tmk: TMA maps of U (boxes of TILE_Y + 6 rows) and K (TILE_Y + 4 rows)
+// rows: the adjoint tile height (16, or 24 for FP32) of the work list
+// `tiles`; tmu, tmk: TMA maps of U (boxes of rows + 6 rows) and K (rows + 4)
 template <class T>
-cudaError_t launch_adjoint(int lim, const InstDev* insts, const int4* tiles, int ntiles, const T* U, const T* K,
-                           double kscale, const T* E, double escale, T* out, const RunDev& run, int n,
+cudaError_t launch_adjoint(int rows, int lim, const InstDev* insts, const int4* tiles, int ntiles, const T* U,
+                           const T* K, double kscale, const T* E, double escale, T* out, const RunDev& run, int n,
                            const TileMaps& tmu, const TileMaps& tmk, cudaStream_t s);
 template <class T>
 cudaError_t launch_objective(const InstDev* insts, const int4* tiles, int ntiles, T* const* slot_tab, int tab_mod,

@@ -66,16 +66,32 @@ cudaError_t launch_stage(int variant, int lim, int stage, int mode, const InstDe
                                  n, tm, s);
 }
 
-template <class T>
-cudaError_t launch_adjoint(int lim, const InstDev* insts, const int4* tiles, int ntiles, const T* U, const T* K,
-                           double kscale, const T* E, double escale, T* out, const RunDev& run, int n,
-                           const TileMaps& tmu, const TileMaps& tmk, cudaStream_t s) {
-  const size_t sm = ADJ_SMEM_ELEMS * sizeof(T);
+template <class T, int AH>
+void launch_adjoint_h(int lim, const InstDev* insts, const int4* tiles, int ntiles, const T* U, const T* K,
+                      double kscale, const T* E, double escale, T* out, const RunDev& run, int n,
+                      const TileMaps& tmu, const TileMaps& tmk, cudaStream_t s) {
+  using G = AdjTile<AH>;
+  const size_t sm = G::SMEM_ELEMS * sizeof(T);
   if (lim == LIM_MINMOD)
-    k_adjoint<T, LIM_MINMOD>
-        <<<ntiles, NTH, sm, s>>>(insts, tiles, U, K, (T)kscale, E, (T)escale, out, run, n, tmu, tmk);
+    k_adjoint<T, LIM_MINMOD, AH>
+        <<<ntiles, G::NT, sm, s>>>(insts, tiles, U, K, (T)kscale, E, (T)escale, out, run, n, tmu, tmk);
   else
-    k_adjoint<T, -1><<<ntiles, NTH, sm, s>>>(insts, tiles, U, K, (T)kscale, E, (T)escale, out, run, n, tmu, tmk);
+    k_adjoint<T, -1, AH><<<ntiles, G::NT, sm, s>>>(insts, tiles, U, K, (T)kscale, E, (T)escale, out, run, n, tmu,
+                                                   tmk);
+}
+
+template <class T>
+cudaError_t launch_adjoint(int rows, int lim, const InstDev* insts, const int4* tiles, int ntiles, const T* U,
+                           const T* K, double kscale, const T* E, double escale, T* out, const RunDev& run, int n,
+                           const TileMaps& tmu, const TileMaps& tmk, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (rows == 24) {
+      launch_adjoint_h<T, 24>(lim, insts, tiles, ntiles, U, K, kscale, E, escale, out, run, n, tmu, tmk, s);
+      return cudaGetLastError();
+    }
+  }
+  if (rows != 16) return cudaErrorInvalidValue;
+  launch_adjoint_h<T, 16>(lim, insts, tiles, ntiles, U, K, kscale, E, escale, out, run, n, tmu, tmk, s);
   return cudaGetLastError();
 }
 
@@ -133,7 +149,10 @@ cudaError_t configure_lim() {
   cudaError_t e = configure_tile<T, LIM, 8>();
   if (e == cudaSuccess) e = configure_tile<T, LIM, 16>();
   if (e == cudaSuccess) e = configure_tile<T, LIM, 32>();
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adjoint<T, LIM>, a, (int)(ADJ_SMEM_ELEMS * sizeof(T)));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adjoint<T, LIM, 16>, a, (int)(AdjTile<16>::SMEM_ELEMS * sizeof(T)));
+  if constexpr (sizeof(T) == 4)
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_adjoint<T, LIM, 24>, a, (int)(AdjTile<24>::SMEM_ELEMS * sizeof(T)));
   return e;
 }
 
@@ -150,7 +169,7 @@ cudaError_t configure_kernels() {
   template cudaError_t launch_stage<T>(int, int, int, int, const InstDev*, const int4*, int, const int4*, int,    \
                                        const T*, const T*, T*, const RunDev&, int, const TileMaps&,              \
                                        cudaStream_t);                                                            \
-  template cudaError_t launch_adjoint<T>(int, const InstDev*, const int4*, int, const T*, const T*, double,       \
+  template cudaError_t launch_adjoint<T>(int, int, const InstDev*, const int4*, int, const T*, const T*, double,  \
                                          const T*, double, T*, const RunDev&, int, const TileMaps&,              \
                                          const TileMaps&, cudaStream_t);                                         \
   template cudaError_t launch_objective<T>(const InstDev*, const int4*, int, T* const*, int, const int*, double*, \

@@ -80,6 +80,11 @@ struct rt_ctx {
   std::vector<int4> h_tiles_h[3];  // tile-stage work lists of 8, 16 (= h_tiles) and 32 rows
   int4* d_tiles_h[3] = {nullptr, nullptr, nullptr};
   int ntiles_h[3] = {0, 0, 0};
+  std::vector<int4> h_tiles_a24;   // adjoint work list of 24-row tiles (FP32)
+  int4* d_tiles_a24 = nullptr;
+  int ntiles_a24 = 0;
+  int adj_rows = 16;               // adjoint tile height in use: 16, or 24 (FP32)
+  double adj_tune_ms[2] = {0, 0};  // adjoint autotuner: ms per launch with 16- and 24-row tiles
   std::vector<int4> h_strips;  // sweep-kernel strips over all instances
   int4* d_strips = nullptr;
   int nstrips = 0;
@@ -308,9 +313,10 @@ cudaError_t tile_maps(const rt_ctx* c, const void* slot, int rows, rt::TileMaps&
 }
 
 // Box rows of the tile stage kernels (tile height + 2 ghost rows each side)
-// and of the adjoint's state (3) and cotangent (2) tiles.
+// and of the adjoint's state (3) and cotangent (2) tiles, for adjoint tiles
+// of 16 and 24 rows.
 constexpr int kStageBoxRows[3] = {8 + 4, rt::TILE_Y + 4, 32 + 4};
-constexpr int kAdjBoxRowsU = rt::TILE_Y + 6, kAdjBoxRowsK = rt::TILE_Y + 4;
+constexpr int kAdjBoxRowsU[2] = {16 + 6, 24 + 6}, kAdjBoxRowsK[2] = {16 + 4, 24 + 4};
 
 // Split the device instances into TMA groups (maximal runs of one grid shape
 // whose rows are 16-byte multiples and that hold a box of every kind), keep
@@ -339,7 +345,8 @@ void assign_tma_groups(rt_ctx* c) {
   for (const rt_ctx::TmaGroup& g : runs) {
     CUtensorMap m;
     bool ok = true;
-    for (int rows : {kStageBoxRows[0], kStageBoxRows[1], kStageBoxRows[2], kAdjBoxRowsU, kAdjBoxRowsK})
+    for (int rows : {kStageBoxRows[0], kStageBoxRows[1], kStageBoxRows[2], kAdjBoxRowsU[0], kAdjBoxRowsK[0],
+                     kAdjBoxRowsU[1], kAdjBoxRowsK[1]})
       ok = ok && encode_group(c, g, probe, rows, &m);
     if (!ok) continue;
     const int gi = (int)c->tma_groups.size();
@@ -366,13 +373,14 @@ cudaError_t stage(rt_ctx* c, int st, int mode, const T* src, const T* base, T* d
 
 template <class T>
 cudaError_t adjoint(rt_ctx* c, const T* U, const T* K, double ks, const T* E, double es, T* out, int n) {
+  const int a = c->adj_rows == 24 ? 1 : 0;
   rt::TileMaps tmu, tmk;
-  cudaError_t e = tile_maps(c, U, kAdjBoxRowsU, tmu);
-  if (e == cudaSuccess) e = tile_maps(c, K, kAdjBoxRowsK, tmk);
+  cudaError_t e = tile_maps(c, U, kAdjBoxRowsU[a], tmu);
+  if (e == cudaSuccess) e = tile_maps(c, K, kAdjBoxRowsK[a], tmk);
   if (e != cudaSuccess) return e;
   const int ev = timing_begin(c, 2);
-  e = rt::launch_adjoint<T>(c->lim, c->d_inst, c->d_tiles, c->ntiles, U, K, ks, E, es, out, c->run, n, tmu, tmk,
-                            c->stream);
+  e = rt::launch_adjoint<T>(c->adj_rows, c->lim, c->d_inst, a ? c->d_tiles_a24 : c->d_tiles,
+                            a ? c->ntiles_a24 : c->ntiles, U, K, ks, E, es, out, c->run, n, tmu, tmk, c->stream);
   timing_end(c, ev);
   return e == cudaSuccess ? exchange(c, out) : e;
 }
@@ -1037,6 +1045,43 @@ rt_status autotune_stage(rt_ctx* c) {
   }
   c->stage_variant = best_v;
   c->have_run = false;
+  return RT_OK;
+}
+
+// Adjoint autotuner (FP32): time three launches of the adjoint with 16- and
+// 24-row tiles on the unperturbed batch at step 0 and keep the faster (both
+// give the same values). RT_CNOP_ADJ_ROWS=16|24 fixes the choice instead.
+template <class T>
+rt_status autotune_adjoint(rt_ctx* c) {
+  const char* f = getenv("RT_CNOP_ADJ_ROWS");
+  if (f && (atoi(f) == 16 || atoi(f) == 24)) {
+    c->adj_rows = sizeof(T) == 4 ? atoi(f) : 16;
+    return RT_OK;
+  }
+  c->adj_rows = 16;
+  if constexpr (sizeof(T) == 4) {
+    CU(cudaMemsetAsync(c->d_v, 0, c->total_v * sizeof(double), c->stream));
+    CHK(inject<T>(c, c->d_v, c->sA));
+    CU(cudaMemsetAsync(c->lA, 0, c->slot_bytes, c->stream));
+    const int reps = 3;
+    double best = 1e300;
+    int best_rows = 16;
+    for (int k = 0; k < 2; ++k) {
+      c->adj_rows = k ? 24 : 16;
+      CU(adjoint<T>(c, slotp<T>(c->sA), slotp<T>(c->lA), 1.0, nullptr, 0.0, slotp<T>(c->lB), 0));  // warm-up
+      CU(cudaEventRecord(c->ev0, c->stream));
+      for (int r = 0; r < reps; ++r)
+        CU(adjoint<T>(c, slotp<T>(c->sA), slotp<T>(c->lA), 1.0, nullptr, 0.0, slotp<T>(c->lB), 0));
+      CU(cudaEventRecord(c->ev1, c->stream));
+      CU(cudaEventSynchronize(c->ev1));
+      float ms = 0.f;
+      CU(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+      c->adj_tune_ms[k] = ms / reps;
+      if (ms < best) { best = ms; best_rows = c->adj_rows; }
+    }
+    c->adj_rows = best_rows;
+    c->have_run = false;
+  }
   return RT_OK;
 }
 
@@ -1760,6 +1805,9 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
         for (int x0 = 0; x0 < P.nx; x0 += rt::TILE_X)
           c->h_tiles.push_back(make_int4(d, x0, ty, i | (std::min(rt::TILE_Y, I.own1 - ty) << 24)));
       I.tile_end = (int)c->h_tiles.size();
+      for (int ty = I.own0; ty < I.own1; ty += 24)  // the adjoint list of 24-row tiles
+        for (int x0 = 0; x0 < P.nx; x0 += rt::TILE_X)
+          c->h_tiles_a24.push_back(make_int4(d, x0, ty, i | (std::min(24, I.own1 - ty) << 24)));
       for (int L : {0, 2}) {  // the tile-stage lists of 8 and 32 rows
         const int h = L == 0 ? 8 : 32;
         for (int ty = I.own0; ty < I.own1; ty += h)
@@ -1867,6 +1915,9 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
     INIT_CU(cudaMemcpy(c->d_tiles_h[L], c->h_tiles_h[L].data(), c->ntiles_h[L] * sizeof(int4),
                        cudaMemcpyHostToDevice));
   }
+  c->ntiles_a24 = (int)c->h_tiles_a24.size();
+  INIT_CU(cudaMalloc(&c->d_tiles_a24, c->ntiles_a24 * sizeof(int4)));
+  INIT_CU(cudaMemcpy(c->d_tiles_a24, c->h_tiles_a24.data(), c->ntiles_a24 * sizeof(int4), cudaMemcpyHostToDevice));
   INIT_CU(cudaMalloc(&c->d_strips, c->nstrips * sizeof(int4)));
   INIT_CU(cudaMemcpy(c->d_strips, c->h_strips.data(), c->nstrips * sizeof(int4), cudaMemcpyHostToDevice));
   void** bufs[6] = {&c->sA, &c->sB, &c->sU1, &c->lA, &c->lB, &c->l1};
@@ -1928,6 +1979,11 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
     fail(c, RT_EINVAL, "stage_kernel");
     return bail(RT_EINVAL);
   }
+  {
+    rt_status s = ensure_fields(c, false);
+    if (s == RT_OK) s = c->esz == 8 ? autotune_adjoint<double>(c) : autotune_adjoint<float>(c);
+    if (s != RT_OK) return bail(s);
+  }
 #undef INIT_CU
   *out = c;
   return RT_OK;
@@ -1938,6 +1994,7 @@ void rt_destroy(rt_ctx* c) {
   if (c->d_pinst && c->d_pinst != c->d_inst) cudaFree(c->d_pinst);
   if (c->d_tiles_h[0]) cudaFree(c->d_tiles_h[0]);
   if (c->d_tiles_h[2]) cudaFree(c->d_tiles_h[2]);
+  if (c->d_tiles_a24) cudaFree(c->d_tiles_a24);
   void* ptrs[] = {c->d_inst, c->d_tiles, c->d_strips, c->d_base, c->d_base_f, c->d_ek0, c->d_ek, c->sA, c->sB, c->sU1, c->lA, c->lB,
                   c->l1, c->d_tab, c->run.dtrec, c->run.wrec, c->d_blast, c->d_coef, c->run.dtc, c->run.counter, c->run.t, c->run.nstep, c->run.wmin, c->run.status,
                   c->run.bad_cell, c->d_partials, c->d_sums, c->d_scal, c->d_v, c->d_g, c->d_w1, c->d_w2,
@@ -2258,6 +2315,15 @@ rt_status rt_stage_tuning(const rt_ctx* c, double* ms) {
   ms[2] = c->tune_ms[rt::STAGE_TILE];
   ms[3] = c->tune_ms[rt::STAGE_TILE32];
   return RT_OK;
+}
+
+int rt_adjoint_rows(const rt_ctx* c, double* ms) {
+  if (!c) return 0;
+  if (ms) {
+    ms[0] = c->adj_tune_ms[0];
+    ms[1] = c->adj_tune_ms[1];
+  }
+  return c->adj_rows;
 }
 
 rt_status rt_kernel_times(rt_ctx* c, double* mean_ms, long long* samples, long long* launches) {
