@@ -135,8 +135,9 @@ typedef struct {
   double ckpt_hbm_cap_bytes;/* cap on checkpoint + segment memory; 0 = 60% of free memory.
                                REVOLVE uses cap / slot size - 4 binomial checkpoint slots */
   int max_steps;            /* upper bound on steps per run (sizes the dt record); 0 = 200000 */
-  int stage_kernel;         /* RT_STAGE_AUTO (time both at rt_init, keep the faster),
-                               RT_STAGE_SWEEP or RT_STAGE_TILE; both give identical values */
+  int stage_kernel;         /* RT_STAGE_AUTO (time the four variants at rt_init, keep the
+                               fastest), RT_STAGE_SWEEP, RT_STAGE_TILE, RT_STAGE_TILE8 or
+                               RT_STAGE_TILE32; all give the same values (FP64 bit for bit) */
   int y_slabs;              /* 0 or 1: each problem is one device instance. k > 1: each
                                problem is split into k y-slabs of nearly equal height
                                (at least 3 rows each, so ny >= 3k), each holding its rows
