@@ -336,10 +336,14 @@ typedef struct {
  *    (||v||/||gh|| when none); if <gh, p> <= 0 the pairs are dropped and
  *    p = (||v||/||gh||) gh; trial points P(v + lam p), lam = 1, 1/2, ...,
  *    accepted once J >= min(last gll_memory J) + armijo_c <gh, P(v + lam p) - v>.
- *  RT_CNOP_SPG: d = P(v + alpha g) - v, trial points v + lam d accepted once
- *    J >= min(last gll_memory J) + armijo_c lam <g, d>, and the
- *    Barzilai-Borwein step alpha = <s,s>/<s,y> clipped to
- *    [alpha_min, alpha_max] (alpha_max when <s,y> <= 0).
+ *  RT_CNOP_SPG: steps in the energy inner product <a,b>_E = sum rho0 a b dA
+ *    of Eq. constraint, in which P is the exact projection onto the ball, so
+ *    that its fixed points are the KKT points g = lambda dC/dv: with
+ *    q = g / (rho0 dA) the representer of g, d = P(v + alpha q) - v, trial
+ *    points v + lam d accepted once J >= min(last gll_memory J) +
+ *    armijo_c lam <g, d>, and the Barzilai-Borwein step
+ *    alpha = <s,s>_E / <s,y> clipped to [alpha_min, alpha_max] (alpha_max
+ *    when <s,y> <= 0); the first alpha is ||v||_E / ||q||_E.
  * On return v_inout holds the CNOP of every instance and J_out[i] (nullable)
  * its objective. Errors: as rt_gradient; RT_EINVAL for an unknown method, or
  * a checkpoint written for another context, method, memory, precision or

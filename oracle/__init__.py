@@ -316,30 +316,50 @@ def random_start(w, xi, h_loc, eps):
 
 
 def projected_spg(value, value_and_grad, proj, v_start, iters, memory=10, armijo=1e-4, alpha_min=1e-30,
-                  alpha_max=1e30, max_backtracks=30, log=None):
+                  alpha_max=1e30, max_backtracks=30, log=None, metric=None):
     """Spectral projected gradient ascent of value(v) over the set onto which
     proj projects, with the non-monotone Armijo backtracking line search of
     Grippo, Lampariello & Lucidi (Sec. 3.4): a trial is measured against the
     worst, i.e. smallest, of the last ``memory`` accepted values, so that J
     may dip temporarily.
 
-    Iteration k: d = proj(v + alpha g) - v; accept v + lam d once
+    ``metric`` (an array like v, or None for the identity) is the diagonal of
+    the inner product <a, b>_M = sum a M b in which the method steps: the
+    ascent direction is the gradient's representer q = g / M, and the
+    spectral step uses M-norms. With proj the exact projection in that inner
+    product, the fixed points (d = 0) are the first-order (KKT) points of the
+    constrained maximisation.
+
+    Iteration k: d = proj(v + alpha q) - v; accept v + lam d once
     value(v + lam d) >= min_recent + armijo * lam * <g, d>, halving lam
-    otherwise; then alpha = <s, s> / <s, y'> with s the step and
+    otherwise; then alpha = <s, s>_M / <s, y'> with s the step and
     y' = -(g_new - g_old) (the gradient change of the minimised objective
     -value), clipped to [alpha_min, alpha_max], and alpha_max when
-    <s, y'> <= 0. The first alpha is ||v0|| / ||g0||. The stationarity chi of
-    App. A is recorded per iteration. Returns a dict with v, J, the history,
-    the per-iteration records and the evaluation counts."""
+    <s, y'> <= 0. The first alpha is ||v0||_M / ||q0||_M. The stationarity
+    chi of App. A (with the gradient g) is recorded per iteration. Returns a
+    dict with v, J, the history, the per-iteration records and the
+    evaluation counts."""
+    Mw = None if metric is None else np.asarray(metric, dtype=np.float64)
+
+    def rep(g):
+        return g if Mw is None else g / Mw
+
+    def mdot(a, b):
+        return float(np.sum(a * b)) if Mw is None else float(np.sum(a * Mw * b))
+
+    def mnorm(a):
+        return float(np.linalg.norm(a)) if Mw is None else float(np.sqrt(mdot(a, a)))
+
     v = proj(v_start)
     J, g = value_and_grad(v)
     evals, grads = 1, 1
     hist = [J]
-    alpha = float(np.linalg.norm(v) / max(np.linalg.norm(g), 1e-300))
+    q = rep(g)
+    alpha = mnorm(v) / max(mnorm(q), 1e-300)
     alpha = min(max(alpha, alpha_min), alpha_max)
     records = []
     for k in range(iters):
-        d = proj(v + alpha * g) - v
+        d = proj(v + alpha * rep(g)) - v
         gd = float(np.sum(g * d))
         Jref = min(hist[-memory:])
         lam = 1.0
@@ -359,7 +379,7 @@ def projected_spg(value, value_and_grad, proj, v_start, iters, memory=10, armijo
         s = vt - v
         yv = -(gn - g)
         sy = float(np.sum(s * yv))
-        alpha = alpha_max if sy <= 0.0 else min(max(float(np.sum(s * s)) / sy, alpha_min), alpha_max)
+        alpha = alpha_max if sy <= 0.0 else min(max(mdot(s, s) / sy, alpha_min), alpha_max)
         v, J, g = vt, Jn, gn
         hist.append(J)
         chi = float(np.max(np.abs(proj(v + g) - v)))
@@ -374,7 +394,12 @@ def spg(w, v_start, eps, iters, memory=10, armijo=1e-4, alpha_min=1e-30, alpha_m
         max_backtracks=30, ek0=None, log=None):
     """Spectral projected gradient ascent (projected_spg) of the workload's
     objective over {C <= eps} with the radial projection of Eq. projection
-    (Sec. 3.4), starting from P(v_start)."""
+    (Sec. 3.4), starting from P(v_start). It steps in the energy inner product
+    of Eq. constraint, <a, b>_E = sum rho0 a b dx dy, in which the radial
+    rescale is the exact projection onto the ball, so that its fixed points
+    are the KKT points grad J = lambda grad C; with the Euclidean gradient
+    instead they would be the points where grad J is parallel to v, which
+    differ wherever rho0 varies."""
     def value(v):
         return objective_value(w, forward(w, v, ek0=ek0))
 
@@ -382,9 +407,11 @@ def spg(w, v_start, eps, iters, memory=10, armijo=1e-4, alpha_min=1e-30, alpha_m
         J, g, _ = value_and_gradient(w, v, ek0)
         return J, g
 
+    vs = np.asarray(v_start, dtype=np.float64)
+    metric = constraint_normal(w, np.ones(vs.size)).reshape(vs.shape)
     return projected_spg(value, value_and_grad, lambda v: project(w, v, eps), v_start, iters, memory=memory,
                          armijo=armijo, alpha_min=alpha_min, alpha_max=alpha_max,
-                         max_backtracks=max_backtracks, log=log)
+                         max_backtracks=max_backtracks, log=log, metric=metric)
 
 
 # ------------------------------------- projected L-BFGS, Sec. 3.4 (Eq. projection)

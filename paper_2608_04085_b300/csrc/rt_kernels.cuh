@@ -1487,9 +1487,12 @@ __global__ void __launch_bounds__(NTH) k_field_axpby(const InstDev* __restrict__
 }
 
 // out = rho0(y) dA a on perturbation fields: the gradient of the constraint
-// C (Eq. constraint) at a, the normal of the budget surface.
+// C (Eq. constraint) at a, the normal of the budget surface. inverse != 0:
+// out = a / (rho0(y) dA), the representer of the linear form a in the energy
+// inner product <x, y>_E = sum rho0 x y dA that C induces.
 __global__ void __launch_bounds__(NTH) k_field_weight(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,
-                                                      double* __restrict__ out, const double* __restrict__ a) {
+                                                      double* __restrict__ out, const double* __restrict__ a,
+                                                      int inverse) {
   const int4 tl = tiles[blockIdx.x];
   const InstDev& I = insts[tl.x];
   for (int e = threadIdx.x; e < TX * TY; e += NTH) {
@@ -1499,7 +1502,7 @@ __global__ void __launch_bounds__(NTH) k_field_weight(const InstDev* __restrict_
     const double w = I.rho0[gy];
     for (int k = 0; k < I.ncomp; ++k) {
       const long long idx = c + k * I.v_plane;
-      out[idx] = w * a[idx] * I.dA;
+      out[idx] = inverse ? a[idx] / (w * I.dA) : w * a[idx] * I.dA;
     }
   }
 }

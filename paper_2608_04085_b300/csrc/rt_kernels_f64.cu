@@ -47,8 +47,8 @@ cudaError_t launch_field_axpby(const InstDev* insts, const int4* tiles, int ntil
 }
 
 cudaError_t launch_field_weight(const InstDev* insts, const int4* tiles, int ntiles, double* out, const double* a,
-                                cudaStream_t s) {
-  k_field_weight<<<ntiles, NTH, 0, s>>>(insts, tiles, out, a);
+                                int inverse, cudaStream_t s) {
+  k_field_weight<<<ntiles, NTH, 0, s>>>(insts, tiles, out, a, inverse);
   return cudaGetLastError();
 }
 

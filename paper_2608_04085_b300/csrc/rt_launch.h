@@ -62,9 +62,10 @@ cudaError_t launch_field_reduce(int mode, const InstDev* insts, const int4* tile
 cudaError_t launch_field_axpby(const InstDev* insts, const int4* tiles, int ntiles, double* out,
                                const double* alpha, const double* a, const double* beta, const double* b,
                                cudaStream_t s);
-// out = rho0(y) dA a (gradient of the constraint C at a)
+// out = rho0(y) dA a (gradient of the constraint C at a), or with inverse
+// != 0 out = a / (rho0(y) dA) (the representer of a in the energy inner product)
 cudaError_t launch_field_weight(const InstDev* insts, const int4* tiles, int ntiles, double* out, const double* a,
-                                cudaStream_t s);
+                                int inverse, cudaStream_t s);
 cudaError_t launch_localise(const InstDev* insts, const int4* tiles, int ntiles, double h_loc, double* v,
                             cudaStream_t s);
 

@@ -1354,7 +1354,7 @@ rt_status cnop_run(rt_ctx* c, const cnop_params* prm, double* v_inout, int flags
   auto model_gradient = [&](const double* x, double* gx) -> rt_status {
     CHK(field_sums(c, 0, x, nullptr, C));
     for (int i = 0; i < N; ++i) on_surf[i] = C[i] >= eps[i] * (1.0 - 1e-10);
-    CU(rt::launch_field_weight(c->d_inst, c->d_tiles, c->ntiles, nrm, x, c->stream));
+    CU(rt::launch_field_weight(c->d_inst, c->d_tiles, c->ntiles, nrm, x, 0, c->stream));
     std::vector<double> gx_x, n_x, coef(N, 0.0);
     CHK(field_sums(c, 1, gx, x, gx_x));
     CHK(field_sums(c, 1, nrm, x, n_x));
@@ -1371,12 +1371,18 @@ rt_status cnop_run(rt_ctx* c, const cnop_params* prm, double* v_inout, int flags
       if (sel[i] && on_surf[i] && running(i)) coef[i] = -(np_[i] / nn[i]);
     return axpby(c, p, ones, p, &coef, nrm);
   };
+  // SPG steps in the energy inner product <a, b>_E = sum rho0 a b dA of
+  // Eq. constraint (<a, a>_E = 2 C(a)), in which the radial rescale P is the
+  // exact projection onto the ball: its ascent direction is q = g / (rho0 dA),
+  // the representer of g, so that its fixed points are the KKT points
+  // g = lambda dC/dv. First step alpha = ||v||_E / ||q||_E; tmp is scratch.
   auto spg_alpha0 = [&]() -> rt_status {
-    std::vector<double> vv, gg;
-    CHK(field_sums(c, 1, v, v, vv));
-    CHK(field_sums(c, 1, g, g, gg));
+    std::vector<double> cv, cq;
+    CU(rt::launch_field_weight(c->d_inst, c->d_tiles, c->ntiles, tmp, g, 1, c->stream));
+    CHK(field_sums(c, 0, v, nullptr, cv));
+    CHK(field_sums(c, 0, tmp, nullptr, cq));
     for (int i = 0; i < N; ++i)
-      st.alpha[i] = std::min(std::max(std::sqrt(vv[i]) / std::max(std::sqrt(gg[i]), 1e-300), amin), amax);
+      st.alpha[i] = std::min(std::max(std::sqrt(cv[i]) / std::max(std::sqrt(cq[i]), 1e-300), amin), amax);
     return RT_OK;
   };
 
@@ -1415,7 +1421,7 @@ rt_status cnop_run(rt_ctx* c, const cnop_params* prm, double* v_inout, int flags
       // on_surf and nrm at v, as the last model_gradient left them
       CHK(field_sums(c, 0, v, nullptr, C));
       for (int i = 0; i < N; ++i) on_surf[i] = C[i] >= eps[i] * (1.0 - 1e-10);
-      CU(rt::launch_field_weight(c->d_inst, c->d_tiles, c->ntiles, nrm, v, c->stream));
+      CU(rt::launch_field_weight(c->d_inst, c->d_tiles, c->ntiles, nrm, v, 0, c->stream));
     }
   } else {
     CHK(cnop_start(c, prm, v_inout, flags, eps));
@@ -1501,8 +1507,9 @@ rt_status cnop_run(rt_ctx* c, const cnop_params* prm, double* v_inout, int flags
         CHK(tangent(restart));
       }
     } else {
-      // d = P(v + alpha g) - v and <g, d>
-      CHK(axpby(c, vt, ones, v, &st.alpha, g));
+      // d = P(v + alpha q) - v, q = g / (rho0 dA), and <g, d>
+      CU(rt::launch_field_weight(c->d_inst, c->d_tiles, c->ntiles, tmp, g, 1, c->stream));
+      CHK(axpby(c, vt, ones, v, &st.alpha, tmp));
       CHK(field_sums(c, 0, vt, nullptr, C));
       for (int i = 0; i < N; ++i) sc[i] = C[i] <= eps[i] ? 1.0 : std::sqrt(eps[i] / C[i]);
       CHK(axpby(c, vt, sc, vt, nullptr, nullptr));
@@ -1582,15 +1589,15 @@ rt_status cnop_run(rt_ctx* c, const cnop_params* prm, double* v_inout, int flags
       }
       ++st.stored_iters;
     } else {
-      // alpha = <s,s>/<s,y'>, y' = -(g_new - g)
-      std::vector<double> ss, sg, sgt;
-      CHK(field_sums(c, 1, tmp, tmp, ss));
+      // alpha = <s,s>_E / <s,y'>, y' = -(g_new - g), <s,s>_E = 2 C(s)
+      std::vector<double> cs, sg, sgt;
+      CHK(field_sums(c, 0, tmp, nullptr, cs));
       CHK(field_sums(c, 1, tmp, g, sg));
       CHK(field_sums(c, 1, tmp, gt, sgt));
       for (int i = 0; i < N; ++i) {
         if (!running(i)) continue;
         const double sy = sg[i] - sgt[i];
-        st.alpha[i] = sy <= 0.0 ? amax : std::min(std::max(ss[i] / sy, amin), amax);
+        st.alpha[i] = sy <= 0.0 ? amax : std::min(std::max(2.0 * cs[i] / sy, amin), amax);
       }
     }
     for (int i = 0; i < N; ++i) {

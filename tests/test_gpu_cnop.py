@@ -37,6 +37,30 @@ def test_cnop_fp64_matches_oracle_spg():
 
 
 @pytest.mark.parametrize("method", [0, 1], ids=["spg", "lbfgs"])
+def test_cnop_fp64_at_finite_amplitude_is_a_kkt_point(method):
+    """Both GPU optimisers reach a first-order (KKT) point of the maximisation
+    on {C <= eps} at an amplitude where the CNOP is far from the linear one
+    (the case of the oracle's KKT pins): C = eps and dJ/dv parallel to
+    dC/dv = rho0 v dx dy with a positive multiplier, checked with the GPU's
+    own gradient and the oracle's constraint normal."""
+    import oracle
+    import paper_2608_04085_b300 as rt
+    w = I.rt_box(8, 16, nsteps=60, g_y=-1.0, limiter=I.LIM_NONE)
+    eps = 1e-3
+    v0 = _start(w, 21, eps)
+    with rt.Context([w], precision=rt.RT_FP64) as ctx:
+        v, J, res = ctx.cnop(v0.ravel(), eps, 60, method=method)
+        assert res["status"] == rt.RT_OK
+        Jg, g, _ = ctx.gradient(v)
+    n = oracle.constraint_normal(w, v).ravel()
+    assert oracle.constraint(w, v.reshape(v0.shape)) == pytest.approx(eps, rel=1e-12)
+    cos = float(g @ n / (np.linalg.norm(g) * np.linalg.norm(n)))
+    assert 1.0 - cos <= 1e-5, 1.0 - cos
+    assert J[0] == pytest.approx(Jg[0], rel=1e-12)
+    assert J[0] > 2.0 * eps  # the oracle's maximum here is J / C = 2.20
+
+
+@pytest.mark.parametrize("method", [0, 1], ids=["spg", "lbfgs"])
 def test_cnop_batch_equals_single_runs(method):
     import paper_2608_04085_b300 as rt
     ws = [I.rt_box(16, 32, nsteps=15), I.rt_box(12, 40, nsteps=12, ncomp=I.PERT_VY, limiter=I.LIM_MC)]
