@@ -19,12 +19,12 @@ told apart.
 
 Parity status: every function below is pinned by a ``-m "not gpu"`` test
 (``tests/test_oracle_*.py``) against closed forms, textbook solutions,
-invariants or brute force, except ``spg`` and ``lbfgs`` at finite amplitude,
-whose results have no closed form (parity unpinned there); they are pinned in
-the small-amplitude limit, where they must reproduce the leading eigenvector of
-the tangent-linear problem, and their cores ``projected_spg`` and
-``projected_lbfgs`` / ``lbfgs_direction`` are pinned on analytic objectives
-(and the latter against the dense BFGS update).
+invariants or brute force. ``spg`` and ``lbfgs`` at finite amplitude have no
+closed form; they are pinned there by the first-order (KKT) optimality
+conditions of the maximisation on the energy ball, in the small-amplitude
+limit by the leading eigenvector of the tangent-linear problem, and their cores
+``projected_spg`` and ``projected_lbfgs`` / ``lbfgs_direction`` on analytic
+objectives (the latter also against the dense BFGS update).
 """
 from __future__ import annotations
 
