@@ -162,8 +162,13 @@ typedef struct {
   int steps;                /* largest step count over instances in the last run */
   int segments;             /* checkpoint segments of the last gradient (sqrt: > 1;
                                store-all: 1; revolve: minus the recomputed steps) */
-  int bad_instance;         /* first instance with a non-finite state, or -1 */
-  long long bad_cell;       /* its cell index (j*nx + i), or -1 */
+  int bad_instance;         /* RT_ENONFINITE: first instance with a non-finite or
+                               non-positive state; RT_ETIMEOUT: the instance whose tile
+                               load gave up; else -1 */
+  int bad_step;             /* RT_ENONFINITE: the step (from 0) whose result was bad, else -1 */
+  long long bad_cell;       /* RT_ENONFINITE: its first bad cell (j*nx + i), else -1. On a
+                               failed rt_forward / rt_gradient only these three fields are
+                               set (the others are zero) */
   double cell_updates;      /* sum over instances of cells x steps advanced */
   double ms;                /* device time of the call, CUDA events on the stream */
   long long launches;       /* kernels launched by the call */

@@ -74,8 +74,8 @@ class RtOptions(ctypes.Structure):
 
 class RtRunStats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("segments", ctypes.c_int), ("bad_instance", ctypes.c_int),
-                ("bad_cell", ctypes.c_longlong), ("cell_updates", ctypes.c_double), ("ms", ctypes.c_double),
-                ("launches", ctypes.c_longlong)]
+                ("bad_step", ctypes.c_int), ("bad_cell", ctypes.c_longlong), ("cell_updates", ctypes.c_double),
+                ("ms", ctypes.c_double), ("launches", ctypes.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -231,9 +231,11 @@ class Context:
             pass
         return 0
 
-    def _check(self, st):
+    def _check(self, st, stats=None):
         if st != RT_OK:
-            raise RtError(st, library().rt_last_error(self._h).decode())
+            err = RtError(st, library().rt_last_error(self._h).decode())
+            err.stats = stats.as_dict() if stats is not None else None
+            raise err
 
     def _arg(self, a):
         """(pointer, flags, keepalive) for a host ndarray, a host (for example
@@ -271,7 +273,7 @@ class Context:
         Jke = np.zeros(self.n)
         st = RtRunStats()
         self._check(library().rt_forward(self._h, p, flags | (RT_REPLAY_DT if replay else 0), _dptr(J),
-                                          _dptr(Jke), ctypes.byref(st)))
+                                          _dptr(Jke), ctypes.byref(st)), st)
         del keep
         return J, Jke, st.as_dict()
 
@@ -291,7 +293,7 @@ class Context:
         J = np.zeros(self.n)
         st = RtRunStats()
         self._check(library().rt_gradient(self._h, p, flags | (RT_GRAD_DT if dt_grad else 0), _dptr(J), gp,
-                                          ctypes.byref(st)))
+                                          ctypes.byref(st)), st)
         del keep, gkeep
         return J, out, st.as_dict()
 

@@ -27,6 +27,7 @@
 // The Python binding mirrors these layouts with ctypes.
 static_assert(sizeof(rt_problem) == 152, "rt_problem layout");
 static_assert(sizeof(rt_options) == 32, "rt_options layout");
+static_assert(sizeof(rt_run_stats) == 48, "rt_run_stats layout");
 static_assert(sizeof(cnop_params) == 96, "cnop_params layout");
 static_assert(sizeof(cnop_result) == 64, "cnop_result layout");
 
@@ -149,6 +150,9 @@ struct rt_ctx {
   // stage-kernel variant in use and the autotuner's timings (ms per step)
   int stage_variant = rt::STAGE_SWEEP;
   int lim = -1;  // limiter shared by every instance (compile-time specialised kernels), or -1
+  // the first failure of the current call (RT_ENONFINITE / RT_ETIMEOUT), for rt_run_stats
+  int bad_instance = -1, bad_step = -1;
+  long long bad_cell = -1;
   double tune_ms[5] = {0, 0, 0, 0, 0};  // by variant: sweep, tile 16, tile 8, tile 32
   // TMA groups: runs of consecutive device instances of one grid shape whose
   // tiles the tile kernels fetch with tensor copies (InstDev::tma_g)
@@ -434,6 +438,8 @@ rt_status enter(rt_ctx* c) {
 
 void reset_accounting(rt_ctx* c) {
   c->launches = 0;
+  c->bad_instance = c->bad_step = -1;
+  c->bad_cell = -1;
   for (int k = 0; k < 3; ++k) { c->kind_launches[k] = 0; c->kind_ms[k] = 0.0; c->kind_samples[k] = 0; }
   c->evused.clear();
   for (int k = 0; k < 3; ++k) c->kind_pairs[k] = 0;
@@ -509,20 +515,38 @@ rt_status read_run(rt_ctx* c, std::vector<int>& nstep, std::vector<double>& t, s
   return RT_OK;
 }
 
-rt_status nonfinite(rt_ctx* c, const std::vector<int>& status, rt_run_stats* st) {
+// The first instance whose status word is set: RT_ETIMEOUT for a TMA wait
+// that ran out, RT_ENONFINITE for a non-finite or non-positive state, whose
+// cell and step (the stage-2 check of step nstep - 1 found it, and the step
+// control stopped the instance there) are kept for rt_run_stats.
+rt_status nonfinite(rt_ctx* c, const std::vector<int>& nstep, const std::vector<int>& status) {
   for (int i = 0; i < c->n_inst; ++i)
     if (status[i] == 2) {
-      if (st) st->bad_instance = i;
+      c->bad_instance = i;
       return fail(c, RT_ETIMEOUT, "instance %d: a TMA tile load did not complete within its wait limit", i);
     }
   for (int i = 0; i < c->n_inst; ++i)
     if (status[i] != 0) {
       long long cell = -1;
       cudaMemcpy(&cell, c->run.bad_cell + i, sizeof(long long), cudaMemcpyDeviceToHost);
-      if (st) { st->bad_instance = i; st->bad_cell = cell; }
-      return fail(c, RT_ENONFINITE, "instance %d: non-positive density/pressure or NaN at cell %lld", i, cell);
+      c->bad_instance = i;
+      c->bad_cell = cell;
+      c->bad_step = nstep[i] - 1;
+      return fail(c, RT_ENONFINITE, "instance %d: non-positive density/pressure or NaN at cell %lld after step %d",
+                  i, cell, c->bad_step);
     }
   return RT_OK;
+}
+
+// A failed call still reports where the state went bad.
+rt_status failed_call(rt_ctx* c, rt_run_stats* st, rt_status s) {
+  if (st) {
+    std::memset(st, 0, sizeof(*st));
+    st->bad_instance = c->bad_instance;
+    st->bad_step = c->bad_step;
+    st->bad_cell = c->bad_cell;
+  }
+  return s;
 }
 
 // Forward plan: kind 0 = ping-pong sA/sB; kind 1 = ping-pong plus a copy of
@@ -625,7 +649,7 @@ rt_status march(rt_ctx* c, const Plan& plan, int mode, int n_est, int replay_ste
       if (sampler && n % sample_every == 0) CHK((*sampler)(n));
     }
     CHK(read_run(c, nstep, t, status));
-    CHK(nonfinite(c, status, nullptr));
+    CHK(nonfinite(c, nstep, status));
     if (mode == 1 || all_done(c, nstep, t, status)) break;
     target = n + std::max(16, n / 16);
   }
@@ -693,6 +717,7 @@ void fill_stats(rt_ctx* c, rt_run_stats* st, float ms, int segments) {
   st->steps = c->last_steps;
   st->segments = segments;
   st->bad_instance = -1;
+  st->bad_step = -1;
   st->bad_cell = -1;
   double cu = 0.0;
   for (int i = 0; i < c->n_inst; ++i) cu += (double)c->prob[i].nx * c->prob[i].ny * c->h_nstep[i];
@@ -946,7 +971,7 @@ rt_status gradient_impl(rt_ctx* c, const double* d_v, double* J_out, double* d_g
     std::vector<int> nstep, status;
     std::vector<double> t;
     CHK(read_run(c, nstep, t, status));
-    CHK(nonfinite(c, status, nullptr));
+    CHK(nonfinite(c, nstep, status));
   }
   return RT_OK;
 }
@@ -2041,8 +2066,9 @@ rt_status rt_forward(rt_ctx* c, const double* v0, int flags, double* J_out, doub
   Timer tm(c);
   CHK(copy_in(c, v0, flags, c->d_v));
   int steps = 0;
-  CHK(c->esz == 8 ? forward_impl<double>(c, c->d_v, flags, J_out, J_ke_out, &steps)
-                  : forward_impl<float>(c, c->d_v, flags, J_out, J_ke_out, &steps));
+  const rt_status s = c->esz == 8 ? forward_impl<double>(c, c->d_v, flags, J_out, J_ke_out, &steps)
+                                  : forward_impl<float>(c, c->d_v, flags, J_out, J_ke_out, &steps);
+  if (s != RT_OK) return failed_call(c, st, s);
   const float ms = tm.stop();
   collect_timing(c);
   fill_stats(c, st, ms, 0);
@@ -2204,8 +2230,9 @@ rt_status rt_gradient(rt_ctx* c, const double* v0, int flags, double* J_out, dou
   CHK(copy_in(c, v0, flags, c->d_v));
   int segments = 0;
   const bool dtg = (flags & RT_GRAD_DT) != 0;
-  CHK(c->esz == 8 ? gradient_impl<double>(c, c->d_v, J_out, c->d_g, &segments, dtg)
-                  : gradient_impl<float>(c, c->d_v, J_out, c->d_g, &segments, dtg));
+  const rt_status s = c->esz == 8 ? gradient_impl<double>(c, c->d_v, J_out, c->d_g, &segments, dtg)
+                                  : gradient_impl<float>(c, c->d_v, J_out, c->d_g, &segments, dtg);
+  if (s != RT_OK) return failed_call(c, st, s);
   CHK(copy_out(c, c->d_g, flags, grad_out));
   const float ms = tm.stop();
   collect_timing(c);

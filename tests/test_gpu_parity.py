@@ -217,14 +217,32 @@ def test_constraint_and_projection_match_oracle():
 def test_nonfinite_state_is_reported():
     """A random perturbation far beyond the sound speed drives the pressure
     negative within five steps (the oracle shows the same); the kernels flag
-    it and the call returns RT_ENONFINITE (no device fault)."""
+    it and the call returns RT_ENONFINITE (no device fault), with the
+    instance, the step and the first bad cell in the run statistics, for the
+    forward and the gradient."""
+    import oracle
     w = I.rt_box(16, 32, nsteps=5)
     v = 50.0 * I.gaussian_field(1, 2, w.ny, w.nx).ravel()
     rt = _rt()
-    with rt.Context([w], precision=rt.RT_FP64) as ctx:
-        with pytest.raises(rt.RtError) as e:
-            ctx.forward(v)
-        assert e.value.status == rt.RT_ENONFINITE
+    with rt.Context([w, w], precision=rt.RT_FP64) as ctx:
+        vv = np.concatenate([0.0 * v, v])  # the second instance goes bad
+        for call in (ctx.forward, ctx.gradient):
+            with pytest.raises(rt.RtError) as e:
+                call(vv)
+            assert e.value.status == rt.RT_ENONFINITE
+            st = e.value.stats
+            assert st["bad_instance"] == 1
+            assert 0 <= st["bad_step"] < 5
+            assert 0 <= st["bad_cell"] < w.nx * w.ny
+            assert "after step %d" % st["bad_step"] in str(e.value)
+    # the step is the first whose oracle result has a non-finite or
+    # non-positive density or pressure
+    def valid(n):
+        U = oracle.forward(w.replace(nsteps=n), v.reshape(2, w.ny, w.nx))["U"]
+        p = (w.gamma - 1.0) * (U[3] - 0.5 * (U[1] ** 2 + U[2] ** 2) / U[0])
+        return bool(np.all(np.isfinite(U)) and np.all(U[0] > 0) and np.all(p > 0))
+    first_bad = next(n for n in range(1, 6) if not valid(n)) - 1
+    assert st["bad_step"] == first_bad
 
 
 def test_autotuner_picks_a_variant_and_matches_forced_ones():
