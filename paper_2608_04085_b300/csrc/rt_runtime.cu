@@ -17,6 +17,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/rt_cnop.h"
 #include "rt_internal.h"
@@ -165,6 +166,19 @@ struct rt_ctx {
 namespace {
 
 const double kMaxFinite = 1e300;
+
+// NVTX range over a scope (or up to end()), for tracing tools (nsys,
+// ncu --nvtx); without a tool attached the calls do nothing. The ranges mark
+// the host-side submission of the work, which runs asynchronously.
+struct Range {
+  bool open = true;
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  void end() {
+    if (open) nvtxRangePop();
+    open = false;
+  }
+  ~Range() { end(); }
+};
 
 rt_status fail(rt_ctx* c, rt_status s, const char* fmt, ...) {
   char buf[512];
@@ -882,6 +896,7 @@ rt_status gradient_impl(rt_ctx* c, const double* d_v, double* J_out, double* d_g
   int n_done = 0;
   Plan fplan = plan;
   if (plan.kind == 3) fplan = Plan();  // revolve: plain forward first, recomputation from U^0 later
+  Range forward_range("forward sweep");
   rt_status s = march<T>(c, fplan, 0, n_est, 0, &n_done);
   if (s == RT_ENOMEM && plan.kind == 2) {  // the run outgrew the stored-state plan: redo it checkpointed
     plan = Plan();
@@ -895,6 +910,8 @@ rt_status gradient_impl(rt_ctx* c, const double* d_v, double* J_out, double* d_g
   if (s != RT_OK) return s;
   CHK(objective<T>(c, fplan, true, nullptr));
   CHK(read_J(c, J_out, nullptr));
+  forward_range.end();
+  Range reverse_range("reverse sweep");
   const int N = c->last_steps;
   T* lam[2] = {slotp<T>(c->lA), slotp<T>(c->lB)};
   T* l1 = slotp<T>(c->l1);
@@ -949,6 +966,7 @@ rt_status gradient_impl(rt_ctx* c, const double* d_v, double* J_out, double* d_g
     const int S = plan.S;
     segments = (N + S - 1) / S;
     for (int k = segments - 1; k >= 0; --k) {
+      Range segment_range("checkpoint segment: recompute and reverse");
       const int n0 = k * S, n1 = std::min(N, n0 + S);
       auto seg = [&](int n) -> T* { return n == n0 ? slotp<T>(c->pool[S + k]) : slotp<T>(c->pool[n - n0]); };
       auto seg1 = [&](int n) -> T* { return slotp<T>(c->pool1[n - n0]); };
@@ -1470,6 +1488,7 @@ rt_status cnop_run(rt_ctx* c, const cnop_params* prm, double* v_inout, int flags
   bool any_live = false;
   for (int i = 0; i < N; ++i) any_live = any_live || running(i);
   while (st.k < prm->max_iter && any_live) {
+    Range iteration_range("cnop iteration");
     const int k = st.k;
     std::vector<double> gd, lam(N, 1.0), Jref(N), Jt(N), Jn(N);
     if (lbfgs) {
@@ -1722,6 +1741,7 @@ rt_status rt_init(const rt_problem* problems, int n_instances, const rt_options*
   if (!out) return RT_EINVAL;
   *out = nullptr;
   if (!problems || n_instances <= 0) return RT_EINVAL;
+  Range range("rt_init");
   rt_ctx* c = new (std::nothrow) rt_ctx();
   if (!c) return RT_ENOMEM;
   auto bail = [&](rt_status s) {
@@ -2059,6 +2079,7 @@ size_t rt_field_total(const rt_ctx* c) { return c ? c->total_v : 0; }
 
 rt_status rt_forward(rt_ctx* c, const double* v0, int flags, double* J_out, double* J_ke_out, rt_run_stats* st) {
   if (!c || !v0 || !J_out) return fail(c, RT_EINVAL, "null argument");
+  Range range("rt_forward");
   c->err.clear();
   CHK(ensure_fields(c, false));
   CHK(enter(c));
@@ -2221,6 +2242,7 @@ rt_status rt_reconstruct(rt_ctx* c, const double* v, int flags, int kind, double
 
 rt_status rt_gradient(rt_ctx* c, const double* v0, int flags, double* J_out, double* grad_out, rt_run_stats* st) {
   if (!c || !v0 || !J_out || !grad_out) return fail(c, RT_EINVAL, "null argument");
+  Range range("rt_gradient");
   if (flags & RT_REPLAY_DT) return fail(c, RT_EINVAL, "rt_gradient runs its own step control (RT_REPLAY_DT is not accepted)");
   c->err.clear();
   CHK(ensure_fields(c, false));
@@ -2373,6 +2395,7 @@ rt_status rt_kernel_times(rt_ctx* c, double* mean_ms, long long* samples, long l
 rt_status cnop_solve(rt_ctx* c, const cnop_params* prm, double* v_inout, int flags, double* J_out,
                      cnop_result* res) {
   if (!c || !prm || !v_inout || !prm->eps) return fail(c, RT_EINVAL, "null argument");
+  Range range("cnop_solve");
   if (prm->max_iter < 0) return fail(c, RT_EINVAL, "max_iter < 0");
   if (prm->lbfgs_memory < 0) return fail(c, RT_EINVAL, "lbfgs_memory < 0");
   c->err.clear();
