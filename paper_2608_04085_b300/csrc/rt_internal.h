@@ -8,8 +8,9 @@
 
 namespace rt {
 
-// Tile of cells advanced by one CTA: TILE_X x TILE_Y cells, 256 threads,
-// two cells per thread.
+// Tile of cells advanced by one CTA of the tile kernels: TILE_X x TILE_Y
+// cells, 256 threads, two cells per thread (the stage kernel also has tiles of
+// 8 and 32 rows, the FP32 adjoint of 24 rows on 384 threads).
 constexpr int TILE_X = 32;
 constexpr int TILE_Y = 16;
 constexpr int TILE_THREADS = 256;

@@ -732,11 +732,12 @@ struct StTile {
   static constexpr int LIST = H == 8 ? 0 : (H == 16 ? 1 : 2);  // index into InstDev::run_tiles_h
 };
 
-// Tile variant of the stage kernel: one CTA per 32 x 16 tile, primitive
-// states with 2 ghost layers in shared memory, one thread per face, then one
-// thread per cell for the update. Modes as for the sweep variant. FP32
-// launches are held to 6 CTAs per SM (40 registers), which the stage-2
-// variant with the step control would otherwise exceed.
+// Tile variant of the stage kernel: one CTA of 256 threads per tile of 32
+// columns and H = 8, 16 or 32 rows, primitive states with 2 ghost layers in
+// shared memory, one thread per face, then one thread per cell for the
+// update. Modes as for the sweep variant. FP32 launches are held to 6 CTAs per
+// SM for H <= 16 (40 registers) and 4 for H = 32, which the stage-2 variant
+// with the step control would otherwise exceed.
 template <class T, int STAGE, int MODE, int LIM, int H>
 __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? (H <= 16 ? 6 : 4) : 1) k_stage_tile(const InstDev* __restrict__ insts, const int4* __restrict__ tiles,
                                                const T* __restrict__ src, const T* __restrict__ base,
