@@ -400,6 +400,20 @@ rt_status rt_reconstruct(rt_ctx* ctx, const double* v, int flags, int kind, doub
  * Errors: RT_EINVAL (steps < 0 or slots < 0). */
 rt_status rt_revolve_plan(int steps, int slots, long long* recomputed, double* optimum);
 
+/* The TMA tile-load plan (no counterpart in the paper; host arithmetic only,
+ * no device needed): for n device instances of grids nx[i] x ny[i] in slot
+ * order (without y-slabs, the problems in rt_init's order) and an element
+ * size of 4 (FP32 state) or 8 (FP64), which instances the tile kernels fetch
+ * with TMA tensor copies. group_of[i] (host, [n]) receives the instance's
+ * group, or -1 for plain loads; index_of[i] (host, [n]) its index within the
+ * group. A group is a maximal run of consecutive instances of one shape
+ * whose rows are a multiple of 16 bytes and whose grid holds every tile box
+ * (nx >= 72, ny >= 36); at most 4 runs, the largest (cells times instances)
+ * first, ties to the earlier run. rt_init keeps this plan when
+ * rt_options.tile_loads is RT_LOADS_TMA and the driver can encode the tensor
+ * maps. Errors: RT_EINVAL (null arrays, n < 0, another element size). */
+rt_status rt_tma_plan(const int* nx, const int* ny, int n, int elem_bytes, int* group_of, int* index_of);
+
 /* Measured FMA throughput of the current device (measurement support; the
  * paper has no counterpart): independent fused multiply-add chains in every
  * thread of a grid that fills every SM, FP32 and FP64, best of three timed

@@ -39,7 +39,8 @@ EXPORTS = ("rt_init", "rt_destroy", "rt_last_error", "rt_num_instances", "rt_fie
            "rt_field_size", "rt_field_total", "rt_forward", "rt_gradient", "rt_constraint",
            "rt_project", "rt_get_state", "rt_get_dt", "rt_set_kernel_timing", "rt_kernel_times", "rt_stage_kernel",
            "cnop_solve", "rt_objective_noalloc", "rt_forward_series", "rt_spectrum_x", "rt_spectrum_2d",
-           "rt_reconstruct", "rt_fma_peak", "rt_revolve_plan", "rt_stage_tuning", "rt_adjoint_rows")
+           "rt_reconstruct", "rt_fma_peak", "rt_revolve_plan", "rt_stage_tuning", "rt_adjoint_rows",
+           "rt_tma_plan")
 
 
 class RtError(RuntimeError):
@@ -158,6 +159,8 @@ def library():
         L.rt_fma_peak.restype = ip
         L.rt_revolve_plan.argtypes = [ip, ip, ctypes.POINTER(ctypes.c_longlong), dp]
         L.rt_revolve_plan.restype = ip
+        L.rt_tma_plan.argtypes = [vp, vp, ip, ip, vp, vp]
+        L.rt_tma_plan.restype = ip
         L.cnop_solve.argtypes = [vp, ctypes.POINTER(CnopParams), vp, ip, dp, ctypes.POINTER(CnopResult)]
         L.cnop_solve.restype = ip
         _lib = L
@@ -462,3 +465,20 @@ def field_layout(problems):
         out.append((off, n))
         off += n
     return out
+
+
+def tma_plan(shapes, elem_bytes=4):
+    """(group of each instance or -1, index within the group) of the TMA
+    tile-load plan for device instances of grids shapes = [(nx, ny), ...] in
+    slot order (rt_tma_plan; host arithmetic, no device needed)."""
+    n = len(shapes)
+    nx = np.ascontiguousarray([s[0] for s in shapes], dtype=np.int32)
+    ny = np.ascontiguousarray([s[1] for s in shapes], dtype=np.int32)
+    grp = np.zeros(n, dtype=np.int32)
+    idx = np.zeros(n, dtype=np.int32)
+    st = library().rt_tma_plan(nx.ctypes.data_as(ctypes.c_void_p), ny.ctypes.data_as(ctypes.c_void_p), n,
+                               int(elem_bytes), grp.ctypes.data_as(ctypes.c_void_p),
+                               idx.ctypes.data_as(ctypes.c_void_p))
+    if st != RT_OK:
+        raise RtError(st, "rt_tma_plan: element size must be 4 or 8")
+    return grp.tolist(), idx.tolist()

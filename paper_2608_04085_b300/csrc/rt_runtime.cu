@@ -23,6 +23,7 @@
 #include "rt_internal.h"
 #include "rt_launch.h"
 #include "rt_revolve.h"
+#include "rt_tma_plan.h"
 #include "rt_spectra.h"
 
 // The Python binding mirrors these layouts with ctypes.
@@ -157,10 +158,7 @@ struct rt_ctx {
   double tune_ms[5] = {0, 0, 0, 0, 0};  // by variant: sweep, tile 16, tile 8, tile 32
   // TMA groups: runs of consecutive device instances of one grid shape whose
   // tiles the tile kernels fetch with tensor copies (InstDev::tma_g)
-  struct TmaGroup {
-    int first, count, nx, ny;
-  };
-  std::vector<TmaGroup> tma_groups;
+  std::vector<rt::TmaRun> tma_groups;
 };
 
 namespace {
@@ -307,7 +305,7 @@ EncodeTiledFn encode_tiled() {
 
 // Map of group g over a state slot at `slot`: the 4-D tensor (x, y, component,
 // instance) with boxes of TMA_BOX_X x rows x 4 x 1. Host-side encoding only.
-bool encode_group(const rt_ctx* c, const rt_ctx::TmaGroup& g, const void* slot, int rows, CUtensorMap* m) {
+bool encode_group(const rt_ctx* c, const rt::TmaRun& g, const void* slot, int rows, CUtensorMap* m) {
   const EncodeTiledFn enc = encode_tiled();
   if (!enc) return false;
   const cuuint64_t es = c->esz, plane = (cuuint64_t)g.nx * g.ny * es;
@@ -336,9 +334,12 @@ cudaError_t tile_maps(const rt_ctx* c, const void* slot, int rows, rt::TileMaps&
 constexpr int kStageBoxRows[3] = {8 + 4, rt::TILE_Y + 4, 32 + 4};
 constexpr int kAdjBoxRowsU[2] = {16 + 6, 24 + 6}, kAdjBoxRowsK[2] = {16 + 4, 24 + 4};
 
-// Split the device instances into TMA groups (maximal runs of one grid shape
-// whose rows are 16-byte multiples and that hold a box of every kind), keep
-// the TMA_GROUPS largest, and check that their maps encode.
+// Smallest grid that holds a box of every kind: TMA_BOX_X + TILE_X columns,
+// the rows of the tallest box.
+constexpr int kTmaMinNx = rt::TMA_BOX_X + rt::TILE_X, kTmaMinNy = kStageBoxRows[2];
+
+// TMA groups of the device instances (rt_tma_plan.h), kept when their maps
+// encode.
 void assign_tma_groups(rt_ctx* c) {
   c->tma_groups.clear();
   for (InstDev& I : c->h_inst) {
@@ -346,21 +347,15 @@ void assign_tma_groups(rt_ctx* c) {
     I.tma_z = 0;
   }
   if (c->opt.tile_loads == RT_LOADS_PLAIN || !encode_tiled()) return;
-  std::vector<rt_ctx::TmaGroup> runs;
-  for (int d = 0; d < c->n_dev;) {
-    int e = d + 1;
-    while (e < c->n_dev && c->h_inst[e].nx == c->h_inst[d].nx && c->h_inst[e].ny == c->h_inst[d].ny) ++e;
-    const InstDev& I = c->h_inst[d];
-    if ((I.nx * c->esz) % 16 == 0 && I.nx >= rt::TMA_BOX_X + rt::TILE_X && I.ny >= kStageBoxRows[2])
-      runs.push_back({d, e - d, I.nx, I.ny});
-    d = e;
+  std::vector<int> nx(c->n_dev), ny(c->n_dev);
+  for (int d = 0; d < c->n_dev; ++d) {
+    nx[d] = c->h_inst[d].nx;
+    ny[d] = c->h_inst[d].ny;
   }
-  std::stable_sort(runs.begin(), runs.end(), [](const rt_ctx::TmaGroup& a, const rt_ctx::TmaGroup& b) {
-    return (long long)a.count * a.nx * a.ny > (long long)b.count * b.nx * b.ny;
-  });
-  if ((int)runs.size() > rt::TMA_GROUPS) runs.resize(rt::TMA_GROUPS);
+  const std::vector<rt::TmaRun> runs =
+      rt::tma_plan(nx.data(), ny.data(), c->n_dev, c->esz, kTmaMinNx, kTmaMinNy, rt::TMA_GROUPS);
   const void* probe = reinterpret_cast<const void*>(uintptr_t(1) << 20);  // any 256-byte aligned address
-  for (const rt_ctx::TmaGroup& g : runs) {
+  for (const rt::TmaRun& g : runs) {
     CUtensorMap m;
     bool ok = true;
     for (int rows : {kStageBoxRows[0], kStageBoxRows[1], kStageBoxRows[2], kAdjBoxRowsU[0], kAdjBoxRowsK[0],
@@ -2410,6 +2405,22 @@ rt_status cnop_solve(rt_ctx* c, const cnop_params* prm, double* v_inout, int fla
   const float ms = tm.stop();
   if (res) res->ms = ms;
   return s;
+}
+
+rt_status rt_tma_plan(const int* nx, const int* ny, int n, int elem_bytes, int* group_of, int* index_of) {
+  if (!nx || !ny || n < 0 || (elem_bytes != 4 && elem_bytes != 8) || !group_of || !index_of) return RT_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    group_of[i] = -1;
+    index_of[i] = 0;
+  }
+  const std::vector<rt::TmaRun> runs =
+      rt::tma_plan(nx, ny, n, (size_t)elem_bytes, kTmaMinNx, kTmaMinNy, rt::TMA_GROUPS);
+  for (size_t g = 0; g < runs.size(); ++g)
+    for (int k = 0; k < runs[g].count; ++k) {
+      group_of[runs[g].first + k] = (int)g;
+      index_of[runs[g].first + k] = k;
+    }
+  return RT_OK;
 }
 
 rt_status rt_revolve_plan(int steps, int slots, long long* recomputed, double* optimum) {
