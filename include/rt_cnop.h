@@ -28,6 +28,11 @@
  *     work has finished. The time loop and the checkpoint segments of the
  *     reverse sweep run as CUDA graphs captured on first use and replayed
  *     from a per-context cache (environment RT_CNOP_GRAPHS=0 disables them).
+ *   * Other environment switches, read by rt_init: RT_CNOP_ADJ_ROWS=16|24
+ *     fixes the FP32 adjoint's tile height (rt_adjoint_rows), and
+ *     RT_CNOP_TMA_WAIT_FAULT=1 is fault injection for tests: the tile kernels
+ *     arm their TMA barriers without issuing a copy, so every call that runs
+ *     them ends with RT_ETIMEOUT (nothing is left in flight).
  *   * Perturbations and gradients are FP64, layout [instance][component][ny][nx]
  *     (C-contiguous, x fastest); instances are concatenated in order, each
  *     with perturb_ncomp components (1: u_y only; 2: u_x then u_y).
